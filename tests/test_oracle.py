@@ -1,0 +1,203 @@
+"""Pins for the FP64 oracle: closed forms, brute force and invariants.
+
+None of these compares the oracle with itself: energies come from textbook
+closed forms or from exact diagonalisation (a different algorithm), and
+H_eff * psi is compared with the explicit projection W^T H W built from Fock
+space vectors.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import dense, dmrg, ed, hamiltonian, lattice
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def free_fermion_energy(Lx, Ly, n_up, n_dn=None, t=1.0):
+    """Sum of the lowest levels of -2t(cos kx + cos ky) (closed form)."""
+    eps = np.sort([-2 * t * (np.cos(2 * np.pi * a / Lx) + np.cos(2 * np.pi * b / Ly))
+                   for a in range(Lx) for b in range(Ly)])
+    e = eps[:n_up].sum()
+    if n_dn is not None:
+        e += eps[:n_dn].sum()
+    return e
+
+
+def model(Lx, Ly, spinful, target, V=1.0, U=4.0, tp=0.0, rot="haar", seed=2):
+    if spinful:
+        T, V4 = lattice.hubbard(Lx, Ly, 1.0, U)
+    else:
+        T, V4 = lattice.spinless_tV(Lx, Ly, 1.0, tp, V)
+    if rot is not None:
+        Um = lattice.momentum_basis(Lx, Ly)
+        if rot == "haar":
+            Um = Um @ synth.haar_rotation(Lx * Ly, seed)
+        T, V4 = lattice.rotate(T, V4, Um)
+    h, W = hamiltonian.spin_orbital(T, V4, spinful)
+    return dmrg.Model(h, W, spinful, target), h, W
+
+
+def random_generic(n_sites, seed):
+    """Random real Hermitian Eq. 1 coefficients (V[ijkl] = V[lkji])."""
+    rng = np.random.default_rng(seed)
+    T = rng.standard_normal((n_sites, n_sites))
+    T = T + T.T
+    X = rng.standard_normal((n_sites,) * 4) * 0.3
+    V4 = X + X.transpose(3, 2, 1, 0)
+    return T, V4
+
+
+# ---------------------------------------------------------------- ED pins
+
+def test_ed_free_fermion_spinless():
+    m, h, W = model(3, 3, False, (4,), V=0.0, rot=None)
+    assert ed.ground_energy(h, W, 4)[0] == pytest.approx(free_fermion_energy(3, 3, 4), abs=1e-10)
+    assert free_fermion_energy(3, 3, 4) == pytest.approx(-7.0)
+
+
+def test_ed_free_fermion_hubbard():
+    m, h, W = model(3, 3, True, (5, 4), U=0.0, rot="haar")
+    e = ed.ground_energy(h, W, 9, n_up=5)[0]
+    assert e == pytest.approx(free_fermion_energy(3, 3, 5, 4), abs=1e-9)
+    assert free_fermion_energy(3, 3, 5, 4) == pytest.approx(-15.0)
+
+
+def test_ed_hubbard_dimer_closed_form():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "hubbard_dimer.txt"))
+            if l.strip() and not l.startswith("#")]
+    for t, U, E0 in rows:
+        t, U, E0 = float(t), float(U), float(E0)
+        T = np.array([[0.0, -t], [-t, 0.0]])
+        V4 = np.zeros((2, 2, 2, 2))
+        V4[0, 0, 0, 0] = V4[1, 1, 1, 1] = U / 2
+        h, W = hamiltonian.spin_orbital(T, V4, True)
+        assert ed.ground_energy(h, W, 2, n_up=1)[0] == pytest.approx(E0, abs=1e-12)
+        assert E0 == pytest.approx((U - np.sqrt(U * U + 16 * t * t)) / 2, abs=1e-14)
+
+
+def test_rotation_leaves_spectrum_intact():
+    """Sec. III.A: without truncation a unitary mode rotation keeps the spectrum."""
+    T, V4 = lattice.spinless_tV(3, 3, 1.0, 0.4, 0.8)
+    h, W = hamiltonian.spin_orbital(T, V4, False)
+    e0 = ed.ground_energy(h, W, 4, k=4)
+    Q = synth.haar_rotation(9, 7)
+    T2, V2 = lattice.rotate(T, V4, Q)
+    h2, W2 = hamiltonian.spin_orbital(T2, V2, False)
+    assert hamiltonian.check_hermitian(h2, W2)
+    np.testing.assert_allclose(ed.ground_energy(h2, W2, 4, k=4), e0, atol=1e-10)
+
+
+def test_momentum_basis_diagonalises_hopping():
+    for Lx, Ly in ((3, 3), (4, 4), (6, 6)):
+        U = lattice.momentum_basis(Lx, Ly)
+        N = Lx * Ly
+        assert np.abs(U.T @ U - np.eye(N)).max() < 1e-13
+        T, _ = lattice.hubbard(Lx, Ly, 1.0, 0.0) if Lx <= 4 else (None, None)
+        if T is not None:
+            Tk = U.T @ T @ U
+            assert np.abs(Tk - np.diag(np.diag(Tk))).max() < 1e-12
+            np.testing.assert_allclose(np.diag(Tk), np.sort(lattice.momentum_levels(Lx, Ly)),
+                                       atol=1e-12)
+
+
+def test_spin_orbital_antisymmetry():
+    T, V4 = random_generic(3, 1)
+    h, W = hamiltonian.spin_orbital(T, V4, True)
+    assert np.abs(W + W.transpose(1, 0, 2, 3)).max() < 1e-14
+    assert np.abs(W + W.transpose(0, 1, 3, 2)).max() < 1e-14
+    assert hamiltonian.check_hermitian(h, W)
+
+
+# ---------------------------------------------------- H_eff * psi vs W^T H W
+
+def _check_window(m, target, D, l, seed=5):
+    N = m.n_sites
+    li = synth.random_left_isometries(N, m.spinful, target, D, l, seed)
+    ri = synth.random_right_isometries(N, m.spinful, target, D, l + 2, seed + 1)
+    w = dmrg.window_from_mps(m, li, ri, l)
+    psi = np.random.default_rng(seed).standard_normal(w.size)
+    s = w.apply(psi)
+    sd = dense.dense_sigma(m, li, ri, l, w.layout, psi)
+    assert np.linalg.norm(s - sd) <= 1e-13 * np.linalg.norm(sd)
+    # layout agrees with the shared input bookkeeping
+    Ld = synth.block_dims(li[l]) if l > 0 else {m.zero(): 1}
+    Rd = synth.block_dims(ri[l + 2]) if l + 2 < N else {m.zero(): 1}
+    lay = synth.window_layout(N, m.spinful, target, Ld, Rd, l)
+    assert [(a, b, da, db) for a, b, _, da, db in w.layout] == lay
+    return w
+
+
+@pytest.mark.parametrize("l", range(8))
+def test_heff_dense_spinless_3x3(l):
+    m, h, W = model(3, 3, False, (4,))
+    _check_window(m, (4,), 8, l)
+
+
+@pytest.mark.parametrize("l", [0, 4, 7])
+def test_heff_dense_hubbard_3x3(l):
+    m, h, W = model(3, 3, True, (5, 4))
+    _check_window(m, (5, 4), 12, l)
+
+
+def test_heff_dense_generic_spinful():
+    T, V4 = random_generic(4, 3)
+    h, W = hamiltonian.spin_orbital(T, V4, True)
+    m = dmrg.Model(h, W, True, (2, 2))
+    for l in range(3):
+        _check_window(m, (2, 2), 6, l)
+
+
+def test_heff_hermitian_and_sectors():
+    m, h, W = model(4, 4, False, (8,))
+    li = synth.random_left_isometries(16, False, (8,), 24, 7, 1)
+    ri = synth.random_right_isometries(16, False, (8,), 24, 9, 2)
+    w = dmrg.window_from_mps(m, li, ri, 7)
+    rng = np.random.default_rng(0)
+    x, y = rng.standard_normal(w.size), rng.standard_normal(w.size)
+    hx, hy = w.apply(x), w.apply(y)
+    assert abs(x @ hy - hx @ y) <= 1e-13 * np.linalg.norm(x) * np.linalg.norm(hy)
+
+
+# ------------------------------------------------------------- full sweeps
+
+def test_sweep_exact_spinless_3x3():
+    m, h, W = model(3, 3, False, (4,))
+    e_ed = ed.ground_energy(h, W, 4)[0]
+    ri = synth.random_right_isometries(9, False, (4,), 20, 2, 0)
+    E, hist = dmrg.sweep(m, ri, 20, 2)
+    assert E[-1] == pytest.approx(e_ed, abs=1e-10)
+
+
+def test_sweep_exact_generic_spinful():
+    T, V4 = random_generic(4, 11)
+    h, W = hamiltonian.spin_orbital(T, V4, True)
+    m = dmrg.Model(h, W, True, (2, 2))
+    e_ed = ed.ground_energy(h, W, 4, n_up=2)[0]
+    ri = synth.random_right_isometries(4, True, (2, 2), 16, 2, 0)
+    E, hist = dmrg.sweep(m, ri, 16, 2)
+    assert E[-1] == pytest.approx(e_ed, abs=1e-10)
+
+
+def test_sweep_variational_hubbard_3x3():
+    m, h, W = model(3, 3, True, (5, 4), rot="mom")
+    e_ed = ed.ground_energy(h, W, 9, n_up=5)[0]
+    ri = synth.random_right_isometries(9, True, (5, 4), 16, 2, 0)
+    E, hist = dmrg.sweep(m, ri, 16, 1)
+    assert all(e >= e_ed - 1e-10 for _, _, _, e in hist)
+    assert E[-1] <= hist[0][3] + 1e-10
+
+
+@pytest.mark.slow
+def test_paper_4x4_exact_at_D128():
+    """Sec. III.A: 4x4 spinless model exact at D = 128 (t'=0.4, V=0.8)."""
+    line = [l for l in open(os.path.join(GOLDEN, "paper_claims.txt"))
+            if l.startswith("lattice")][0].split()
+    kv = dict(zip(line[0::2], line[1::2]))
+    m, h, W = model(4, 4, False, (8,), V=float(kv["V"]), tp=float(kv["tp"]), rot="mom")
+    e_ed = ed.ground_energy(h, W, 8)[0]
+    ri = synth.random_right_isometries(16, False, (8,), 128, 2, 0)
+    E, hist = dmrg.sweep(m, ri, int(kv["D"]), 2)
+    assert E[-1] == pytest.approx(e_ed, abs=1e-9)
