@@ -1,0 +1,192 @@
+/*
+ * dmrg_b300.h -- C ABI of the B300 two-site DMRG hot path (arXiv 2311.14106).
+ *
+ * The library computes sigma = H_eff * psi for the two-site window of ab
+ * initio DMRG on the generic Hamiltonian of Eq. 1 (Sec. II.A), builds the
+ * renormalized block operators it needs (normal and complementary, Sec. II.A
+ * "renormalized block operators"), runs the Davidson diagonalisation
+ * (Sec. II.A, "Lanczos or Davidson") and two-site sweeps over an MPS (Eq. 4).
+ *
+ * Conventions
+ *   - All calls return int: DMRG_OK (0) or a negative DMRG_ERR_* code.  No
+ *     exception crosses the ABI.  dmrg_last_error(ctx) holds a message.
+ *   - Floating point data are IEEE double, row-major, owned by the caller and
+ *     copied by the library unless stated otherwise.
+ *   - "device pointer" arguments point to CUDA device memory on the current
+ *     device; "host pointer" arguments to ordinary host memory.
+ *   - stream arguments are cudaStream_t passed as void* (NULL = legacy
+ *     default stream).  Device work is stream-ordered; calls that return
+ *     host scalars synchronise that stream.
+ *   - A context is thread-compatible: one thread at a time per context.
+ *     Different contexts may be used concurrently.
+ *
+ * Quantum numbers (QN): spinless model (sym = DMRG_U1) uses (N); spinful
+ * (sym = DMRG_U1U1) uses (N_up, N_dn).  Spin-orbital modes along the chain:
+ * spinless p = i, spinful p = 2 i (up), 2 i + 1 (down); site i = DMRG site i.
+ * Site states are ordered by QN: spinless {0, 1}; spinful
+ * {0, dn, up, updn} = QN (0,0), (0,1), (1,0), (1,1), with |updn> =
+ * c+_up c+_dn |0>.
+ *
+ * Isometries (a basis of the MPS, Eq. 4): left isometry n maps the enlarged
+ * block L_{n-1} x site_{n-1} onto the block L_n; right isometry n maps
+ * site_n x R_{n+1} onto R_n.  For each QN Q of the new block it is a
+ * (rows = dim_enlarged(Q)) x (cols = dim_new(Q)) matrix with orthonormal
+ * columns.  The rows of an enlarged sector run over pieces ordered by the
+ * site state's QN; each piece holds all states of the block sector
+ * Q - q(site state), in that sector's order.
+ *
+ * psi / sigma for window (l, l+1): one block per sector a of L. = L_l x
+ * site_l (ascending QN) paired with the sector target - q_a of
+ * .R = site_{l+1} x R_{l+2}, stored row-major (dim_a x dim_b), concatenated
+ * in that order (dmrg_heff_layout).
+ */
+#ifndef DMRG_B300_H
+#define DMRG_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  DMRG_OK = 0,
+  DMRG_ERR_ARG = -1,            /* invalid argument or size */
+  DMRG_ERR_OOM = -2,            /* device or host allocation failed */
+  DMRG_ERR_CUDA = -3,           /* CUDA runtime / cuSOLVER error */
+  DMRG_ERR_STATE = -4,          /* call made in the wrong order */
+  DMRG_ERR_TIMEOUT = -5,        /* a bounded device wait gave up */
+  DMRG_ERR_NOT_CONVERGED = -6   /* Davidson hit its iteration limit */
+};
+
+enum { DMRG_U1 = 1, DMRG_U1U1 = 2 };                 /* symmetry */
+enum { DMRG_FP64 = 0, DMRG_SPLIT_TF32 = 1 };         /* H_eff*psi precision */
+enum { DMRG_MODEL_SPINLESS_TV = 1, DMRG_MODEL_HUBBARD = 2 };
+
+typedef struct dmrg_ctx dmrg_ctx;   /* opaque, owned by the library */
+
+typedef struct {
+  int sym;                 /* DMRG_U1 (spinless) or DMRG_U1U1 (spinful) */
+  int n_sites;             /* N lattice sites = spatial modes */
+  int n_up;                /* target particles (spinless: N) */
+  int n_dn;                /* target down particles (spinless: ignored) */
+  int d_max;               /* bond dimension D kept by truncation */
+  int precision;           /* DMRG_FP64 or DMRG_SPLIT_TF32 for H_eff*psi */
+  double davidson_tol;     /* residual 2-norm bound, normalized vector */
+  int davidson_max_sub;    /* Davidson subspace size (>= 4) */
+  int davidson_max_iter;   /* Davidson iteration limit */
+  size_t hbm_budget_bytes; /* 0 = no limit */
+  uint64_t seed;           /* seed of the Davidson start vectors */
+} dmrg_config;
+
+const char *dmrg_error_string(int code);
+const char *dmrg_last_error(const dmrg_ctx *ctx);
+
+/* Create a context on the current CUDA device.  cfg is copied.
+ * Errors: ARG (bad sizes), CUDA (no device), OOM. */
+int dmrg_create(dmrg_ctx **out, const dmrg_config *cfg);
+/* Free all device and host memory of ctx.  NULL is accepted. */
+int dmrg_destroy(dmrg_ctx *ctx);
+
+/* a1 -- Eq. 2 / Eq. 3 on an Lx x Ly torus (Sec. II.A), site i = y*Lx + x.
+ * model DMRG_MODEL_SPINLESS_TV: t (NN), tp (NNN), v = V (NN n_i n_j);
+ * model DMRG_MODEL_HUBBARD: t, v = U (on-site), tp ignored.
+ * Hopping enters as -t (c+_i c_j + h.c.).  Writes host arrays
+ * t_out[N*N] and V_out[N^4] in the Eq. 1 order c+_i c+_j c_k c_l
+ * (Hubbard: V[iiii] = U/2 with the spin-independent convention of
+ * dmrg_set_hamiltonian).  Requires Lx, Ly >= 3.  Errors: ARG. */
+int dmrg_lattice_hamiltonian(int model, int Lx, int Ly, double t, double tp,
+                             double v, double *t_out, double *V_out);
+
+/* a2 helper -- real standing-wave momentum modes (Sec. II.B mode basis):
+ * U_out[N*N] host, U[i*N + m] = amplitude of mode m on site i, modes ordered
+ * by (-2(cos kx + cos ky), nx, ny, cos before sin).  Errors: ARG. */
+int dmrg_momentum_basis(int Lx, int Ly, double *U_out);
+
+/* a1/a2 -- Eq. 1 input and the one-particle mode rotation (Sec. II.B):
+ * host pointers t[N*N], V[N^4] (Eq. 1 order), U[N*N] orthogonal or NULL
+ * (identity).  The library rotates the parameters, t' = U^T t U and
+ * V'_abcd = sum V_ijkl U_ia U_jb U_kc U_ld, and forms the spin-orbital
+ * antisymmetrised two-body tensor.  Spinful models use the spin-independent
+ * form sum_{ab} V_ijkl c+_{ia} c+_{jb} c_{kb} c_{la}.
+ * Errors: ARG (NULL, non-orthogonal U, non-Hermitian V: V_ijkl != V_lkji). */
+int dmrg_set_hamiltonian(dmrg_ctx *ctx, const double *t, const double *V,
+                         const double *U);
+
+/* Eq. 4 -- hand one isometry of the MPS basis to the library (copied).
+ * side 0 = left isometry `site` (1..N-1), side 1 = right isometry `site`
+ * (1..N-1).  qn[n_sectors * nq] (nq = 1 or 2), rows[], cols[] per sector,
+ * data = concatenated row-major matrices (host).  Rows must equal the
+ * enlarged sector dimension implied by the previous isometry.
+ * Errors: ARG, STATE (isometries out of order), OOM. */
+int dmrg_set_isometry(dmrg_ctx *ctx, int side, int site, int n_sectors,
+                      const int *qn, const int *rows, const int *cols,
+                      const double *data);
+
+/* a3/a4 -- build the renormalized block operators L_0..L_l and R_N..R_{l+2}
+ * from the isometries, the enlarged blocks L. and .R of window (l, l+1) and
+ * the sector tables of H_eff (Sec. II.A "Tables").  Errors: STATE, OOM, CUDA. */
+int dmrg_build_block_ops(dmrg_ctx *ctx, int l, void *stream);
+
+/* psi layout of the current window: *psi_len elements; *n_blocks blocks;
+ * if blocks != NULL it receives 2*nq + 2 ints per block
+ * (q_a[nq], q_b[nq], dim_a, dim_b).  Errors: STATE. */
+int dmrg_heff_layout(dmrg_ctx *ctx, long long *psi_len, int *n_blocks,
+                     int *blocks);
+
+/* Select the arithmetic of dmrg_heff_apply: DMRG_FP64 or DMRG_SPLIT_TF32. */
+int dmrg_set_precision(dmrg_ctx *ctx, int precision);
+
+/* a5 -- sigma = H_eff * psi (Sec. II.A, Davidson matvec).  psi, sigma:
+ * device pointers, psi_len doubles each, owned by the caller; sigma is
+ * overwritten; psi is not modified.  Stream-ordered, no host sync.
+ * Errors: STATE (no window built), ARG (NULL). */
+int dmrg_heff_apply(dmrg_ctx *ctx, const double *psi, double *sigma,
+                    void *stream);
+
+/* Same as dmrg_heff_apply but with host buffers: copies psi to the device,
+ * applies, copies sigma back, synchronising the stream. */
+int dmrg_heff_apply_host(dmrg_ctx *ctx, const double *psi_host,
+                         double *sigma_host, void *stream);
+
+/* Algorithmic flops of one H_eff*psi of the current window:
+ * sum over nonzero (term, sector) of 2 (m' m n + m' n n'). */
+int dmrg_heff_flops(dmrg_ctx *ctx, double *flops);
+
+/* a6 -- lowest eigenpair of H_eff by Davidson (Sec. II.A).  psi_inout:
+ * device pointer, start vector on input (need not be normalized; a zero
+ * vector means "use a seeded random start"), normalized eigenvector on
+ * output.  The final energy is the FP64 Rayleigh quotient with an FP64
+ * matvec, whatever the precision setting.
+ * Errors: STATE, NOT_CONVERGED (psi and energy still written). */
+int dmrg_davidson(dmrg_ctx *ctx, double *psi_inout, double *energy,
+                  int *iters, void *stream);
+
+/* a7 -- truncate the current window's psi (device pointer, normalized) to
+ * d_max states (largest Schmidt values over all sectors, ties by lower
+ * sector index then lower in-sector index) and renormalize the block on
+ * `side` (0: L. -> L_{l+1}, 1: .R -> R_{l+1}).  Outputs discarded weight and
+ * entropy (either may be NULL). */
+int dmrg_truncate(dmrg_ctx *ctx, const double *psi, int side, int d_max,
+                  double *discarded, double *entropy, void *stream);
+
+/* a6-a8 -- two-site sweeps from the right-canonical MPS given by the right
+ * isometries.  One sweep = windows l = 0..N-2 left to right (truncating to
+ * the left after each window but the last) then l = N-2..0 right to left
+ * (truncating to the right after each window but the last).
+ * d_schedule[n_sweeps] (NULL = cfg.d_max).  energies_out[n_sweeps] (host)
+ * receives the energy of the final window of each sweep.
+ * Errors: STATE, NOT_CONVERGED, OOM, CUDA. */
+int dmrg_sweep(dmrg_ctx *ctx, int n_sweeps, const int *d_schedule,
+               double *energies_out, void *stream);
+
+/* Timing breakdown of the last sweep in seconds, Sec. III.B categories:
+ * out[0] Diag_H, [1] Ren (block ops), [2] Tables, [3] Diag_D, [4] StVec,
+ * [5] Other; out[6] = number of H_eff*psi calls. */
+int dmrg_profile(dmrg_ctx *ctx, double *out7);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DMRG_B300_H */

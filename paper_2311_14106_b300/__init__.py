@@ -1,0 +1,245 @@
+"""Python binding of libdmrgb300 (B300 two-site DMRG hot path, arXiv 2311.14106).
+
+Argument marshalling only: every step runs in the CUDA library through its
+C ABI (include/dmrg_b300.h).  PyTorch tensors are accepted for device
+buffers (psi, sigma) and streams.  There is no CPU fallback: if the shared
+library is missing or cannot be loaded, importing this module fails.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdmrgb300.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} not built; run paper_2311_14106_b300/build.py")
+_lib = ctypes.CDLL(LIB_PATH)
+
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_STATE, ERR_TIMEOUT, ERR_NOT_CONVERGED = 0, -1, -2, -3, -4, -5, -6
+U1, U1U1 = 1, 2
+FP64, SPLIT_TF32 = 0, 1
+MODEL_SPINLESS_TV, MODEL_HUBBARD = 1, 2
+
+HEADER_FUNCTIONS = [
+    "dmrg_error_string", "dmrg_last_error", "dmrg_create", "dmrg_destroy",
+    "dmrg_lattice_hamiltonian", "dmrg_momentum_basis", "dmrg_set_hamiltonian",
+    "dmrg_set_isometry", "dmrg_build_block_ops", "dmrg_heff_layout",
+    "dmrg_set_precision", "dmrg_heff_apply", "dmrg_heff_apply_host",
+    "dmrg_heff_flops", "dmrg_davidson", "dmrg_truncate", "dmrg_sweep",
+    "dmrg_profile",
+]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("sym", ctypes.c_int), ("n_sites", ctypes.c_int), ("n_up", ctypes.c_int),
+        ("n_dn", ctypes.c_int), ("d_max", ctypes.c_int), ("precision", ctypes.c_int),
+        ("davidson_tol", ctypes.c_double), ("davidson_max_sub", ctypes.c_int),
+        ("davidson_max_iter", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int)
+_sig = {
+    "dmrg_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "dmrg_last_error": (ctypes.c_char_p, [_P]),
+    "dmrg_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(Config)]),
+    "dmrg_destroy": (ctypes.c_int, [_P]),
+    "dmrg_lattice_hamiltonian": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_double, ctypes.c_double,
+                                                ctypes.c_double, _D, _D]),
+    "dmrg_momentum_basis": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _D]),
+    "dmrg_set_hamiltonian": (ctypes.c_int, [_P, _D, _D, _D]),
+    "dmrg_set_isometry": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         _I, _I, _I, _D]),
+    "dmrg_build_block_ops": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "dmrg_heff_layout": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong), _I, _I]),
+    "dmrg_set_precision": (ctypes.c_int, [_P, ctypes.c_int]),
+    "dmrg_heff_apply": (ctypes.c_int, [_P, _P, _P, _P]),
+    "dmrg_heff_apply_host": (ctypes.c_int, [_P, _D, _D, _P]),
+    "dmrg_heff_flops": (ctypes.c_int, [_P, _D]),
+    "dmrg_davidson": (ctypes.c_int, [_P, _P, _D, _I, _P]),
+    "dmrg_truncate": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _D, _D, _P]),
+    "dmrg_sweep": (ctypes.c_int, [_P, ctypes.c_int, _I, _D, _P]),
+    "dmrg_profile": (ctypes.c_int, [_P, _D]),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class DmrgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_lib.dmrg_error_string(code).decode()} ({code}): {msg}")
+        self.code = code
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_D)
+
+
+def _iptr(a):
+    return a.ctypes.data_as(_I)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _tensor_ptr(t):
+    if hasattr(t, "data_ptr"):
+        if t.dtype.__repr__() != "torch.float64" or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("expected a contiguous float64 CUDA tensor")
+        return t.data_ptr()
+    return int(t)
+
+
+def lattice_hamiltonian(model, Lx, Ly, t=1.0, tp=0.0, v=1.0):
+    """a1: Eq. 2 / Eq. 3 on an Lx x Ly torus -> (T[N,N], V[N,N,N,N])."""
+    N = Lx * Ly
+    T = np.zeros((N, N))
+    V = np.zeros((N, N, N, N))
+    rc = _lib.dmrg_lattice_hamiltonian(model, Lx, Ly, t, tp, v, _dptr(T), _dptr(V))
+    if rc != OK:
+        raise DmrgError(rc, "lattice_hamiltonian")
+    return T, V
+
+
+def momentum_basis(Lx, Ly):
+    """a2 helper: real standing-wave momentum modes, U[site, mode]."""
+    U = np.zeros((Lx * Ly, Lx * Ly))
+    rc = _lib.dmrg_momentum_basis(Lx, Ly, _dptr(U))
+    if rc != OK:
+        raise DmrgError(rc, "momentum_basis")
+    return U
+
+
+class Dmrg:
+    """One library context (one problem: Hamiltonian, MPS basis, window)."""
+
+    def __init__(self, n_sites, n_up, n_dn=0, spinful=False, d_max=128, precision=FP64,
+                 davidson_tol=1e-8, davidson_max_sub=20, davidson_max_iter=200, seed=0):
+        cfg = Config(U1U1 if spinful else U1, n_sites, n_up, n_dn, d_max, precision,
+                     davidson_tol, davidson_max_sub, davidson_max_iter, 0, seed)
+        h = _P()
+        rc = _lib.dmrg_create(ctypes.byref(h), ctypes.byref(cfg))
+        if rc != OK:
+            raise DmrgError(rc, "dmrg_create")
+        self._h = h
+        self.spinful = spinful
+        self.nq = 2 if spinful else 1
+        self.n_sites = n_sites
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.dmrg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def _check(self, rc, what):
+        if rc != OK:
+            raise DmrgError(rc, f"{what}: {_lib.dmrg_last_error(self._h).decode()}")
+        return rc
+
+    def set_hamiltonian(self, T, V, U=None):
+        T = np.ascontiguousarray(T, dtype=np.float64)
+        V = np.ascontiguousarray(V, dtype=np.float64)
+        Up = None if U is None else _dptr(np.ascontiguousarray(U, dtype=np.float64))
+        self._check(_lib.dmrg_set_hamiltonian(self._h, _dptr(T), _dptr(V), Up), "set_hamiltonian")
+
+    def set_isometry(self, side, site, iso):
+        """iso: {qn tuple: (rows, cols) ndarray}; side 0 left, 1 right."""
+        qs = sorted(iso)
+        qn = np.array([x for q in qs for x in q[: self.nq]], dtype=np.int32)
+        rows = np.array([iso[q].shape[0] for q in qs], dtype=np.int32)
+        cols = np.array([iso[q].shape[1] for q in qs], dtype=np.int32)
+        data = np.concatenate([np.ascontiguousarray(iso[q], dtype=np.float64).ravel() for q in qs])
+        self._check(_lib.dmrg_set_isometry(self._h, side, site, len(qs), _iptr(qn), _iptr(rows),
+                                           _iptr(cols), _dptr(data)), "set_isometry")
+
+    def set_mps(self, left=None, right=None):
+        for n, iso in (left or {}).items():
+            self.set_isometry(0, n, iso)
+        for n, iso in (right or {}).items():
+            self.set_isometry(1, n, iso)
+
+    def build_block_ops(self, l, stream=None):
+        self._check(_lib.dmrg_build_block_ops(self._h, l, _stream_ptr(stream)), "build_block_ops")
+
+    def heff_layout(self):
+        n = ctypes.c_longlong()
+        nb = ctypes.c_int()
+        self._check(_lib.dmrg_heff_layout(self._h, ctypes.byref(n), ctypes.byref(nb), None),
+                    "heff_layout")
+        blocks = np.zeros((nb.value, 2 * self.nq + 2), dtype=np.int32)
+        self._check(_lib.dmrg_heff_layout(self._h, None, None, _iptr(blocks)), "heff_layout")
+        out = []
+        for b in blocks:
+            qa = tuple(int(x) for x in b[: self.nq])
+            qb = tuple(int(x) for x in b[self.nq: 2 * self.nq])
+            out.append((qa, qb, int(b[-2]), int(b[-1])))
+        return n.value, out
+
+    def set_precision(self, p):
+        self._check(_lib.dmrg_set_precision(self._h, p), "set_precision")
+
+    def heff_apply(self, psi, sigma, stream=None):
+        """a5: sigma = H_eff psi on device buffers (torch float64 CUDA tensors)."""
+        self._check(_lib.dmrg_heff_apply(self._h, _tensor_ptr(psi), _tensor_ptr(sigma),
+                                         _stream_ptr(stream)), "heff_apply")
+
+    def heff_apply_host(self, psi, stream=None):
+        psi = np.ascontiguousarray(psi, dtype=np.float64)
+        out = np.zeros_like(psi)
+        self._check(_lib.dmrg_heff_apply_host(self._h, _dptr(psi), _dptr(out),
+                                              _stream_ptr(stream)), "heff_apply_host")
+        return out
+
+    def heff_flops(self):
+        f = ctypes.c_double()
+        self._check(_lib.dmrg_heff_flops(self._h, ctypes.byref(f)), "heff_flops")
+        return f.value
+
+    def davidson(self, psi, stream=None):
+        """a6: lowest eigenpair; psi (device tensor) is start vector and result."""
+        e = ctypes.c_double()
+        it = ctypes.c_int()
+        rc = _lib.dmrg_davidson(self._h, _tensor_ptr(psi), ctypes.byref(e), ctypes.byref(it),
+                                _stream_ptr(stream))
+        if rc not in (OK, ERR_NOT_CONVERGED):
+            self._check(rc, "davidson")
+        return e.value, it.value, rc == OK
+
+    def truncate(self, psi, side, d_max, stream=None):
+        disc = ctypes.c_double()
+        ent = ctypes.c_double()
+        self._check(_lib.dmrg_truncate(self._h, _tensor_ptr(psi), side, d_max, ctypes.byref(disc),
+                                       ctypes.byref(ent), _stream_ptr(stream)), "truncate")
+        return disc.value, ent.value
+
+    def sweep(self, n_sweeps, d_schedule=None, stream=None):
+        E = np.zeros(n_sweeps)
+        ds = None
+        if d_schedule is not None:
+            ds = np.ascontiguousarray(d_schedule, dtype=np.int32)
+        self._check(_lib.dmrg_sweep(self._h, n_sweeps, None if ds is None else _iptr(ds), _dptr(E),
+                                    _stream_ptr(stream)), "sweep")
+        return E
+
+    def profile(self):
+        out = np.zeros(7)
+        self._check(_lib.dmrg_profile(self._h, _dptr(out)), "profile")
+        keys = ["Diag_H", "Ren", "Tables", "Diag_D", "StVec", "Other", "n_matvec"]
+        return dict(zip(keys, out.tolist()))

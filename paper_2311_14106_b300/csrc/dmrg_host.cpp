@@ -1,0 +1,2017 @@
+// Host runtime of libdmrgb300: Hamiltonian set-up (Eq. 1, Sec. II.B
+// rotation), sector tables ("Tables", Sec. III.B), block operators
+// (normal and complementary), the two-site window, H_eff*psi, Davidson,
+// truncation and sweeps.  All bulk arithmetic runs in the CUDA kernels of
+// kernels.cu / heff_tf32.cu; this file builds their work lists.
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/dmrg_b300.h"
+#include "formulas.h"
+#include "heff_tf32.h"
+#include "kernels.h"
+#include "model.h"
+
+using namespace dmrg;
+
+namespace {
+
+struct Err {
+  int code;
+  std::string msg;
+};
+
+#define CK(call)                                                            \
+  do {                                                                      \
+    cudaError_t e_ = (call);                                                \
+    if (e_ != cudaSuccess)                                                  \
+      throw Err{DMRG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+
+[[noreturn]] void fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  throw Err{code, buf};
+}
+
+double now() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct Iso {
+  std::vector<QN> qn;
+  std::vector<int> rows, cols;
+  std::vector<double> host;        // concatenated row-major
+  std::vector<long long> off;
+  double *d = nullptr;
+};
+
+// Device buffers that live for one H_eff window.
+struct WinBuf {
+  std::vector<void *> ptrs;
+  void *alloc(size_t bytes) {
+    void *p = nullptr;
+    if (bytes == 0) bytes = 8;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      fail(DMRG_ERR_OOM, "cudaMalloc(%zu) failed", bytes);
+    }
+    ptrs.push_back(p);
+    return p;
+  }
+  void clear() {
+    for (void *p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+  ~WinBuf() { clear(); }
+};
+
+template <class T>
+T *upload(WinBuf &wb, const std::vector<T> &v, cudaStream_t s) {
+  T *d = (T *)wb.alloc(sizeof(T) * std::max<size_t>(v.size(), 1));
+  if (!v.empty()) CK(cudaMemcpyAsync(d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s));
+  return d;
+}
+
+struct TermF {
+  Fac A, B;
+  double coef;
+};
+
+struct HClass {
+  QN dA;
+  int pB = 0;
+  std::vector<TermF> terms;
+  std::map<int, long long> a_off, b_off, t_off;   // keyed by input psi block
+};
+
+struct S1 {
+  int ci, pi, po;   // H_eff class, input psi block, output psi block
+};
+
+struct PsiBlk {
+  int a, b;          // sector indices in L. and .R
+  long long off;
+  int da, db;
+};
+
+struct Window {
+  bool valid = false;
+  int l = -1;
+  BlockPart Ld, Rd;
+  WinBuf ldbuf, rdbuf;
+  std::vector<PsiBlk> psi;
+  long long psi_len = 0;
+  std::vector<int> a2psi;
+  std::vector<HClass> hc;
+  WinBuf buf;            // stacks, T, descriptors
+  double *Astack = nullptr, *Bstack = nullptr, *T = nullptr;
+  long long nA = 0, nB = 0, nT = 0;
+  GemmDesc *d1 = nullptr, *d2 = nullptr;
+  GemmSeg *s1 = nullptr, *s2 = nullptr;
+  int nd1 = 0, nd2 = 0;
+  long long tiles1 = 0, tiles2 = 0;
+  double flops = 0;
+  double *diag = nullptr;
+  std::vector<S1> s1info;                 // stage-1 regions (class, psi in, psi out)
+  std::vector<GemmDesc> stage1, stage2;   // host copies (split-path planning)
+  std::vector<GemmSeg> seg1, seg2;
+  Tf32Plan tf;           // split-precision plan (heff_tf32)
+  bool tf_ready = false;
+  std::vector<Split2D> psi_split_host;
+  std::vector<CUtensorMap> maps_host;
+  std::vector<TSeg> seg_host;
+  std::vector<TWork> w1_host, w2_host;
+};
+
+}  // namespace
+
+struct dmrg_ctx {
+  dmrg_config cfg;
+  std::string err;
+  bool spinful = false;
+  int N = 0, M = 0;
+  QN target{0, 0};
+  std::vector<double> h, W;
+  bool ham = false;
+  std::map<int, Iso> liso, riso;
+  std::vector<std::unique_ptr<BlockPart>> L;        // L[n], n sites
+  std::map<int, std::unique_ptr<BlockPart>> R;      // R[n], sites n..N-1
+  std::map<BlockPart *, std::unique_ptr<WinBuf>> partbuf;
+  Window win;
+  cudaStream_t stream = nullptr;
+  cusolverDnHandle_t solver = nullptr;
+  int precision = DMRG_FP64;
+  double prof[7] = {0};
+  // Davidson scratch
+  WinBuf dav;
+  long long dav_n = 0;
+  double *V = nullptr, *AV = nullptr, *work = nullptr, *small = nullptr, *r = nullptr;
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Hamiltonian
+// ---------------------------------------------------------------------------
+inline double &W4(std::vector<double> &W, int M, int p, int q, int r, int s) {
+  return W[(((size_t)p * M + q) * M + r) * M + s];
+}
+
+void torus_bonds(int Lx, int Ly, bool nnn, std::vector<std::pair<int, int>> &out) {
+  for (int y = 0; y < Ly; ++y)
+    for (int x = 0; x < Lx; ++x) {
+      int r = y * Lx + x;
+      if (!nnn) {
+        out.push_back({r, y * Lx + (x + 1) % Lx});
+        out.push_back({r, ((y + 1) % Ly) * Lx + x});
+      } else {
+        out.push_back({r, ((y + 1) % Ly) * Lx + (x + 1) % Lx});
+        out.push_back({r, ((y - 1 + Ly) % Ly) * Lx + (x + 1) % Lx});
+      }
+    }
+}
+
+// quarter transform along one index of a 4-index tensor: out[..a..] =
+// sum_i in[..i..] U[i,a]
+void quarter(const std::vector<double> &in, std::vector<double> &out, const double *U,
+             int N, int axis) {
+  out.assign(in.size(), 0.0);
+  size_t st[4] = {(size_t)N * N * N, (size_t)N * N, (size_t)N, 1};
+  for (size_t e = 0; e < in.size(); ++e) {
+    double v = in[e];
+    if (v == 0.0) continue;
+    int i = (int)((e / st[axis]) % N);
+    size_t base = e - (size_t)i * st[axis];
+    const double *u = U + (size_t)i * N;
+    for (int a = 0; a < N; ++a) out[base + (size_t)a * st[axis]] += v * u[a];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// site operators (exact)
+// ---------------------------------------------------------------------------
+struct Mat4 {
+  double m[16] = {0};
+};
+Mat4 mm(const Mat4 &a, const Mat4 &b) {
+  Mat4 c;
+  for (int i = 0; i < 4; ++i)
+    for (int k = 0; k < 4; ++k) {
+      double v = a.m[i * 4 + k];
+      if (v == 0.0) continue;
+      for (int j = 0; j < 4; ++j) c.m[i * 4 + j] += v * b.m[k * 4 + j];
+    }
+  return c;
+}
+Mat4 tr(const Mat4 &a) {
+  Mat4 c;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) c.m[i * 4 + j] = a.m[j * 4 + i];
+  return c;
+}
+void axpy(Mat4 &y, double a, const Mat4 &x) {
+  for (int i = 0; i < 16; ++i) y.m[i] += a * x.m[i];
+}
+
+QN shift_c(const dmrg_ctx *C, int p) {
+  if (!C->spinful) return {-1, 0};
+  return (p % 2 == 0) ? QN{-1, 0} : QN{0, -1};
+}
+
+SiteOp mkop(const Mat4 &m, QN shift) {
+  SiteOp o;
+  o.shift = shift;
+  o.parity = qparity(shift);
+  memcpy(o.m, m.m, sizeof o.m);
+  return o;
+}
+
+SitePart make_site(const dmrg_ctx *C, int i) {
+  SitePart s;
+  s.site = i;
+  const int M = C->M;
+  if (C->spinful) {
+    s.modes = {2 * i, 2 * i + 1};
+    s.d = 4;
+    s.sq = {{0, 0}, {0, 1}, {1, 0}, {1, 1}};
+  } else {
+    s.modes = {i};
+    s.d = 2;
+    s.sq = {{0, 0}, {1, 0}};
+  }
+  // local state index -> occupation bits (bit j = mode j of the site)
+  std::vector<int> bits = C->spinful ? std::vector<int>{0, 2, 1, 3} : std::vector<int>{0, 1};
+  std::vector<int> pos(4, -1);
+  for (int k = 0; k < s.d; ++k) pos[bits[k]] = k;
+  std::map<int, Mat4> cl;
+  for (size_t j = 0; j < s.modes.size(); ++j) {
+    Mat4 c;
+    for (int k = 0; k < s.d; ++k) {
+      int b = bits[k];
+      if (!((b >> j) & 1)) continue;
+      int below = __builtin_popcount(b & ((1 << j) - 1));
+      c.m[pos[b & ~(1 << j)] * 4 + k] = (below & 1) ? -1.0 : 1.0;
+    }
+    cl[s.modes[j]] = c;
+  }
+  Mat4 I;
+  for (int k = 0; k < s.d; ++k) I.m[k * 4 + k] = 1.0;
+  s.I = mkop(I, {0, 0});
+  auto hh = [&](int p, int q) { return C->h[(size_t)p * M + q]; };
+  auto WW = [&](int p, int q, int r, int t) {
+    return C->W[(((size_t)p * M + q) * M + r) * M + t];
+  };
+  Mat4 H;
+  for (int p : s.modes)
+    for (int q : s.modes) axpy(H, hh(p, q), mm(tr(cl[p]), cl[q]));
+  for (int p : s.modes)
+    for (int q : s.modes)
+      for (int r : s.modes)
+        for (int t : s.modes) {
+          double w = WW(p, q, r, t);
+          if (w != 0.0) axpy(H, w, mm(mm(tr(cl[p]), tr(cl[q])), mm(cl[r], cl[t])));
+        }
+  s.H = mkop(H, {0, 0});
+  for (int p : s.modes) s.c[p] = mkop(cl[p], shift_c(C, p));
+  for (size_t a = 0; a < s.modes.size(); ++a)
+    for (size_t b = a + 1; b < s.modes.size(); ++b) {
+      int p = s.modes[a], q = s.modes[b];
+      s.cc[{p, q}] = mkop(mm(cl[p], cl[q]), qadd(shift_c(C, p), shift_c(C, q)));
+    }
+  for (int p : s.modes)
+    for (int r : s.modes) s.cdc[{p, r}] = mkop(mm(tr(cl[p]), cl[r]), qsub(shift_c(C, r), shift_c(C, p)));
+  std::vector<int> others;
+  for (int y = 0; y < M; ++y)
+    if (!has(s.modes, y)) others.push_back(y);
+  for (int y : others) {
+    Mat4 S;
+    for (int q : s.modes) axpy(S, 0.5 * hh(y, q), cl[q]);
+    for (int q : s.modes)
+      for (int r : s.modes)
+        for (int t : s.modes) {
+          double w = WW(y, q, r, t);
+          if (w != 0.0) axpy(S, 2.0 * w, mm(tr(cl[q]), mm(cl[r], cl[t])));
+        }
+    s.S[y] = mkop(S, shift_c(C, y));
+  }
+  for (size_t a = 0; a < others.size(); ++a)
+    for (size_t b = a + 1; b < others.size(); ++b) {
+      int x = others[a], z = others[b];
+      Mat4 P;
+      for (int p : s.modes)
+        for (int q : s.modes) {
+          double w = WW(x, z, p, q);
+          if (w != 0.0) axpy(P, w, mm(cl[p], cl[q]));
+        }
+      s.P[{x, z}] = mkop(P, qadd(shift_c(C, x), shift_c(C, z)));
+    }
+  for (int x : others)
+    for (int z : others) {
+      Mat4 Qm;
+      for (int p : s.modes)
+        for (int q : s.modes) {
+          double w = WW(x, p, z, q);
+          if (w != 0.0) axpy(Qm, w, mm(tr(cl[p]), cl[q]));
+        }
+      s.Q[{x, z}] = mkop(Qm, qsub(shift_c(C, x), shift_c(C, z)));
+    }
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// operator classes
+// ---------------------------------------------------------------------------
+struct OpSpec {
+  int kind;   // 0 H, 1 c, 2 S, 3 cc, 4 cdc, 5 P, 6 Q
+  int i, j;
+  QN shift;
+};
+
+QN spec_shift(const dmrg_ctx *C, int kind, int i, int j) {
+  switch (kind) {
+    case 0: return {0, 0};
+    case 1: case 2: return shift_c(C, i);
+    case 3: case 5: return qadd(shift_c(C, i), shift_c(C, j));
+    case 4: return qsub(shift_c(C, j), shift_c(C, i));
+    default: return qsub(shift_c(C, i), shift_c(C, j));
+  }
+}
+
+// All operators a block holds ("both normal and complementary" policy).
+std::vector<OpSpec> block_specs(const dmrg_ctx *C, const std::vector<int> &modes) {
+  std::vector<OpSpec> v;
+  v.push_back({0, 0, 0, {0, 0}});
+  for (int x : modes) v.push_back({1, x, 0, spec_shift(C, 1, x, 0)});
+  std::vector<int> out;
+  for (int y = 0; y < C->M; ++y)
+    if (!has(modes, y)) out.push_back(y);
+  for (int y : out) v.push_back({2, y, 0, spec_shift(C, 2, y, 0)});
+  for (size_t a = 0; a < modes.size(); ++a)
+    for (size_t b = a + 1; b < modes.size(); ++b)
+      v.push_back({3, modes[a], modes[b], spec_shift(C, 3, modes[a], modes[b])});
+  for (int p : modes)
+    for (int r : modes) v.push_back({4, p, r, spec_shift(C, 4, p, r)});
+  for (size_t a = 0; a < out.size(); ++a)
+    for (size_t b = a + 1; b < out.size(); ++b)
+      v.push_back({5, out[a], out[b], spec_shift(C, 5, out[a], out[b])});
+  for (int x : out)
+    for (int z : out) v.push_back({6, x, z, spec_shift(C, 6, x, z)});
+  return v;
+}
+
+void set_ref(BlockPart &B, const OpSpec &s, Ref r) {
+  switch (s.kind) {
+    case 0: B.H = r; break;
+    case 1: B.c[s.i] = r; break;
+    case 2: B.S[s.i] = r; break;
+    case 3: B.cc[{s.i, s.j}] = r; break;
+    case 4: B.cdc[{s.i, s.j}] = r; break;
+    case 5: B.P[{s.i, s.j}] = r; break;
+    default: B.Q[{s.i, s.j}] = r; break;
+  }
+}
+
+// Assign operators to classes by QN shift and lay out the blocks.  Returns
+// for every spec its Ref.  Device memory is allocated from wb.
+std::vector<Ref> make_classes(BlockPart &B, const std::vector<OpSpec> &specs, WinBuf &wb,
+                              cudaStream_t s) {
+  std::map<QN, int> byshift;
+  std::vector<Ref> refs(specs.size());
+  for (size_t k = 0; k < specs.size(); ++k) {
+    auto it = byshift.find(specs[k].shift);
+    int ci;
+    if (it == byshift.end()) {
+      ci = (int)B.cls.size();
+      byshift[specs[k].shift] = ci;
+      OpClass oc;
+      oc.shift = specs[k].shift;
+      oc.parity = qparity(oc.shift);
+      B.cls.push_back(oc);
+    } else {
+      ci = it->second;
+    }
+    refs[k] = {ci, B.cls[ci].nops++};
+  }
+  const int ns = (int)B.basis.qn.size();
+  for (auto &oc : B.cls) {
+    oc.in2blk.assign(ns, -1);
+    long long off = 0;
+    for (int i = 0; i < ns; ++i) {
+      int j = B.basis.find(qadd(B.basis.qn[i], oc.shift));
+      if (j < 0) continue;
+      oc.in2blk[i] = (int)oc.blk_in.size();
+      oc.blk_in.push_back(i);
+      oc.blk_out.push_back(j);
+      oc.blk_off.push_back(off);
+      off += (long long)B.basis.dim[j] * B.basis.dim[i];
+    }
+    oc.nnz = off;
+    oc.d = (double *)wb.alloc(sizeof(double) * std::max<long long>(1, oc.nnz * oc.nops));
+    oc.d_in2blk = upload(wb, oc.in2blk, s);
+    oc.d_blk_out = upload(wb, oc.blk_out, s);
+    oc.d_blk_off = upload(wb, oc.blk_off, s);
+  }
+  // drop empty classes' references: an op whose class has no block is zero
+  for (size_t k = 0; k < specs.size(); ++k) {
+    Ref r = refs[k];
+    if (B.cls[r.cls].nnz == 0) r.cls = -1;
+    set_ref(B, specs[k], r);
+  }
+  return refs;
+}
+
+bool allowed_q(const dmrg_ctx *C, const QN &q, int cap) {
+  for (int k = 0; k < (C->spinful ? 2 : 1); ++k) {
+    int d = C->target[k] - q[k];
+    if (d < 0 || d > cap) return false;
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// enlarged block: X x site (left) or site x X (right)
+// ---------------------------------------------------------------------------
+void enlarge(dmrg_ctx *C, const BlockPart &X, const SitePart &st, bool site_first, int cap,
+             BlockPart &U, WinBuf &wb) {
+  cudaStream_t s = C->stream;
+  // basis with pieces ordered by site state
+  std::map<QN, std::vector<Piece>> pm;
+  for (int k = 0; k < st.d; ++k)
+    for (size_t j = 0; j < X.basis.qn.size(); ++j) {
+      QN Q = qadd(X.basis.qn[j], st.sq[k]);
+      if (!allowed_q(C, Q, cap)) continue;
+      pm[Q].push_back({k, (int)j, 0, X.basis.dim[j]});
+    }
+  U.basis = Basis();
+  U.pieces.clear();
+  for (auto &kv : pm) {
+    int off = 0;
+    for (auto &p : kv.second) {
+      p.off = off;
+      off += p.dim;
+    }
+    U.basis.qn.push_back(kv.first);
+    U.basis.dim.push_back(off);
+    U.pieces.push_back(kv.second);
+  }
+  U.enlarged = true;
+  U.site_first = site_first;
+  U.modes.clear();
+  if (site_first) {
+    U.modes = st.modes;
+    U.modes.insert(U.modes.end(), X.modes.begin(), X.modes.end());
+  } else {
+    U.modes = X.modes;
+    U.modes.insert(U.modes.end(), st.modes.begin(), st.modes.end());
+  }
+  std::vector<OpSpec> specs = block_specs(C, U.modes);
+  make_classes(U, specs, wb, s);
+
+  Side sx, ss;
+  sx.b = &X;
+  ss.s = &st;
+  const Side &F = site_first ? ss : sx;
+  const Side &G = site_first ? sx : ss;
+  const bool block_first = !site_first;
+
+  // per class, per op: terms
+  std::vector<std::vector<std::vector<GTerm>>> terms(U.cls.size());
+  for (size_t ci = 0; ci < U.cls.size(); ++ci) terms[ci].resize(U.cls[ci].nops);
+  std::map<std::tuple<int, int, int>, int> keyidx;
+  for (size_t k = 0; k < specs.size(); ++k) {
+    const OpSpec &sp = specs[k];
+    Ref r;
+    switch (sp.kind) {
+      case 0: r = U.H; break;
+      case 1: r = U.c[sp.i]; break;
+      case 2: r = U.S[sp.i]; break;
+      case 3: r = U.cc[{sp.i, sp.j}]; break;
+      case 4: r = U.cdc[{sp.i, sp.j}]; break;
+      case 5: r = U.P[{sp.i, sp.j}]; break;
+      default: r = U.Q[{sp.i, sp.j}]; break;
+    }
+    if (r.cls < 0) continue;
+    std::map<std::tuple<int, int, int>, GTerm> acc;
+    AddFn add = [&](const Fac &A, const Fac &B, double coef) {
+      if (A.kind == 0 || B.kind == 0) return;
+      const Fac &Xf = block_first ? A : B;
+      const Fac &Sf = block_first ? B : A;
+      if (Sf.kind != 3 || Xf.kind == 3) fail(DMRG_ERR_STATE, "internal: bad enlarged term");
+      QN tot = qadd(A.shift, B.shift);
+      if (tot != sp.shift) fail(DMRG_ERR_STATE, "internal: shift mismatch in enlarged op");
+      double c = coef * A.scale * B.scale;
+      std::tuple<int, int, int> key = Xf.kind == 2 ? std::make_tuple(-1, 0, 0)
+                                                   : std::make_tuple(Xf.ref.cls, Xf.ref.idx, Xf.trans);
+      auto it = acc.find(key);
+      if (it == acc.end()) {
+        GTerm t;
+        memset(&t, 0, sizeof t);
+        t.src = std::get<0>(key);
+        t.idx = std::get<1>(key);
+        t.trans = std::get<2>(key);
+        t.p2 = B.parity;
+        it = acc.emplace(key, t).first;
+      }
+      for (int e = 0; e < 16; ++e) it->second.m[e] += c * Sf.so.m[e];
+    };
+    switch (sp.kind) {
+      case 0: formula_H(F, G, add, true); break;
+      case 1: formula_c(F, G, sp.i, add); break;
+      case 2: formula_S(F, G, sp.i, add); break;
+      case 3: formula_cc(F, G, sp.i, sp.j, add); break;
+      case 4: formula_cdc(F, G, sp.i, sp.j, add); break;
+      case 5: formula_P(F, G, sp.i, sp.j, C->W.data(), C->M, add); break;
+      default: formula_Q(F, G, sp.i, sp.j, C->W.data(), C->M, add); break;
+    }
+    auto &dst = terms[r.cls][r.idx];
+    for (auto &kv : acc) {
+      bool nz = false;
+      for (int e = 0; e < 16; ++e) nz |= kv.second.m[e] != 0.0;
+      if (nz) dst.push_back(kv.second);
+    }
+  }
+  // flatten terms, CSR per class
+  std::vector<GTerm> all;
+  std::vector<std::vector<int>> ptr(U.cls.size());
+  for (size_t ci = 0; ci < U.cls.size(); ++ci) {
+    ptr[ci].push_back((int)all.size());
+    for (auto &tl : terms[ci]) {
+      all.insert(all.end(), tl.begin(), tl.end());
+      ptr[ci].push_back((int)all.size());
+    }
+  }
+  WinBuf tmp;   // work lists, released once the gather has run
+  GTerm *d_terms = upload(tmp, all, s);
+  std::vector<int *> d_ptr(U.cls.size());
+  for (size_t ci = 0; ci < U.cls.size(); ++ci) d_ptr[ci] = upload(tmp, ptr[ci], s);
+  std::vector<GSrc> srcs;
+  for (auto &oc : X.cls) srcs.push_back({oc.d, oc.nnz, oc.d_in2blk, oc.d_blk_out, oc.d_blk_off});
+  GSrc *d_srcs = upload(tmp, srcs, s);
+  std::vector<GSub> subs;
+  int max_ops = 0;
+  for (size_t ci = 0; ci < U.cls.size(); ++ci) {
+    const OpClass &oc = U.cls[ci];
+    if (oc.nnz == 0) continue;
+    max_ops = std::max(max_ops, oc.nops);
+    for (size_t b = 0; b < oc.blk_in.size(); ++b) {
+      int qi = oc.blk_in[b], qo = oc.blk_out[b];
+      int ld = U.basis.dim[qi];
+      for (const Piece &po : U.pieces[qo])
+        for (const Piece &pi : U.pieces[qi]) {
+          GSub g;
+          g.out = oc.d;
+          g.nnz_out = oc.nnz;
+          g.out_off = oc.blk_off[b] + (long long)po.off * ld + pi.off;
+          g.out_ld = ld;
+          g.rows = po.dim;
+          g.cols = pi.dim;
+          g.so = po.site_state;
+          g.si = pi.site_state;
+          g.a_out = po.blk_sector;
+          g.a_in = pi.blk_sector;
+          g.n_in = site_first ? qnum(st.sq[pi.site_state]) : qnum(X.basis.qn[pi.blk_sector]);
+          g.nops = oc.nops;
+          g.term_ptr = d_ptr[ci];
+          subs.push_back(g);
+        }
+    }
+  }
+  GSub *d_subs = upload(tmp, subs, s);
+  CK(launch_gather(d_subs, (int)subs.size(), max_ops, d_terms, d_srcs, 4, s));
+  CK(cudaStreamSynchronize(s));
+}
+
+// ---------------------------------------------------------------------------
+// renormalization: B = T^T U T  (T = isometry on U's sectors)
+// ---------------------------------------------------------------------------
+void renormalize(dmrg_ctx *C, const BlockPart &U, const Iso &T, BlockPart &B, WinBuf &wb) {
+  cudaStream_t s = C->stream;
+  B.basis = Basis();
+  std::vector<int> u_of(T.qn.size());
+  for (size_t k = 0; k < T.qn.size(); ++k) {
+    int j = U.basis.find(T.qn[k]);
+    if (j < 0 || U.basis.dim[j] != T.rows[k])
+      fail(DMRG_ERR_ARG, "isometry sector %zu (QN %d,%d): rows %d do not match enlarged dim %d",
+           k, T.qn[k][0], T.qn[k][1], T.rows[k], j < 0 ? 0 : U.basis.dim[j]);
+    u_of[k] = j;
+    B.basis.qn.push_back(T.qn[k]);
+    B.basis.dim.push_back(T.cols[k]);
+  }
+  B.modes = U.modes;
+  B.enlarged = false;
+  // same operators, same shifts
+  std::vector<OpSpec> specs = block_specs(C, B.modes);
+  make_classes(B, specs, wb, s);
+  // U's class for each shift
+  std::map<QN, int> ushift;
+  for (size_t ci = 0; ci < U.cls.size(); ++ci) ushift[U.cls[ci].shift] = (int)ci;
+  std::vector<GemmDesc> d1, d2;
+  std::vector<GemmSeg> s1, s2;
+  long long tmp_total = 0;
+  struct Job {
+    int bc, bb, uc, ub;
+    long long tmp;
+  };
+  std::vector<Job> jobs;
+  for (size_t bc = 0; bc < B.cls.size(); ++bc) {
+    const OpClass &ob = B.cls[bc];
+    if (ob.nnz == 0) continue;
+    auto it = ushift.find(ob.shift);
+    if (it == ushift.end()) fail(DMRG_ERR_STATE, "internal: missing class in renormalize");
+    const OpClass &ou = U.cls[it->second];
+    if (ou.nops != ob.nops) fail(DMRG_ERR_STATE, "internal: op count mismatch");
+    for (size_t b = 0; b < ob.blk_in.size(); ++b) {
+      int ki = ob.blk_in[b], ko = ob.blk_out[b];
+      int ub = ou.in2blk[u_of[ki]];
+      if (ub < 0 || ou.blk_out[ub] != u_of[ko]) fail(DMRG_ERR_STATE, "internal: block mismatch");
+      jobs.push_back({(int)bc, (int)b, it->second, ub, tmp_total});
+      tmp_total += (long long)ob.nops * U.basis.dim[u_of[ko]] * T.cols[ki];
+    }
+  }
+  WinBuf work;   // intermediate products and work lists of this call
+  double *tmp = (double *)work.alloc(sizeof(double) * std::max<long long>(tmp_total, 1));
+  long long t1 = 0, t2 = 0;
+  for (const Job &j : jobs) {
+    const OpClass &ob = B.cls[j.bc];
+    const OpClass &ou = U.cls[j.uc];
+    int ki = ob.blk_in[j.bb], ko = ob.blk_out[j.bb];
+    int du_o = U.basis.dim[u_of[ko]], du_i = U.basis.dim[u_of[ki]];
+    int db_o = T.cols[ko], db_i = T.cols[ki];
+    // tmp_k = U_k (du_o x du_i) * T_i (du_i x db_i)
+    GemmSeg g;
+    memset(&g, 0, sizeof g);
+    g.A = ou.d + ou.blk_off[j.ub];
+    g.a_rs = du_i; g.a_cs = 1; g.a_bs = ou.nnz;
+    g.B = T.d + T.off[ki];
+    g.b_rs = db_i; g.b_cs = 1; g.b_bs = 0;
+    g.K = du_i;
+    GemmDesc d;
+    memset(&d, 0, sizeof d);
+    d.C = tmp + j.tmp;
+    d.c_rs = db_i; d.c_cs = 1; d.c_bs = (long long)du_o * db_i;
+    d.M = du_o; d.N = db_i; d.batch = ob.nops;
+    d.seg0 = (int)s1.size(); d.nseg = 1;
+    d.tiles_m = (du_o + 63) / 64; d.tiles_n = (db_i + 63) / 64;
+    d.alpha = 1.0; d.beta = 0.0;
+    d.tile0 = t1;
+    t1 += (long long)d.tiles_m * d.tiles_n * d.batch;
+    s1.push_back(g);
+    d1.push_back(d);
+    // out_k = T_o^T (db_o x du_o) * tmp_k (du_o x db_i)
+    GemmSeg g2;
+    memset(&g2, 0, sizeof g2);
+    g2.A = T.d + T.off[ko];
+    g2.a_rs = 1; g2.a_cs = db_o; g2.a_bs = 0;
+    g2.B = tmp + j.tmp;
+    g2.b_rs = db_i; g2.b_cs = 1; g2.b_bs = (long long)du_o * db_i;
+    g2.K = du_o;
+    GemmDesc e;
+    memset(&e, 0, sizeof e);
+    e.C = ob.d + ob.blk_off[j.bb];
+    e.c_rs = db_i; e.c_cs = 1; e.c_bs = ob.nnz;
+    e.M = db_o; e.N = db_i; e.batch = ob.nops;
+    e.seg0 = (int)s2.size(); e.nseg = 1;
+    e.tiles_m = (db_o + 63) / 64; e.tiles_n = (db_i + 63) / 64;
+    e.alpha = 1.0; e.beta = 0.0;
+    e.tile0 = t2;
+    t2 += (long long)e.tiles_m * e.tiles_n * e.batch;
+    s2.push_back(g2);
+    d2.push_back(e);
+  }
+  if (!jobs.empty()) {
+    GemmDesc *dd1 = upload(work, d1, s), *dd2 = upload(work, d2, s);
+    GemmSeg *ss1 = upload(work, s1, s), *ss2 = upload(work, s2, s);
+    CK(launch_gemm_f64(dd1, (int)d1.size(), ss1, t1, s));
+    CK(launch_gemm_f64(dd2, (int)d2.size(), ss2, t2, s));
+  }
+  CK(cudaStreamSynchronize(s));
+}
+
+}  // namespace
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// blocks from isometries
+// ---------------------------------------------------------------------------
+void free_part(dmrg_ctx *C, BlockPart *B) {
+  auto it = C->partbuf.find(B);
+  if (it != C->partbuf.end()) C->partbuf.erase(it);
+}
+
+WinBuf &buf_of(dmrg_ctx *C, BlockPart *B) {
+  auto &p = C->partbuf[B];
+  if (!p) p.reset(new WinBuf());
+  return *p;
+}
+
+std::unique_ptr<BlockPart> vacuum(dmrg_ctx *C) {
+  std::unique_ptr<BlockPart> v(new BlockPart());
+  v->basis.qn.push_back({0, 0});
+  v->basis.dim.push_back(1);
+  // every operator of the vacuum is zero: no classes, all references empty
+  return v;
+}
+
+void upload_iso(dmrg_ctx *C, Iso &T) {
+  if (T.d) return;
+  WinBuf &wb = buf_of(C, nullptr);
+  T.d = (double *)wb.alloc(sizeof(double) * std::max<size_t>(T.host.size(), 1));
+  CK(cudaMemcpyAsync(T.d, T.host.data(), sizeof(double) * T.host.size(), cudaMemcpyHostToDevice,
+                     C->stream));
+}
+
+// L_n = T_n^T (L_{n-1} x site_{n-1}) T_n
+void grow_left(dmrg_ctx *C, int n, const Iso &T) {
+  SitePart st = make_site(C, n - 1);
+  BlockPart U;
+  WinBuf ub;
+  enlarge(C, *C->L[n - 1], st, false, C->N - n, U, ub);
+  std::unique_ptr<BlockPart> B(new BlockPart());
+  renormalize(C, U, T, *B, buf_of(C, B.get()));
+  if ((int)C->L.size() <= n) C->L.resize(n + 1);
+  if (C->L[n]) free_part(C, C->L[n].get());
+  C->L[n] = std::move(B);
+}
+
+// R_n = T_n^T (site_n x R_{n+1}) T_n
+void grow_right(dmrg_ctx *C, int n, const Iso &T) {
+  SitePart st = make_site(C, n);
+  BlockPart U;
+  WinBuf ub;
+  enlarge(C, *C->R[n + 1], st, true, n, U, ub);
+  std::unique_ptr<BlockPart> B(new BlockPart());
+  renormalize(C, U, T, *B, buf_of(C, B.get()));
+  if (C->R.count(n)) free_part(C, C->R[n].get());
+  C->R[n] = std::move(B);
+}
+
+// ---------------------------------------------------------------------------
+// the window (l, l+1): enlarged blocks, H_eff term stacks, GEMM lists
+// ---------------------------------------------------------------------------
+
+void block_src(const BlockPart &P, const Fac &f, int in_sec, int out_sec, SCopy &cp) {
+  // operator f restricted to block (out_sec <- in_sec) as a copy source
+  cp.src = nullptr;
+  cp.ident = 0;
+  cp.trans = 0;
+  if (f.kind == 2) {
+    cp.ident = (in_sec == out_sec);
+    return;
+  }
+  if (f.kind != 1) return;
+  const OpClass &oc = P.cls[f.ref.cls];
+  const double *base = oc.d + (long long)f.ref.idx * oc.nnz;
+  if (!f.trans) {
+    int b = oc.in2blk[in_sec];
+    if (b < 0 || oc.blk_out[b] != out_sec) return;
+    cp.src = base + oc.blk_off[b];
+    cp.src_ld = P.basis.dim[in_sec];
+  } else {
+    int b = oc.in2blk[out_sec];
+    if (b < 0 || oc.blk_out[b] != in_sec) return;
+    cp.src = base + oc.blk_off[b];
+    cp.trans = 1;
+    cp.src_ld = P.basis.dim[out_sec];
+  }
+}
+
+void build_window(dmrg_ctx *C, int l) {
+  Window &w = C->win;
+  cudaStream_t s = C->stream;
+  w.valid = false;
+  w.buf.clear();
+  w.ldbuf.clear();
+  w.rdbuf.clear();
+  w.tf_ready = false;
+  w.Ld = BlockPart();
+  w.Rd = BlockPart();
+  w.hc.clear();
+  w.psi.clear();
+  w.l = l;
+  double t0 = now();
+  {
+    SitePart sl = make_site(C, l), sr = make_site(C, l + 1);
+    enlarge(C, *C->L[l], sl, false, C->N - l - 1, w.Ld, w.ldbuf);
+    enlarge(C, *C->R[l + 2], sr, true, l + 1, w.Rd, w.rdbuf);
+  }
+  C->prof[1] += now() - t0;
+  t0 = now();
+  // psi layout
+  w.a2psi.assign(w.Ld.basis.qn.size(), -1);
+  long long off = 0;
+  for (size_t a = 0; a < w.Ld.basis.qn.size(); ++a) {
+    int b = w.Rd.basis.find(qsub(C->target, w.Ld.basis.qn[a]));
+    if (b < 0) continue;
+    w.a2psi[a] = (int)w.psi.size();
+    w.psi.push_back({(int)a, b, off, w.Ld.basis.dim[a], w.Rd.basis.dim[b]});
+    off += (long long)w.Ld.basis.dim[a] * w.Rd.basis.dim[b];
+  }
+  w.psi_len = off;
+  // H_eff terms, grouped by the shift of the L. factor
+  Side F, G;
+  F.b = &w.Ld;
+  G.b = &w.Rd;
+  std::map<QN, int> cidx;
+  AddFn add = [&](const Fac &A, const Fac &B, double coef) {
+    if (A.kind == 0 || B.kind == 0) return;
+    if (qadd(A.shift, B.shift) != QN{0, 0}) fail(DMRG_ERR_STATE, "internal: H_eff term shift");
+    auto it = cidx.find(A.shift);
+    int ci;
+    if (it == cidx.end()) {
+      ci = (int)w.hc.size();
+      cidx[A.shift] = ci;
+      HClass h;
+      h.dA = A.shift;
+      h.pB = B.parity;
+      w.hc.push_back(h);
+    } else {
+      ci = it->second;
+    }
+    w.hc[ci].terms.push_back({A, B, coef});
+  };
+  formula_H(F, G, add, true);
+  // stacks and T layout
+  long long nA = 0, nB = 0, nT = 0;
+  std::vector<SCopy> cps;
+  std::vector<S1> s1list;
+  for (size_t ci = 0; ci < w.hc.size(); ++ci) {
+    HClass &h = w.hc[ci];
+    const long long n = (long long)h.terms.size();
+    for (size_t pi = 0; pi < w.psi.size(); ++pi) {
+      const PsiBlk &p = w.psi[pi];
+      int ao = w.Ld.basis.find(qadd(w.Ld.basis.qn[p.a], h.dA));
+      if (ao < 0 || w.a2psi[ao] < 0) continue;
+      const PsiBlk &q = w.psi[w.a2psi[ao]];
+      h.a_off[(int)pi] = nA;
+      h.b_off[(int)pi] = nB;
+      h.t_off[(int)pi] = nT;
+      nA += (long long)q.da * n * p.da;
+      nB += (long long)q.db * n * p.db;
+      nT += (long long)q.da * n * p.db;
+      s1list.push_back({(int)ci, (int)pi, w.a2psi[ao]});
+    }
+  }
+  w.nA = nA;
+  w.nB = nB;
+  w.nT = nT;
+  w.Astack = (double *)w.buf.alloc(8 * std::max<long long>(nA, 1));
+  w.Bstack = (double *)w.buf.alloc(8 * std::max<long long>(nB, 1));
+  w.T = (double *)w.buf.alloc(8 * std::max<long long>(nT, 1));
+  for (const S1 &e : s1list) {
+    HClass &h = w.hc[e.ci];
+    const PsiBlk &p = w.psi[e.pi], &q = w.psi[e.po];
+    const int n = (int)h.terms.size();
+    for (int k = 0; k < n; ++k) {
+      const TermF &t = h.terms[k];
+      SCopy a;
+      memset(&a, 0, sizeof a);
+      block_src(w.Ld, t.A, p.a, q.a, a);
+      a.coef = t.A.scale;
+      a.rows = q.da;
+      a.cols = p.da;
+      a.dst = w.Astack + h.a_off[e.pi] + (long long)k * p.da;
+      a.dst_ld = (long long)n * p.da;
+      cps.push_back(a);
+      SCopy b;
+      memset(&b, 0, sizeof b);
+      block_src(w.Rd, t.B, p.b, q.b, b);
+      b.coef = t.coef * t.B.scale;
+      b.rows = q.db;
+      b.cols = p.db;
+      b.dst = w.Bstack + h.b_off[e.pi] + (long long)k * p.db;
+      b.dst_ld = (long long)n * p.db;
+      cps.push_back(b);
+    }
+  }
+  {
+    WinBuf tmp;
+    SCopy *d = upload(tmp, cps, s);
+    CK(launch_stack_copy(d, (int)cps.size(), s));
+    CK(cudaStreamSynchronize(s));
+  }
+  // stage 1: T[(a',k), b] = A[(a',k), a] psi[a, b] * sign
+  // stage 2: sigma[a', b'] = sum_classes T[a', (k,b)] B[b', (k,b)]^T
+  std::vector<GemmDesc> d1, d2;
+  std::vector<GemmSeg> g1, g2;
+  long long t1 = 0, t2 = 0;
+  double flops = 0;
+  std::vector<std::vector<S1>> into(w.psi.size());
+  for (const S1 &e : s1list) {
+    HClass &h = w.hc[e.ci];
+    const PsiBlk &p = w.psi[e.pi], &q = w.psi[e.po];
+    const int n = (int)h.terms.size();
+    GemmSeg g;
+    memset(&g, 0, sizeof g);
+    g.A = w.Astack + h.a_off[e.pi];
+    g.a_rs = p.da; g.a_cs = 1;
+    g.B = nullptr;            // psi, bound at apply time (offset kept in b_bs)
+    g.b_bs = p.off;
+    g.b_rs = p.db; g.b_cs = 1;
+    g.K = p.da;
+    GemmDesc d;
+    memset(&d, 0, sizeof d);
+    d.C = w.T + h.t_off[e.pi];
+    d.c_rs = p.db; d.c_cs = 1;
+    d.M = q.da * n; d.N = p.db; d.batch = 1;
+    d.seg0 = (int)g1.size(); d.nseg = 1;
+    d.tiles_m = (d.M + 63) / 64; d.tiles_n = (d.N + 63) / 64;
+    int nl = qnum(w.Ld.basis.qn[p.a]);
+    d.alpha = (h.pB && (nl & 1)) ? -1.0 : 1.0;
+    d.beta = 0.0;
+    d.tile0 = t1;
+    t1 += (long long)d.tiles_m * d.tiles_n;
+    g1.push_back(g);
+    d1.push_back(d);
+    into[e.po].push_back(e);
+    flops += 2.0 * q.da * (double)n * p.da * p.db + 2.0 * q.da * (double)n * p.db * q.db;
+  }
+  for (size_t po = 0; po < w.psi.size(); ++po) {
+    const PsiBlk &q = w.psi[po];
+    GemmDesc d;
+    memset(&d, 0, sizeof d);
+    d.C = nullptr;            // sigma, bound at apply time
+    d.c_bs = q.off;
+    d.c_rs = q.db; d.c_cs = 1;
+    d.M = q.da; d.N = q.db; d.batch = 1;
+    d.seg0 = (int)g2.size(); d.nseg = (int)into[po].size();
+    d.tiles_m = (d.M + 63) / 64; d.tiles_n = (d.N + 63) / 64;
+    d.alpha = 1.0; d.beta = 0.0;
+    d.tile0 = t2;
+    t2 += (long long)d.tiles_m * d.tiles_n;
+    for (const S1 &e : into[po]) {
+      HClass &h = w.hc[e.ci];
+      const PsiBlk &p = w.psi[e.pi];
+      const int n = (int)h.terms.size();
+      GemmSeg g;
+      memset(&g, 0, sizeof g);
+      g.A = w.T + h.t_off[e.pi];
+      g.a_rs = (long long)n * p.db; g.a_cs = 1;
+      g.B = w.Bstack + h.b_off[e.pi];
+      g.b_rs = 1; g.b_cs = (long long)n * p.db;
+      g.K = n * p.db;
+      g2.push_back(g);
+    }
+    d2.push_back(d);
+  }
+  w.flops = flops;
+  w.tiles1 = t1;
+  w.tiles2 = t2;
+  w.nd1 = (int)d1.size();
+  w.nd2 = (int)d2.size();
+  w.stage1 = d1;
+  w.seg1 = g1;
+  w.stage2 = d2;
+  w.seg2 = g2;
+  w.d1 = upload(w.buf, w.stage1, s);
+  w.s1 = upload(w.buf, w.seg1, s);
+  w.d2 = upload(w.buf, w.stage2, s);
+  w.s2 = upload(w.buf, w.seg2, s);
+  w.s1info = s1list;
+  // diagonal of H_eff for the Davidson preconditioner: shift-0 class terms
+  w.diag = (double *)w.buf.alloc(8 * std::max<long long>(w.psi_len, 1));
+  CK(cudaMemsetAsync(w.diag, 0, 8 * std::max<long long>(w.psi_len, 1), s));
+  {
+    std::vector<GemmDesc> dd;
+    std::vector<GemmSeg> gg;
+    long long tt = 0;
+    for (size_t ci = 0; ci < w.hc.size(); ++ci) {
+      HClass &h = w.hc[ci];
+      if (h.dA != QN{0, 0}) continue;
+      const int n = (int)h.terms.size();
+      for (auto &kv : h.a_off) {
+        const PsiBlk &p = w.psi[kv.first];
+        GemmSeg g;
+        memset(&g, 0, sizeof g);
+        g.A = w.Astack + kv.second;            // A[i][k][i]
+        g.a_rs = (long long)n * p.da + 1; g.a_cs = p.da;
+        g.B = w.Bstack + h.b_off[kv.first];    // B[j][k][j]
+        g.b_rs = p.db; g.b_cs = (long long)n * p.db + 1;
+        g.K = n;
+        GemmDesc d;
+        memset(&d, 0, sizeof d);
+        d.C = w.diag + p.off;
+        d.c_rs = p.db; d.c_cs = 1;
+        d.M = p.da; d.N = p.db; d.batch = 1;
+        d.seg0 = (int)gg.size(); d.nseg = 1;
+        d.tiles_m = (p.da + 63) / 64; d.tiles_n = (p.db + 63) / 64;
+        d.alpha = 1.0; d.beta = 0.0;
+        d.tile0 = tt;
+        tt += (long long)d.tiles_m * d.tiles_n;
+        gg.push_back(g);
+        dd.push_back(d);
+      }
+    }
+    if (!dd.empty()) {
+      WinBuf tmp;
+      GemmDesc *a = upload(tmp, dd, s);
+      GemmSeg *b = upload(tmp, gg, s);
+      CK(launch_gemm_f64(a, (int)dd.size(), b, tt, s));
+      CK(cudaStreamSynchronize(s));
+    }
+  }
+  C->prof[2] += now() - t0;
+  w.valid = true;
+}
+
+void apply_fp64(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s) {
+  Window &w = C->win;
+  CK(launch_gemm_f64(w.d1, w.nd1, w.s1, w.tiles1, s, psi, nullptr));
+  CK(launch_gemm_f64(w.d2, w.nd2, w.s2, w.tiles2, s, nullptr, sigma));
+}
+
+}  // namespace
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// split-precision plan: TF32 (hi, lo) copies of the stacks, tensor maps and
+// tile lists of the two tcgen05 stages
+// ---------------------------------------------------------------------------
+long long r4(long long x) { return (x + 3) & ~3LL; }
+long long a64(long long x) { return (x + 63) & ~63LL; }
+int ntile_of(int n) { return n > 128 ? 128 : ((n + 15) / 16) * 16; }
+
+void build_tf32(dmrg_ctx *C) {
+  Window &w = C->win;
+  cudaStream_t s = C->stream;
+  Tf32Plan &P = w.tf;
+  const auto &E = w.s1info;
+  const size_t ne = E.size(), np = w.psi.size();
+  std::vector<long long> offA(ne), offT(ne), offB(ne), offP(np);
+  std::vector<long long> ldA(ne), ldT(ne), ldB(ne), ldP(np);
+  long long nA = 0, nT = 0, nB = 0, nP = 0;
+  for (size_t i = 0; i < ne; ++i) {
+    const HClass &h = w.hc[E[i].ci];
+    const PsiBlk &p = w.psi[E[i].pi], &q = w.psi[E[i].po];
+    const long long n = (long long)h.terms.size();
+    ldA[i] = r4(p.da);
+    offA[i] = nA;
+    nA += a64(q.da * n * ldA[i]);
+    ldT[i] = r4(n * p.db);
+    offT[i] = nT;
+    nT += a64(q.da * ldT[i]);
+    ldB[i] = r4(n * p.db);
+    offB[i] = nB;
+    nB += a64(q.db * ldB[i]);
+  }
+  for (size_t i = 0; i < np; ++i) {
+    ldP[i] = r4(w.psi[i].da);
+    offP[i] = nP;
+    nP += a64(w.psi[i].db * ldP[i]);
+  }
+  auto fl = [&](long long n) { return (float *)w.buf.alloc(4 * std::max<long long>(n, 64)); };
+  P.A_hi = fl(nA); P.A_lo = fl(nA);
+  P.T_hi = fl(nT); P.T_lo = fl(nT);
+  P.B_hi = fl(nB); P.B_lo = fl(nB);
+  P.P_hi = fl(nP); P.P_lo = fl(nP);
+  // split the operator stacks once per window
+  std::vector<Split2D> sp;
+  for (size_t i = 0; i < ne; ++i) {
+    const HClass &h = w.hc[E[i].ci];
+    const PsiBlk &p = w.psi[E[i].pi], &q = w.psi[E[i].po];
+    const int n = (int)h.terms.size();
+    Split2D a;
+    memset(&a, 0, sizeof a);
+    a.src = w.Astack + h.a_off.at(E[i].pi);
+    a.src_ld = p.da;
+    a.rows = q.da * n;
+    a.cols = p.da;
+    a.hi = P.A_hi + offA[i];
+    a.lo = P.A_lo + offA[i];
+    a.dst_ld = ldA[i];
+    sp.push_back(a);
+    Split2D b;
+    memset(&b, 0, sizeof b);
+    b.src = w.Bstack + h.b_off.at(E[i].pi);
+    b.src_ld = (long long)n * p.db;
+    b.rows = q.db;
+    b.cols = n * p.db;
+    b.hi = P.B_hi + offB[i];
+    b.lo = P.B_lo + offB[i];
+    b.dst_ld = ldB[i];
+    sp.push_back(b);
+  }
+  {
+    WinBuf tmp;
+    Split2D *d = upload(tmp, sp, s);
+    CK(launch_split2d(d, (int)sp.size(), s));
+    CK(cudaStreamSynchronize(s));
+  }
+  // psi split descriptors (transposed: psi_a^T is the K-major B of stage 1)
+  std::vector<Split2D> ps;
+  for (size_t i = 0; i < np; ++i) {
+    Split2D d;
+    memset(&d, 0, sizeof d);
+    d.src = nullptr;
+    d.src_off = w.psi[i].off;
+    d.src_ld = w.psi[i].db;
+    d.rows = w.psi[i].da;
+    d.cols = w.psi[i].db;
+    d.trans = 1;
+    d.hi = P.P_hi + offP[i];
+    d.lo = P.P_lo + offP[i];
+    d.dst_ld = ldP[i];
+    ps.push_back(d);
+  }
+  w.psi_split_host = ps;
+  P.psi_split = upload(w.buf, w.psi_split_host, s);
+  P.npsi = (int)np;
+  // tensor maps
+  std::vector<CUtensorMap> maps;
+  auto mk = [&](const float *base, long long rows, long long cols, long long ld, int box) {
+    CUtensorMap m;
+    int rc = encode_map(&m, base, (int)rows, (int)cols, ld, box);
+    if (rc != 0) fail(DMRG_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) rows %lld cols %lld", rc, rows, cols);
+    maps.push_back(m);
+    return (int)maps.size() - 1;
+  };
+  std::vector<int> mPhi(np), mPlo(np);
+  for (size_t i = 0; i < np; ++i) {
+    const PsiBlk &p = w.psi[i];
+    int box = ntile_of(p.db);
+    mPhi[i] = mk(P.P_hi + offP[i], p.db, p.da, ldP[i], box);
+    mPlo[i] = mk(P.P_lo + offP[i], p.db, p.da, ldP[i], box);
+  }
+  std::vector<TSeg> segs;
+  std::vector<TWork> w1, w2;
+  std::vector<std::vector<int>> into(np);
+  std::vector<int> mThi(ne), mTlo(ne), mBhi(ne), mBlo(ne);
+  for (size_t i = 0; i < ne; ++i) {
+    const HClass &h = w.hc[E[i].ci];
+    const PsiBlk &p = w.psi[E[i].pi], &q = w.psi[E[i].po];
+    const int n = (int)h.terms.size();
+    int ahi = mk(P.A_hi + offA[i], (long long)q.da * n, p.da, ldA[i], 128);
+    int alo = mk(P.A_lo + offA[i], (long long)q.da * n, p.da, ldA[i], 128);
+    mThi[i] = mk(P.T_hi + offT[i], q.da, (long long)n * p.db, ldT[i], 128);
+    mTlo[i] = mk(P.T_lo + offT[i], q.da, (long long)n * p.db, ldT[i], 128);
+    int bbox = ntile_of(q.db);
+    mBhi[i] = mk(P.B_hi + offB[i], q.db, (long long)n * p.db, ldB[i], bbox);
+    mBlo[i] = mk(P.B_lo + offB[i], q.db, (long long)n * p.db, ldB[i], bbox);
+    TSeg sg;
+    sg.mA_hi = ahi; sg.mA_lo = alo; sg.mB_hi = mPhi[E[i].pi]; sg.mB_lo = mPlo[E[i].pi];
+    sg.K = p.da;
+    sg.pad = 0;
+    int seg = (int)segs.size();
+    segs.push_back(sg);
+    const int M = q.da * n, N = p.db, nt = ntile_of(N);
+    int nl = qnum(w.Ld.basis.qn[p.a]);
+    float alpha = (h.pB && (nl & 1)) ? -1.f : 1.f;
+    for (int m0 = 0; m0 < M; m0 += 128)
+      for (int n0 = 0; n0 < N; n0 += nt) {
+        TWork t;
+        memset(&t, 0, sizeof t);
+        t.seg0 = seg; t.nseg = 1;
+        t.M = M; t.N = N; t.m0 = m0; t.n0 = n0; t.ntile = nt;
+        t.mode = 0; t.alpha = alpha;
+        t.out_hi = P.T_hi + offT[i];
+        t.out_lo = P.T_lo + offT[i];
+        t.nrep = n; t.rep = p.db; t.ld = ldT[i];
+        w1.push_back(t);
+      }
+    into[E[i].po].push_back((int)i);
+  }
+  for (size_t po = 0; po < np; ++po) {
+    const PsiBlk &q = w.psi[po];
+    int seg0 = (int)segs.size();
+    for (int i : into[po]) {
+      const HClass &h = w.hc[E[i].ci];
+      const PsiBlk &p = w.psi[E[i].pi];
+      TSeg sg;
+      sg.mA_hi = mThi[i]; sg.mA_lo = mTlo[i]; sg.mB_hi = mBhi[i]; sg.mB_lo = mBlo[i];
+      sg.K = (int)h.terms.size() * p.db;
+      sg.pad = 0;
+      segs.push_back(sg);
+    }
+    const int nseg = (int)segs.size() - seg0;
+    const int M = q.da, N = q.db, nt = ntile_of(N);
+    for (int m0 = 0; m0 < M; m0 += 128)
+      for (int n0 = 0; n0 < N; n0 += nt) {
+        TWork t;
+        memset(&t, 0, sizeof t);
+        t.seg0 = seg0; t.nseg = nseg;
+        t.M = M; t.N = N; t.m0 = m0; t.n0 = n0; t.ntile = nt;
+        t.mode = 1; t.alpha = 1.f;
+        t.off64 = q.off; t.ld = q.db;
+        w2.push_back(t);
+      }
+  }
+  w.maps_host = maps;
+  w.seg_host = segs;
+  w.w1_host = w1;
+  w.w2_host = w2;
+  P.maps = upload(w.buf, w.maps_host, s);
+  P.seg = upload(w.buf, w.seg_host, s);
+  P.work1 = upload(w.buf, w.w1_host, s);
+  P.work2 = upload(w.buf, w.w2_host, s);
+  P.nwork1 = (int)w1.size();
+  P.nwork2 = (int)w2.size();
+  P.err = (int *)w.buf.alloc(sizeof(int));
+  CK(cudaMemsetAsync(P.err, 0, sizeof(int), s));
+  CK(cudaStreamSynchronize(s));
+  w.tf_ready = true;
+}
+
+void apply_tf32(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s) {
+  Window &w = C->win;
+  if (!w.tf_ready) {
+    cudaStream_t save = C->stream;
+    C->stream = s;
+    build_tf32(C);
+    C->stream = save;
+  }
+  Tf32Plan &P = w.tf;
+  CK(launch_split2d((const Split2D *)P.psi_split, P.npsi, s, psi));
+  CK(tf32_gemm(P.work1, P.nwork1, P.seg, P.maps, nullptr, P.err, s));
+  CK(tf32_gemm(P.work2, P.nwork2, P.seg, P.maps, sigma, P.err, s));
+}
+
+void check_err_flag(dmrg_ctx *C, cudaStream_t s) {
+  Window &w = C->win;
+  if (!w.tf_ready) return;
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, w.tf.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (e) fail(DMRG_ERR_TIMEOUT, "tcgen05 kernel: bounded wait %d gave up", e);
+}
+
+void apply(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s, int precision) {
+  if (precision == DMRG_SPLIT_TF32) apply_tf32(C, psi, sigma, s);
+  else apply_fp64(C, psi, sigma, s);
+}
+
+// ---------------------------------------------------------------------------
+// Davidson (FP64 orthogonalisation, subspace, residual)
+// ---------------------------------------------------------------------------
+void jacobi_eig(int n, std::vector<double> A, std::vector<double> &w, std::vector<double> &V) {
+  V.assign(n * n, 0.0);
+  for (int i = 0; i < n; ++i) V[i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0, tot = 0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        tot += A[i * n + j] * A[i * n + j];
+        if (i != j) off += A[i * n + j] * A[i * n + j];
+      }
+    if (off <= 1e-30 * std::max(tot, 1e-300)) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        double apq = A[p * n + q];
+        if (std::fabs(apq) < 1e-300) continue;
+        double theta = (A[q * n + q] - A[p * n + p]) / (2 * apq);
+        double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1));
+        double c = 1 / std::sqrt(t * t + 1), sn = t * c;
+        for (int k = 0; k < n; ++k) {
+          double akp = A[k * n + p], akq = A[k * n + q];
+          A[k * n + p] = c * akp - sn * akq;
+          A[k * n + q] = sn * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {
+          double apk = A[p * n + k], aqk = A[q * n + k];
+          A[p * n + k] = c * apk - sn * aqk;
+          A[q * n + k] = sn * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          double vkp = V[k * n + p], vkq = V[k * n + q];
+          V[k * n + p] = c * vkp - sn * vkq;
+          V[k * n + q] = sn * vkp + c * vkq;
+        }
+      }
+  }
+  w.resize(n);
+  for (int i = 0; i < n; ++i) w[i] = A[i * n + i];
+}
+
+struct DavBuf {
+  double *V, *AV, *t, *u, *work, *coef, *dots;
+};
+
+DavBuf dav_buffers(dmrg_ctx *C, long long n, int m) {
+  if (C->dav_n != n || !C->V) {
+    C->dav.clear();
+    C->V = (double *)C->dav.alloc(8 * (size_t)n * m);
+    C->AV = (double *)C->dav.alloc(8 * (size_t)n * m);
+    C->r = (double *)C->dav.alloc(8 * (size_t)n * 2);
+    C->work = (double *)C->dav.alloc(8 * 296 * (size_t)(m + 2));
+    C->small = (double *)C->dav.alloc(8 * 4 * (size_t)(m + 2));
+    C->dav_n = n;
+  }
+  return {C->V, C->AV, C->r, C->r + n, C->work, C->small, C->small + 2 * (m + 2)};
+}
+
+double dot1(dmrg_ctx *C, const double *a, const double *b, long long n, DavBuf &B, cudaStream_t s) {
+  CK(launch_dots(a, 1, n, b, n, B.work, B.dots, s));
+  double v;
+  CK(cudaMemcpyAsync(&v, B.dots, 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return v;
+}
+
+void dots(dmrg_ctx *C, const double *V, int k, long long n, const double *x, DavBuf &B,
+          std::vector<double> &out, cudaStream_t s) {
+  out.resize(k);
+  CK(launch_dots(V, k, n, x, n, B.work, B.dots, s));
+  CK(cudaMemcpyAsync(out.data(), B.dots, 8 * k, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+}
+
+// out = a*out + sum c_i V_i
+void lincomb(double *out, const double *V, const std::vector<double> &c, double a, long long n,
+             DavBuf &B, cudaStream_t s) {
+  std::vector<double> h(c);
+  h.push_back(a);
+  CK(cudaMemcpyAsync(B.coef, h.data(), 8 * h.size(), cudaMemcpyHostToDevice, s));
+  CK(launch_lincomb(out, V, (int)c.size(), n, B.coef, a != 0.0 ? B.coef + c.size() : nullptr, n, s));
+  CK(cudaStreamSynchronize(s));
+}
+
+int davidson(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_t s) {
+  Window &w = C->win;
+  const long long n = w.psi_len;
+  const int m = std::max(4, std::min(C->cfg.davidson_max_sub, 64));
+  const int maxit = std::max(1, C->cfg.davidson_max_iter);
+  const double tol = C->cfg.davidson_tol > 0 ? C->cfg.davidson_tol : 1e-8;
+  const int prec = C->precision;
+  DavBuf B = dav_buffers(C, n, m);
+  double t0 = now();
+  int nmv = 0;
+  // start vector
+  double nx = dot1(C, x, x, n, B, s);
+  if (!(nx > 0)) {
+    static uint64_t counter = 0;
+    CK(launch_random(x, n, C->cfg.seed + 7919 * (++counter), s));
+    nx = dot1(C, x, x, n, B, s);
+  }
+  CK(cudaMemcpyAsync(B.V, x, 8 * n, cudaMemcpyDeviceToDevice, s));
+  lincomb(B.V, B.V, {}, 1.0 / std::sqrt(nx), n, B, s);
+  apply(C, B.V, B.AV, s, prec);
+  ++nmv;
+  std::vector<double> S(m * m, 0.0), col;
+  dots(C, B.V, 1, n, B.AV, B, col, s);
+  S[0] = col[0];
+  int k = 1, it = 0;
+  double theta = S[0], rnorm = 1e300;
+  std::vector<double> y(1, 1.0);
+  bool conv = false;
+  for (it = 0; it < maxit; ++it) {
+    std::vector<double> Sk(k * k), ev, evec;
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) Sk[i * k + j] = 0.5 * (S[i * m + j] + S[j * m + i]);
+    jacobi_eig(k, Sk, ev, evec);
+    int imin = (int)(std::min_element(ev.begin(), ev.end()) - ev.begin());
+    theta = ev[imin];
+    y.assign(k, 0.0);
+    for (int i = 0; i < k; ++i) y[i] = evec[i * k + imin];
+    // residual r = AV y - theta V y
+    std::vector<double> ny(k);
+    for (int i = 0; i < k; ++i) ny[i] = -theta * y[i];
+    lincomb(B.t, B.AV, y, 0.0, n, B, s);
+    lincomb(B.t, B.V, ny, 1.0, n, B, s);
+    rnorm = std::sqrt(std::max(0.0, dot1(C, B.t, B.t, n, B, s)));
+    if (rnorm < tol) {
+      conv = true;
+      break;
+    }
+    if (k == m) {   // restart with the Ritz vector
+      lincomb(B.u, B.V, y, 0.0, n, B, s);
+      CK(cudaMemcpyAsync(B.V, B.u, 8 * n, cudaMemcpyDeviceToDevice, s));
+      lincomb(B.u, B.AV, y, 0.0, n, B, s);
+      CK(cudaMemcpyAsync(B.AV, B.u, 8 * n, cudaMemcpyDeviceToDevice, s));
+      std::fill(S.begin(), S.end(), 0.0);
+      S[0] = theta;
+      k = 1;
+      y.assign(1, 1.0);
+    }
+    // correction vector: preconditioned residual
+    double *th = B.coef + m + 1;
+    CK(cudaMemcpyAsync(th, &theta, 8, cudaMemcpyHostToDevice, s));
+    CK(launch_precond(B.t, w.diag, th, n, s));
+    for (int pass = 0; pass < 2; ++pass) {
+      std::vector<double> c;
+      dots(C, B.V, k, n, B.t, B, c, s);
+      for (auto &v : c) v = -v;
+      lincomb(B.t, B.V, c, 1.0, n, B, s);
+    }
+    double nt = std::sqrt(std::max(0.0, dot1(C, B.t, B.t, n, B, s)));
+    if (!(nt > 1e-14)) {
+      conv = rnorm < 10 * tol;
+      break;
+    }
+    double *vk = B.V + (long long)k * n;
+    CK(cudaMemcpyAsync(vk, B.t, 8 * n, cudaMemcpyDeviceToDevice, s));
+    lincomb(vk, vk, {}, 1.0 / nt, n, B, s);
+    apply(C, vk, B.AV + (long long)k * n, s, prec);
+    ++nmv;
+    dots(C, B.V, k + 1, n, B.AV + (long long)k * n, B, col, s);
+    for (int i = 0; i <= k; ++i) {
+      S[i * m + k] = col[i];
+      S[k * m + i] = col[i];
+    }
+    ++k;
+  }
+  // Ritz vector
+  lincomb(x, B.V, y, 0.0, n, B, s);
+  double nn = dot1(C, x, x, n, B, s);
+  lincomb(x, x, {}, 1.0 / std::sqrt(nn), n, B, s);
+  double e = theta;
+  if (prec != DMRG_FP64) {   // FP64 Rayleigh quotient for the reported energy
+    check_err_flag(C, s);
+    apply_fp64(C, x, B.t, s);
+    ++nmv;
+    e = dot1(C, x, B.t, n, B, s);
+  }
+  *energy = e;
+  if (iters) *iters = it;
+  C->prof[0] += now() - t0;
+  C->prof[6] += nmv;
+  return conv ? DMRG_OK : DMRG_ERR_NOT_CONVERGED;
+}
+
+// ---------------------------------------------------------------------------
+// truncation: reduced density matrix per sector, cuSOLVER eigensolver
+// ---------------------------------------------------------------------------
+void truncate(dmrg_ctx *C, const double *psi, int side, int D, double *disc, double *ent,
+              cudaStream_t s) {
+  Window &w = C->win;
+  double t0 = now();
+  if (!C->solver) {
+    if (cusolverDnCreate(&C->solver) != CUSOLVER_STATUS_SUCCESS) fail(DMRG_ERR_CUDA, "cusolverDnCreate failed");
+  }
+  cusolverDnSetStream(C->solver, s);
+  const size_t np = w.psi.size();
+  std::vector<int> dim(np);
+  std::vector<long long> roff(np);
+  long long tot = 0;
+  for (size_t i = 0; i < np; ++i) {
+    dim[i] = side == 0 ? w.psi[i].da : w.psi[i].db;
+    roff[i] = tot;
+    tot += (long long)dim[i] * dim[i];
+  }
+  WinBuf tmp;
+  double *rho = (double *)tmp.alloc(8 * std::max<long long>(tot, 1));
+  double *eval = (double *)tmp.alloc(8 * std::max<long long>(std::accumulate(dim.begin(), dim.end(), 0LL), 1));
+  std::vector<GemmDesc> dd;
+  std::vector<GemmSeg> gg;
+  long long tt = 0;
+  for (size_t i = 0; i < np; ++i) {
+    const PsiBlk &p = w.psi[i];
+    GemmSeg g;
+    memset(&g, 0, sizeof g);
+    g.A = psi + p.off;
+    g.B = psi + p.off;
+    if (side == 0) {
+      g.a_rs = p.db; g.a_cs = 1; g.b_rs = 1; g.b_cs = p.db; g.K = p.db;
+    } else {
+      g.a_rs = 1; g.a_cs = p.db; g.b_rs = p.db; g.b_cs = 1; g.K = p.da;
+    }
+    GemmDesc d;
+    memset(&d, 0, sizeof d);
+    d.C = rho + roff[i];
+    d.c_rs = dim[i]; d.c_cs = 1;
+    d.M = dim[i]; d.N = dim[i]; d.batch = 1;
+    d.seg0 = (int)gg.size(); d.nseg = 1;
+    d.tiles_m = (dim[i] + 63) / 64; d.tiles_n = d.tiles_m;
+    d.alpha = 1.0; d.beta = 0.0;
+    d.tile0 = tt;
+    tt += (long long)d.tiles_m * d.tiles_n;
+    gg.push_back(g);
+    dd.push_back(d);
+  }
+  {
+    GemmDesc *a = upload(tmp, dd, s);
+    GemmSeg *b = upload(tmp, gg, s);
+    CK(launch_gemm_f64(a, (int)dd.size(), b, tt, s));
+  }
+  int *info = (int *)tmp.alloc(sizeof(int) * np);
+  std::vector<long long> eoff(np);
+  long long eo = 0;
+  int lwork_max = 0;
+  for (size_t i = 0; i < np; ++i) {
+    eoff[i] = eo;
+    eo += dim[i];
+    int lw = 0;
+    if (cusolverDnDsyevd_bufferSize(C->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
+                                    dim[i], rho + roff[i], dim[i], eval + eoff[i], &lw) !=
+        CUSOLVER_STATUS_SUCCESS)
+      fail(DMRG_ERR_CUDA, "syevd bufferSize failed");
+    lwork_max = std::max(lwork_max, lw);
+  }
+  double *wk = (double *)tmp.alloc(8 * (size_t)std::max(lwork_max, 1));
+  for (size_t i = 0; i < np; ++i)
+    if (cusolverDnDsyevd(C->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, dim[i],
+                         rho + roff[i], dim[i], eval + eoff[i], wk, lwork_max, info + i) !=
+        CUSOLVER_STATUS_SUCCESS)
+      fail(DMRG_ERR_CUDA, "syevd failed");
+  std::vector<double> ev(eo);
+  std::vector<int> hinfo(np);
+  CK(cudaMemcpyAsync(ev.data(), eval, 8 * eo, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(hinfo.data(), info, sizeof(int) * np, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (size_t i = 0; i < np; ++i)
+    if (hinfo[i] != 0) fail(DMRG_ERR_CUDA, "syevd info %d", hinfo[i]);
+  // candidates: (-weight, sector, position in descending order)
+  struct Cand {
+    double v;
+    int sec, k;
+  };
+  std::vector<Cand> cand;
+  for (size_t i = 0; i < np; ++i)
+    for (int k = 0; k < dim[i]; ++k) cand.push_back({std::max(0.0, ev[eoff[i] + dim[i] - 1 - k]), (int)i, k});
+  std::sort(cand.begin(), cand.end(), [](const Cand &a, const Cand &b) {
+    if (a.v != b.v) return a.v > b.v;
+    if (a.sec != b.sec) return a.sec < b.sec;
+    return a.k < b.k;
+  });
+  const size_t keep = std::min<size_t>(D, cand.size());
+  double wk_tot = 0, wk_keep = 0;
+  for (auto &c : cand) wk_tot += c.v;
+  std::vector<std::vector<int>> kept(np);
+  for (size_t j = 0; j < keep; ++j) {
+    kept[cand[j].sec].push_back(cand[j].k);
+    wk_keep += cand[j].v;
+  }
+  double e = 0;
+  for (size_t j = 0; j < keep; ++j) {
+    double pj = cand[j].v / std::max(wk_keep, 1e-300);
+    if (pj > 0) e -= pj * std::log(pj);
+  }
+  if (disc) *disc = wk_tot - wk_keep;
+  if (ent) *ent = e;
+  // isometry, sectors in ascending QN order of the new block
+  std::vector<std::pair<QN, int>> order;
+  for (size_t i = 0; i < np; ++i)
+    if (!kept[i].empty()) {
+      QN q = side == 0 ? w.Ld.basis.qn[w.psi[i].a] : w.Rd.basis.qn[w.psi[i].b];
+      order.push_back({q, (int)i});
+    }
+  std::sort(order.begin(), order.end());
+  Iso T;
+  long long off = 0;
+  for (auto &o : order) {
+    std::sort(kept[o.second].begin(), kept[o.second].end());
+    T.qn.push_back(o.first);
+    T.rows.push_back(dim[o.second]);
+    T.cols.push_back((int)kept[o.second].size());
+    T.off.push_back(off);
+    off += (long long)dim[o.second] * kept[o.second].size();
+  }
+  std::unique_ptr<BlockPart> Bn(new BlockPart());
+  WinBuf &bb = buf_of(C, Bn.get());
+  T.d = (double *)bb.alloc(8 * std::max<long long>(off, 1));
+  for (size_t j = 0; j < order.size(); ++j) {
+    int i = order[j].second;
+    std::vector<int> colsel;
+    for (int k : kept[i]) colsel.push_back(dim[i] - 1 - k);
+    int *dc = upload(tmp, colsel, s);
+    CK(launch_select_cols(rho + roff[i], dim[i], dim[i], dc, (int)colsel.size(), T.d + T.off[j], s));
+  }
+  CK(cudaStreamSynchronize(s));
+  C->prof[3] += now() - t0;
+  t0 = now();
+  cudaStream_t save = C->stream;
+  C->stream = s;
+  if (side == 0) {
+    renormalize(C, w.Ld, T, *Bn, bb);
+    int n = w.l + 1;
+    if ((int)C->L.size() <= n) C->L.resize(n + 1);
+    if (C->L[n]) free_part(C, C->L[n].get());
+    C->L[n] = std::move(Bn);
+  } else {
+    renormalize(C, w.Rd, T, *Bn, bb);
+    int n = w.l + 1;
+    if (C->R.count(n)) free_part(C, C->R[n].get());
+    C->R[n] = std::move(Bn);
+  }
+  C->stream = save;
+  C->prof[1] += now() - t0;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+namespace {
+
+int guard(dmrg_ctx *C, const std::function<void()> &f) {
+  try {
+    f();
+    if (C) C->err.clear();
+    return DMRG_OK;
+  } catch (const Err &e) {
+    if (C) C->err = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc &) {
+    if (C) C->err = "host allocation failed";
+    return DMRG_ERR_OOM;
+  }
+}
+
+void sweep_impl(dmrg_ctx *C, int nsw, const int *dsched, double *E, cudaStream_t s) {
+  const int N = C->N;
+  if (!C->ham) fail(DMRG_ERR_STATE, "dmrg_set_hamiltonian first");
+  for (int n = 1; n <= N - 1; ++n)
+    if (!C->riso.count(n)) fail(DMRG_ERR_STATE, "right isometry %d missing", n);
+  C->stream = s;
+  for (double &p : C->prof) p = 0;
+  double t0 = now();
+  C->R.clear();
+  C->R[N] = vacuum(C);
+  for (int n = N - 1; n >= 2; --n) {
+    upload_iso(C, C->riso[n]);
+    grow_right(C, n, C->riso[n]);
+  }
+  C->L.clear();
+  C->L.push_back(vacuum(C));
+  C->prof[1] += now() - t0;
+  WinBuf xb;
+  double e = 0;
+  int it;
+  for (int sw = 0; sw < nsw; ++sw) {
+    const int D = dsched ? dsched[sw] : C->cfg.d_max;
+    for (int l = 0; l <= N - 2; ++l) {
+      build_window(C, l);
+      double *x = (double *)xb.alloc(8 * std::max<long long>(C->win.psi_len, 1));
+      CK(cudaMemsetAsync(x, 0, 8 * C->win.psi_len, s));
+      int rc = davidson(C, x, &e, &it, s);
+      (void)rc;
+      if (l < N - 2) truncate(C, x, 0, D, nullptr, nullptr, s);
+      xb.clear();
+    }
+    for (int l = N - 2; l >= 0; --l) {
+      build_window(C, l);
+      double *x = (double *)xb.alloc(8 * std::max<long long>(C->win.psi_len, 1));
+      CK(cudaMemsetAsync(x, 0, 8 * C->win.psi_len, s));
+      int rc = davidson(C, x, &e, &it, s);
+      (void)rc;
+      if (l > 0) truncate(C, x, 1, D, nullptr, nullptr, s);
+      xb.clear();
+    }
+    if (E) E[sw] = e;
+  }
+  C->prof[5] = std::max(0.0, now() - t0 - C->prof[0] - C->prof[1] - C->prof[2] - C->prof[3] - C->prof[4]);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *dmrg_error_string(int code) {
+  switch (code) {
+    case DMRG_OK: return "ok";
+    case DMRG_ERR_ARG: return "invalid argument";
+    case DMRG_ERR_OOM: return "out of memory";
+    case DMRG_ERR_CUDA: return "CUDA error";
+    case DMRG_ERR_STATE: return "call out of order";
+    case DMRG_ERR_TIMEOUT: return "bounded device wait gave up";
+    case DMRG_ERR_NOT_CONVERGED: return "Davidson not converged";
+    default: return "unknown error";
+  }
+}
+
+const char *dmrg_last_error(const dmrg_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+int dmrg_create(dmrg_ctx **out, const dmrg_config *cfg) {
+  if (!out || !cfg) return DMRG_ERR_ARG;
+  *out = nullptr;
+  if ((cfg->sym != DMRG_U1 && cfg->sym != DMRG_U1U1) || cfg->n_sites < 2 || cfg->n_up < 0 ||
+      cfg->d_max < 1)
+    return DMRG_ERR_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return DMRG_ERR_CUDA;
+  }
+  dmrg_ctx *C = new (std::nothrow) dmrg_ctx();
+  if (!C) return DMRG_ERR_OOM;
+  C->cfg = *cfg;
+  if (C->cfg.davidson_max_sub < 4) C->cfg.davidson_max_sub = 20;
+  if (C->cfg.davidson_max_iter < 1) C->cfg.davidson_max_iter = 200;
+  C->spinful = cfg->sym == DMRG_U1U1;
+  C->N = cfg->n_sites;
+  C->M = C->spinful ? 2 * C->N : C->N;
+  C->target = C->spinful ? QN{cfg->n_up, cfg->n_dn} : QN{cfg->n_up, 0};
+  C->precision = cfg->precision;
+  *out = C;
+  return DMRG_OK;
+}
+
+int dmrg_destroy(dmrg_ctx *ctx) {
+  if (!ctx) return DMRG_OK;
+  cudaDeviceSynchronize();
+  ctx->win.buf.clear();
+  ctx->win.ldbuf.clear();
+  ctx->win.rdbuf.clear();
+  ctx->L.clear();
+  ctx->R.clear();
+  ctx->partbuf.clear();
+  ctx->dav.clear();
+  if (ctx->solver) cusolverDnDestroy(ctx->solver);
+  delete ctx;
+  return DMRG_OK;
+}
+
+int dmrg_lattice_hamiltonian(int model, int Lx, int Ly, double t, double tp, double v,
+                             double *t_out, double *V_out) {
+  if (Lx < 3 || Ly < 3 || !t_out || !V_out) return DMRG_ERR_ARG;
+  if (model != DMRG_MODEL_SPINLESS_TV && model != DMRG_MODEL_HUBBARD) return DMRG_ERR_ARG;
+  const int N = Lx * Ly;
+  std::fill(t_out, t_out + (size_t)N * N, 0.0);
+  std::fill(V_out, V_out + (size_t)N * N * N * N, 0.0);
+  std::vector<std::pair<int, int>> nn, nnn;
+  torus_bonds(Lx, Ly, false, nn);
+  for (auto &b : nn) {
+    t_out[(size_t)b.first * N + b.second] += -t;
+    t_out[(size_t)b.second * N + b.first] += -t;
+    if (model == DMRG_MODEL_SPINLESS_TV)
+      V_out[(((size_t)b.first * N + b.second) * N + b.second) * N + b.first] += v;
+  }
+  if (model == DMRG_MODEL_SPINLESS_TV && tp != 0.0) {
+    torus_bonds(Lx, Ly, true, nnn);
+    for (auto &b : nnn) {
+      t_out[(size_t)b.first * N + b.second] += -tp;
+      t_out[(size_t)b.second * N + b.first] += -tp;
+    }
+  }
+  if (model == DMRG_MODEL_HUBBARD)
+    for (int i = 0; i < N; ++i) V_out[(((size_t)i * N + i) * N + i) * N + i] = v / 2.0;
+  return DMRG_OK;
+}
+
+int dmrg_momentum_basis(int Lx, int Ly, double *U) {
+  if (Lx < 1 || Ly < 1 || !U) return DMRG_ERR_ARG;
+  const int N = Lx * Ly;
+  const double PI = 3.14159265358979323846;
+  struct Mode {
+    double eps;
+    int nx, ny, sn;
+    bool self;
+  };
+  std::vector<Mode> modes;
+  std::vector<char> seen(N, 0);
+  for (int ny = 0; ny < Ly; ++ny)
+    for (int nx = 0; nx < Lx; ++nx) {
+      if (seen[ny * Lx + nx]) continue;
+      int mx = (Lx - nx) % Lx, my = (Ly - ny) % Ly;
+      seen[ny * Lx + nx] = seen[my * Lx + mx] = 1;
+      int rx = nx, ry = ny;
+      if (std::make_pair(mx, my) < std::make_pair(nx, ny)) rx = mx, ry = my;
+      double eps = -2.0 * (std::cos(2 * PI * rx / Lx) + std::cos(2 * PI * ry / Ly));
+      eps = std::round(eps * 1e12) / 1e12;
+      bool self = (mx == nx && my == ny);
+      modes.push_back({eps, rx, ry, 0, self});
+      if (!self) modes.push_back({eps, rx, ry, 1, false});
+    }
+  std::sort(modes.begin(), modes.end(), [](const Mode &a, const Mode &b) {
+    if (a.eps != b.eps) return a.eps < b.eps;
+    if (a.nx != b.nx) return a.nx < b.nx;
+    if (a.ny != b.ny) return a.ny < b.ny;
+    return a.sn < b.sn;
+  });
+  for (int m = 0; m < N; ++m) {
+    const Mode &md = modes[m];
+    double kx = 2 * PI * md.nx / Lx, ky = 2 * PI * md.ny / Ly;
+    for (int i = 0; i < N; ++i) {
+      double ph = kx * (i % Lx) + ky * (i / Lx);
+      double amp = md.self ? std::sqrt(1.0 / N) : std::sqrt(2.0 / N);
+      U[(size_t)i * N + m] = amp * (md.sn ? std::sin(ph) : std::cos(ph));
+    }
+  }
+  return DMRG_OK;
+}
+
+int dmrg_set_hamiltonian(dmrg_ctx *C, const double *t, const double *V, const double *U) {
+  if (!C || !t || !V) return DMRG_ERR_ARG;
+  return guard(C, [&] {
+    const int N = C->N;
+    const size_t N2 = (size_t)N * N, N4 = N2 * N2;
+    double vmax = 0;
+    for (size_t e = 0; e < N4; ++e) vmax = std::max(vmax, std::fabs(V[e]));
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j) {
+        if (std::fabs(t[(size_t)i * N + j] - t[(size_t)j * N + i]) > 1e-12 * (1 + std::fabs(t[(size_t)i * N + j])))
+          fail(DMRG_ERR_ARG, "t is not symmetric at (%d,%d)", i, j);
+        for (int k = 0; k < N; ++k)
+          for (int l = 0; l < N; ++l) {
+            double a = V[((i * (size_t)N + j) * N + k) * N + l];
+            double b = V[((l * (size_t)N + k) * N + j) * N + i];
+            if (std::fabs(a - b) > 1e-12 * (1 + vmax))
+              fail(DMRG_ERR_ARG, "V is not Hermitian: V[%d,%d,%d,%d] != V[%d,%d,%d,%d]", i, j, k, l, l, k, j, i);
+          }
+      }
+    std::vector<double> tt(t, t + N2), VV(V, V + N4);
+    if (U) {
+      for (int a = 0; a < N; ++a)
+        for (int b = 0; b < N; ++b) {
+          double s = 0;
+          for (int i = 0; i < N; ++i) s += U[(size_t)i * N + a] * U[(size_t)i * N + b];
+          if (std::fabs(s - (a == b)) > 1e-10) fail(DMRG_ERR_ARG, "mode rotation is not orthogonal");
+        }
+      std::vector<double> tmp(N2, 0.0);
+      for (int i = 0; i < N; ++i)
+        for (int b = 0; b < N; ++b) {
+          double s = 0;
+          for (int j = 0; j < N; ++j) s += t[(size_t)i * N + j] * U[(size_t)j * N + b];
+          tmp[(size_t)i * N + b] = s;
+        }
+      for (int a = 0; a < N; ++a)
+        for (int b = 0; b < N; ++b) {
+          double s = 0;
+          for (int i = 0; i < N; ++i) s += U[(size_t)i * N + a] * tmp[(size_t)i * N + b];
+          tt[(size_t)a * N + b] = s;
+        }
+      std::vector<double> w2;
+      for (int ax = 0; ax < 4; ++ax) {
+        quarter(VV, w2, U, N, ax);
+        VV.swap(w2);
+      }
+    }
+    const int M = C->M;
+    C->h.assign((size_t)M * M, 0.0);
+    C->W.assign((size_t)M * M * M * M, 0.0);
+    auto sp = [&](int p) { return C->spinful ? p / 2 : p; };
+    auto sg = [&](int p) { return C->spinful ? p % 2 : 0; };
+    for (int p = 0; p < M; ++p)
+      for (int q = 0; q < M; ++q)
+        if (sg(p) == sg(q)) C->h[(size_t)p * M + q] = tt[(size_t)sp(p) * N + sp(q)];
+    auto X = [&](int p, int q, int r, int s) -> double {
+      if (sg(p) != sg(s) || sg(q) != sg(r)) return 0.0;
+      return VV[(((size_t)sp(p) * N + sp(q)) * N + sp(r)) * N + sp(s)];
+    };
+    for (int p = 0; p < M; ++p)
+      for (int q = 0; q < M; ++q)
+        for (int r = 0; r < M; ++r)
+          for (int s = 0; s < M; ++s)
+            C->W[(((size_t)p * M + q) * M + r) * M + s] =
+                0.25 * (X(p, q, r, s) - X(q, p, r, s) - X(p, q, s, r) + X(q, p, s, r));
+    C->ham = true;
+    C->L.clear();
+    C->R.clear();
+    C->win.valid = false;
+  });
+}
+
+int dmrg_set_isometry(dmrg_ctx *C, int side, int site, int ns, const int *qn, const int *rows,
+                      const int *cols, const double *data) {
+  if (!C || (side != 0 && side != 1) || site < 1 || site > C->N - 1 || ns < 1 || !qn || !rows ||
+      !cols || !data)
+    return DMRG_ERR_ARG;
+  return guard(C, [&] {
+    Iso T;
+    const int nq = C->spinful ? 2 : 1;
+    long long off = 0;
+    for (int k = 0; k < ns; ++k) {
+      QN q{qn[k * nq], nq == 2 ? qn[k * nq + 1] : 0};
+      if (rows[k] < 1 || cols[k] < 1 || cols[k] > rows[k]) fail(DMRG_ERR_ARG, "bad isometry shape in sector %d", k);
+      T.qn.push_back(q);
+      T.rows.push_back(rows[k]);
+      T.cols.push_back(cols[k]);
+      T.off.push_back(off);
+      off += (long long)rows[k] * cols[k];
+    }
+    T.host.assign(data, data + off);
+    auto &m = side == 0 ? C->liso : C->riso;
+    m[site] = std::move(T);
+  });
+}
+
+int dmrg_build_block_ops(dmrg_ctx *C, int l, void *stream) {
+  if (!C) return DMRG_ERR_ARG;
+  return guard(C, [&] {
+    const int N = C->N;
+    if (!C->ham) fail(DMRG_ERR_STATE, "dmrg_set_hamiltonian first");
+    if (l < 0 || l > N - 2) fail(DMRG_ERR_ARG, "window %d out of range", l);
+    for (int n = 1; n <= l; ++n)
+      if (!C->liso.count(n)) fail(DMRG_ERR_STATE, "left isometry %d missing", n);
+    for (int n = l + 2; n <= N - 1; ++n)
+      if (!C->riso.count(n)) fail(DMRG_ERR_STATE, "right isometry %d missing", n);
+    cudaStream_t s = (cudaStream_t)stream;
+    C->stream = s;
+    double t0 = now();
+    C->L.clear();
+    C->L.push_back(vacuum(C));
+    for (int n = 1; n <= l; ++n) {
+      upload_iso(C, C->liso[n]);
+      grow_left(C, n, C->liso[n]);
+    }
+    C->R.clear();
+    C->R[N] = vacuum(C);
+    for (int n = N - 1; n >= l + 2; --n) {
+      upload_iso(C, C->riso[n]);
+      grow_right(C, n, C->riso[n]);
+    }
+    C->prof[1] += now() - t0;
+    build_window(C, l);
+  });
+}
+
+int dmrg_heff_layout(dmrg_ctx *C, long long *psi_len, int *n_blocks, int *blocks) {
+  if (!C) return DMRG_ERR_ARG;
+  if (!C->win.valid) {
+    C->err = "no window built";
+    return DMRG_ERR_STATE;
+  }
+  const Window &w = C->win;
+  if (psi_len) *psi_len = w.psi_len;
+  if (n_blocks) *n_blocks = (int)w.psi.size();
+  if (blocks) {
+    const int nq = C->spinful ? 2 : 1;
+    int k = 0;
+    for (const PsiBlk &p : w.psi) {
+      for (int i = 0; i < nq; ++i) blocks[k++] = w.Ld.basis.qn[p.a][i];
+      for (int i = 0; i < nq; ++i) blocks[k++] = w.Rd.basis.qn[p.b][i];
+      blocks[k++] = p.da;
+      blocks[k++] = p.db;
+    }
+  }
+  return DMRG_OK;
+}
+
+int dmrg_set_precision(dmrg_ctx *C, int precision) {
+  if (!C || (precision != DMRG_FP64 && precision != DMRG_SPLIT_TF32)) return DMRG_ERR_ARG;
+  C->precision = precision;
+  return DMRG_OK;
+}
+
+int dmrg_heff_apply(dmrg_ctx *C, const double *psi, double *sigma, void *stream) {
+  if (!C || !psi || !sigma) return DMRG_ERR_ARG;
+  if (!C->win.valid) {
+    C->err = "no window built";
+    return DMRG_ERR_STATE;
+  }
+  return guard(C, [&] { apply(C, psi, sigma, (cudaStream_t)stream, C->precision); });
+}
+
+int dmrg_heff_apply_host(dmrg_ctx *C, const double *psi_h, double *sigma_h, void *stream) {
+  if (!C || !psi_h || !sigma_h) return DMRG_ERR_ARG;
+  if (!C->win.valid) {
+    C->err = "no window built";
+    return DMRG_ERR_STATE;
+  }
+  return guard(C, [&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long n = C->win.psi_len;
+    WinBuf b;
+    double *dp = (double *)b.alloc(8 * std::max<long long>(n, 1));
+    double *ds = (double *)b.alloc(8 * std::max<long long>(n, 1));
+    CK(cudaMemcpyAsync(dp, psi_h, 8 * n, cudaMemcpyHostToDevice, s));
+    apply(C, dp, ds, s, C->precision);
+    CK(cudaMemcpyAsync(sigma_h, ds, 8 * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    check_err_flag(C, s);
+  });
+}
+
+int dmrg_heff_flops(dmrg_ctx *C, double *flops) {
+  if (!C || !flops) return DMRG_ERR_ARG;
+  if (!C->win.valid) return DMRG_ERR_STATE;
+  *flops = C->win.flops;
+  return DMRG_OK;
+}
+
+int dmrg_davidson(dmrg_ctx *C, double *psi, double *energy, int *iters, void *stream) {
+  if (!C || !psi || !energy) return DMRG_ERR_ARG;
+  if (!C->win.valid) {
+    C->err = "no window built";
+    return DMRG_ERR_STATE;
+  }
+  int rc = DMRG_OK;
+  int g = guard(C, [&] { rc = davidson(C, psi, energy, iters, (cudaStream_t)stream); });
+  return g != DMRG_OK ? g : rc;
+}
+
+int dmrg_truncate(dmrg_ctx *C, const double *psi, int side, int d_max, double *disc, double *ent,
+                  void *stream) {
+  if (!C || !psi || (side != 0 && side != 1) || d_max < 1) return DMRG_ERR_ARG;
+  if (!C->win.valid) return DMRG_ERR_STATE;
+  return guard(C, [&] { truncate(C, psi, side, d_max, disc, ent, (cudaStream_t)stream); });
+}
+
+int dmrg_sweep(dmrg_ctx *C, int n_sweeps, const int *d_schedule, double *E, void *stream) {
+  if (!C || n_sweeps < 1) return DMRG_ERR_ARG;
+  return guard(C, [&] { sweep_impl(C, n_sweeps, d_schedule, E, (cudaStream_t)stream); });
+}
+
+int dmrg_profile(dmrg_ctx *C, double *out7) {
+  if (!C || !out7) return DMRG_ERR_ARG;
+  for (int i = 0; i < 7; ++i) out7[i] = C->prof[i];
+  return DMRG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,61 @@
+// Split-precision (3 x TF32) H_eff*psi on the 5th-generation tensor cores.
+//
+// Operands are FP64 numbers split as x = hi + lo (both TF32); a product is
+// hi*hi + hi*lo + lo*hi accumulated in FP32 in tensor memory (TMEM).  All
+// operands are K-major row-major float matrices whose row stride is a
+// multiple of 4 floats; tiles are fetched by TMA with 128-byte swizzle.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+namespace dmrg {
+
+// One K-segment: A (M x K) and B (N x K), each as (hi, lo) tensor maps.
+struct TSeg {
+  int mA_hi, mA_lo, mB_hi, mB_lo;   // indices into the tensor-map table
+  int K;
+  int pad;
+};
+
+// One 128 x ntile output tile.
+struct TWork {
+  int seg0, nseg;
+  int M, N;          // full problem extent (for masking)
+  int m0, n0;        // tile origin
+  int ntile;         // UMMA N of this tile (multiple of 16, <= 128)
+  int mode;          // 0: write split TF32 (hi, lo) to T; 1: write FP64
+  float alpha;
+  // mode 0: element (r, c) -> base + (r / nrep) * ld + (r % nrep) * rep + c
+  float *out_hi, *out_lo;
+  int nrep, rep;
+  long long ld;
+  // mode 1: element (r, c) -> out64[r * ld + c] (bound sigma + offset)
+  long long off64;
+};
+
+struct Tf32Plan {
+  // split operand storage (float, padded rows)
+  float *A_hi = nullptr, *A_lo = nullptr, *B_hi = nullptr, *B_lo = nullptr;
+  float *P_hi = nullptr, *P_lo = nullptr, *T_hi = nullptr, *T_lo = nullptr;
+  CUtensorMap *maps = nullptr;      // device copy of the tensor maps
+  TSeg *seg = nullptr;
+  TWork *work1 = nullptr, *work2 = nullptr;
+  int nwork1 = 0, nwork2 = 0;
+  void *psi_split = nullptr;        // SplitT descriptors (device), one per psi block
+  int npsi = 0;
+  int *err = nullptr;               // device error flag (bounded waits)
+};
+
+// Encode a 2-D tensor map over a row-major float matrix (rows x cols,
+// row stride ld floats, ld % 4 == 0, base 16-byte aligned) with a
+// (32 x box_rows) box and 128-byte swizzle.  Returns 0 on success.
+int encode_map(CUtensorMap *out, const float *base, int rows, int cols, long long ld,
+               int box_rows);
+
+cudaError_t tf32_gemm(const TWork *work, int nwork, const TSeg *seg, const CUtensorMap *maps,
+                      double *out64, int *err, cudaStream_t s);
+
+}  // namespace dmrg

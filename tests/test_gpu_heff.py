@@ -1,0 +1,150 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Both sides get the same seeded inputs (lattice parameters, the Haar factor
+of the mode rotation, random isometries, random psi) and build everything
+else -- lattice Hamiltonian, momentum basis, rotation, block operators --
+with their own code.
+
+Tolerances
+  * FP64 path: relative 2-norm error of sigma <= 1e-12 (spec bound).
+  * split 3xTF32 path: relative 2-norm error of sigma <= 2e-5.  Operands
+    carry ~22 significant bits (hi + lo) and the accumulation is FP32, so
+    the expected error is a few 1e-7 times sqrt(K) for K up to ~1e3.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import dmrg as odmrg
+from oracle import ed, hamiltonian, lattice
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2311_14106_b300 as lib  # noqa: E402
+
+TOL64 = 1e-12
+TOL_SPLIT = 2e-5
+
+
+def problem(Lx, Ly, spinful, target, rot_seed=2, V=1.0, U=4.0, tp=0.0):
+    N = Lx * Ly
+    Q = synth.haar_rotation(N, rot_seed) if rot_seed is not None else np.eye(N)
+    # oracle side
+    if spinful:
+        To, Vo = lattice.hubbard(Lx, Ly, 1.0, U)
+    else:
+        To, Vo = lattice.spinless_tV(Lx, Ly, 1.0, tp, V)
+    Uo = lattice.momentum_basis(Lx, Ly) @ Q
+    To, Vo = lattice.rotate(To, Vo, Uo)
+    h, W = hamiltonian.spin_orbital(To, Vo, spinful)
+    model = odmrg.Model(h, W, spinful, target)
+    # library side (its own lattice and momentum basis)
+    if spinful:
+        Tg, Vg = lib.lattice_hamiltonian(lib.MODEL_HUBBARD, Lx, Ly, 1.0, 0.0, U)
+    else:
+        Tg, Vg = lib.lattice_hamiltonian(lib.MODEL_SPINLESS_TV, Lx, Ly, 1.0, tp, V)
+    Ug = lib.momentum_basis(Lx, Ly) @ Q
+    return model, (Tg, Vg, Ug), h, W
+
+
+def make_gpu(n_sites, target, spinful, ham, **kw):
+    d = lib.Dmrg(n_sites, target[0], target[1] if spinful else 0, spinful=spinful, **kw)
+    d.set_hamiltonian(*ham)
+    return d
+
+
+def window_case(Lx, Ly, spinful, target, D, l, seed=5):
+    model, ham, h, W = problem(Lx, Ly, spinful, target)
+    N = Lx * Ly
+    li = synth.random_left_isometries(N, spinful, target, D, l, seed)
+    ri = synth.random_right_isometries(N, spinful, target, D, l + 2, seed + 1)
+    w = odmrg.window_from_mps(model, li, ri, l)
+    g = make_gpu(N, target, spinful, ham, d_max=D)
+    g.set_mps(li, ri)
+    g.build_block_ops(l)
+    n, lay = g.heff_layout()
+    assert n == w.size
+    assert lay == [(a, b, da, db) for a, b, _, da, db in w.layout]
+    return w, g
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+CASES = ([("s3", 3, 3, False, (4,), 8, l) for l in range(8)]
+         + [("h3", 3, 3, True, (5, 4), 16, l) for l in (0, 4, 7)]
+         + [("s4", 4, 4, False, (8,), 64, 7), ("s4b", 4, 4, False, (8,), 128, 5)])
+
+
+@pytest.mark.parametrize("name,Lx,Ly,spinful,target,D,l", CASES)
+def test_heff_fp64_and_split_vs_oracle(name, Lx, Ly, spinful, target, D, l):
+    w, g = window_case(Lx, Ly, spinful, target, D, l)
+    psi = synth.random_psi([(a, b, da, db) for a, b, _, da, db in w.layout], 11)
+    ref = w.apply(psi)
+    g.set_precision(lib.FP64)
+    s64 = g.heff_apply_host(psi)
+    assert rel(s64, ref) <= TOL64, rel(s64, ref)
+    g.set_precision(lib.SPLIT_TF32)
+    s32 = g.heff_apply_host(psi)
+    assert rel(s32, ref) <= TOL_SPLIT, rel(s32, ref)
+    # device-pointer entry point agrees with the host one
+    x = torch.tensor(psi, device="cuda")
+    y = torch.empty_like(x)
+    g.set_precision(lib.FP64)
+    g.heff_apply(x, y)
+    torch.cuda.synchronize()
+    assert np.array_equal(y.cpu().numpy(), s64)
+
+
+def test_heff_flops_matches_layout_count():
+    w, g = window_case(4, 4, False, (8,), 64, 7)
+    f = g.heff_flops()
+    assert f > 0
+    # every term contributes 2 (m'mn + m'nn') per nonzero sector block; the
+    # oracle's term list includes identity factors exactly as the library's
+    assert f >= 2 * sum(da * da * db for _, _, _, da, db in w.layout)
+
+
+def test_davidson_energy_vs_oracle():
+    w, g = window_case(4, 4, False, (8,), 64, 7)
+    e_ref, _ = w.solve(tol=1e-12)
+    for prec in (lib.FP64, lib.SPLIT_TF32):
+        g.set_precision(prec)
+        x = torch.zeros(w.size, dtype=torch.float64, device="cuda")
+        e, it, conv = g.davidson(x)
+        assert conv
+        assert abs(e - e_ref) <= 1e-9 * abs(e_ref), (prec, e, e_ref)
+        v = x.cpu().numpy()
+        assert abs(np.linalg.norm(v) - 1) < 1e-10
+
+
+def test_sweep_matches_ed_spinless_3x3():
+    model, ham, h, W = problem(3, 3, False, (4,))
+    e_ed = ed.ground_energy(h, W, 4)[0]
+    g = make_gpu(9, (4,), False, ham, d_max=20, davidson_tol=1e-9)
+    g.set_mps(right=synth.random_right_isometries(9, False, (4,), 20, 1, 0))
+    E = g.sweep(2)
+    assert abs(E[-1] - e_ed) <= 1e-9 * abs(e_ed), (E, e_ed)
+
+
+def test_sweep_split_matches_ed_spinless_3x3():
+    model, ham, h, W = problem(3, 3, False, (4,))
+    e_ed = ed.ground_energy(h, W, 4)[0]
+    g = make_gpu(9, (4,), False, ham, d_max=20, davidson_tol=1e-9, precision=lib.SPLIT_TF32)
+    g.set_mps(right=synth.random_right_isometries(9, False, (4,), 20, 1, 0))
+    E = g.sweep(2)
+    assert abs(E[-1] - e_ed) <= 1e-9 * abs(e_ed), (E, e_ed)
+
+
+def test_sweep_hubbard_3x3_variational_and_matches_oracle():
+    model, ham, h, W = problem(3, 3, True, (5, 4), rot_seed=None)
+    e_ed = ed.ground_energy(h, W, 9, n_up=5)[0]
+    ri = synth.random_right_isometries(9, True, (5, 4), 16, 1, 0)
+    g = make_gpu(9, (5, 4), True, ham, d_max=16, davidson_tol=1e-9)
+    g.set_mps(right=ri)
+    E = g.sweep(1)
+    Eo, hist = odmrg.sweep(model, {n: ri[n] for n in ri if n >= 2}, 16, 1)
+    assert E[-1] >= e_ed - 1e-9
+    assert abs(E[-1] - Eo[-1]) <= 1e-6 * abs(e_ed), (E, Eo)
