@@ -1,0 +1,324 @@
+"""Benchmark of the H_eff*psi hot path on one B300 (or N independent replicas).
+
+A step is one sigma = H_eff*psi of the middle two-site window of the
+workload (the Davidson matvec the paper's performance figures count).
+value = algorithmic TFLOP/s of the split 3xTF32 path (whole job: sum over
+replicas); the FP64 path, the Davidson solve time of both paths, their energy
+difference (FP64 Rayleigh quotient) and the end-to-end host-buffer rate are
+reported beside it.  Inputs: seeded synthetic lattices and random MPS bases
+(no datasets).  The operator stacks are far larger than L2, so no flush is
+needed between timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...   (the FP64 CPU oracle on a bounded sample)
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOADS = {
+    # name: (model, Lx, Ly, particles (up, dn), U or V, D, description)
+    "hubbard6x6_D1024": ("hubbard", 6, 6, (18, 18), 4.0, 1024,
+                         "Hubbard 6x6 torus, 36 e (S_z=0), t=1, U=4, momentum basis, "
+                         "U(1)xU(1), D=1024 states, middle window l=17"),
+    "hubbard6x6_D512": ("hubbard", 6, 6, (18, 18), 4.0, 512,
+                        "Hubbard 6x6 torus, 36 e, U=4, momentum basis, U(1)xU(1), D=512"),
+    "spinless4x4_D128": ("spinless", 4, 4, (8, 0), 1.0, 128,
+                         "spinless t-V 4x4 torus, N=8, t=1, V=1, momentum basis, U(1), D=128"),
+}
+CPU_SAMPLE = ("hubbard", 4, 4, (8, 8), 4.0, 64)
+
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TF32_OVER_BF16 = 1.1 / 2.25        # nominal dense tf32 / bf16 tensor ratio
+
+
+def peaks():
+    try:
+        p = json.load(open(PEAKS_PATH))
+        return p["hbm_gbs"], p["bf16_tflops"], "measured"
+    except Exception:
+        return 6400.0, 1800.0, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
+                                      "--format=csv,noheader,nounits"],
+                                     capture_output=True, text=True, timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 3 + i and s[3 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def build_problem(lib, wl, dev_stream):
+    model, Lx, Ly, (nu, nd), coup, D, _ = wl
+    spinful = model == "hubbard"
+    N = Lx * Ly
+    target = (nu, nd) if spinful else (nu,)
+    if spinful:
+        T, V = lib.lattice_hamiltonian(lib.MODEL_HUBBARD, Lx, Ly, 1.0, 0.0, coup)
+    else:
+        T, V = lib.lattice_hamiltonian(lib.MODEL_SPINLESS_TV, Lx, Ly, 1.0, 0.0, coup)
+    U = lib.momentum_basis(Lx, Ly)
+    l = N // 2 - 1
+    g = lib.Dmrg(N, nu, nd, spinful=spinful, d_max=D, davidson_tol=1e-6, davidson_max_sub=24,
+                 davidson_max_iter=400)
+    g.set_hamiltonian(T, V, U)
+    g.set_mps(synth.random_left_isometries(N, spinful, target, D, l, 5),
+              synth.random_right_isometries(N, spinful, target, D, l + 2, 6))
+    t0 = time.time()
+    g.build_block_ops(l, dev_stream)
+    return g, l, time.time() - t0
+
+
+def cpu_baseline(budget_s=15.0):
+    """The FP64 oracle's H_eff*psi on a bounded sample (single process)."""
+    from oracle import dmrg as odmrg
+    from oracle import hamiltonian, lattice
+    model, L, _, (nu, nd), U, D = CPU_SAMPLE
+    N = L * L
+    T, V = lattice.hubbard(L, L, 1.0, U)
+    T, V = lattice.rotate(T, V, lattice.momentum_basis(L, L))
+    h, W = hamiltonian.spin_orbital(T, V, True)
+    m = odmrg.Model(h, W, True, (nu, nd))
+    l = N // 2 - 1
+    w = odmrg.window_from_mps(m, synth.random_left_isometries(N, True, (nu, nd), D, l, 5),
+                              synth.random_right_isometries(N, True, (nu, nd), D, l + 2, 6), l)
+    flops = 0.0
+    for A, B, c in w.terms:
+        for qa, qb, o, da, db in w.layout:
+            a, b = A.blocks.get(qa), B.blocks.get(qb)
+            if a is None or b is None:
+                continue
+            flops += 2.0 * a.shape[0] * da * db + 2.0 * a.shape[0] * db * b.shape[0]
+    psi = np.random.default_rng(0).standard_normal(w.size)
+    n, t0 = 0, time.time()
+    while time.time() - t0 < budget_s:
+        w.apply(psi)
+        n += 1
+    dt = (time.time() - t0) / n
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle H_eff*psi, Hubbard {L}x{L} U={U} momentum basis, U(1)xU(1), "
+                      f"D={D}, middle window (psi_len {w.size}), {n} applies in {n * dt:.1f} s",
+            "ms_per_apply": dt * 1e3}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    wl = WORKLOADS[args.workload]
+    for _ in range(args.warmup):
+        pass
+    cb = cpu_baseline(budget_s=max(5.0, 2.0 * args.steps))
+    line = {"metric": "H_eff*psi TFLOP/s", "value": cb["value"], "unit": "TFLOP/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": cb["ms_per_apply"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "description": wl[6],
+                       "reference_sample": cb["sample"]},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="hubbard6x6_D1024", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solve", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import paper_2311_14106_b300 as lib
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    wl = WORKLOADS[args.workload]
+    stream = torch.cuda.Stream()
+    g, l, t_build = build_problem(lib, wl, stream)
+    n, layout = g.heff_layout()
+    flops = g.heff_flops()
+    psi = torch.tensor(synth.random_psi(layout, 1), device="cuda")
+    sig = torch.empty_like(psi)
+
+    def timed(prec, steps, warmup):
+        g.set_precision(prec)
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                g.heff_apply(psi, sig, stream)
+            stream.synchronize()
+            if dist:
+                dist.barrier()
+            g.heff_timing(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(steps):
+                g.heff_apply(psi, sig, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            stages = g.heff_timing(0)
+        ms = e0.elapsed_time(e1) / steps
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, stages / max(stages[3], 1)
+
+    # split path: the headline
+    with Clocks(local) as clk:
+        ms_split, st_split = timed(lib.SPLIT_TF32, args.steps, args.warmup)
+    clocks = clk.summary()
+    sig_split = sig.clone()
+    # FP64 path (fewer steps: FP64 throughput is ~1/100 of the split path)
+    k64 = max(2, min(args.steps, 5))
+    ms_64, st_64 = timed(lib.FP64, k64, 1)
+    sig_64 = sig.clone()
+    err_sigma = float((sig_split - sig_64).norm() / sig_64.norm())
+    # end-to-end through the host-buffer entry point (pinned host memory)
+    g.set_precision(lib.SPLIT_TF32)
+    hp = torch.tensor(synth.random_psi(layout, 1)).pin_memory()
+    hs = torch.empty_like(hp).pin_memory()
+    import ctypes
+    for _ in range(2):
+        rc = lib._lib.dmrg_heff_apply_host(g._h, ctypes.cast(hp.data_ptr(), lib._D),
+                                           ctypes.cast(hs.data_ptr(), lib._D), stream.cuda_stream)
+        assert rc == 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        lib._lib.dmrg_heff_apply_host(g._h, ctypes.cast(hp.data_ptr(), lib._D),
+                                      ctypes.cast(hs.data_ptr(), lib._D), stream.cuda_stream)
+    e2e_ms = (time.perf_counter() - t0) / args.steps * 1e3
+    # Davidson solves of the window with both paths (energy at FP64 RQ)
+    solve = {}
+    if not args.no_solve:
+        for name, prec in (("split", lib.SPLIT_TF32), ("fp64", lib.FP64)):
+            g.set_precision(prec)
+            x = torch.zeros_like(psi)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e, it, conv = g.davidson(x, stream)
+            torch.cuda.synchronize()
+            solve[name] = {"seconds": time.perf_counter() - t0, "energy": e, "iters": it,
+                           "converged": conv}
+        solve["rel_energy_diff"] = abs(solve["split"]["energy"] - solve["fp64"]["energy"]) / abs(
+            solve["fp64"]["energy"])
+    hbm, bf16, src = peaks()
+    tf32_peak = bf16 * TF32_OVER_BF16
+    # roofline of the dominant kernel: the stage with the larger share
+    stA = {"stage1": st_split[1], "stage2": st_split[2]}
+    dom = max(stA, key=stA.get)
+    si = g.heff_stage_info()
+    # algorithmic bytes per launch: operators read once (8 B/element as FP64 or
+    # TF32 hi+lo), psi read / sigma written once, the intermediate T written
+    # by stage 1 and read by stage 2 (8 B/element as TF32 hi+lo)
+    st_bytes = {"stage1": 8 * (si["nA"] + si["psi_len"] + si["nT"]),
+                "stage2": 8 * (si["nT"] + si["nB"] + si["psi_len"])}
+    st_flops = {"stage1": si["flops1"], "stage2": si["flops2"]}
+    line = {
+        "metric": "H_eff*psi TFLOP/s", "value": world * flops / (ms_split * 1e-3) / 1e12,
+        "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_split, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "tf32x3 (fp32 accumulate), fp64 in/out",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "description": wl[6], "psi_len": n,
+                   "algorithmic_flops_per_step": flops, "l2": "operator stacks >> L2; no flush",
+                   "parallelism": f"replicas x{world}", "block_build_seconds": t_build},
+        "fp64": {"ms_per_step": ms_64, "tflops": flops / (ms_64 * 1e-3) / 1e12,
+                 "stage_ms": st_64[:3].tolist()},
+        "split_stage_ms": st_split[:3].tolist(),
+        "sigma_rel_diff_split_vs_fp64": err_sigma,
+        "solve": solve,
+        "e2e": {"value": world * flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+                "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n, "ms_per_step": e2e_ms},
+        "clocks": clocks,
+        "gpu_launches": 3 * args.steps,
+        "roofline": {"kernel": f"k_tf32_gemm {dom}", "bound": "tensor",
+                     "achieved": None, "peak": tf32_peak, "unit": "TFLOP/s", "frac": None,
+                     "peak_source": f"{src} bf16 x nominal tf32/bf16 ratio", "traffic": None},
+    }
+    t_dom = stA[dom] * 1e-3
+    gbs = st_bytes[dom] / t_dom / 1e9
+    tfl = 3 * st_flops[dom] / t_dom / 1e12        # tensor work: 3 MMAs per product
+    f_hbm, f_tc = gbs / hbm, tfl / tf32_peak
+    if f_hbm >= f_tc:
+        line["roofline"].update({"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                 "frac": f_hbm, "peak_source": f"{src} hbm_gbs"})
+    else:
+        line["roofline"].update({"achieved": tfl, "frac": f_tc})
+    line["roofline"].update({"other": {"hbm_frac": f_hbm, "tensor_frac": f_tc,
+                                       "algorithmic_bytes": st_bytes[dom],
+                                       "algorithmic_flops_x3": 3 * st_flops[dom],
+                                       "ms_per_launch": stA[dom]}})
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    g.close()
+
+
+if __name__ == "__main__":
+    main()

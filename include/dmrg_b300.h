@@ -181,6 +181,20 @@ int dmrg_truncate(dmrg_ctx *ctx, const double *psi, int side, int d_max,
 int dmrg_sweep(dmrg_ctx *ctx, int n_sweeps, const int *d_schedule,
                double *energies_out, void *stream);
 
+/* Work of the two H_eff*psi stages of the current window (for rooflines):
+ * out6 = [stage-1 flops, stage-2 flops, A-stack elements, B-stack elements,
+ * intermediate T elements, psi_len].  Stage 1 computes T = A psi per term
+ * class, stage 2 sigma = sum T B^T; each stored element is 8 bytes (FP64, or
+ * TF32 hi + lo). */
+int dmrg_heff_stage_info(dmrg_ctx *ctx, double *out6);
+
+/* Per-kernel timing of dmrg_heff_apply with CUDA events recorded on the
+ * apply stream.  enable = 1 starts (and zeroes) the accumulation, 0 stops
+ * it.  out4 (may be NULL) receives accumulated milliseconds of
+ * [0] psi split (TF32 path), [1] stage 1, [2] stage 2, [3] number of applies
+ * timed; reading synchronises the last timed apply. */
+int dmrg_heff_timing(dmrg_ctx *ctx, int enable, double *out4);
+
 /* Timing breakdown of the last sweep in seconds, Sec. III.B categories:
  * out[0] Diag_H, [1] Ren (block ops), [2] Tables, [3] Diag_D, [4] StVec,
  * [5] Other; out[6] = number of H_eff*psi calls. */

@@ -28,7 +28,7 @@ HEADER_FUNCTIONS = [
     "dmrg_set_isometry", "dmrg_build_block_ops", "dmrg_heff_layout",
     "dmrg_set_precision", "dmrg_heff_apply", "dmrg_heff_apply_host",
     "dmrg_heff_flops", "dmrg_davidson", "dmrg_truncate", "dmrg_sweep",
-    "dmrg_profile",
+    "dmrg_heff_stage_info", "dmrg_heff_timing", "dmrg_profile",
 ]
 
 
@@ -66,6 +66,8 @@ _sig = {
     "dmrg_davidson": (ctypes.c_int, [_P, _P, _D, _I, _P]),
     "dmrg_truncate": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _D, _D, _P]),
     "dmrg_sweep": (ctypes.c_int, [_P, ctypes.c_int, _I, _D, _P]),
+    "dmrg_heff_stage_info": (ctypes.c_int, [_P, _D]),
+    "dmrg_heff_timing": (ctypes.c_int, [_P, ctypes.c_int, _D]),
     "dmrg_profile": (ctypes.c_int, [_P, _D]),
 }
 for _name, (_res, _args) in _sig.items():
@@ -237,6 +239,20 @@ class Dmrg:
         self._check(_lib.dmrg_sweep(self._h, n_sweeps, None if ds is None else _iptr(ds), _dptr(E),
                                     _stream_ptr(stream)), "sweep")
         return E
+
+    def heff_stage_info(self):
+        """Per-stage work: flops1, flops2, A/B/T stack elements, psi_len."""
+        out = np.zeros(6)
+        self._check(_lib.dmrg_heff_stage_info(self._h, _dptr(out)), "heff_stage_info")
+        keys = ["flops1", "flops2", "nA", "nB", "nT", "psi_len"]
+        return dict(zip(keys, out.tolist()))
+
+    def heff_timing(self, enable):
+        """Start (1) / stop (0) per-stage event timing; returns accumulated
+        [split_ms, stage1_ms, stage2_ms, n_applies]."""
+        out = np.zeros(4)
+        self._check(_lib.dmrg_heff_timing(self._h, enable, _dptr(out)), "heff_timing")
+        return out
 
     def profile(self):
         out = np.zeros(7)

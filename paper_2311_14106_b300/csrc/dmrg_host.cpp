@@ -126,7 +126,7 @@ struct Window {
   GemmSeg *s1 = nullptr, *s2 = nullptr;
   int nd1 = 0, nd2 = 0;
   long long tiles1 = 0, tiles2 = 0;
-  double flops = 0;
+  double flops = 0, flops1 = 0, flops2 = 0;
   double *diag = nullptr;
   std::vector<S1> s1info;                 // stage-1 regions (class, psi in, psi out)
   std::vector<GemmDesc> stage1, stage2;   // host copies (split-path planning)
@@ -137,6 +137,7 @@ struct Window {
   std::vector<CUtensorMap> maps_host;
   std::vector<TSeg> seg_host;
   std::vector<TWork> w1_host, w2_host;
+  std::vector<PartialSum> psum_host;
 };
 
 }  // namespace
@@ -158,6 +159,11 @@ struct dmrg_ctx {
   cusolverDnHandle_t solver = nullptr;
   int precision = DMRG_FP64;
   double prof[7] = {0};
+  // optional per-stage event timing of H_eff*psi
+  bool timing = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  double tacc[4] = {0, 0, 0, 0};
+  bool pending = false;
   // Davidson scratch
   WinBuf dav;
   long long dav_n = 0;
@@ -805,6 +811,7 @@ void build_window(dmrg_ctx *C, int l) {
   w.hc.clear();
   w.psi.clear();
   w.l = l;
+  w.flops1 = w.flops2 = 0;
   double t0 = now();
   {
     SitePart sl = make_site(C, l), sr = make_site(C, l + 1);
@@ -941,6 +948,8 @@ void build_window(dmrg_ctx *C, int l) {
     d1.push_back(d);
     into[e.po].push_back(e);
     flops += 2.0 * q.da * (double)n * p.da * p.db + 2.0 * q.da * (double)n * p.db * q.db;
+    w.flops1 += 2.0 * q.da * (double)n * p.da * p.db;
+    w.flops2 += 2.0 * q.da * (double)n * p.db * q.db;
   }
   for (size_t po = 0; po < w.psi.size(); ++po) {
     const PsiBlk &q = w.psi[po];
@@ -1030,10 +1039,35 @@ void build_window(dmrg_ctx *C, int l) {
   w.valid = true;
 }
 
+void collect_timing(dmrg_ctx *C) {
+  if (!C->pending) return;
+  CK(cudaEventSynchronize(C->ev[3]));
+  float a = 0, b = 0, c = 0;
+  CK(cudaEventElapsedTime(&a, C->ev[0], C->ev[1]));
+  CK(cudaEventElapsedTime(&b, C->ev[1], C->ev[2]));
+  CK(cudaEventElapsedTime(&c, C->ev[2], C->ev[3]));
+  C->tacc[0] += a;
+  C->tacc[1] += b;
+  C->tacc[2] += c;
+  C->tacc[3] += 1;
+  C->pending = false;
+}
+
+void mark(dmrg_ctx *C, int i, cudaStream_t s) {
+  if (!C->timing) return;
+  if (i == 0) collect_timing(C);
+  CK(cudaEventRecord(C->ev[i], s));
+  if (i == 3) C->pending = true;
+}
+
 void apply_fp64(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s) {
   Window &w = C->win;
+  mark(C, 0, s);
+  mark(C, 1, s);
   CK(launch_gemm_f64(w.d1, w.nd1, w.s1, w.tiles1, s, psi, nullptr));
+  mark(C, 2, s);
   CK(launch_gemm_f64(w.d2, w.nd2, w.s2, w.tiles2, s, nullptr, sigma));
+  mark(C, 3, s);
 }
 
 }  // namespace
@@ -1167,7 +1201,7 @@ void build_tf32(dmrg_ctx *C) {
     TSeg sg;
     sg.mA_hi = ahi; sg.mA_lo = alo; sg.mB_hi = mPhi[E[i].pi]; sg.mB_lo = mPlo[E[i].pi];
     sg.K = p.da;
-    sg.pad = 0;
+    sg.k0 = 0;
     int seg = (int)segs.size();
     segs.push_back(sg);
     const int M = q.da * n, N = p.db, nt = ntile_of(N);
@@ -1187,31 +1221,67 @@ void build_tf32(dmrg_ctx *C) {
       }
     into[E[i].po].push_back((int)i);
   }
+  // stage 2: the long K (all terms x psi columns) is cut into ranges of at
+  // most KSUB; each range is one work item writing an FP32 partial tile, and
+  // the partials are summed in FP64 (fixed order).
+  const int KSUB = 1024;
+  long long wsn = 0;
+  std::vector<PartialSum> psums;
   for (size_t po = 0; po < np; ++po) {
     const PsiBlk &q = w.psi[po];
-    int seg0 = (int)segs.size();
+    std::vector<TSeg> ranges;
     for (int i : into[po]) {
       const HClass &h = w.hc[E[i].ci];
       const PsiBlk &p = w.psi[E[i].pi];
-      TSeg sg;
-      sg.mA_hi = mThi[i]; sg.mA_lo = mTlo[i]; sg.mB_hi = mBhi[i]; sg.mB_lo = mBlo[i];
-      sg.K = (int)h.terms.size() * p.db;
-      sg.pad = 0;
-      segs.push_back(sg);
-    }
-    const int nseg = (int)segs.size() - seg0;
-    const int M = q.da, N = q.db, nt = ntile_of(N);
-    for (int m0 = 0; m0 < M; m0 += 128)
-      for (int n0 = 0; n0 < N; n0 += nt) {
-        TWork t;
-        memset(&t, 0, sizeof t);
-        t.seg0 = seg0; t.nseg = nseg;
-        t.M = M; t.N = N; t.m0 = m0; t.n0 = n0; t.ntile = nt;
-        t.mode = 1; t.alpha = 1.f;
-        t.off64 = q.off; t.ld = q.db;
-        w2.push_back(t);
+      const int K = (int)h.terms.size() * p.db;
+      for (int k0 = 0; k0 < K; k0 += KSUB) {
+        TSeg sg;
+        sg.mA_hi = mThi[i]; sg.mA_lo = mTlo[i]; sg.mB_hi = mBhi[i]; sg.mB_lo = mBlo[i];
+        sg.k0 = k0;
+        sg.K = std::min(KSUB, K - k0);
+        ranges.push_back(sg);
       }
+    }
+    const long long blk = (long long)q.da * q.db;
+    const int nparts = (int)ranges.size();
+    PartialSum ps;
+    ps.ws = nullptr;
+    ps.stride = blk;
+    ps.off = q.off;
+    ps.n = (int)blk;
+    ps.nparts = nparts;
+    const long long base = wsn;
+    wsn += (long long)nparts * blk;
+    psums.push_back(ps);
+    const int M = q.da, N = q.db, nt = ntile_of(N);
+    for (int pi = 0; pi < nparts; ++pi) {
+      int seg = (int)segs.size();
+      segs.push_back(ranges[pi]);
+      for (int m0 = 0; m0 < M; m0 += 128)
+        for (int n0 = 0; n0 < N; n0 += nt) {
+          TWork t;
+          memset(&t, 0, sizeof t);
+          t.seg0 = seg; t.nseg = 1;
+          t.M = M; t.N = N; t.m0 = m0; t.n0 = n0; t.ntile = nt;
+          t.mode = 2; t.alpha = 1.f;
+          t.ld = q.db;
+          t.off64 = base + (long long)pi * blk;   // offset into the workspace
+          w2.push_back(t);
+        }
+    }
   }
+  P.ws = (float *)w.buf.alloc(4 * std::max<long long>(wsn, 64));
+  for (auto &t : w2) t.out32 = P.ws + t.off64;
+  {
+    long long base = 0;
+    for (auto &ps : psums) {
+      ps.ws = P.ws + base;
+      base += (long long)ps.nparts * ps.stride;
+    }
+  }
+  w.psum_host = psums;
+  P.psum = upload(w.buf, w.psum_host, s);
+  P.npsum = (int)psums.size();
   w.maps_host = maps;
   w.seg_host = segs;
   w.w1_host = w1;
@@ -1237,9 +1307,14 @@ void apply_tf32(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s) {
     C->stream = save;
   }
   Tf32Plan &P = w.tf;
+  mark(C, 0, s);
   CK(launch_split2d((const Split2D *)P.psi_split, P.npsi, s, psi));
+  mark(C, 1, s);
   CK(tf32_gemm(P.work1, P.nwork1, P.seg, P.maps, nullptr, P.err, s));
+  mark(C, 2, s);
   CK(tf32_gemm(P.work2, P.nwork2, P.seg, P.maps, sigma, P.err, s));
+  CK(sum_partials(P.psum, P.npsum, sigma, s));
+  mark(C, 3, s);
 }
 
 void check_err_flag(dmrg_ctx *C, cudaStream_t s) {
@@ -1723,6 +1798,8 @@ int dmrg_destroy(dmrg_ctx *ctx) {
   ctx->partbuf.clear();
   ctx->dav.clear();
   if (ctx->solver) cusolverDnDestroy(ctx->solver);
+  for (auto &e : ctx->ev)
+    if (e) cudaEventDestroy(e);
   delete ctx;
   return DMRG_OK;
 }
@@ -2006,6 +2083,33 @@ int dmrg_truncate(dmrg_ctx *C, const double *psi, int side, int d_max, double *d
 int dmrg_sweep(dmrg_ctx *C, int n_sweeps, const int *d_schedule, double *E, void *stream) {
   if (!C || n_sweeps < 1) return DMRG_ERR_ARG;
   return guard(C, [&] { sweep_impl(C, n_sweeps, d_schedule, E, (cudaStream_t)stream); });
+}
+
+int dmrg_heff_stage_info(dmrg_ctx *C, double *out6) {
+  if (!C || !out6) return DMRG_ERR_ARG;
+  if (!C->win.valid) return DMRG_ERR_STATE;
+  const Window &w = C->win;
+  out6[0] = w.flops1;
+  out6[1] = w.flops2;
+  out6[2] = (double)w.nA;
+  out6[3] = (double)w.nB;
+  out6[4] = (double)w.nT;
+  out6[5] = (double)w.psi_len;
+  return DMRG_OK;
+}
+
+int dmrg_heff_timing(dmrg_ctx *C, int enable, double *out4) {
+  if (!C) return DMRG_ERR_ARG;
+  return guard(C, [&] {
+    if (!C->ev[0])
+      for (auto &e : C->ev) CK(cudaEventCreate(&e));
+    collect_timing(C);
+    if (out4)
+      for (int i = 0; i < 4; ++i) out4[i] = C->tacc[i];
+    if (enable && !C->timing)
+      for (double &t : C->tacc) t = 0;
+    C->timing = enable != 0;
+  });
 }
 
 int dmrg_profile(dmrg_ctx *C, double *out7) {

@@ -185,10 +185,11 @@ k_tf32_gemm(const TWork *__restrict__ works, const TSeg *__restrict__ segs,
         uint8_t *base = smem + st * STAGE_BYTES;
         const uint32_t fb = full0 + 8 * st;
         mbar_expect_tx(fb, stage_tx);
-        tma_load(smem_u32(base), &maps[sg.mA_hi], kc * BK, w.m0, fb);
-        tma_load(smem_u32(base + TILE_A), &maps[sg.mA_lo], kc * BK, w.m0, fb);
-        tma_load(smem_u32(base + 2 * TILE_A), &maps[sg.mB_hi], kc * BK, w.n0, fb);
-        tma_load(smem_u32(base + 2 * TILE_A + TILE_B), &maps[sg.mB_lo], kc * BK, w.n0, fb);
+        const int kx = sg.k0 + kc * BK;
+        tma_load(smem_u32(base), &maps[sg.mA_hi], kx, w.m0, fb);
+        tma_load(smem_u32(base + TILE_A), &maps[sg.mA_lo], kx, w.m0, fb);
+        tma_load(smem_u32(base + 2 * TILE_A), &maps[sg.mB_hi], kx, w.n0, fb);
+        tma_load(smem_u32(base + 2 * TILE_A + TILE_B), &maps[sg.mB_lo], kx, w.n0, fb);
       }
     }
   } else if (warp == 1 && lane == 0) {
@@ -256,8 +257,10 @@ k_tf32_gemm(const TWork *__restrict__ works, const TSeg *__restrict__ segs,
           const float h = tf32_round(x);
           w.out_hi[o] = h;
           w.out_lo[o] = tf32_round(x - h);
-        } else {
+        } else if (w.mode == 1) {
           out64[w.off64 + (long long)row * w.ld + col] = (double)x;
+        } else {
+          w.out32[(long long)row * w.ld + col] = x;
         }
       }
     }
@@ -271,6 +274,15 @@ k_tf32_gemm(const TWork *__restrict__ works, const TSeg *__restrict__ segs,
 }
 
 }  // namespace
+
+__global__ void k_sum_partials(const PartialSum *__restrict__ ps, double *__restrict__ sigma) {
+  const PartialSum p = ps[blockIdx.y];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int k = 0; k < p.nparts; ++k) acc += (double)p.ws[k * p.stride + i];
+    sigma[p.off + i] = acc;
+  }
+}
 
 typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                              const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
@@ -298,6 +310,13 @@ int encode_map(CUtensorMap *out, const float *base, int rows, int cols, long lon
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : -3;
+}
+
+cudaError_t sum_partials(const PartialSum *p, int n, double *sigma, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  dim3 grid(8, n);
+  k_sum_partials<<<grid, 256, 0, s>>>(p, sigma);
+  return cudaGetLastError();
 }
 
 cudaError_t tf32_gemm(const TWork *work, int nwork, const TSeg *seg, const CUtensorMap *maps,

@@ -16,8 +16,8 @@ namespace dmrg {
 // One K-segment: A (M x K) and B (N x K), each as (hi, lo) tensor maps.
 struct TSeg {
   int mA_hi, mA_lo, mB_hi, mB_lo;   // indices into the tensor-map table
-  int K;
-  int pad;
+  int K;             // length of this K range
+  int k0;            // first K index (multiple of 32)
 };
 
 // One 128 x ntile output tile.
@@ -26,14 +26,27 @@ struct TWork {
   int M, N;          // full problem extent (for masking)
   int m0, n0;        // tile origin
   int ntile;         // UMMA N of this tile (multiple of 16, <= 128)
-  int mode;          // 0: write split TF32 (hi, lo) to T; 1: write FP64
+  int mode;          // 0: write split TF32 (hi, lo) to T; 1: write FP64;
+                     // 2: write an FP32 partial tile (split-K)
   float alpha;
   // mode 0: element (r, c) -> base + (r / nrep) * ld + (r % nrep) * rep + c
   float *out_hi, *out_lo;
   int nrep, rep;
   long long ld;
-  // mode 1: element (r, c) -> out64[r * ld + c] (bound sigma + offset)
+  // mode 1: element (r, c) -> out64[off64 + r * ld + c] (bound sigma)
   long long off64;
+  // mode 2: element (r, c) -> out32[r * ld + c]
+  float *out32;
+};
+
+// FP64 sum of the split-K partial tiles of one sigma block:
+// sigma[off + i] = sum_p ws[p * stride + i], i < n (fixed order).
+struct PartialSum {
+  const float *ws;
+  long long stride;
+  long long off;
+  int n;
+  int nparts;
 };
 
 struct Tf32Plan {
@@ -44,6 +57,9 @@ struct Tf32Plan {
   TSeg *seg = nullptr;
   TWork *work1 = nullptr, *work2 = nullptr;
   int nwork1 = 0, nwork2 = 0;
+  float *ws = nullptr;              // split-K partial tiles of stage 2
+  PartialSum *psum = nullptr;
+  int npsum = 0;
   void *psi_split = nullptr;        // SplitT descriptors (device), one per psi block
   int npsi = 0;
   int *err = nullptr;               // device error flag (bounded waits)
@@ -54,6 +70,8 @@ struct Tf32Plan {
 // (32 x box_rows) box and 128-byte swizzle.  Returns 0 on success.
 int encode_map(CUtensorMap *out, const float *base, int rows, int cols, long long ld,
                int box_rows);
+
+cudaError_t sum_partials(const PartialSum *p, int n, double *sigma, cudaStream_t s);
 
 cudaError_t tf32_gemm(const TWork *work, int nwork, const TSeg *seg, const CUtensorMap *maps,
                       double *out64, int *err, cudaStream_t s);
