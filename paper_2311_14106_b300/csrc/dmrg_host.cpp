@@ -110,6 +110,16 @@ struct PsiBlk {
   int da, db;
 };
 
+// Host tables of the split path (psi split descriptors, tensor maps, K
+// ranges, tile lists, partial sums) for given scratch pointers.
+struct Tf32Tables {
+  std::vector<Split2D> psi_split;
+  std::vector<CUtensorMap> maps;
+  std::vector<TSeg> segs;
+  std::vector<TWork> w1, w2;
+  std::vector<PartialSum> psums;
+};
+
 struct Window {
   bool valid = false;
   int l = -1;
@@ -133,11 +143,9 @@ struct Window {
   std::vector<GemmSeg> seg1, seg2;
   Tf32Plan tf;           // split-precision plan (heff_tf32)
   bool tf_ready = false;
-  std::vector<Split2D> psi_split_host;
-  std::vector<CUtensorMap> maps_host;
-  std::vector<TSeg> seg_host;
-  std::vector<TWork> w1_host, w2_host;
-  std::vector<PartialSum> psum_host;
+  bool tf_copies = false;            // TF32 copies of the operator stacks exist
+  std::vector<long long> offA, offB, ldA, ldB;
+  long long gen = 0;                 // build counter of this window
 };
 
 }  // namespace
@@ -155,6 +163,7 @@ struct dmrg_ctx {
   std::map<int, std::unique_ptr<BlockPart>> R;      // R[n], sites n..N-1
   std::map<BlockPart *, std::unique_ptr<WinBuf>> partbuf;
   Window win;
+  Tf32Tables tables;     // host copy of the split-path tables of the window
   cudaStream_t stream = nullptr;
   cusolverDnHandle_t solver = nullptr;
   int precision = DMRG_FP64;
@@ -806,6 +815,9 @@ void build_window(dmrg_ctx *C, int l) {
   w.ldbuf.clear();
   w.rdbuf.clear();
   w.tf_ready = false;
+  w.tf_copies = false;
+  static long long build_counter = 0;
+  w.gen = ++build_counter;
   w.Ld = BlockPart();
   w.Rd = BlockPart();
   w.hc.clear();
@@ -1082,40 +1094,76 @@ long long r4(long long x) { return (x + 3) & ~3LL; }
 long long a64(long long x) { return (x + 63) & ~63LL; }
 int ntile_of(int n) { return n > 128 ? 128 : ((n + 15) / 16) * 16; }
 
-void build_tf32(dmrg_ctx *C) {
-  Window &w = C->win;
-  cudaStream_t s = C->stream;
-  Tf32Plan &P = w.tf;
+// Sizes (floats) of the per-apply scratch of the split path: psi split
+// (P hi/lo), stage-1 intermediate (T hi/lo) and stage-2 partial tiles (ws).
+struct Tf32Scratch {
+  long long nP = 0, nT = 0, nws = 0;
+  std::vector<long long> offP, offT, ldP, ldT;
+};
+
+const int KSUB = 1024;   // longest K range of one stage-2 work item
+
+Tf32Scratch tf32_scratch_sizes(const Window &w) {
+  Tf32Scratch z;
   const auto &E = w.s1info;
   const size_t ne = E.size(), np = w.psi.size();
-  std::vector<long long> offA(ne), offT(ne), offB(ne), offP(np);
-  std::vector<long long> ldA(ne), ldT(ne), ldB(ne), ldP(np);
-  long long nA = 0, nT = 0, nB = 0, nP = 0;
+  z.offT.resize(ne);
+  z.ldT.resize(ne);
+  z.offP.resize(np);
+  z.ldP.resize(np);
   for (size_t i = 0; i < ne; ++i) {
     const HClass &h = w.hc[E[i].ci];
     const PsiBlk &p = w.psi[E[i].pi], &q = w.psi[E[i].po];
     const long long n = (long long)h.terms.size();
-    ldA[i] = r4(p.da);
-    offA[i] = nA;
-    nA += a64(q.da * n * ldA[i]);
-    ldT[i] = r4(n * p.db);
-    offT[i] = nT;
-    nT += a64(q.da * ldT[i]);
-    ldB[i] = r4(n * p.db);
-    offB[i] = nB;
-    nB += a64(q.db * ldB[i]);
+    z.ldT[i] = r4(n * p.db);
+    z.offT[i] = z.nT;
+    z.nT += a64(q.da * z.ldT[i]);
   }
   for (size_t i = 0; i < np; ++i) {
-    ldP[i] = r4(w.psi[i].da);
-    offP[i] = nP;
-    nP += a64(w.psi[i].db * ldP[i]);
+    z.ldP[i] = r4(w.psi[i].da);
+    z.offP[i] = z.nP;
+    z.nP += a64(w.psi[i].db * z.ldP[i]);
+  }
+  std::vector<long long> Ksum(np, 0);
+  for (size_t po = 0; po < np; ++po) {
+    long long parts = 0;
+    for (size_t i = 0; i < ne; ++i)
+      if (E[i].po == (int)po) {
+        const long long K = (long long)w.hc[E[i].ci].terms.size() * w.psi[E[i].pi].db;
+        parts += (K + KSUB - 1) / KSUB;
+      }
+    z.nws += parts * w.psi[po].da * w.psi[po].db;
+  }
+  return z;
+}
+
+// TF32 (hi, lo) copies of the operator stacks: built once per window and
+// owned by the context (they are inputs of every split-path apply).
+void tf32_operator_copies(dmrg_ctx *C) {
+  Window &w = C->win;
+  cudaStream_t s = C->stream;
+  Tf32Plan &P = w.tf;
+  const auto &E = w.s1info;
+  const size_t ne = E.size();
+  w.offA.assign(ne, 0);
+  w.offB.assign(ne, 0);
+  w.ldA.assign(ne, 0);
+  w.ldB.assign(ne, 0);
+  long long nA = 0, nB = 0;
+  for (size_t i = 0; i < ne; ++i) {
+    const HClass &h = w.hc[E[i].ci];
+    const PsiBlk &p = w.psi[E[i].pi], &q = w.psi[E[i].po];
+    const long long n = (long long)h.terms.size();
+    w.ldA[i] = r4(p.da);
+    w.offA[i] = nA;
+    nA += a64(q.da * n * w.ldA[i]);
+    w.ldB[i] = r4(n * p.db);
+    w.offB[i] = nB;
+    nB += a64(q.db * w.ldB[i]);
   }
   auto fl = [&](long long n) { return (float *)w.buf.alloc(4 * std::max<long long>(n, 64)); };
   P.A_hi = fl(nA); P.A_lo = fl(nA);
-  P.T_hi = fl(nT); P.T_lo = fl(nT);
   P.B_hi = fl(nB); P.B_lo = fl(nB);
-  P.P_hi = fl(nP); P.P_lo = fl(nP);
-  // split the operator stacks once per window
   std::vector<Split2D> sp;
   for (size_t i = 0; i < ne; ++i) {
     const HClass &h = w.hc[E[i].ci];
@@ -1127,9 +1175,9 @@ void build_tf32(dmrg_ctx *C) {
     a.src_ld = p.da;
     a.rows = q.da * n;
     a.cols = p.da;
-    a.hi = P.A_hi + offA[i];
-    a.lo = P.A_lo + offA[i];
-    a.dst_ld = ldA[i];
+    a.hi = P.A_hi + w.offA[i];
+    a.lo = P.A_lo + w.offA[i];
+    a.dst_ld = w.ldA[i];
     sp.push_back(a);
     Split2D b;
     memset(&b, 0, sizeof b);
@@ -1137,19 +1185,24 @@ void build_tf32(dmrg_ctx *C) {
     b.src_ld = (long long)n * p.db;
     b.rows = q.db;
     b.cols = n * p.db;
-    b.hi = P.B_hi + offB[i];
-    b.lo = P.B_lo + offB[i];
-    b.dst_ld = ldB[i];
+    b.hi = P.B_hi + w.offB[i];
+    b.lo = P.B_lo + w.offB[i];
+    b.dst_ld = w.ldB[i];
     sp.push_back(b);
   }
-  {
-    WinBuf tmp;
-    Split2D *d = upload(tmp, sp, s);
-    CK(launch_split2d(d, (int)sp.size(), s));
-    CK(cudaStreamSynchronize(s));
-  }
-  // psi split descriptors (transposed: psi_a^T is the K-major B of stage 1)
-  std::vector<Split2D> ps;
+  WinBuf tmp;
+  Split2D *d = upload(tmp, sp, s);
+  CK(launch_split2d(d, (int)sp.size(), s));
+  CK(cudaStreamSynchronize(s));
+  w.tf_copies = true;
+}
+
+void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo, float *T_hi,
+                 float *T_lo, float *ws, Tf32Tables &out) {
+  const Tf32Plan &P = w.tf;
+  const auto &E = w.s1info;
+  const size_t ne = E.size(), np = w.psi.size();
+  out = Tf32Tables();
   for (size_t i = 0; i < np; ++i) {
     Split2D d;
     memset(&d, 0, sizeof d);
@@ -1159,16 +1212,12 @@ void build_tf32(dmrg_ctx *C) {
     d.rows = w.psi[i].da;
     d.cols = w.psi[i].db;
     d.trans = 1;
-    d.hi = P.P_hi + offP[i];
-    d.lo = P.P_lo + offP[i];
-    d.dst_ld = ldP[i];
-    ps.push_back(d);
+    d.hi = P_hi + z.offP[i];
+    d.lo = P_lo + z.offP[i];
+    d.dst_ld = z.ldP[i];
+    out.psi_split.push_back(d);
   }
-  w.psi_split_host = ps;
-  P.psi_split = upload(w.buf, w.psi_split_host, s);
-  P.npsi = (int)np;
-  // tensor maps
-  std::vector<CUtensorMap> maps;
+  auto &maps = out.maps;
   auto mk = [&](const float *base, long long rows, long long cols, long long ld, int box) {
     CUtensorMap m;
     int rc = encode_map(&m, base, (int)rows, (int)cols, ld, box);
@@ -1180,24 +1229,25 @@ void build_tf32(dmrg_ctx *C) {
   for (size_t i = 0; i < np; ++i) {
     const PsiBlk &p = w.psi[i];
     int box = ntile_of(p.db);
-    mPhi[i] = mk(P.P_hi + offP[i], p.db, p.da, ldP[i], box);
-    mPlo[i] = mk(P.P_lo + offP[i], p.db, p.da, ldP[i], box);
+    mPhi[i] = mk(P_hi + z.offP[i], p.db, p.da, z.ldP[i], box);
+    mPlo[i] = mk(P_lo + z.offP[i], p.db, p.da, z.ldP[i], box);
   }
-  std::vector<TSeg> segs;
-  std::vector<TWork> w1, w2;
+  auto &segs = out.segs;
+  auto &w1 = out.w1;
+  auto &w2 = out.w2;
   std::vector<std::vector<int>> into(np);
   std::vector<int> mThi(ne), mTlo(ne), mBhi(ne), mBlo(ne);
   for (size_t i = 0; i < ne; ++i) {
     const HClass &h = w.hc[E[i].ci];
     const PsiBlk &p = w.psi[E[i].pi], &q = w.psi[E[i].po];
     const int n = (int)h.terms.size();
-    int ahi = mk(P.A_hi + offA[i], (long long)q.da * n, p.da, ldA[i], 128);
-    int alo = mk(P.A_lo + offA[i], (long long)q.da * n, p.da, ldA[i], 128);
-    mThi[i] = mk(P.T_hi + offT[i], q.da, (long long)n * p.db, ldT[i], 128);
-    mTlo[i] = mk(P.T_lo + offT[i], q.da, (long long)n * p.db, ldT[i], 128);
+    int ahi = mk(P.A_hi + w.offA[i], (long long)q.da * n, p.da, w.ldA[i], 128);
+    int alo = mk(P.A_lo + w.offA[i], (long long)q.da * n, p.da, w.ldA[i], 128);
+    mThi[i] = mk(T_hi + z.offT[i], q.da, (long long)n * p.db, z.ldT[i], 128);
+    mTlo[i] = mk(T_lo + z.offT[i], q.da, (long long)n * p.db, z.ldT[i], 128);
     int bbox = ntile_of(q.db);
-    mBhi[i] = mk(P.B_hi + offB[i], q.db, (long long)n * p.db, ldB[i], bbox);
-    mBlo[i] = mk(P.B_lo + offB[i], q.db, (long long)n * p.db, ldB[i], bbox);
+    mBhi[i] = mk(P.B_hi + w.offB[i], q.db, (long long)n * p.db, w.ldB[i], bbox);
+    mBlo[i] = mk(P.B_lo + w.offB[i], q.db, (long long)n * p.db, w.ldB[i], bbox);
     TSeg sg;
     sg.mA_hi = ahi; sg.mA_lo = alo; sg.mB_hi = mPhi[E[i].pi]; sg.mB_lo = mPlo[E[i].pi];
     sg.K = p.da;
@@ -1214,9 +1264,9 @@ void build_tf32(dmrg_ctx *C) {
         t.seg0 = seg; t.nseg = 1;
         t.M = M; t.N = N; t.m0 = m0; t.n0 = n0; t.ntile = nt;
         t.mode = 0; t.alpha = alpha;
-        t.out_hi = P.T_hi + offT[i];
-        t.out_lo = P.T_lo + offT[i];
-        t.nrep = n; t.rep = p.db; t.ld = ldT[i];
+        t.out_hi = T_hi + z.offT[i];
+        t.out_lo = T_lo + z.offT[i];
+        t.nrep = n; t.rep = p.db; t.ld = z.ldT[i];
         w1.push_back(t);
       }
     into[E[i].po].push_back((int)i);
@@ -1224,9 +1274,7 @@ void build_tf32(dmrg_ctx *C) {
   // stage 2: the long K (all terms x psi columns) is cut into ranges of at
   // most KSUB; each range is one work item writing an FP32 partial tile, and
   // the partials are summed in FP64 (fixed order).
-  const int KSUB = 1024;
   long long wsn = 0;
-  std::vector<PartialSum> psums;
   for (size_t po = 0; po < np; ++po) {
     const PsiBlk &q = w.psi[po];
     std::vector<TSeg> ranges;
@@ -1245,14 +1293,12 @@ void build_tf32(dmrg_ctx *C) {
     const long long blk = (long long)q.da * q.db;
     const int nparts = (int)ranges.size();
     PartialSum ps;
-    ps.ws = nullptr;
+    ps.ws = ws + wsn;
     ps.stride = blk;
     ps.off = q.off;
     ps.n = (int)blk;
     ps.nparts = nparts;
-    const long long base = wsn;
-    wsn += (long long)nparts * blk;
-    psums.push_back(ps);
+    out.psums.push_back(ps);
     const int M = q.da, N = q.db, nt = ntile_of(N);
     for (int pi = 0; pi < nparts; ++pi) {
       int seg = (int)segs.size();
@@ -1265,33 +1311,37 @@ void build_tf32(dmrg_ctx *C) {
           t.M = M; t.N = N; t.m0 = m0; t.n0 = n0; t.ntile = nt;
           t.mode = 2; t.alpha = 1.f;
           t.ld = q.db;
-          t.off64 = base + (long long)pi * blk;   // offset into the workspace
+          t.out32 = ws + wsn + (long long)pi * blk;
           w2.push_back(t);
         }
     }
+    wsn += (long long)nparts * blk;
   }
-  P.ws = (float *)w.buf.alloc(4 * std::max<long long>(wsn, 64));
-  for (auto &t : w2) t.out32 = P.ws + t.off64;
-  {
-    long long base = 0;
-    for (auto &ps : psums) {
-      ps.ws = P.ws + base;
-      base += (long long)ps.nparts * ps.stride;
-    }
-  }
-  w.psum_host = psums;
-  P.psum = upload(w.buf, w.psum_host, s);
-  P.npsum = (int)psums.size();
-  w.maps_host = maps;
-  w.seg_host = segs;
-  w.w1_host = w1;
-  w.w2_host = w2;
-  P.maps = upload(w.buf, w.maps_host, s);
-  P.seg = upload(w.buf, w.seg_host, s);
-  P.work1 = upload(w.buf, w.w1_host, s);
-  P.work2 = upload(w.buf, w.w2_host, s);
-  P.nwork1 = (int)w1.size();
-  P.nwork2 = (int)w2.size();
+  if (wsn > z.nws) fail(DMRG_ERR_STATE, "internal: partial-tile workspace size");
+}
+
+void build_tf32(dmrg_ctx *C) {
+  Window &w = C->win;
+  cudaStream_t s = C->stream;
+  Tf32Plan &P = w.tf;
+  if (!w.tf_copies) tf32_operator_copies(C);
+  Tf32Scratch z = tf32_scratch_sizes(w);
+  auto fl = [&](long long n) { return (float *)w.buf.alloc(4 * std::max<long long>(n, 64)); };
+  P.P_hi = fl(z.nP); P.P_lo = fl(z.nP);
+  P.T_hi = fl(z.nT); P.T_lo = fl(z.nT);
+  P.ws = fl(z.nws);
+  Tf32Tables &tb = C->tables;
+  tf32_tables(w, z, P.P_hi, P.P_lo, P.T_hi, P.T_lo, P.ws, tb);
+  P.psi_split = upload(w.buf, tb.psi_split, s);
+  P.npsi = (int)tb.psi_split.size();
+  P.maps = upload(w.buf, tb.maps, s);
+  P.seg = upload(w.buf, tb.segs, s);
+  P.work1 = upload(w.buf, tb.w1, s);
+  P.work2 = upload(w.buf, tb.w2, s);
+  P.nwork1 = (int)tb.w1.size();
+  P.nwork2 = (int)tb.w2.size();
+  P.psum = upload(w.buf, tb.psums, s);
+  P.npsum = (int)tb.psums.size();
   P.err = (int *)w.buf.alloc(sizeof(int));
   CK(cudaMemsetAsync(P.err, 0, sizeof(int), s));
   CK(cudaStreamSynchronize(s));
