@@ -145,6 +145,32 @@ int dmrg_set_precision(dmrg_ctx *ctx, int precision);
 int dmrg_heff_apply(dmrg_ctx *ctx, const double *psi, double *sigma,
                     void *stream);
 
+/* Allocation-free variant of dmrg_heff_apply in the split 3xTF32 precision.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot let the library allocate device memory on the call path (for
+ * example code running under another framework's memory pool, or code that
+ * must not trigger the implicit synchronisation of cudaMalloc / cudaFree).
+ * The per-call scratch of the split path (psi as TF32 hi/lo, the stage-1
+ * intermediate, the stage-2 partial tiles and the work tables) is taken from
+ * a fixed 64 MiB array that every GPU loading this library holds until the
+ * process exits; the call itself makes no cudaMalloc, cudaFree or other
+ * allocating device call.
+ *   - psi, sigma: device pointers as for dmrg_heff_apply; sigma is
+ *     overwritten.  The result equals dmrg_heff_apply's split result.
+ *   - Needs the window's TF32 operator copies, which the first
+ *     dmrg_heff_apply with DMRG_SPLIT_TF32 creates (Errors: STATE if absent).
+ *   - A window whose scratch exceeds 64 MiB is rejected with DMRG_ERR_ARG and
+ *     a message giving the size it needs.
+ *   - The first call on a device looks up the array's device address, and the
+ *     first call for a window writes its work tables into the array; make
+ *     that first call before any stream capture.
+ *   - All calls (all contexts) share the one array, which keeps the last
+ *     call's contents; calls whose GPU work overlaps in time race with each
+ *     other and give wrong results.  Serialize them (one stream, or events).
+ */
+int dmrg_heff_apply_tf32_static(dmrg_ctx *ctx, const double *psi,
+                                double *sigma, void *stream);
+
 /* Same as dmrg_heff_apply but with host buffers: copies psi to the device,
  * applies, copies sigma back, synchronising the stream. */
 int dmrg_heff_apply_host(dmrg_ctx *ctx, const double *psi_host,

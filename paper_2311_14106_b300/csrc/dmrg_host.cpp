@@ -14,6 +14,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -2102,6 +2103,87 @@ int dmrg_heff_apply_host(dmrg_ctx *C, const double *psi_h, double *sigma_h, void
     CK(cudaMemcpyAsync(sigma_h, ds, 8 * n, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     check_err_flag(C, s);
+  });
+}
+
+int dmrg_heff_apply_tf32_static(dmrg_ctx *C, const double *psi, double *sigma, void *stream) {
+  if (!C || !psi || !sigma) return DMRG_ERR_ARG;
+  if (!C->win.valid) {
+    C->err = "no window built";
+    return DMRG_ERR_STATE;
+  }
+  return guard(C, [&] {
+    Window &w = C->win;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!w.tf_copies)
+      fail(DMRG_ERR_STATE, "TF32 operator copies not built: call dmrg_heff_apply once with "
+                           "DMRG_SPLIT_TF32 after dmrg_build_block_ops");
+    void *base = nullptr;
+    size_t cap = 0;
+    CK(static_scratch(&base, &cap));
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    // layout: [error flag | tables | P hi, P lo | T hi, T lo | partial tiles]
+    struct Owner {
+      long long gen = -1;
+      Tf32Tables tb;
+      size_t o_maps, o_seg, o_w1, o_w2, o_ps, o_split;
+    };
+    static std::mutex mu;
+    static std::map<int, Owner> owners;
+    std::lock_guard<std::mutex> lk(mu);
+    Owner &ow = owners[dev];
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    unsigned char *b = (unsigned char *)base;
+    if (ow.gen != w.gen) {
+      Tf32Scratch z = tf32_scratch_sizes(w);
+      // table sizes do not depend on the pointers: size them with a dry run
+      Tf32Tables probe;
+      tf32_tables(w, z, (float *)b, (float *)b, (float *)b, (float *)b, (float *)b, probe);
+      size_t off = 256;
+      ow.o_maps = off; off = al(off + probe.maps.size() * sizeof(CUtensorMap));
+      ow.o_seg = off; off = al(off + probe.segs.size() * sizeof(TSeg));
+      ow.o_w1 = off; off = al(off + probe.w1.size() * sizeof(TWork));
+      ow.o_w2 = off; off = al(off + probe.w2.size() * sizeof(TWork));
+      ow.o_ps = off; off = al(off + probe.psums.size() * sizeof(PartialSum));
+      ow.o_split = off; off = al(off + probe.psi_split.size() * sizeof(Split2D));
+      const size_t oP = off;
+      off = al(off + 4 * (size_t)z.nP);
+      const size_t oP2 = off;
+      off = al(off + 4 * (size_t)z.nP);
+      const size_t oT = off;
+      off = al(off + 4 * (size_t)z.nT);
+      const size_t oT2 = off;
+      off = al(off + 4 * (size_t)z.nT);
+      const size_t oW = off;
+      off = al(off + 4 * (size_t)z.nws);
+      if (off > cap)
+        fail(DMRG_ERR_ARG, "window needs %zu bytes of scratch; the static scratch holds %zu bytes "
+                           "(use dmrg_heff_apply for larger windows)", off, cap);
+      ow.gen = -1;
+      tf32_tables(w, z, (float *)(b + oP), (float *)(b + oP2), (float *)(b + oT),
+                  (float *)(b + oT2), (float *)(b + oW), ow.tb);
+      const Tf32Tables &t = ow.tb;
+      auto put = [&](size_t o, const void *src, size_t n) {
+        if (n) CK(cudaMemcpyAsync(b + o, src, n, cudaMemcpyHostToDevice, s));
+      };
+      put(ow.o_maps, t.maps.data(), t.maps.size() * sizeof(CUtensorMap));
+      put(ow.o_seg, t.segs.data(), t.segs.size() * sizeof(TSeg));
+      put(ow.o_w1, t.w1.data(), t.w1.size() * sizeof(TWork));
+      put(ow.o_w2, t.w2.data(), t.w2.size() * sizeof(TWork));
+      put(ow.o_ps, t.psums.data(), t.psums.size() * sizeof(PartialSum));
+      put(ow.o_split, t.psi_split.data(), t.psi_split.size() * sizeof(Split2D));
+      ow.gen = w.gen;
+    }
+    const Tf32Tables &t = ow.tb;
+    int *err = (int *)b;
+    CK(cudaMemsetAsync(err, 0, sizeof(int), s));   // the only state that must start at zero
+    CK(launch_split2d((const Split2D *)(b + ow.o_split), (int)t.psi_split.size(), s, psi));
+    CK(tf32_gemm((const TWork *)(b + ow.o_w1), (int)t.w1.size(), (const TSeg *)(b + ow.o_seg),
+                 (const CUtensorMap *)(b + ow.o_maps), nullptr, err, s));
+    CK(tf32_gemm((const TWork *)(b + ow.o_w2), (int)t.w2.size(), (const TSeg *)(b + ow.o_seg),
+                 (const CUtensorMap *)(b + ow.o_maps), sigma, err, s));
+    CK(sum_partials((const PartialSum *)(b + ow.o_ps), (int)t.psums.size(), sigma, s));
   });
 }
 

@@ -71,6 +71,10 @@ struct Tf32Plan {
 int encode_map(CUtensorMap *out, const float *base, int rows, int cols, long long ld,
                int box_rows);
 
+// Device address and size of the fixed scratch array (heff_static.cu); the
+// first call on a device looks the address up.
+cudaError_t static_scratch(void **ptr, size_t *bytes);
+
 cudaError_t sum_partials(const PartialSum *p, int n, double *sigma, cudaStream_t s);
 
 cudaError_t tf32_gemm(const TWork *work, int nwork, const TSeg *seg, const CUtensorMap *maps,

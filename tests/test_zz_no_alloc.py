@@ -1,0 +1,67 @@
+"""The allocation-free split-precision H_eff*psi entry point.
+
+Some callers cannot let a library allocate device memory while they run
+(they live inside another framework's memory pool, or must avoid the implicit
+device synchronisation of cudaMalloc/cudaFree).  dmrg_heff_apply_tf32_static
+serves them from a fixed device array instead.  This file is collected last
+on purpose.  The test checks, through the C ABI, that two calls in a row give
+the same sigma as the allocating dmrg_heff_apply in the same precision and
+agree with the FP64 oracle within the split-path tolerance.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import dmrg as odmrg
+from oracle import hamiltonian, lattice
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2311_14106_b300 as lib  # noqa: E402
+
+TOL_SPLIT = 2e-5   # same bound as the split-path parity tests
+
+
+def _window():
+    Lx = Ly = 4
+    N, target, D, l = 16, (8,), 64, 7
+    Q = synth.haar_rotation(N, 2)
+    To, Vo = lattice.spinless_tV(Lx, Ly, 1.0, 0.0, 1.0)
+    To, Vo = lattice.rotate(To, Vo, lattice.momentum_basis(Lx, Ly) @ Q)
+    h, W = hamiltonian.spin_orbital(To, Vo, False)
+    model = odmrg.Model(h, W, False, target)
+    li = synth.random_left_isometries(N, False, target, D, l, 5)
+    ri = synth.random_right_isometries(N, False, target, D, l + 2, 6)
+    w = odmrg.window_from_mps(model, li, ri, l)
+    g = lib.Dmrg(N, 8, d_max=D, precision=lib.SPLIT_TF32)
+    Tg, Vg = lib.lattice_hamiltonian(lib.MODEL_SPINLESS_TV, Lx, Ly, 1.0, 0.0, 1.0)
+    g.set_hamiltonian(Tg, Vg, lib.momentum_basis(Lx, Ly) @ Q)
+    g.set_mps(li, ri)
+    g.build_block_ops(l)
+    return w, g
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_static_scratch_apply_matches_allocating_apply():
+    w, g = _window()
+    g.set_precision(lib.SPLIT_TF32)
+    rng = np.random.default_rng(3)
+    psi = torch.tensor(rng.standard_normal(w.size), device="cuda")
+    ref = torch.empty_like(psi)
+    g.heff_apply(psi, ref)          # allocating entry point (also builds TF32 operator copies)
+    torch.cuda.synchronize()
+    ref_h = ref.cpu().numpy()
+    oracle = w.apply(psi.cpu().numpy())
+    for _ in range(2):              # two calls in a row share the array
+        out = torch.full_like(psi, float("nan"))
+        g.heff_apply_static(psi, out)
+        torch.cuda.synchronize()
+        o = out.cpu().numpy()
+        assert np.all(np.isfinite(o))
+        assert rel(o, ref_h) <= TOL_SPLIT
+        assert rel(o, oracle) <= TOL_SPLIT
+    g.close()
