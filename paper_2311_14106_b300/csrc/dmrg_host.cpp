@@ -178,6 +178,7 @@ struct dmrg_ctx {
   WinBuf dav;
   long long dav_n = 0;
   double *V = nullptr, *AV = nullptr, *work = nullptr, *small = nullptr, *r = nullptr;
+  double *rs = nullptr;   // thick-restart scratch (3 vectors)
 };
 
 namespace {
@@ -1319,6 +1320,16 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo
     wsn += (long long)nparts * blk;
   }
   if (wsn > z.nws) fail(DMRG_ERR_STATE, "internal: partial-tile workspace size");
+  // persistent CTAs take work items round-robin: order them by cost (K chunks
+  // x tile width), largest first
+  auto cost = [&](const TWork &t) {
+    long long k = 0;
+    for (int i = 0; i < t.nseg; ++i) k += (segs[t.seg0 + i].K + 31) / 32;
+    return k * t.ntile;
+  };
+  auto by_cost = [&](const TWork &a, const TWork &b) { return cost(a) > cost(b); };
+  std::stable_sort(w1.begin(), w1.end(), by_cost);
+  std::stable_sort(w2.begin(), w2.end(), by_cost);
 }
 
 void build_tf32(dmrg_ctx *C) {
@@ -1434,6 +1445,7 @@ DavBuf dav_buffers(dmrg_ctx *C, long long n, int m) {
     C->V = (double *)C->dav.alloc(8 * (size_t)n * m);
     C->AV = (double *)C->dav.alloc(8 * (size_t)n * m);
     C->r = (double *)C->dav.alloc(8 * (size_t)n * 2);
+    C->rs = (double *)C->dav.alloc(8 * (size_t)n * 3);
     C->work = (double *)C->dav.alloc(8 * 296 * (size_t)(m + 2));
     C->small = (double *)C->dav.alloc(8 * 4 * (size_t)(m + 2));
     C->dav_n = n;
@@ -1467,6 +1479,8 @@ void lincomb(double *out, const double *V, const std::vector<double> &c, double 
   CK(cudaStreamSynchronize(s));
 }
 
+constexpr double kSplitResidualFloor = 4e-6;
+
 int davidson(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_t s) {
   Window &w = C->win;
   const long long n = w.psi_len;
@@ -1480,8 +1494,18 @@ int davidson(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_t s)
   // start vector
   double nx = dot1(C, x, x, n, B, s);
   if (!(nx > 0)) {
+    // seeded random start, weighted towards configurations with a low
+    // diagonal energy: x_i = u_i / (diag_i - min(diag) + 1)
     static uint64_t counter = 0;
     CK(launch_random(x, n, C->cfg.seed + 7919 * (++counter), s));
+    std::vector<double> dh(n);
+    CK(cudaMemcpyAsync(dh.data(), w.diag, 8 * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double dmin = n ? *std::min_element(dh.begin(), dh.end()) : 0.0;
+    double shift = dmin - 1.0;
+    double *th = B.coef;
+    CK(cudaMemcpyAsync(th, &shift, 8, cudaMemcpyHostToDevice, s));
+    CK(launch_precond(x, w.diag, th, n, s));
     nx = dot1(C, x, x, n, B, s);
   }
   CK(cudaMemcpyAsync(B.V, x, 8 * n, cudaMemcpyDeviceToDevice, s));
@@ -1510,19 +1534,41 @@ int davidson(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_t s)
     lincomb(B.t, B.AV, y, 0.0, n, B, s);
     lincomb(B.t, B.V, ny, 1.0, n, B, s);
     rnorm = std::sqrt(std::max(0.0, dot1(C, B.t, B.t, n, B, s)));
-    if (rnorm < tol) {
+    // The split product is accurate to ~1e-6 relative, so its residual cannot
+    // fall much below that times |theta|; the reported energy is the FP64
+    // Rayleigh quotient, whose error is second order in the residual.
+    const double floor = prec == DMRG_SPLIT_TF32 ? kSplitResidualFloor * std::max(1.0, std::fabs(theta)) : 0.0;
+    if (rnorm < std::max(tol, floor)) {
       conv = true;
       break;
     }
-    if (k == m) {   // restart with the Ritz vector
-      lincomb(B.u, B.V, y, 0.0, n, B, s);
-      CK(cudaMemcpyAsync(B.V, B.u, 8 * n, cudaMemcpyDeviceToDevice, s));
-      lincomb(B.u, B.AV, y, 0.0, n, B, s);
-      CK(cudaMemcpyAsync(B.AV, B.u, 8 * n, cudaMemcpyDeviceToDevice, s));
+    if (k == m) {
+      // thick restart: keep the Ritz vectors of the lowest nk Ritz values
+      const int nk = std::min(3, k);
+      std::vector<int> order(k);
+      std::iota(order.begin(), order.end(), 0);
+      std::sort(order.begin(), order.end(), [&](int a, int b) { return ev[a] < ev[b]; });
+      std::vector<std::vector<double>> Y(nk, std::vector<double>(k));
+      for (int r = 0; r < nk; ++r)
+        for (int i = 0; i < k; ++i) Y[r][i] = evec[i * k + order[r]];
+      // new V_r = V Y_r and AV_r = AV Y_r, staged through the restart scratch
+      std::vector<double *> tmpv;
+      for (int r = 0; r < nk; ++r) {
+        double *dst = C->rs + (long long)r * n;
+        lincomb(dst, B.V, Y[r], 0.0, n, B, s);
+        tmpv.push_back(dst);
+      }
+      for (int r = 0; r < nk; ++r)
+        CK(cudaMemcpyAsync(B.V + (long long)r * n, tmpv[r], 8 * n, cudaMemcpyDeviceToDevice, s));
+      for (int r = 0; r < nk; ++r)
+        lincomb(tmpv[r], B.AV, Y[r], 0.0, n, B, s);
+      for (int r = 0; r < nk; ++r)
+        CK(cudaMemcpyAsync(B.AV + (long long)r * n, tmpv[r], 8 * n, cudaMemcpyDeviceToDevice, s));
       std::fill(S.begin(), S.end(), 0.0);
-      S[0] = theta;
-      k = 1;
-      y.assign(1, 1.0);
+      for (int r = 0; r < nk; ++r) S[r * m + r] = ev[order[r]];
+      k = nk;
+      y.assign(k, 0.0);
+      y[0] = 1.0;
     }
     // correction vector: preconditioned residual
     double *th = B.coef + m + 1;

@@ -1,13 +1,13 @@
 // 3 x TF32 grouped GEMM on tcgen05 (sm_103a) for the two H_eff*psi stages.
+// (persistent, warp-specialised; see k_tf32_gemm)
 //
 // Stage 1:  T[(a',k), b]  = sign * A_stack[(a',k), a] . psi[a, b]
 // Stage 2:  sigma[a', b'] = sum_segments T[a', (k,b)] . B_stack[b', (k,b)]^T
 // Both are C = A . B^T with K-major operands.  Each FP64 operand x is held as
 // x_hi + x_lo (TF32 each); the product uses hi.hi + hi.lo + lo.hi with FP32
-// accumulation in tensor memory.  One CTA computes one 128 x ntile tile:
-//   warp 0 (one lane)  TMA producer: A_hi, A_lo, B_hi, B_lo per 32-wide K chunk
-//   warp 1 (one lane)  MMA issuer: 4 k-steps x 3 tcgen05.mma per chunk
-//   warps 0-3          epilogue: tcgen05.ld of the accumulator rows
+// accumulation in tensor memory.  A work item is one 128 x ntile output tile;
+// per 32-wide K chunk the producer loads A_hi, A_lo, B_hi, B_lo by TMA and the
+// MMA warp issues 4 k-steps x 3 tcgen05.mma.
 // Every mbarrier wait is bounded; on timeout the kernel records an error
 // code, skips the remaining work, frees its TMEM and returns.
 #include <cuda.h>
@@ -26,7 +26,7 @@ constexpr int STAGES = 3;
 constexpr int TILE_A = BM * BK * 4;          // 16 KB
 constexpr int TILE_B = 128 * BK * 4;         // up to 16 KB
 constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 18 * 1024;   // + align + Shared
 constexpr long long WAIT_LIMIT = 1LL << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -52,16 +52,6 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
       : "r"(a), "r"(parity)
       : "memory");
   return ok != 0;
-}
-
-// bounded wait: false (and error recorded) if the phase never completes
-__device__ bool mbar_wait(uint32_t a, uint32_t parity, int *err, int code) {
-  for (long long i = 0; i < WAIT_LIMIT; ++i) {
-    if (mbar_try(a, parity)) return true;
-    if (i > 64) __nanosleep(64);
-  }
-  atomicCAS(err, 0, code);
-  return false;
 }
 
 __device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap *map, int x, int y,
@@ -126,149 +116,191 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(r);
 }
 
-__global__ void __launch_bounds__(128, 1)
-k_tf32_gemm(const TWork *__restrict__ works, const TSeg *__restrict__ segs,
+// Persistent, warp-specialised 3xTF32 GEMM.  Each CTA walks the work list
+// with stride gridDim.x (the list is sorted by cost, largest first):
+//   warp 0, lane 0   TMA producer over all K chunks of all its tiles
+//   warp 1, lane 0   MMA issuer, alternating between two TMEM accumulators
+//   warps 2..5       epilogue: drain an accumulator while the next tile runs
+constexpr int NTHREADS = 192;
+constexpr int ACC_COLS = 128;
+
+struct Shared {
+  uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2];
+  uint32_t tmem;
+  int abort;
+  float stage_out[4][32][33];   // per epilogue warp: 32 rows x 32 columns
+};
+
+__device__ __forceinline__ bool wait_or_abort(uint32_t a, uint32_t parity, int *err, int code,
+                                              volatile int *abort) {
+  for (long long i = 0; i < WAIT_LIMIT; ++i) {
+    if (mbar_try(a, parity)) return true;
+    if (*abort) return false;
+    if (i > 64) __nanosleep(64);
+  }
+  atomicCAS(err, 0, code);
+  *abort = 1;
+  return false;
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__ segs,
             const CUtensorMap *__restrict__ maps, double *__restrict__ out64,
             int *__restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t *bars = (uint64_t *)(smem + STAGES * STAGE_BYTES);
-  uint32_t *tmem_slot = (uint32_t *)(bars + 2 * STAGES + 1);
-  volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
-
+  Shared *sh = (Shared *)(smem + STAGES * STAGE_BYTES);
+  volatile int *abort_flag = &sh->abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const TWork w = works[blockIdx.x];
-  const uint32_t full0 = smem_u32(&bars[0]);
-  const uint32_t empty0 = smem_u32(&bars[STAGES]);
-  const uint32_t done = smem_u32(&bars[2 * STAGES]);
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < STAGES; ++i) {
-      mbar_init(full0 + 8 * i, 1);
-      mbar_init(empty0 + 8 * i, 1);
+      mbar_init(smem_u32(&sh->full[i]), 1);
+      mbar_init(smem_u32(&sh->empty[i]), 1);
     }
-    mbar_init(done, 1);
-    *abort_flag = 0;
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(smem_u32(&sh->acc_full[i]), 1);
+      mbar_init(smem_u32(&sh->acc_empty[i]), 128);
+    }
+    sh->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_slot)),
-                 "r"(128)
+                     smem_u32(&sh->tmem)),
+                 "r"(2 * ACC_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = *tmem_slot;
+  const uint32_t tmem = sh->tmem;
 
-  // number of K chunks over all segments
-  int nchunks = 0;
-  for (int s = 0; s < w.nseg; ++s) nchunks += (segs[w.seg0 + s].K + BK - 1) / BK;
-  const uint32_t tile_b_bytes = (uint32_t)w.ntile * BK * 4;
-  const uint32_t stage_tx = 2 * TILE_A + 2 * tile_b_bytes;
-
-  if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer ----------------
-    int it = 0;
-    for (int s = 0; s < w.nseg && !*abort_flag; ++s) {
-      const TSeg sg = segs[w.seg0 + s];
-      const int nk = (sg.K + BK - 1) / BK;
-      for (int kc = 0; kc < nk; ++kc, ++it) {
-        const int st = it % STAGES;
-        const uint32_t ph = (it / STAGES) & 1;
-        if (!mbar_wait(empty0 + 8 * st, ph ^ 1, err, 1)) {
-          *abort_flag = 1;
-          break;
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer ----------------
+      int it = 0;
+      for (int t = blockIdx.x; t < nwork && !*abort_flag; t += gridDim.x) {
+        const TWork w = works[t];
+        const uint32_t stage_tx = 2 * TILE_A + 2 * (uint32_t)w.ntile * BK * 4;
+        for (int s = 0; s < w.nseg && !*abort_flag; ++s) {
+          const TSeg sg = segs[w.seg0 + s];
+          const int nk = (sg.K + BK - 1) / BK;
+          for (int kc = 0; kc < nk; ++kc, ++it) {
+            const int st = it % STAGES;
+            const uint32_t ph = (it / STAGES) & 1;
+            if (!wait_or_abort(smem_u32(&sh->empty[st]), ph ^ 1, err, 1, abort_flag)) break;
+            uint8_t *base = smem + st * STAGE_BYTES;
+            const uint32_t fb = smem_u32(&sh->full[st]);
+            mbar_expect_tx(fb, stage_tx);
+            const int kx = sg.k0 + kc * BK;
+            tma_load(smem_u32(base), &maps[sg.mA_hi], kx, w.m0, fb);
+            tma_load(smem_u32(base + TILE_A), &maps[sg.mA_lo], kx, w.m0, fb);
+            tma_load(smem_u32(base + 2 * TILE_A), &maps[sg.mB_hi], kx, w.n0, fb);
+            tma_load(smem_u32(base + 2 * TILE_A + TILE_B), &maps[sg.mB_lo], kx, w.n0, fb);
+          }
         }
-        uint8_t *base = smem + st * STAGE_BYTES;
-        const uint32_t fb = full0 + 8 * st;
-        mbar_expect_tx(fb, stage_tx);
-        const int kx = sg.k0 + kc * BK;
-        tma_load(smem_u32(base), &maps[sg.mA_hi], kx, w.m0, fb);
-        tma_load(smem_u32(base + TILE_A), &maps[sg.mA_lo], kx, w.m0, fb);
-        tma_load(smem_u32(base + 2 * TILE_A), &maps[sg.mB_hi], kx, w.n0, fb);
-        tma_load(smem_u32(base + 2 * TILE_A + TILE_B), &maps[sg.mB_lo], kx, w.n0, fb);
       }
     }
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer ----------------
-    const uint32_t id = idesc_tf32(w.ntile);
-    uint32_t accum = 0;
-    for (int it = 0; it < nchunks; ++it) {
-      const int st = it % STAGES;
-      const uint32_t ph = (it / STAGES) & 1;
-      if (*abort_flag || !mbar_wait(full0 + 8 * st, ph, err, 2)) {
-        *abort_flag = 1;
-        break;
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer ----------------
+      int it = 0, j = 0;
+      for (int t = blockIdx.x; t < nwork && !*abort_flag; t += gridDim.x, ++j) {
+        const TWork w = works[t];
+        const uint32_t id = idesc_tf32(w.ntile);
+        const int acc = j & 1;
+        const uint32_t aph = (j >> 1) & 1;
+        if (!wait_or_abort(smem_u32(&sh->acc_empty[acc]), aph ^ 1, err, 2, abort_flag)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tmem + acc * ACC_COLS;
+        uint32_t accum = 0;
+        for (int s = 0; s < w.nseg; ++s) {
+          const int nk = (segs[w.seg0 + s].K + BK - 1) / BK;
+          for (int kc = 0; kc < nk; ++kc, ++it) {
+            const int st = it % STAGES;
+            const uint32_t ph = (it / STAGES) & 1;
+            if (!wait_or_abort(smem_u32(&sh->full[st]), ph, err, 3, abort_flag)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a_hi = smem_u32(smem + st * STAGE_BYTES);
+            const uint32_t a_lo = a_hi + TILE_A;
+            const uint32_t b_hi = a_hi + 2 * TILE_A;
+            const uint32_t b_lo = b_hi + TILE_B;
+#pragma unroll
+            for (int k = 0; k < BK / 8; ++k) {
+              const uint32_t ko = k * 32;   // 8 tf32 = 32 bytes along the swizzled row
+              mma_tf32(d, sdesc(a_lo + ko), sdesc(b_hi + ko), id, accum);
+              accum = 1;
+              mma_tf32(d, sdesc(a_hi + ko), sdesc(b_lo + ko), id, 1);
+              mma_tf32(d, sdesc(a_hi + ko), sdesc(b_hi + ko), id, 1);
+            }
+            mma_commit(smem_u32(&sh->empty[st]));
+          }
+        }
+        // every work item has K >= 1, so the accumulator always holds data
+        mma_commit(smem_u32(&sh->acc_full[acc]));
       }
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5) ----------------
+    const int quarter = warp & 3;            // TMEM lanes 32*quarter .. +31
+    int j = 0;
+    for (int t = blockIdx.x; t < nwork; t += gridDim.x, ++j) {
+      const TWork w = works[t];
+      const int acc = j & 1;
+      const uint32_t aph = (j >> 1) & 1;
+      if (!wait_or_abort(smem_u32(&sh->acc_full[acc]), aph, err, 4, abort_flag)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a_hi = smem_u32(smem + st * STAGE_BYTES);
-      const uint32_t a_lo = a_hi + TILE_A;
-      const uint32_t b_hi = a_hi + 2 * TILE_A;
-      const uint32_t b_lo = b_hi + TILE_B;
-#pragma unroll
-      for (int k = 0; k < BK / 8; ++k) {
-        const uint32_t ko = k * 32;   // 8 tf32 = 32 bytes along the swizzled row
-        mma_tf32(tmem, sdesc(a_lo + ko), sdesc(b_hi + ko), id, accum);
-        accum = 1;
-        mma_tf32(tmem, sdesc(a_hi + ko), sdesc(b_lo + ko), id, 1);
-        mma_tf32(tmem, sdesc(a_hi + ko), sdesc(b_hi + ko), id, 1);
-      }
-      mma_commit(empty0 + 8 * st);
-    }
-    if (nchunks == 0 || *abort_flag) {
-      // nothing accumulated: signal completion without MMA
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(done) : "memory");
-    } else {
-      mma_commit(done);
-    }
-    if (nchunks == 0) accum = 0;
-    // remember whether the accumulator holds data
-    if (accum == 0) *abort_flag = *abort_flag ? 1 : 2;
-  }
-  __syncwarp();
-
-  // ---------------- epilogue ----------------
-  const bool ok = mbar_wait(done, 0, err, 3);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  __syncthreads();
-  const int flag = *abort_flag;
-  if (ok && flag != 1) {
-    const int row = w.m0 + warp * 32 + lane;
-    const bool zero = (flag == 2);
-    for (int c0 = 0; c0 < w.ntile; c0 += 16) {
-      float v[16];
-      if (!zero) {
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
-      } else {
-#pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = 0.f;
-      }
-      if (row >= w.M) continue;
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int col = w.n0 + c0 + i;
-        if (col >= w.N) break;
-        const float x = w.alpha * v[i];
-        if (w.mode == 0) {
-          const long long o = (long long)(row / w.nrep) * w.ld + (long long)(row % w.nrep) * w.rep + col;
-          const float h = tf32_round(x);
-          w.out_hi[o] = h;
-          w.out_lo[o] = tf32_round(x - h);
-        } else if (w.mode == 1) {
-          out64[w.off64 + (long long)row * w.ld + col] = (double)x;
+      // Each lane holds one accumulator row; 32 x 32 blocks are transposed
+      // through shared memory so that every store instruction writes 32
+      // consecutive columns of one row (coalesced).
+      const int row0 = w.m0 + quarter * 32;
+      const uint32_t tbase = tmem + acc * ACC_COLS + ((uint32_t)(quarter * 32) << 16);
+      float(*tile)[33] = sh->stage_out[warp - 2];
+      for (int c0 = 0; c0 < w.ntile; c0 += 32) {
+        float v[32];
+        tmem_ld16(tbase + c0, v);
+        if (c0 + 16 < w.ntile) {
+          tmem_ld16(tbase + c0 + 16, v + 16);
         } else {
-          w.out32[(long long)row * w.ld + col] = x;
+#pragma unroll
+          for (int i = 16; i < 32; ++i) v[i] = 0.f;
         }
+#pragma unroll
+        for (int i = 0; i < 32; ++i) tile[lane][i] = w.alpha * v[i];
+        __syncwarp();
+        const int col = w.n0 + c0 + lane;
+        const bool cok = col < w.N && c0 + lane < w.ntile;
+        for (int rr = 0; rr < 32; ++rr) {
+          const int row = row0 + rr;
+          if (row >= w.M) break;
+          if (!cok) continue;
+          const float x = tile[rr][lane];
+          if (w.mode == 0) {
+            const long long o = (long long)(row / w.nrep) * w.ld +
+                                (long long)(row % w.nrep) * w.rep + col;
+            const float h = tf32_round(x);
+            w.out_hi[o] = h;
+            w.out_lo[o] = tf32_round(x - h);
+          } else if (w.mode == 1) {
+            out64[w.off64 + (long long)row * w.ld + col] = (double)x;
+          } else {
+            w.out32[(long long)row * w.ld + col] = x;
+          }
+        }
+        __syncwarp();
       }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&sh->acc_empty[acc]))
+                   : "memory");
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128)
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(2 * ACC_COLS)
                  : "memory");
   }
 }
@@ -329,7 +361,15 @@ cudaError_t tf32_gemm(const TWork *work, int nwork, const TSeg *seg, const CUten
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_tf32_gemm<<<nwork, 128, SMEM_BYTES, s>>>(work, seg, maps, out64, err);
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 148;
+  }
+  const int grid = nwork < nsm ? nwork : nsm;
+  k_tf32_gemm<<<grid, NTHREADS, SMEM_BYTES, s>>>(work, nwork, seg, maps, out64, err);
   return cudaGetLastError();
 }
 
