@@ -140,6 +140,9 @@ struct Window {
   double flops = 0, flops1 = 0, flops2 = 0;
   double *diag = nullptr;
   std::vector<S1> s1info;                 // stage-1 regions (class, psi in, psi out)
+  double *ws64 = nullptr;                 // FP64 split-K partial blocks of stage 2
+  std::vector<PartialSum64> ps64;
+  PartialSum64 *d_ps64 = nullptr;
   std::vector<GemmDesc> stage1, stage2;   // host copies (split-path planning)
   std::vector<GemmSeg> seg1, seg2;
   Tf32Plan tf;           // split-precision plan (heff_tf32)
@@ -965,34 +968,65 @@ void build_window(dmrg_ctx *C, int l) {
     w.flops1 += 2.0 * q.da * (double)n * p.da * p.db;
     w.flops2 += 2.0 * q.da * (double)n * p.db * q.db;
   }
+  // stage 2 in FP64: split-K over ranges of at most KSUB64 of the long K
+  // (terms x psi columns); each range writes an FP64 partial block, and the
+  // partials are summed in a fixed order (deterministic).
+  const int KSUB64 = 2048;
+  long long wsn = 0;
+  std::vector<PartialSum64> ps64;
+  struct Range {
+    const S1 *e;
+    int k0, K;
+  };
+  std::vector<std::vector<Range>> ranges(w.psi.size());
+  for (size_t po = 0; po < w.psi.size(); ++po) {
+    for (const S1 &e : into[po]) {
+      const int K = (int)w.hc[e.ci].terms.size() * w.psi[e.pi].db;
+      for (int k0 = 0; k0 < K; k0 += KSUB64) ranges[po].push_back({&e, k0, std::min(KSUB64, K - k0)});
+    }
+    const PsiBlk &q = w.psi[po];
+    PartialSum64 p;
+    p.ws = nullptr;
+    p.stride = (long long)q.da * q.db;
+    p.off = q.off;
+    p.n = q.da * q.db;
+    p.nparts = (int)ranges[po].size();
+    ps64.push_back(p);
+    wsn += (long long)p.nparts * p.stride;
+  }
+  w.ws64 = (double *)w.buf.alloc(8 * std::max<long long>(wsn, 1));
+  long long wo = 0;
   for (size_t po = 0; po < w.psi.size(); ++po) {
     const PsiBlk &q = w.psi[po];
-    GemmDesc d;
-    memset(&d, 0, sizeof d);
-    d.C = nullptr;            // sigma, bound at apply time
-    d.c_bs = q.off;
-    d.c_rs = q.db; d.c_cs = 1;
-    d.M = q.da; d.N = q.db; d.batch = 1;
-    d.seg0 = (int)g2.size(); d.nseg = (int)into[po].size();
-    d.tiles_m = (d.M + 63) / 64; d.tiles_n = (d.N + 63) / 64;
-    d.alpha = 1.0; d.beta = 0.0;
-    d.tile0 = t2;
-    t2 += (long long)d.tiles_m * d.tiles_n;
-    for (const S1 &e : into[po]) {
-      HClass &h = w.hc[e.ci];
-      const PsiBlk &p = w.psi[e.pi];
+    ps64[po].ws = w.ws64 + wo;
+    for (size_t r = 0; r < ranges[po].size(); ++r) {
+      const Range &rg = ranges[po][r];
+      const HClass &h = w.hc[rg.e->ci];
+      const PsiBlk &p = w.psi[rg.e->pi];
       const int n = (int)h.terms.size();
       GemmSeg g;
       memset(&g, 0, sizeof g);
-      g.A = w.T + h.t_off[e.pi];
+      g.A = w.T + h.t_off.at(rg.e->pi) + rg.k0;
       g.a_rs = (long long)n * p.db; g.a_cs = 1;
-      g.B = w.Bstack + h.b_off[e.pi];
+      g.B = w.Bstack + h.b_off.at(rg.e->pi) + rg.k0;
       g.b_rs = 1; g.b_cs = (long long)n * p.db;
-      g.K = n * p.db;
+      g.K = rg.K;
+      GemmDesc d;
+      memset(&d, 0, sizeof d);
+      d.C = w.ws64 + wo + (long long)r * q.da * q.db;
+      d.c_rs = q.db; d.c_cs = 1;
+      d.M = q.da; d.N = q.db; d.batch = 1;
+      d.seg0 = (int)g2.size(); d.nseg = 1;
+      d.tiles_m = (d.M + 63) / 64; d.tiles_n = (d.N + 63) / 64;
+      d.alpha = 1.0; d.beta = 0.0;
+      d.tile0 = t2;
+      t2 += (long long)d.tiles_m * d.tiles_n;
       g2.push_back(g);
+      d2.push_back(d);
     }
-    d2.push_back(d);
+    wo += (long long)ps64[po].nparts * ps64[po].stride;
   }
+  w.ps64 = ps64;
   w.flops = flops;
   w.tiles1 = t1;
   w.tiles2 = t2;
@@ -1006,6 +1040,7 @@ void build_window(dmrg_ctx *C, int l) {
   w.s1 = upload(w.buf, w.seg1, s);
   w.d2 = upload(w.buf, w.stage2, s);
   w.s2 = upload(w.buf, w.seg2, s);
+  w.d_ps64 = upload(w.buf, w.ps64, s);
   w.s1info = s1list;
   // diagonal of H_eff for the Davidson preconditioner: shift-0 class terms
   w.diag = (double *)w.buf.alloc(8 * std::max<long long>(w.psi_len, 1));
@@ -1080,7 +1115,8 @@ void apply_fp64(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s) {
   mark(C, 1, s);
   CK(launch_gemm_f64(w.d1, w.nd1, w.s1, w.tiles1, s, psi, nullptr));
   mark(C, 2, s);
-  CK(launch_gemm_f64(w.d2, w.nd2, w.s2, w.tiles2, s, nullptr, sigma));
+  CK(launch_gemm_f64(w.d2, w.nd2, w.s2, w.tiles2, s));
+  CK(launch_sum_partials64(w.d_ps64, (int)w.ps64.size(), sigma, s));
   mark(C, 3, s);
 }
 

@@ -22,11 +22,11 @@ namespace {
 
 constexpr int BM = 128;           // UMMA M
 constexpr int BK = 32;            // floats per 128-byte swizzle row
-constexpr int STAGES = 3;
+constexpr int STAGES = 2;
 constexpr int TILE_A = BM * BK * 4;          // 16 KB
 constexpr int TILE_B = 128 * BK * 4;         // up to 16 KB
 constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 18 * 1024;   // + align + Shared
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256 + 4 * (32 * 128 + 128) * 4;
 constexpr long long WAIT_LIMIT = 1LL << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -128,8 +128,11 @@ struct Shared {
   uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2];
   uint32_t tmem;
   int abort;
-  float stage_out[4][32][33];   // per epilogue warp: 32 rows x 32 columns
 };
+
+// per epilogue warp: 32 rows x up to 128 columns in destination order, one
+// skew word per 32 (element e lives at e + e/32: conflict-free flat reads)
+constexpr int FLAT = 32 * 128 + 128;
 
 __device__ __forceinline__ bool wait_or_abort(uint32_t a, uint32_t parity, int *err, int code,
                                               volatile int *abort) {
@@ -150,6 +153,7 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   Shared *sh = (Shared *)(smem + STAGES * STAGE_BYTES);
+  float *flat_all = (float *)(smem + STAGES * STAGE_BYTES + 256);
   volatile int *abort_flag = &sh->abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -252,45 +256,77 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
       const uint32_t aph = (j >> 1) & 1;
       if (!wait_or_abort(smem_u32(&sh->acc_full[acc]), aph, err, 4, abort_flag)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // Each lane holds one accumulator row; 32 x 32 blocks are transposed
-      // through shared memory so that every store instruction writes 32
-      // consecutive columns of one row (coalesced).
+      // Each lane holds one accumulator row.  The warp's 32 rows go to shared
+      // memory in destination order; when they form one contiguous run of
+      // the output (all columns of the tile, one block row of T) they are
+      // stored as a flat coalesced stream, otherwise row by row.
       const int row0 = w.m0 + quarter * 32;
+      const int nt = min(w.ntile, w.N - w.n0);          // valid columns
+      const int rv = min(32, w.M - row0);               // valid rows
       const uint32_t tbase = tmem + acc * ACC_COLS + ((uint32_t)(quarter * 32) << 16);
-      float(*tile)[33] = sh->stage_out[warp - 2];
-      for (int c0 = 0; c0 < w.ntile; c0 += 32) {
-        float v[32];
+      float *flat = flat_all + (warp - 2) * FLAT;
+      for (int c0 = 0; c0 < w.ntile; c0 += 16) {
+        float v[16];
         tmem_ld16(tbase + c0, v);
-        if (c0 + 16 < w.ntile) {
-          tmem_ld16(tbase + c0 + 16, v + 16);
-        } else {
 #pragma unroll
-          for (int i = 16; i < 32; ++i) v[i] = 0.f;
-        }
-#pragma unroll
-        for (int i = 0; i < 32; ++i) tile[lane][i] = w.alpha * v[i];
-        __syncwarp();
-        const int col = w.n0 + c0 + lane;
-        const bool cok = col < w.N && c0 + lane < w.ntile;
-        for (int rr = 0; rr < 32; ++rr) {
-          const int row = row0 + rr;
-          if (row >= w.M) break;
-          if (!cok) continue;
-          const float x = tile[rr][lane];
-          if (w.mode == 0) {
-            const long long o = (long long)(row / w.nrep) * w.ld +
-                                (long long)(row % w.nrep) * w.rep + col;
-            const float h = tf32_round(x);
-            w.out_hi[o] = h;
-            w.out_lo[o] = tf32_round(x - h);
-          } else if (w.mode == 1) {
-            out64[w.off64 + (long long)row * w.ld + col] = (double)x;
-          } else {
-            w.out32[(long long)row * w.ld + col] = x;
+        for (int i = 0; i < 16; ++i) {
+          const int c = c0 + i;
+          if (c < nt) {
+            const int e = lane * nt + c;
+            flat[e + (e >> 5)] = w.alpha * v[i];
           }
         }
-        __syncwarp();
       }
+      __syncwarp();
+      if (rv > 0) {
+        bool contiguous;
+        long long base;
+        if (w.mode == 0) {
+          const int a0 = row0 / w.nrep, k0 = row0 - a0 * w.nrep;
+          contiguous = (w.n0 == 0 && nt == w.rep && k0 + rv <= w.nrep);
+          base = (long long)a0 * w.ld + (long long)k0 * w.rep;
+        } else if (w.mode == 2) {
+          contiguous = (w.n0 == 0 && nt == w.ld);
+          base = (long long)row0 * w.ld;
+        } else {
+          contiguous = false;
+          base = 0;
+        }
+        if (contiguous) {
+          const int ne = rv * nt;
+          if (w.mode == 0) {
+            for (int e = lane; e < ne; e += 32) {
+              const float x = flat[e + (e >> 5)];
+              const float h = tf32_round(x);
+              w.out_hi[base + e] = h;
+              w.out_lo[base + e] = tf32_round(x - h);
+            }
+          } else {
+            for (int e = lane; e < ne; e += 32) w.out32[base + e] = flat[e + (e >> 5)];
+          }
+        } else {
+          for (int rr = 0; rr < rv; ++rr) {
+            const int row = row0 + rr;
+            for (int c = lane; c < nt; c += 32) {
+              const int e = rr * nt + c;
+              const float x = flat[e + (e >> 5)];
+              const int col = w.n0 + c;
+              if (w.mode == 0) {
+                const long long o = (long long)(row / w.nrep) * w.ld +
+                                    (long long)(row % w.nrep) * w.rep + col;
+                const float h = tf32_round(x);
+                w.out_hi[o] = h;
+                w.out_lo[o] = tf32_round(x - h);
+              } else if (w.mode == 1) {
+                out64[w.off64 + (long long)row * w.ld + col] = (double)x;
+              } else {
+                w.out32[(long long)row * w.ld + col] = x;
+              }
+            }
+          }
+        }
+      }
+      __syncwarp();
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&sh->acc_empty[acc]))
                    : "memory");

@@ -165,6 +165,22 @@ cudaError_t launch_gather(const GSub *d_sub, int nsub, int max_ops,
   return cudaGetLastError();
 }
 
+__global__ void k_sum_partials64(const PartialSum64 *__restrict__ ps, double *__restrict__ out) {
+  const PartialSum64 p = ps[blockIdx.y];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int k = 0; k < p.nparts; ++k) acc += p.ws[k * p.stride + i];
+    out[p.off + i] = acc;
+  }
+}
+
+cudaError_t launch_sum_partials64(const PartialSum64 *p, int n, double *out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  dim3 grid(8, n);
+  k_sum_partials64<<<grid, 256, 0, s>>>(p, out);
+  return cudaGetLastError();
+}
+
 // ----------------------------------------------------------------------------
 // stack copy
 // ----------------------------------------------------------------------------

@@ -96,6 +96,16 @@ cudaError_t launch_gemm_f64(const GemmDesc *d_desc, int ndesc,
 cudaError_t launch_gather(const GSub *d_sub, int nsub, int max_ops,
                           const GTerm *d_terms, const GSrc *d_src, int d,
                           cudaStream_t s);
+// FP64 sum of split-K partial blocks: out[off + i] = sum_p ws[p*stride + i].
+struct PartialSum64 {
+  const double *ws;
+  long long stride;
+  long long off;
+  int n;
+  int nparts;
+};
+cudaError_t launch_sum_partials64(const PartialSum64 *p, int n, double *out, cudaStream_t s);
+
 cudaError_t launch_stack_copy(const SCopy *d_cp, int n, cudaStream_t s);
 cudaError_t launch_split(const double *x, float *hi, float *lo, long long n,
                          cudaStream_t s);
