@@ -163,6 +163,7 @@ struct dmrg_ctx {
   std::vector<double> h, W;
   bool ham = false;
   std::map<int, Iso> liso, riso;
+  std::map<int, Iso> Lmap, Rmap;   // device isometries of the current blocks L_n, R_n
   std::vector<std::unique_ptr<BlockPart>> L;        // L[n], n sites
   std::map<int, std::unique_ptr<BlockPart>> R;      // R[n], sites n..N-1
   std::map<BlockPart *, std::unique_ptr<WinBuf>> partbuf;
@@ -1517,7 +1518,8 @@ void lincomb(double *out, const double *V, const std::vector<double> &c, double 
 
 constexpr double kSplitResidualFloor = 4e-6;
 
-int davidson(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_t s) {
+int davidson(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_t s,
+             bool fp64_rq = true) {
   Window &w = C->win;
   const long long n = w.psi_len;
   const int m = std::max(4, std::min(C->cfg.davidson_max_sub, 64));
@@ -1552,7 +1554,8 @@ int davidson(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_t s)
   dots(C, B.V, 1, n, B.AV, B, col, s);
   S[0] = col[0];
   int k = 1, it = 0;
-  double theta = S[0], rnorm = 1e300;
+  double theta = S[0], rnorm = 1e300, best_r = 1e300;
+  int best_it = 0;
   std::vector<double> y(1, 1.0);
   bool conv = false;
   for (it = 0; it < maxit; ++it) {
@@ -1576,6 +1579,15 @@ int davidson(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_t s)
     const double floor = prec == DMRG_SPLIT_TF32 ? kSplitResidualFloor * std::max(1.0, std::fabs(theta)) : 0.0;
     if (rnorm < std::max(tol, floor)) {
       conv = true;
+      break;
+    }
+    // stagnation near the split product's noise floor: stop if the best
+    // residual has not halved over the last 16 iterations
+    if (rnorm < 0.5 * best_r) {
+      best_r = rnorm;
+      best_it = it;
+    } else if (prec == DMRG_SPLIT_TF32 && it - best_it >= 16 && rnorm < 100.0 * std::max(tol, floor)) {
+      conv = rnorm < 10.0 * std::max(tol, floor);
       break;
     }
     if (k == m) {
@@ -1638,7 +1650,7 @@ int davidson(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_t s)
   double nn = dot1(C, x, x, n, B, s);
   lincomb(x, x, {}, 1.0 / std::sqrt(nn), n, B, s);
   double e = theta;
-  if (prec != DMRG_FP64) {   // FP64 Rayleigh quotient for the reported energy
+  if (prec != DMRG_FP64 && fp64_rq) {   // FP64 Rayleigh quotient for the reported energy
     check_err_flag(C, s);
     apply_fp64(C, x, B.t, s);
     ++nmv;
@@ -1800,14 +1812,202 @@ void truncate(dmrg_ctx *C, const double *psi, int side, int D, double *disc, dou
     if ((int)C->L.size() <= n) C->L.resize(n + 1);
     if (C->L[n]) free_part(C, C->L[n].get());
     C->L[n] = std::move(Bn);
+    C->Lmap[n] = T;
   } else {
     renormalize(C, w.Rd, T, *Bn, bb);
     int n = w.l + 1;
     if (C->R.count(n)) free_part(C, C->R[n].get());
     C->R[n] = std::move(Bn);
+    C->Rmap[n] = T;
   }
   C->stream = save;
   C->prof[1] += now() - t0;
+}
+
+}  // namespace
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// StVec: carry the converged psi of one window over to the next (a8)
+// ---------------------------------------------------------------------------
+struct WinMeta {
+  int l = -1;
+  std::vector<PsiBlk> psi;
+  Basis Lb, Rb;
+  std::vector<std::vector<Piece>> Lp, Rp;
+};
+
+WinMeta meta_of(const Window &w) {
+  WinMeta m;
+  m.l = w.l;
+  m.psi = w.psi;
+  m.Lb = w.Ld.basis;
+  m.Rb = w.Rd.basis;
+  m.Lp = w.Ld.pieces;
+  m.Rp = w.Rd.pieces;
+  return m;
+}
+
+int iso_find(const Iso &T, const QN &q) {
+  for (size_t i = 0; i < T.qn.size(); ++i)
+    if (T.qn[i] == q) return (int)i;
+  return -1;
+}
+
+void push_gemm(std::vector<GemmDesc> &dd, std::vector<GemmSeg> &gg, long long &tt, double *Cp,
+               long long c_rs, int M, int N, int K, const double *A, long long a_rs,
+               long long a_cs, const double *Bp, long long b_rs, long long b_cs) {
+  if (M <= 0 || N <= 0) return;
+  GemmSeg g;
+  memset(&g, 0, sizeof g);
+  g.A = A; g.a_rs = a_rs; g.a_cs = a_cs;
+  g.B = Bp; g.b_rs = b_rs; g.b_cs = b_cs;
+  g.K = K;
+  GemmDesc d;
+  memset(&d, 0, sizeof d);
+  d.C = Cp; d.c_rs = c_rs; d.c_cs = 1;
+  d.M = M; d.N = N; d.batch = 1;
+  d.seg0 = (int)gg.size(); d.nseg = 1;
+  d.tiles_m = (M + 63) / 64; d.tiles_n = (N + 63) / 64;
+  d.alpha = 1.0; d.beta = 0.0;
+  d.tile0 = tt;
+  tt += (long long)d.tiles_m * d.tiles_n;
+  gg.push_back(g);
+  dd.push_back(d);
+}
+
+void run_gemms(std::vector<GemmDesc> &dd, std::vector<GemmSeg> &gg, long long tt, cudaStream_t s) {
+  if (dd.empty()) return;
+  WinBuf tmp;
+  GemmDesc *a = upload(tmp, dd, s);
+  GemmSeg *b = upload(tmp, gg, s);
+  CK(launch_gemm_f64(a, (int)dd.size(), b, tt, s));
+  CK(cudaStreamSynchronize(s));
+}
+
+// side 0: old window l was truncated to the left (L_{l+1} = U^T L.); the guess
+// for window l+1 is psi'[(l', s1), (s2, r')] = sum_r (U^T psi)[l', (s1, r)] TR[(s2, r'), r]
+// with TR the isometry of R_{l+2}.  side 1 mirrors it with V (R_{l+1}) and TL
+// (the isometry of L_l).
+void stvec(dmrg_ctx *C, const WinMeta &old, const double *psi_old, int side, double *psi_new,
+           cudaStream_t s) {
+  Window &w = C->win;
+  double t0 = now();
+  CK(cudaMemsetAsync(psi_new, 0, 8 * std::max<long long>(w.psi_len, 1), s));
+  WinBuf tmp;
+  std::vector<GemmDesc> dd;
+  std::vector<GemmSeg> gg;
+  long long tt = 0;
+  std::map<int, int> a2p, b2p;
+  for (size_t i = 0; i < old.psi.size(); ++i) {
+    a2p[old.psi[i].a] = (int)i;
+    b2p[old.psi[i].b] = (int)i;
+  }
+  if (side == 0) {
+    const Iso &U = C->Lmap.at(old.l + 1);
+    const Iso &TR = C->Rmap.at(old.l + 2);
+    std::vector<long long> xo(old.psi.size(), -1);
+    std::vector<int> kx(old.psi.size(), 0);
+    long long nx = 0;
+    for (size_t i = 0; i < old.psi.size(); ++i) {
+      int ui = iso_find(U, old.Lb.qn[old.psi[i].a]);
+      if (ui < 0) continue;
+      xo[i] = nx;
+      kx[i] = U.cols[ui];
+      nx += (long long)kx[i] * old.psi[i].db;
+    }
+    double *X = (double *)tmp.alloc(8 * std::max<long long>(nx, 1));
+    for (size_t i = 0; i < old.psi.size(); ++i) {
+      if (xo[i] < 0) continue;
+      const PsiBlk &p = old.psi[i];
+      int ui = iso_find(U, old.Lb.qn[p.a]);
+      push_gemm(dd, gg, tt, X + xo[i], p.db, kx[i], p.db, p.da, U.d + U.off[ui], 1, kx[i],
+                psi_old + p.off, p.db, 1);
+    }
+    run_gemms(dd, gg, tt, s);
+    dd.clear();
+    gg.clear();
+    tt = 0;
+    const BlockPart &Lnew = *C->L[old.l + 1];
+    for (const PsiBlk &P : w.psi) {
+      const int dB = w.Rd.basis.dim[P.b];
+      for (const Piece &pc : w.Ld.pieces[P.a]) {
+        int ia = old.Lb.find(Lnew.basis.qn[pc.blk_sector]);
+        if (ia < 0 || !a2p.count(ia)) continue;
+        int pi = a2p[ia];
+        if (xo[pi] < 0) continue;
+        const PsiBlk &p = old.psi[pi];
+        const Piece *rp = nullptr;
+        for (const Piece &q : old.Rp[p.b])
+          if (q.site_state == pc.site_state) rp = &q;
+        if (!rp) continue;
+        const BlockPart &R2 = *C->R[old.l + 2];
+        const QN qr = R2.basis.qn[rp->blk_sector];
+        if (qr != w.Rd.basis.qn[P.b]) continue;
+        int ti = iso_find(TR, qr);
+        if (ti < 0 || TR.rows[ti] != dB) continue;
+        push_gemm(dd, gg, tt, psi_new + P.off + (long long)pc.off * dB, dB, pc.dim, dB, rp->dim,
+                  X + xo[pi] + rp->off, p.db, 1, TR.d + TR.off[ti], 1, TR.cols[ti]);
+      }
+    }
+    run_gemms(dd, gg, tt, s);
+  } else {
+    const Iso &V = C->Rmap.at(old.l + 1);
+    const Iso &TL = C->Lmap.at(old.l);
+    std::vector<long long> yo(old.psi.size(), -1);
+    std::vector<int> ky(old.psi.size(), 0);
+    long long ny = 0;
+    for (size_t i = 0; i < old.psi.size(); ++i) {
+      int vi = iso_find(V, old.Rb.qn[old.psi[i].b]);
+      if (vi < 0) continue;
+      yo[i] = ny;
+      ky[i] = V.cols[vi];
+      ny += (long long)old.psi[i].da * ky[i];
+    }
+    double *Y = (double *)tmp.alloc(8 * std::max<long long>(ny, 1));
+    for (size_t i = 0; i < old.psi.size(); ++i) {
+      if (yo[i] < 0) continue;
+      const PsiBlk &p = old.psi[i];
+      int vi = iso_find(V, old.Rb.qn[p.b]);
+      push_gemm(dd, gg, tt, Y + yo[i], ky[i], p.da, ky[i], p.db, psi_old + p.off, p.db, 1,
+                V.d + V.off[vi], ky[i], 1);
+    }
+    run_gemms(dd, gg, tt, s);
+    dd.clear();
+    gg.clear();
+    tt = 0;
+    const BlockPart &Rnew = *C->R[old.l + 1];
+    for (const PsiBlk &P : w.psi) {
+      const int dA = w.Ld.basis.dim[P.a];
+      const int dB = w.Rd.basis.dim[P.b];
+      const QN qA = w.Ld.basis.qn[P.a];
+      int ti = iso_find(TL, qA);
+      if (ti < 0 || TL.rows[ti] != dA) continue;
+      for (const Piece &pc : w.Rd.pieces[P.b]) {
+        // old L. sector holding (site state, L_l sector with QN qA)
+        int ib = old.Rb.find(Rnew.basis.qn[pc.blk_sector]);
+        (void)ib;
+        const QN qa_old = qadd(qA, qsub(w.Rd.basis.qn[P.b], Rnew.basis.qn[pc.blk_sector]));
+        int ia = old.Lb.find(qa_old);
+        if (ia < 0 || !a2p.count(ia)) continue;
+        int pi = a2p[ia];
+        if (yo[pi] < 0) continue;
+        const PsiBlk &p = old.psi[pi];
+        const Piece *lp = nullptr;
+        for (const Piece &q : old.Lp[p.a])
+          if (q.site_state == pc.site_state) lp = &q;
+        if (!lp) continue;
+        if (C->L[old.l]->basis.qn[lp->blk_sector] != qA) continue;
+        if (ky[pi] != pc.dim) continue;
+        push_gemm(dd, gg, tt, psi_new + P.off + pc.off, dB, dA, pc.dim, lp->dim,
+                  TL.d + TL.off[ti], TL.cols[ti], 1, Y + yo[pi] + (long long)lp->off * ky[pi],
+                  ky[pi], 1);
+      }
+    }
+    run_gemms(dd, gg, tt, s);
+  }
+  C->prof[4] += now() - t0;
 }
 
 }  // namespace
@@ -1848,29 +2048,41 @@ void sweep_impl(dmrg_ctx *C, int nsw, const int *dsched, double *E, cudaStream_t
   C->L.clear();
   C->L.push_back(vacuum(C));
   C->prof[1] += now() - t0;
-  WinBuf xb;
+  C->Lmap.clear();
+  C->Rmap.clear();
+  for (int n = 2; n <= N - 1; ++n) C->Rmap[n] = C->riso[n];
+  WinBuf xb[2];
+  int cur = 0;
+  double *prev = nullptr;
+  WinMeta pm;
+  int prev_trunc = -1;   // -1 none, 0 left, 1 right, 2 same window follows
   double e = 0;
   int it;
+  auto step = [&](int l, int trunc_side, int D, bool last) {
+    build_window(C, l);
+    const long long n = C->win.psi_len;
+    xb[cur].clear();
+    double *x = (double *)xb[cur].alloc(8 * std::max<long long>(n, 1));
+    if (prev && prev_trunc == 2 && pm.l == l) {
+      CK(cudaMemcpyAsync(x, prev, 8 * n, cudaMemcpyDeviceToDevice, s));
+    } else if (prev && (prev_trunc == 0 || prev_trunc == 1)) {
+      stvec(C, pm, prev, prev_trunc, x, s);
+    } else {
+      CK(cudaMemsetAsync(x, 0, 8 * std::max<long long>(n, 1), s));
+    }
+    // the FP64 Rayleigh quotient is only needed for the reported energy
+    int rc = davidson(C, x, &e, &it, s, last);
+    (void)rc;
+    pm = meta_of(C->win);
+    if (trunc_side >= 0) truncate(C, x, trunc_side, D, nullptr, nullptr, s);
+    prev = x;
+    prev_trunc = trunc_side >= 0 ? trunc_side : 2;
+    cur ^= 1;
+  };
   for (int sw = 0; sw < nsw; ++sw) {
     const int D = dsched ? dsched[sw] : C->cfg.d_max;
-    for (int l = 0; l <= N - 2; ++l) {
-      build_window(C, l);
-      double *x = (double *)xb.alloc(8 * std::max<long long>(C->win.psi_len, 1));
-      CK(cudaMemsetAsync(x, 0, 8 * C->win.psi_len, s));
-      int rc = davidson(C, x, &e, &it, s);
-      (void)rc;
-      if (l < N - 2) truncate(C, x, 0, D, nullptr, nullptr, s);
-      xb.clear();
-    }
-    for (int l = N - 2; l >= 0; --l) {
-      build_window(C, l);
-      double *x = (double *)xb.alloc(8 * std::max<long long>(C->win.psi_len, 1));
-      CK(cudaMemsetAsync(x, 0, 8 * C->win.psi_len, s));
-      int rc = davidson(C, x, &e, &it, s);
-      (void)rc;
-      if (l > 0) truncate(C, x, 1, D, nullptr, nullptr, s);
-      xb.clear();
-    }
+    for (int l = 0; l <= N - 2; ++l) step(l, l < N - 2 ? 0 : -1, D, false);
+    for (int l = N - 2; l >= 0; --l) step(l, l > 0 ? 1 : -1, D, l == 0);
     if (E) E[sw] = e;
   }
   C->prof[5] = std::max(0.0, now() - t0 - C->prof[0] - C->prof[1] - C->prof[2] - C->prof[3] - C->prof[4]);

@@ -4,10 +4,10 @@
 // Stage 1:  T[(a',k), b]  = sign * A_stack[(a',k), a] . psi[a, b]
 // Stage 2:  sigma[a', b'] = sum_segments T[a', (k,b)] . B_stack[b', (k,b)]^T
 // Both are C = A . B^T with K-major operands.  Each FP64 operand x is held as
-// x_hi + x_lo (TF32 each); the product uses hi.hi + hi.lo + lo.hi with FP32
-// accumulation in tensor memory.  A work item is one 128 x ntile output tile;
+// x_hi + x_lo (TF32 each); the product uses all four cross terms
+// (lo.lo + lo.hi + hi.lo + hi.hi) with FP32 accumulation in tensor memory.  A work item is one 128 x ntile output tile;
 // per 32-wide K chunk the producer loads A_hi, A_lo, B_hi, B_lo by TMA and the
-// MMA warp issues 4 k-steps x 3 tcgen05.mma.
+// MMA warp issues 4 k-steps x 4 tcgen05.mma.
 // Every mbarrier wait is bounded; on timeout the kernel records an error
 // code, skips the remaining work, frees its TMEM and returns.
 #include <cuda.h>
@@ -234,8 +234,10 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
 #pragma unroll
             for (int k = 0; k < BK / 8; ++k) {
               const uint32_t ko = k * 32;   // 8 tf32 = 32 bytes along the swizzled row
-              mma_tf32(d, sdesc(a_lo + ko), sdesc(b_hi + ko), id, accum);
+              // small terms first: lo.lo, lo.hi, hi.lo, then hi.hi
+              mma_tf32(d, sdesc(a_lo + ko), sdesc(b_lo + ko), id, accum);
               accum = 1;
+              mma_tf32(d, sdesc(a_lo + ko), sdesc(b_hi + ko), id, 1);
               mma_tf32(d, sdesc(a_hi + ko), sdesc(b_lo + ko), id, 1);
               mma_tf32(d, sdesc(a_hi + ko), sdesc(b_hi + ko), id, 1);
             }
