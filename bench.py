@@ -195,6 +195,7 @@ def main():
     ap.add_argument("--workload", default="hubbard6x6_D1024", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -275,6 +276,21 @@ def main():
                            "converged": conv}
         solve["rel_energy_diff"] = abs(solve["split"]["energy"] - solve["fp64"]["energy"]) / abs(
             solve["fp64"]["energy"])
+    # serving stream: Poisson arrivals of independent solves (config-4 pattern,
+    # reduced to 4x4 lattices and D <= 128 so that both arms fit in a minute)
+    serving_out = None
+    if not args.no_serving and rank == 0:
+        from paper_2311_14106_b300 import serving as srvmod
+        mix = [("spinless", 4, 4, (0.0, 4.0), [64, 128]), ("hubbard", 4, 4, (0.0, 8.0), [64, 128])]
+        serving_out = {"stream": "12 requests, exponential inter-arrival mean 0.1 s (seed 3); "
+                                 "spinless 4x4 V~U[0,4] and Hubbard 4x4 U~U[0,8], D in {64,128}, "
+                                 "2 sweeps each, 4 slots"}
+        for name, prec in (("split", lib.SPLIT_TF32), ("fp64", lib.FP64)):
+            reqs = srvmod.poisson_stream(12, 0.1, 3, mix, sweeps=2)
+            srv = srvmod.Server(precision=prec, slots=4, hbm_budget=200e9, davidson_tol=1e-7)
+            serving_out[name] = srv.run(reqs)
+        serving_out["solves_per_s_ratio_split_over_fp64"] = (
+            serving_out["split"]["solves_per_s"] / max(serving_out["fp64"]["solves_per_s"], 1e-12))
     hbm, bf16, src = peaks()
     tf32_peak = bf16 * TF32_OVER_BF16
     # roofline of the dominant kernel: the stage with the larger share
@@ -301,6 +317,7 @@ def main():
         "split_stage_ms": st_split[:3].tolist(),
         "sigma_rel_diff_split_vs_fp64": err_sigma,
         "solve": solve,
+        "serving": serving_out,
         "e2e": {"value": world * flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
                 "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n, "ms_per_step": e2e_ms},
         "clocks": clocks,

@@ -7,6 +7,7 @@
 #include <cusolverDn.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -183,6 +184,7 @@ struct dmrg_ctx {
   long long dav_n = 0;
   double *V = nullptr, *AV = nullptr, *work = nullptr, *small = nullptr, *r = nullptr;
   double *rs = nullptr;   // thick-restart scratch (3 vectors)
+  uint64_t start_count = 0;
 };
 
 namespace {
@@ -822,7 +824,7 @@ void build_window(dmrg_ctx *C, int l) {
   w.rdbuf.clear();
   w.tf_ready = false;
   w.tf_copies = false;
-  static long long build_counter = 0;
+  static std::atomic<long long> build_counter{0};
   w.gen = ++build_counter;
   w.Ld = BlockPart();
   w.Rd = BlockPart();
@@ -1534,8 +1536,9 @@ int davidson(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_t s,
   if (!(nx > 0)) {
     // seeded random start, weighted towards configurations with a low
     // diagonal energy: x_i = u_i / (diag_i - min(diag) + 1)
-    static uint64_t counter = 0;
-    CK(launch_random(x, n, C->cfg.seed + 7919 * (++counter), s));
+    // seeded per context: the same solve starts from the same vector whatever
+    // other contexts do (results are the same alone and in a mix)
+    CK(launch_random(x, n, C->cfg.seed + 7919 * (++C->start_count), s));
     std::vector<double> dh(n);
     CK(cudaMemcpyAsync(dh.data(), w.diag, 8 * n, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
