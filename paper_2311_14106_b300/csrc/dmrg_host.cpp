@@ -118,7 +118,8 @@ struct Tf32Tables {
   std::vector<Split2D> psi_split;
   std::vector<CUtensorMap> maps;
   std::vector<TSeg> segs;
-  std::vector<TWork> w1, w2;
+  std::vector<TWork> w1, w2;      // grouped by tile width (<= 32, <= 64, <= 128)
+  int n1[3] = {0, 0, 0}, n2[3] = {0, 0, 0};
   std::vector<PartialSum> psums;
 };
 
@@ -1366,9 +1367,16 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo
     for (int i = 0; i < t.nseg; ++i) k += (segs[t.seg0 + i].K + 31) / 32;
     return k * t.ntile;
   };
-  auto by_cost = [&](const TWork &a, const TWork &b) { return cost(a) > cost(b); };
-  std::stable_sort(w1.begin(), w1.end(), by_cost);
-  std::stable_sort(w2.begin(), w2.end(), by_cost);
+  // group by tile width (one launch per width class), largest cost first
+  auto bucket = [](const TWork &t) { return t.ntile <= 32 ? 0 : (t.ntile <= 64 ? 1 : 2); };
+  auto order = [&](const TWork &a, const TWork &b) {
+    if (bucket(a) != bucket(b)) return bucket(a) < bucket(b);
+    return cost(a) > cost(b);
+  };
+  std::stable_sort(w1.begin(), w1.end(), order);
+  std::stable_sort(w2.begin(), w2.end(), order);
+  for (const TWork &t : w1) out.n1[bucket(t)]++;
+  for (const TWork &t : w2) out.n2[bucket(t)]++;
 }
 
 void build_tf32(dmrg_ctx *C) {
@@ -1391,6 +1399,10 @@ void build_tf32(dmrg_ctx *C) {
   P.work2 = upload(w.buf, tb.w2, s);
   P.nwork1 = (int)tb.w1.size();
   P.nwork2 = (int)tb.w2.size();
+  for (int i = 0; i < 3; ++i) {
+    P.n1[i] = tb.n1[i];
+    P.n2[i] = tb.n2[i];
+  }
   P.psum = upload(w.buf, tb.psums, s);
   P.npsum = (int)tb.psums.size();
   P.err = (int *)w.buf.alloc(sizeof(int));
@@ -1411,9 +1423,9 @@ void apply_tf32(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s) {
   mark(C, 0, s);
   CK(launch_split2d((const Split2D *)P.psi_split, P.npsi, s, psi));
   mark(C, 1, s);
-  CK(tf32_gemm(P.work1, P.nwork1, P.seg, P.maps, nullptr, P.err, s));
+  CK(tf32_gemm(P.work1, P.n1, P.seg, P.maps, nullptr, P.err, s));
   mark(C, 2, s);
-  CK(tf32_gemm(P.work2, P.nwork2, P.seg, P.maps, sigma, P.err, s));
+  CK(tf32_gemm(P.work2, P.n2, P.seg, P.maps, sigma, P.err, s));
   CK(sum_partials(P.psum, P.npsum, sigma, s));
   mark(C, 3, s);
 }
@@ -1519,6 +1531,7 @@ void lincomb(double *out, const double *V, const std::vector<double> &c, double 
 }
 
 constexpr double kSplitResidualFloor = 4e-6;
+constexpr int kKrylovWarmup = 12;
 
 int davidson(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_t s,
              bool fp64_rq = true) {
@@ -1624,7 +1637,11 @@ int davidson(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_t s,
     // correction vector: preconditioned residual
     double *th = B.coef + m + 1;
     CK(cudaMemcpyAsync(th, &theta, 8, cudaMemcpyHostToDevice, s));
-    CK(launch_precond(B.t, w.diag, th, n, s));
+    // The first iterations expand a plain Krylov space (t = r): it converges to
+    // the extremal eigenvalue first, so the diagonal preconditioner, which
+    // amplifies whatever eigenvalue theta is close to, cannot lock onto an
+    // interior state from an unlucky start.
+    if (it >= kKrylovWarmup) CK(launch_precond(B.t, w.diag, th, n, s));
     for (int pass = 0; pass < 2; ++pass) {
       std::vector<double> c;
       dots(C, B.V, k, n, B.t, B, c, s);
@@ -2476,9 +2493,9 @@ int dmrg_heff_apply_tf32_static(dmrg_ctx *C, const double *psi, double *sigma, v
     int *err = (int *)b;
     CK(cudaMemsetAsync(err, 0, sizeof(int), s));   // the only state that must start at zero
     CK(launch_split2d((const Split2D *)(b + ow.o_split), (int)t.psi_split.size(), s, psi));
-    CK(tf32_gemm((const TWork *)(b + ow.o_w1), (int)t.w1.size(), (const TSeg *)(b + ow.o_seg),
+    CK(tf32_gemm((const TWork *)(b + ow.o_w1), t.n1, (const TSeg *)(b + ow.o_seg),
                  (const CUtensorMap *)(b + ow.o_maps), nullptr, err, s));
-    CK(tf32_gemm((const TWork *)(b + ow.o_w2), (int)t.w2.size(), (const TSeg *)(b + ow.o_seg),
+    CK(tf32_gemm((const TWork *)(b + ow.o_w2), t.n2, (const TSeg *)(b + ow.o_seg),
                  (const CUtensorMap *)(b + ow.o_maps), sigma, err, s));
     CK(sum_partials((const PartialSum *)(b + ow.o_ps), (int)t.psums.size(), sigma, s));
   });

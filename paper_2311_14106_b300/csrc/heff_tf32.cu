@@ -22,11 +22,22 @@ namespace {
 
 constexpr int BM = 128;           // UMMA M
 constexpr int BK = 32;            // floats per 128-byte swizzle row
-constexpr int STAGES = 2;
 constexpr int TILE_A = BM * BK * 4;          // 16 KB
-constexpr int TILE_B = 128 * BK * 4;         // up to 16 KB
-constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256 + 4 * (32 * 128 + 128) * 4;
+constexpr int MAX_SMEM = 232448;             // 227 KB per CTA
+constexpr int NACC = 4;                      // TMEM accumulators (4 x 128 columns)
+constexpr int STAGE_OUT = 4 * 32 * 33 * 4;   // epilogue transpose buffers
+
+// Pipeline geometry for a launch whose tiles are at most NT columns wide:
+// a stage holds A_hi, A_lo (128 x 32 each) and B_hi, B_lo (NT x 32 each).
+template <int NT>
+struct Geo {
+  static constexpr int TILE_B = NT * BK * 4;
+  static constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;
+  static constexpr int STAGES_RAW = (MAX_SMEM - 1024 - 512 - STAGE_OUT) / STAGE_BYTES;
+  static constexpr int STAGES = STAGES_RAW > 6 ? 6 : STAGES_RAW;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 512 + STAGE_OUT;
+};
+static_assert(Geo<128>::STAGES >= 3, "pipeline too shallow");
 constexpr long long WAIT_LIMIT = 1LL << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -125,14 +136,11 @@ constexpr int NTHREADS = 192;
 constexpr int ACC_COLS = 128;
 
 struct Shared {
-  uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2];
+  uint64_t full[8], empty[8], acc_full[NACC], acc_empty[NACC];
   uint32_t tmem;
   int abort;
 };
-
-// per epilogue warp: 32 rows x up to 128 columns in destination order, one
-// skew word per 32 (element e lives at e + e/32: conflict-free flat reads)
-constexpr int FLAT = 32 * 128 + 128;
+static_assert(sizeof(Shared) <= 512, "barrier area");
 
 __device__ __forceinline__ bool wait_or_abort(uint32_t a, uint32_t parity, int *err, int code,
                                               volatile int *abort) {
@@ -146,14 +154,19 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t a, uint32_t parity, int *
   return false;
 }
 
+template <int NT>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__ segs,
             const CUtensorMap *__restrict__ maps, double *__restrict__ out64,
             int *__restrict__ err) {
+  using G = Geo<NT>;
+  constexpr int STAGES = G::STAGES;
+  constexpr int STAGE_BYTES = G::STAGE_BYTES;
+  constexpr int TILE_B = G::TILE_B;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   Shared *sh = (Shared *)(smem + STAGES * STAGE_BYTES);
-  float *flat_all = (float *)(smem + STAGES * STAGE_BYTES + 256);
+  float(*stage_out)[32][33] = (float(*)[32][33])(smem + STAGES * STAGE_BYTES + 512);
   volatile int *abort_flag = &sh->abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -162,7 +175,7 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
       mbar_init(smem_u32(&sh->full[i]), 1);
       mbar_init(smem_u32(&sh->empty[i]), 1);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < NACC; ++i) {
       mbar_init(smem_u32(&sh->acc_full[i]), 1);
       mbar_init(smem_u32(&sh->acc_empty[i]), 128);
     }
@@ -172,7 +185,7 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&sh->tmem)),
-                 "r"(2 * ACC_COLS)
+                 "r"(NACC * ACC_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -214,8 +227,8 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
       for (int t = blockIdx.x; t < nwork && !*abort_flag; t += gridDim.x, ++j) {
         const TWork w = works[t];
         const uint32_t id = idesc_tf32(w.ntile);
-        const int acc = j & 1;
-        const uint32_t aph = (j >> 1) & 1;
+        const int acc = j % NACC;
+        const uint32_t aph = (j / NACC) & 1;
         if (!wait_or_abort(smem_u32(&sh->acc_empty[acc]), aph ^ 1, err, 2, abort_flag)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t d = tmem + acc * ACC_COLS;
@@ -254,65 +267,88 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
     int j = 0;
     for (int t = blockIdx.x; t < nwork; t += gridDim.x, ++j) {
       const TWork w = works[t];
-      const int acc = j & 1;
-      const uint32_t aph = (j >> 1) & 1;
+      const int acc = j % NACC;
+      const uint32_t aph = (j / NACC) & 1;
       if (!wait_or_abort(smem_u32(&sh->acc_full[acc]), aph, err, 4, abort_flag)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // Each lane holds one accumulator row.  The warp's 32 rows go to shared
-      // memory in destination order; when they form one contiguous run of
-      // the output (all columns of the tile, one block row of T) they are
-      // stored as a flat coalesced stream, otherwise row by row.
+      // Each lane holds one accumulator row.  When the warp's rows are one
+      // contiguous run of the output (all columns of the tile, one block row
+      // of T), they are staged in shared memory in destination order, R rows
+      // at a time (R x nt <= 1024 floats), and stored as a flat coalesced
+      // stream; otherwise each row's 32-column blocks are transposed through
+      // shared memory and stored as 128-byte runs.
       const int row0 = w.m0 + quarter * 32;
       const int nt = min(w.ntile, w.N - w.n0);          // valid columns
       const int rv = min(32, w.M - row0);               // valid rows
       const uint32_t tbase = tmem + acc * ACC_COLS + ((uint32_t)(quarter * 32) << 16);
-      float *flat = flat_all + (warp - 2) * FLAT;
-      for (int c0 = 0; c0 < w.ntile; c0 += 16) {
-        float v[16];
-        tmem_ld16(tbase + c0, v);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int c = c0 + i;
-          if (c < nt) {
-            const int e = lane * nt + c;
-            flat[e + (e >> 5)] = w.alpha * v[i];
-          }
-        }
-      }
-      __syncwarp();
-      if (rv > 0) {
-        bool contiguous;
-        long long base;
+      float(*tile)[33] = stage_out[warp - 2];
+      float *flat = &tile[0][0];
+      bool contiguous = false;
+      long long base = 0;
+      if (w.n0 == 0 && rv > 0) {
         if (w.mode == 0) {
           const int a0 = row0 / w.nrep, k0 = row0 - a0 * w.nrep;
-          contiguous = (w.n0 == 0 && nt == w.rep && k0 + rv <= w.nrep);
+          contiguous = (nt == w.rep && k0 + rv <= w.nrep);
           base = (long long)a0 * w.ld + (long long)k0 * w.rep;
         } else if (w.mode == 2) {
-          contiguous = (w.n0 == 0 && nt == w.ld);
+          contiguous = (nt == w.ld);
           base = (long long)row0 * w.ld;
-        } else {
-          contiguous = false;
-          base = 0;
         }
-        if (contiguous) {
-          const int ne = rv * nt;
+      }
+      if (contiguous) {
+        const int R = nt >= 32 ? 1024 / nt : 32;           // rows per phase
+        for (int r0 = 0; r0 < rv; r0 += R) {
+          const bool mine = lane >= r0 && lane < r0 + R;
+          for (int c0 = 0; c0 < w.ntile; c0 += 16) {
+            float v[16];
+            tmem_ld16(tbase + c0, v);
+            if (mine) {
+#pragma unroll
+              for (int i = 0; i < 16; ++i) {
+                const int c = c0 + i;
+                if (c < nt) {
+                  const int e = (lane - r0) * nt + c;
+                  flat[e + (e >> 5)] = w.alpha * v[i];
+                }
+              }
+            }
+          }
+          __syncwarp();
+          const int ne = min(R, rv - r0) * nt;
+          const long long b0 = base + (long long)r0 * nt;
           if (w.mode == 0) {
             for (int e = lane; e < ne; e += 32) {
               const float x = flat[e + (e >> 5)];
               const float h = tf32_round(x);
-              w.out_hi[base + e] = h;
-              w.out_lo[base + e] = tf32_round(x - h);
+              w.out_hi[b0 + e] = h;
+              w.out_lo[b0 + e] = tf32_round(x - h);
             }
           } else {
-            for (int e = lane; e < ne; e += 32) w.out32[base + e] = flat[e + (e >> 5)];
+            for (int e = lane; e < ne; e += 32) w.out32[b0 + e] = flat[e + (e >> 5)];
           }
-        } else {
-          for (int rr = 0; rr < rv; ++rr) {
-            const int row = row0 + rr;
-            for (int c = lane; c < nt; c += 32) {
-              const int e = rr * nt + c;
-              const float x = flat[e + (e >> 5)];
-              const int col = w.n0 + c;
+          __syncwarp();
+        }
+      } else {
+        for (int c0 = 0; c0 < w.ntile; c0 += 32) {
+          float v[32];
+          tmem_ld16(tbase + c0, v);
+          if (c0 + 16 < w.ntile) {
+            tmem_ld16(tbase + c0 + 16, v + 16);
+          } else {
+#pragma unroll
+            for (int i = 16; i < 32; ++i) v[i] = 0.f;
+          }
+          const int ncol = min(32, nt - c0);
+          if (ncol > 0) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) tile[lane][i] = w.alpha * v[i];
+            __syncwarp();
+            const int col = w.n0 + c0 + lane;
+            const bool cok = lane < ncol;
+            for (int rr = 0; rr < rv; ++rr) {
+              const int row = row0 + rr;
+              if (!cok) continue;
+              const float x = tile[rr][lane];
               if (w.mode == 0) {
                 const long long o = (long long)(row / w.nrep) * w.ld +
                                     (long long)(row % w.nrep) * w.rep + col;
@@ -326,9 +362,9 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
               }
             }
           }
+          __syncwarp();
         }
       }
-      __syncwarp();
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&sh->acc_empty[acc]))
                    : "memory");
@@ -338,7 +374,7 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
   __syncthreads();
   if (warp == 1) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(2 * ACC_COLS)
+                 "r"(NACC * ACC_COLS)
                  : "memory");
   }
 }
@@ -389,13 +425,14 @@ cudaError_t sum_partials(const PartialSum *p, int n, double *sigma, cudaStream_t
   return cudaGetLastError();
 }
 
-cudaError_t tf32_gemm(const TWork *work, int nwork, const TSeg *seg, const CUtensorMap *maps,
+template <int NT>
+cudaError_t launch_nt(const TWork *work, int nwork, const TSeg *seg, const CUtensorMap *maps,
                       double *out64, int *err, cudaStream_t s) {
   if (nwork <= 0) return cudaSuccess;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_tf32_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(k_tf32_gemm<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Geo<NT>::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -407,8 +444,18 @@ cudaError_t tf32_gemm(const TWork *work, int nwork, const TSeg *seg, const CUten
     if (nsm <= 0) nsm = 148;
   }
   const int grid = nwork < nsm ? nwork : nsm;
-  k_tf32_gemm<<<grid, NTHREADS, SMEM_BYTES, s>>>(work, nwork, seg, maps, out64, err);
+  k_tf32_gemm<NT><<<grid, NTHREADS, Geo<NT>::SMEM_BYTES, s>>>(work, nwork, seg, maps, out64, err);
   return cudaGetLastError();
+}
+
+cudaError_t tf32_gemm(const TWork *work, const int *nwork3, const TSeg *seg,
+                      const CUtensorMap *maps, double *out64, int *err, cudaStream_t s) {
+  // work items are grouped by tile width: [<= 32 | <= 64 | <= 128]
+  cudaError_t e = launch_nt<32>(work, nwork3[0], seg, maps, out64, err, s);
+  if (e != cudaSuccess) return e;
+  e = launch_nt<64>(work + nwork3[0], nwork3[1], seg, maps, out64, err, s);
+  if (e != cudaSuccess) return e;
+  return launch_nt<128>(work + nwork3[0] + nwork3[1], nwork3[2], seg, maps, out64, err, s);
 }
 
 }  // namespace dmrg

@@ -57,6 +57,7 @@ struct Tf32Plan {
   TSeg *seg = nullptr;
   TWork *work1 = nullptr, *work2 = nullptr;
   int nwork1 = 0, nwork2 = 0;
+  int n1[3] = {0, 0, 0}, n2[3] = {0, 0, 0};   // per tile-width bucket
   float *ws = nullptr;              // split-K partial tiles of stage 2
   PartialSum *psum = nullptr;
   int npsum = 0;
@@ -77,7 +78,9 @@ cudaError_t static_scratch(void **ptr, size_t *bytes);
 
 cudaError_t sum_partials(const PartialSum *p, int n, double *sigma, cudaStream_t s);
 
-cudaError_t tf32_gemm(const TWork *work, int nwork, const TSeg *seg, const CUtensorMap *maps,
-                      double *out64, int *err, cudaStream_t s);
+// work holds nwork3[0] items with ntile <= 32, then nwork3[1] with ntile <= 64,
+// then nwork3[2] with ntile <= 128 (one launch each, pipeline sized to the width).
+cudaError_t tf32_gemm(const TWork *work, const int *nwork3, const TSeg *seg,
+                      const CUtensorMap *maps, double *out64, int *err, cudaStream_t s);
 
 }  // namespace dmrg
