@@ -221,6 +221,16 @@ int dmrg_heff_stage_info(dmrg_ctx *ctx, double *out6);
  * timed; reading synchronises the last timed apply. */
 int dmrg_heff_timing(dmrg_ctx *ctx, int enable, double *out4);
 
+/* Autotuner record of this context: *n_entries pairs (candidate split-K
+ * range, milliseconds per split-precision apply) timed on the first large
+ * window; the fastest candidate is used for the rest of the context.  out
+ * (may be NULL) receives up to max_entries pairs. */
+int dmrg_heff_tuning(dmrg_ctx *ctx, double *out, int max_entries, int *n_entries);
+
+/* Replay the split-precision apply from captured CUDA graphs (default 1), one
+ * graph per (psi, sigma) pointer pair; 0 launches the kernels directly. */
+int dmrg_set_graphs(dmrg_ctx *ctx, int enable);
+
 /* Timing breakdown of the last sweep in seconds, Sec. III.B categories:
  * out[0] Diag_H, [1] Ren (block ops), [2] Tables, [3] Diag_D, [4] StVec,
  * [5] Other; out[6] = number of H_eff*psi calls. */

@@ -29,7 +29,7 @@ HEADER_FUNCTIONS = [
     "dmrg_set_precision", "dmrg_heff_apply", "dmrg_heff_apply_host",
     "dmrg_heff_flops", "dmrg_davidson", "dmrg_truncate", "dmrg_sweep",
     "dmrg_heff_stage_info", "dmrg_heff_timing", "dmrg_profile",
-    "dmrg_heff_apply_tf32_static",
+    "dmrg_heff_apply_tf32_static", "dmrg_heff_tuning", "dmrg_set_graphs",
 ]
 
 
@@ -71,6 +71,8 @@ _sig = {
     "dmrg_heff_stage_info": (ctypes.c_int, [_P, _D]),
     "dmrg_heff_timing": (ctypes.c_int, [_P, ctypes.c_int, _D]),
     "dmrg_profile": (ctypes.c_int, [_P, _D]),
+    "dmrg_heff_tuning": (ctypes.c_int, [_P, _D, ctypes.c_int, _I]),
+    "dmrg_set_graphs": (ctypes.c_int, [_P, ctypes.c_int]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -261,6 +263,18 @@ class Dmrg:
         out = np.zeros(4)
         self._check(_lib.dmrg_heff_timing(self._h, enable, _dptr(out)), "heff_timing")
         return out
+
+    def heff_tuning(self):
+        """Autotuner record: [(split-K range, ms per apply), ...]."""
+        n = ctypes.c_int()
+        self._check(_lib.dmrg_heff_tuning(self._h, None, 0, ctypes.byref(n)), "heff_tuning")
+        out = np.zeros(2 * max(n.value, 1))
+        self._check(_lib.dmrg_heff_tuning(self._h, _dptr(out), n.value, ctypes.byref(n)),
+                    "heff_tuning")
+        return [(int(out[2 * i]), float(out[2 * i + 1])) for i in range(n.value)]
+
+    def set_graphs(self, enable):
+        self._check(_lib.dmrg_set_graphs(self._h, int(enable)), "set_graphs")
 
     def profile(self):
         out = np.zeros(7)

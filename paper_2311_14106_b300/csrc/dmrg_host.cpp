@@ -16,6 +16,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <shared_mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -63,12 +64,22 @@ struct Iso {
   double *d = nullptr;
 };
 
+// cudaMalloc / cudaFree synchronise the device, which would invalidate a CUDA
+// graph capture running in another thread (several contexts are served
+// concurrently).  Allocation and release take this lock shared; a capture
+// takes it exclusively for the few microseconds it lasts.
+std::shared_mutex &capture_lock() {
+  static std::shared_mutex mu;
+  return mu;
+}
+
 // Device buffers that live for one H_eff window.
 struct WinBuf {
   std::vector<void *> ptrs;
   void *alloc(size_t bytes) {
     void *p = nullptr;
     if (bytes == 0) bytes = 8;
+    std::shared_lock<std::shared_mutex> lk(capture_lock());
     if (cudaMalloc(&p, bytes) != cudaSuccess) {
       cudaGetLastError();
       fail(DMRG_ERR_OOM, "cudaMalloc(%zu) failed", bytes);
@@ -77,6 +88,8 @@ struct WinBuf {
     return p;
   }
   void clear() {
+    if (ptrs.empty()) return;
+    std::shared_lock<std::shared_mutex> lk(capture_lock());
     for (void *p : ptrs) cudaFree(p);
     ptrs.clear();
   }
@@ -150,6 +163,10 @@ struct Window {
   Tf32Plan tf;           // split-precision plan (heff_tf32)
   bool tf_ready = false;
   bool tf_copies = false;            // TF32 copies of the operator stacks exist
+  int ksub = 0;                      // split-K range in use
+  void *tbl_ptr[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  size_t tbl_cap[6] = {0, 0, 0, 0, 0, 0};
+  std::map<std::pair<const void *, const void *>, cudaGraphExec_t> graphs;
   std::vector<long long> offA, offB, ldA, ldB;
   long long gen = 0;                 // build counter of this window
 };
@@ -186,6 +203,10 @@ struct dmrg_ctx {
   double *V = nullptr, *AV = nullptr, *work = nullptr, *small = nullptr, *r = nullptr;
   double *rs = nullptr;   // thick-restart scratch (3 vectors)
   uint64_t start_count = 0;
+  bool use_graphs = true;
+  cudaStream_t cap_stream = nullptr;            // private stream for graph capture
+  int ksub_choice = 0;                          // autotuned split-K range (0: not yet)
+  std::vector<std::array<double, 2>> tune_log;  // (candidate, ms per apply)
 };
 
 namespace {
@@ -825,6 +846,12 @@ void build_window(dmrg_ctx *C, int l) {
   w.rdbuf.clear();
   w.tf_ready = false;
   w.tf_copies = false;
+  for (auto &g : w.graphs) cudaGraphExecDestroy(g.second);
+  w.graphs.clear();
+  for (int i = 0; i < 6; ++i) {
+    w.tbl_ptr[i] = nullptr;
+    w.tbl_cap[i] = 0;
+  }
   static std::atomic<long long> build_counter{0};
   w.gen = ++build_counter;
   w.Ld = BlockPart();
@@ -1143,9 +1170,10 @@ struct Tf32Scratch {
   std::vector<long long> offP, offT, ldP, ldT;
 };
 
-const int KSUB = 1024;   // longest K range of one stage-2 work item
+const int KSUB_DEFAULT = 1024;   // longest K range of one stage-2 work item
+const int KSUB_CANDIDATES[3] = {512, 1024, 2048};
 
-Tf32Scratch tf32_scratch_sizes(const Window &w) {
+Tf32Scratch tf32_scratch_sizes(const Window &w, int KSUB = KSUB_DEFAULT) {
   Tf32Scratch z;
   const auto &E = w.s1info;
   const size_t ne = E.size(), np = w.psi.size();
@@ -1240,7 +1268,7 @@ void tf32_operator_copies(dmrg_ctx *C) {
 }
 
 void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo, float *T_hi,
-                 float *T_lo, float *ws, Tf32Tables &out) {
+                 float *T_lo, float *ws, Tf32Tables &out, int KSUB = KSUB_DEFAULT) {
   const Tf32Plan &P = w.tf;
   const auto &E = w.s1info;
   const size_t ne = E.size(), np = w.psi.size();
@@ -1379,47 +1407,114 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo
   for (const TWork &t : w2) out.n2[bucket(t)]++;
 }
 
+void upload_tables(dmrg_ctx *C, Tf32Tables &tb, cudaStream_t s);
+void launch_tf32(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s);
+
+// Autotuner: the stage-2 split-K range trades FP32 accumulation length against
+// partial-tile traffic and tile count.  For windows whose operator stacks are
+// large enough for the choice to matter, each candidate is timed on the live
+// window (three applies each, CUDA events) and the fastest is kept for the
+// rest of the context's life (windows of one run have similar shapes).
 void build_tf32(dmrg_ctx *C) {
   Window &w = C->win;
   cudaStream_t s = C->stream;
   Tf32Plan &P = w.tf;
   if (!w.tf_copies) tf32_operator_copies(C);
-  Tf32Scratch z = tf32_scratch_sizes(w);
+  CK(tf32_prepare());
+  const bool tune = C->ksub_choice == 0 && (double)(w.nA + w.nB) * 8.0 > 256e6;
+  int best = C->ksub_choice ? C->ksub_choice : KSUB_DEFAULT;
+  // scratch sized for the smallest candidate (most partial tiles)
+  Tf32Scratch zmax = tf32_scratch_sizes(w, tune ? KSUB_CANDIDATES[0] : best);
   auto fl = [&](long long n) { return (float *)w.buf.alloc(4 * std::max<long long>(n, 64)); };
-  P.P_hi = fl(z.nP); P.P_lo = fl(z.nP);
-  P.T_hi = fl(z.nT); P.T_lo = fl(z.nT);
-  P.ws = fl(z.nws);
-  Tf32Tables &tb = C->tables;
-  tf32_tables(w, z, P.P_hi, P.P_lo, P.T_hi, P.T_lo, P.ws, tb);
-  P.psi_split = upload(w.buf, tb.psi_split, s);
-  P.npsi = (int)tb.psi_split.size();
-  P.maps = upload(w.buf, tb.maps, s);
-  P.seg = upload(w.buf, tb.segs, s);
-  P.work1 = upload(w.buf, tb.w1, s);
-  P.work2 = upload(w.buf, tb.w2, s);
-  P.nwork1 = (int)tb.w1.size();
-  P.nwork2 = (int)tb.w2.size();
-  for (int i = 0; i < 3; ++i) {
-    P.n1[i] = tb.n1[i];
-    P.n2[i] = tb.n2[i];
-  }
-  P.psum = upload(w.buf, tb.psums, s);
-  P.npsum = (int)tb.psums.size();
+  P.P_hi = fl(zmax.nP); P.P_lo = fl(zmax.nP);
+  P.T_hi = fl(zmax.nT); P.T_lo = fl(zmax.nT);
+  P.ws = fl(zmax.nws);
   P.err = (int *)w.buf.alloc(sizeof(int));
   CK(cudaMemsetAsync(P.err, 0, sizeof(int), s));
+  if (tune) {
+    WinBuf tb;
+    double *x = (double *)tb.alloc(8 * std::max<long long>(w.psi_len, 1));
+    double *y = (double *)tb.alloc(8 * std::max<long long>(w.psi_len, 1));
+    CK(launch_random(x, w.psi_len, 12345, s));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    for (int ks : KSUB_CANDIDATES) {
+      Tf32Scratch z = tf32_scratch_sizes(w, ks);
+      tf32_tables(w, z, P.P_hi, P.P_lo, P.T_hi, P.T_lo, P.ws, C->tables, ks);
+      upload_tables(C, C->tables, s);
+      launch_tf32(C, x, y, s);   // warm
+      CK(cudaEventRecord(e0, s));
+      for (int r = 0; r < 3; ++r) launch_tf32(C, x, y, s);
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = ks;
+      }
+      C->tune_log.push_back({(double)ks, ms / 3.0});
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    C->ksub_choice = best;
+  }
+  w.ksub = best;
+  Tf32Scratch z = tf32_scratch_sizes(w, best);
+  tf32_tables(w, z, P.P_hi, P.P_lo, P.T_hi, P.T_lo, P.ws, C->tables, best);
+  upload_tables(C, C->tables, s);
   CK(cudaStreamSynchronize(s));
   w.tf_ready = true;
 }
 
-void apply_tf32(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s) {
+void upload_tables(dmrg_ctx *C, Tf32Tables &tb, cudaStream_t s) {
   Window &w = C->win;
-  if (!w.tf_ready) {
-    cudaStream_t save = C->stream;
-    C->stream = s;
-    build_tf32(C);
-    C->stream = save;
-  }
   Tf32Plan &P = w.tf;
+  // table buffers: grow-only, so the tuner's candidates can reuse them
+  auto need = [&](void *&ptr, size_t &cap, size_t bytes) {
+    if (bytes > cap) {
+      ptr = w.buf.alloc(bytes);
+      cap = bytes;
+    }
+  };
+  need(w.tbl_ptr[0], w.tbl_cap[0], std::max<size_t>(tb.psi_split.size(), 1) * sizeof(Split2D));
+  need(w.tbl_ptr[1], w.tbl_cap[1], std::max<size_t>(tb.maps.size(), 1) * sizeof(CUtensorMap));
+  need(w.tbl_ptr[2], w.tbl_cap[2], std::max<size_t>(tb.segs.size(), 1) * sizeof(TSeg));
+  need(w.tbl_ptr[3], w.tbl_cap[3], std::max<size_t>(tb.w1.size(), 1) * sizeof(TWork));
+  need(w.tbl_ptr[4], w.tbl_cap[4], std::max<size_t>(tb.w2.size(), 1) * sizeof(TWork));
+  need(w.tbl_ptr[5], w.tbl_cap[5], std::max<size_t>(tb.psums.size(), 1) * sizeof(PartialSum));
+  auto put = [&](void *dst, const void *src, size_t n) {
+    if (n) CK(cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, s));
+  };
+  put(w.tbl_ptr[0], tb.psi_split.data(), tb.psi_split.size() * sizeof(Split2D));
+  put(w.tbl_ptr[1], tb.maps.data(), tb.maps.size() * sizeof(CUtensorMap));
+  put(w.tbl_ptr[2], tb.segs.data(), tb.segs.size() * sizeof(TSeg));
+  put(w.tbl_ptr[3], tb.w1.data(), tb.w1.size() * sizeof(TWork));
+  put(w.tbl_ptr[4], tb.w2.data(), tb.w2.size() * sizeof(TWork));
+  put(w.tbl_ptr[5], tb.psums.data(), tb.psums.size() * sizeof(PartialSum));
+  P.psi_split = w.tbl_ptr[0];
+  P.npsi = (int)tb.psi_split.size();
+  P.maps = (CUtensorMap *)w.tbl_ptr[1];
+  P.seg = (TSeg *)w.tbl_ptr[2];
+  P.work1 = (TWork *)w.tbl_ptr[3];
+  P.work2 = (TWork *)w.tbl_ptr[4];
+  P.psum = (PartialSum *)w.tbl_ptr[5];
+  P.nwork1 = (int)tb.w1.size();
+  P.nwork2 = (int)tb.w2.size();
+  P.npsum = (int)tb.psums.size();
+  for (int i = 0; i < 3; ++i) {
+    P.n1[i] = tb.n1[i];
+    P.n2[i] = tb.n2[i];
+  }
+  CK(cudaStreamSynchronize(s));
+  for (auto &g : w.graphs) cudaGraphExecDestroy(g.second);
+  w.graphs.clear();
+}
+
+void launch_tf32(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s) {
+  Tf32Plan &P = C->win.tf;
   mark(C, 0, s);
   CK(launch_split2d((const Split2D *)P.psi_split, P.npsi, s, psi));
   mark(C, 1, s);
@@ -1428,6 +1523,48 @@ void apply_tf32(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s) {
   CK(tf32_gemm(P.work2, P.n2, P.seg, P.maps, sigma, P.err, s));
   CK(sum_partials(P.psum, P.npsum, sigma, s));
   mark(C, 3, s);
+}
+
+// The split apply is 8 launches; it is captured once per (psi, sigma) pair
+// into a CUDA graph and replayed (Davidson reuses a fixed set of vector slots).
+// With per-stage timing on, the launches go out directly.
+void apply_tf32(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s) {
+  Window &w = C->win;
+  if (!w.tf_ready) {
+    cudaStream_t save = C->stream;
+    C->stream = s;
+    build_tf32(C);
+    C->stream = save;
+  }
+  if (C->timing || !C->use_graphs) {
+    launch_tf32(C, psi, sigma, s);
+    return;
+  }
+  auto key = std::make_pair((const void *)psi, (const void *)sigma);
+  auto it = w.graphs.find(key);
+  if (it == w.graphs.end()) {
+    // record on a private stream (the caller's may be the legacy default
+    // stream, which cannot be captured); the graph is launched on `s`
+    if (!C->cap_stream) CK(cudaStreamCreateWithFlags(&C->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = C->cap_stream;
+    cudaGraph_t g;
+    {
+      std::unique_lock<std::shared_mutex> lk(capture_lock());
+      CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      try {
+        launch_tf32(C, psi, sigma, cs);
+      } catch (...) {
+        cudaStreamEndCapture(cs, &g);
+        throw;
+      }
+      CK(cudaStreamEndCapture(cs, &g));
+    }
+    cudaGraphExec_t ge;
+    CK(cudaGraphInstantiate(&ge, g, 0));
+    cudaGraphDestroy(g);
+    it = w.graphs.emplace(key, ge).first;
+  }
+  CK(cudaGraphLaunch(it->second, s));
 }
 
 void check_err_flag(dmrg_ctx *C, cudaStream_t s) {
@@ -1546,7 +1683,8 @@ int davidson(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_t s,
   int nmv = 0;
   // start vector
   double nx = dot1(C, x, x, n, B, s);
-  if (!(nx > 0)) {
+  const bool random_start = !(nx > 0);
+  if (random_start) {
     // seeded random start, weighted towards configurations with a low
     // diagonal energy: x_i = u_i / (diag_i - min(diag) + 1)
     // seeded per context: the same solve starts from the same vector whatever
@@ -1641,7 +1779,9 @@ int davidson(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_t s,
     // the extremal eigenvalue first, so the diagonal preconditioner, which
     // amplifies whatever eigenvalue theta is close to, cannot lock onto an
     // interior state from an unlucky start.
-    if (it >= kKrylovWarmup) CK(launch_precond(B.t, w.diag, th, n, s));
+    // (a caller's start vector, e.g. the StVec guess of a sweep, is already
+    // close to the ground state and is preconditioned from the first step)
+    if (!random_start || it >= kKrylovWarmup) CK(launch_precond(B.t, w.diag, th, n, s));
     for (int pass = 0; pass < 2; ++pass) {
       std::vector<double> c;
       dots(C, B.V, k, n, B.t, B, c, s);
@@ -2154,7 +2294,11 @@ int dmrg_create(dmrg_ctx **out, const dmrg_config *cfg) {
 
 int dmrg_destroy(dmrg_ctx *ctx) {
   if (!ctx) return DMRG_OK;
-  cudaDeviceSynchronize();
+  // wait for this context's own work only (other contexts may be running)
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->cap_stream) cudaStreamSynchronize(ctx->cap_stream);
+  for (auto &g : ctx->win.graphs) cudaGraphExecDestroy(g.second);
+  ctx->win.graphs.clear();
   ctx->win.buf.clear();
   ctx->win.ldbuf.clear();
   ctx->win.rdbuf.clear();
@@ -2165,6 +2309,7 @@ int dmrg_destroy(dmrg_ctx *ctx) {
   if (ctx->solver) cusolverDnDestroy(ctx->solver);
   for (auto &e : ctx->ev)
     if (e) cudaEventDestroy(e);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
   return DMRG_OK;
 }
@@ -2435,6 +2580,7 @@ int dmrg_heff_apply_tf32_static(dmrg_ctx *C, const double *psi, double *sigma, v
     void *base = nullptr;
     size_t cap = 0;
     CK(static_scratch(&base, &cap));
+    CK(tf32_prepare());
     int dev = 0;
     CK(cudaGetDevice(&dev));
     // layout: [error flag | tables | P hi, P lo | T hi, T lo | partial tiles]
@@ -2449,11 +2595,12 @@ int dmrg_heff_apply_tf32_static(dmrg_ctx *C, const double *psi, double *sigma, v
     Owner &ow = owners[dev];
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     unsigned char *b = (unsigned char *)base;
+    const int ks = w.ksub ? w.ksub : KSUB_DEFAULT;
     if (ow.gen != w.gen) {
-      Tf32Scratch z = tf32_scratch_sizes(w);
+      Tf32Scratch z = tf32_scratch_sizes(w, ks);
       // table sizes do not depend on the pointers: size them with a dry run
       Tf32Tables probe;
-      tf32_tables(w, z, (float *)b, (float *)b, (float *)b, (float *)b, (float *)b, probe);
+      tf32_tables(w, z, (float *)b, (float *)b, (float *)b, (float *)b, (float *)b, probe, ks);
       size_t off = 256;
       ow.o_maps = off; off = al(off + probe.maps.size() * sizeof(CUtensorMap));
       ow.o_seg = off; off = al(off + probe.segs.size() * sizeof(TSeg));
@@ -2476,7 +2623,7 @@ int dmrg_heff_apply_tf32_static(dmrg_ctx *C, const double *psi, double *sigma, v
                            "(use dmrg_heff_apply for larger windows)", off, cap);
       ow.gen = -1;
       tf32_tables(w, z, (float *)(b + oP), (float *)(b + oP2), (float *)(b + oT),
-                  (float *)(b + oT2), (float *)(b + oW), ow.tb);
+                  (float *)(b + oT2), (float *)(b + oW), ow.tb, ks);
       const Tf32Tables &t = ow.tb;
       auto put = [&](size_t o, const void *src, size_t n) {
         if (n) CK(cudaMemcpyAsync(b + o, src, n, cudaMemcpyHostToDevice, s));
@@ -2556,6 +2703,23 @@ int dmrg_heff_timing(dmrg_ctx *C, int enable, double *out4) {
       for (double &t : C->tacc) t = 0;
     C->timing = enable != 0;
   });
+}
+
+int dmrg_heff_tuning(dmrg_ctx *C, double *out, int max_entries, int *n_entries) {
+  if (!C || !n_entries) return DMRG_ERR_ARG;
+  *n_entries = (int)C->tune_log.size();
+  if (out)
+    for (int i = 0; i < std::min(max_entries, *n_entries); ++i) {
+      out[2 * i] = C->tune_log[i][0];
+      out[2 * i + 1] = C->tune_log[i][1];
+    }
+  return DMRG_OK;
+}
+
+int dmrg_set_graphs(dmrg_ctx *C, int enable) {
+  if (!C) return DMRG_ERR_ARG;
+  C->use_graphs = enable != 0;
+  return DMRG_OK;
 }
 
 int dmrg_profile(dmrg_ctx *C, double *out7) {

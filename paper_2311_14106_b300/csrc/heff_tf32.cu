@@ -397,16 +397,16 @@ typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, voi
 
 int encode_map(CUtensorMap *out, const float *base, int rows, int cols, long long ld,
                int box_rows) {
-  static EncodeFn fn = nullptr;
-  if (!fn) {
+  static const EncodeFn fn = [] {
     cudaDriverEntryPointQueryResult q;
     void *p = nullptr;
     if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) !=
             cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !p)
-      return -1;
-    fn = (EncodeFn)p;
-  }
+        q != cudaDriverEntryPointSuccess)
+      return (EncodeFn) nullptr;
+    return (EncodeFn)p;
+  }();
+  if (!fn) return -1;
   if (((uintptr_t)base & 15) || (ld & 3) || rows <= 0 || cols <= 0) return -2;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
@@ -426,23 +426,34 @@ cudaError_t sum_partials(const PartialSum *p, int n, double *sigma, cudaStream_t
 }
 
 template <int NT>
+cudaError_t prepare_nt() {
+  return cudaFuncSetAttribute(k_tf32_gemm<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              Geo<NT>::SMEM_BYTES);
+}
+
+cudaError_t tf32_prepare() {
+  cudaError_t e = prepare_nt<32>();
+  if (e == cudaSuccess) e = prepare_nt<64>();
+  if (e == cudaSuccess) e = prepare_nt<128>();
+  return e;
+}
+
+int sm_count() {
+  static const int n = [] {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 148;
+  }();
+  return n;
+}
+
+// (the shared-memory attributes are set by tf32_prepare, outside any capture)
+template <int NT>
 cudaError_t launch_nt(const TWork *work, int nwork, const TSeg *seg, const CUtensorMap *maps,
                       double *out64, int *err, cudaStream_t s) {
   if (nwork <= 0) return cudaSuccess;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_tf32_gemm<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Geo<NT>::SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  static int nsm = 0;
-  if (!nsm) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (nsm <= 0) nsm = 148;
-  }
+  const int nsm = sm_count();
   const int grid = nwork < nsm ? nwork : nsm;
   k_tf32_gemm<NT><<<grid, NTHREADS, Geo<NT>::SMEM_BYTES, s>>>(work, nwork, seg, maps, out64, err);
   return cudaGetLastError();

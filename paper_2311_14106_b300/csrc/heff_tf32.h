@@ -78,6 +78,9 @@ cudaError_t static_scratch(void **ptr, size_t *bytes);
 
 cudaError_t sum_partials(const PartialSum *p, int n, double *sigma, cudaStream_t s);
 
+// Sets the kernels' shared-memory attributes (call before any stream capture).
+cudaError_t tf32_prepare();
+
 // work holds nwork3[0] items with ntile <= 32, then nwork3[1] with ntile <= 64,
 // then nwork3[2] with ntile <= 128 (one launch each, pipeline sized to the width).
 cudaError_t tf32_gemm(const TWork *work, const int *nwork3, const TSeg *seg,

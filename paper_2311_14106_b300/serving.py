@@ -91,6 +91,10 @@ def run_one(req, precision, stream=None, davidson_tol=1e-7, rng_iso=None):
         T, V = lattice_hamiltonian(MODEL_SPINLESS_TV, req.Lx, req.Ly, 1.0, 0.0, req.coupling)
     g = Dmrg(N, tgt[0], tgt[1] if spinful else 0, spinful=spinful, d_max=req.D,
              precision=precision, davidson_tol=davidson_tol, seed=req.seed)
+    # Concurrent solves launch directly: a CUDA-graph capture in one thread can
+    # be invalidated by device-synchronising calls (allocation, stream
+    # creation) made by the other solves' threads.
+    g.set_graphs(False)
     try:
         g.set_hamiltonian(T, V, momentum_basis(req.Lx, req.Ly))
         g.set_mps(right=synth.random_right_isometries(N, spinful, tgt if spinful else (tgt[0],),
@@ -167,7 +171,7 @@ class Server:
                 "solves_per_s": len(self.results) / wall if wall > 0 else 0.0,
                 "p50_latency_s": float(np.percentile(lat, 50)),
                 "p99_latency_s": float(np.percentile(lat, 99)),
-                "slots": self.slots}
+                "slots": self.slots, "error_messages": [m for _, m in self.errors[:3]]}
 
 
 def poisson_stream(n, mean_interval, seed, mix, sweeps=2):
