@@ -190,6 +190,7 @@ struct dmrg_ctx {
   Tf32Tables tables;     // host copy of the split-path tables of the window
   cudaStream_t stream = nullptr;
   cusolverDnHandle_t solver = nullptr;
+  cusolverDnParams_t solver_params = nullptr;
   int precision = DMRG_FP64;
   double prof[7] = {0};
   // optional per-stage event timing of H_eff*psi
@@ -1835,19 +1836,35 @@ void truncate(dmrg_ctx *C, const double *psi, int side, int D, double *disc, dou
   }
   cusolverDnSetStream(C->solver, s);
   const size_t np = w.psi.size();
-  std::vector<int> dim(np);
-  std::vector<long long> roff(np);
-  long long tot = 0;
+  // Blocks up to 256 are padded to a power of two and solved in batches
+  // (cusolverDnXsyevBatched) with -1 on the padded diagonal: rho is positive
+  // semi-definite, so the padding eigenpairs separate exactly and come first
+  // in ascending order.  Larger blocks use syevd one by one.
+  std::vector<int> dim(np), npad(np);
+  std::vector<long long> roff(np), eoff(np);
+  std::map<int, std::vector<int>> bucket;
   for (size_t i = 0; i < np; ++i) {
     dim[i] = side == 0 ? w.psi[i].da : w.psi[i].db;
-    roff[i] = tot;
-    tot += (long long)dim[i] * dim[i];
+    int q = 8;
+    while (q < dim[i]) q <<= 1;
+    npad[i] = dim[i] <= 256 ? q : dim[i];
+    bucket[npad[i] <= 256 ? npad[i] : -(int)i - 1].push_back((int)i);
   }
+  long long tot = 0, eo = 0;
+  for (auto &kv : bucket)
+    for (int i : kv.second) {
+      roff[i] = tot;
+      tot += (long long)npad[i] * npad[i];
+      eoff[i] = eo;
+      eo += npad[i];
+    }
   WinBuf tmp;
   double *rho = (double *)tmp.alloc(8 * std::max<long long>(tot, 1));
-  double *eval = (double *)tmp.alloc(8 * std::max<long long>(std::accumulate(dim.begin(), dim.end(), 0LL), 1));
+  double *eval = (double *)tmp.alloc(8 * std::max<long long>(eo, 1));
+  CK(cudaMemsetAsync(rho, 0, 8 * std::max<long long>(tot, 1), s));
   std::vector<GemmDesc> dd;
   std::vector<GemmSeg> gg;
+  std::vector<SCopy> pads;
   long long tt = 0;
   for (size_t i = 0; i < np; ++i) {
     const PsiBlk &p = w.psi[i];
@@ -1863,7 +1880,7 @@ void truncate(dmrg_ctx *C, const double *psi, int side, int D, double *disc, dou
     GemmDesc d;
     memset(&d, 0, sizeof d);
     d.C = rho + roff[i];
-    d.c_rs = dim[i]; d.c_cs = 1;
+    d.c_rs = npad[i]; d.c_cs = 1;
     d.M = dim[i]; d.N = dim[i]; d.batch = 1;
     d.seg0 = (int)gg.size(); d.nseg = 1;
     d.tiles_m = (dim[i] + 63) / 64; d.tiles_n = d.tiles_m;
@@ -1872,39 +1889,80 @@ void truncate(dmrg_ctx *C, const double *psi, int side, int D, double *disc, dou
     tt += (long long)d.tiles_m * d.tiles_n;
     gg.push_back(g);
     dd.push_back(d);
+    if (npad[i] > dim[i]) {
+      SCopy c;
+      memset(&c, 0, sizeof c);
+      c.src = nullptr;
+      c.ident = 1;
+      c.coef = -1.0;
+      c.rows = c.cols = npad[i] - dim[i];
+      c.dst = rho + roff[i] + (long long)dim[i] * npad[i] + dim[i];
+      c.dst_ld = npad[i];
+      pads.push_back(c);
+    }
   }
   {
     GemmDesc *a = upload(tmp, dd, s);
     GemmSeg *b = upload(tmp, gg, s);
     CK(launch_gemm_f64(a, (int)dd.size(), b, tt, s));
+    if (!pads.empty()) {
+      SCopy *c = upload(tmp, pads, s);
+      CK(launch_stack_copy(c, (int)pads.size(), s));
+    }
+  }
+  if (!C->solver_params) {
+    if (cusolverDnCreateParams(&C->solver_params) != CUSOLVER_STATUS_SUCCESS)
+      fail(DMRG_ERR_CUDA, "cusolverDnCreateParams failed");
   }
   int *info = (int *)tmp.alloc(sizeof(int) * np);
-  std::vector<long long> eoff(np);
-  long long eo = 0;
-  int lwork_max = 0;
-  for (size_t i = 0; i < np; ++i) {
-    eoff[i] = eo;
-    eo += dim[i];
-    int lw = 0;
-    if (cusolverDnDsyevd_bufferSize(C->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
-                                    dim[i], rho + roff[i], dim[i], eval + eoff[i], &lw) !=
-        CUSOLVER_STATUS_SUCCESS)
-      fail(DMRG_ERR_CUDA, "syevd bufferSize failed");
-    lwork_max = std::max(lwork_max, lw);
+  int info_off = 0;
+  std::vector<int> info_of(np);
+  for (auto &kv : bucket) {
+    const std::vector<int> &ids = kv.second;
+    const int first = ids[0];
+    const int64_t n = npad[first];
+    if (kv.first > 0) {
+      size_t dws = 0, hws = 0;
+      if (cusolverDnXsyevBatched_bufferSize(C->solver, C->solver_params, CUSOLVER_EIG_MODE_VECTOR,
+                                            CUBLAS_FILL_MODE_LOWER, n, CUDA_R_64F, rho + roff[first],
+                                            n, CUDA_R_64F, eval + eoff[first], CUDA_R_64F, &dws,
+                                            &hws, (int64_t)ids.size()) != CUSOLVER_STATUS_SUCCESS)
+        fail(DMRG_ERR_CUDA, "syevBatched bufferSize failed");
+      void *dw = tmp.alloc(std::max<size_t>(dws, 8));
+      std::vector<char> hw(std::max<size_t>(hws, 8));
+      if (cusolverDnXsyevBatched(C->solver, C->solver_params, CUSOLVER_EIG_MODE_VECTOR,
+                                 CUBLAS_FILL_MODE_LOWER, n, CUDA_R_64F, rho + roff[first], n,
+                                 CUDA_R_64F, eval + eoff[first], CUDA_R_64F, dw, dws, hw.data(), hws,
+                                 info + info_off, (int64_t)ids.size()) != CUSOLVER_STATUS_SUCCESS)
+        fail(DMRG_ERR_CUDA, "syevBatched failed");
+      for (size_t j = 0; j < ids.size(); ++j) info_of[ids[j]] = info_off + (int)j;
+      info_off += (int)ids.size();
+      CK(cudaStreamSynchronize(s));   // host workspace lifetime
+    } else {
+      int lw = 0;
+      if (cusolverDnDsyevd_bufferSize(C->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
+                                      (int)n, rho + roff[first], (int)n, eval + eoff[first], &lw) !=
+          CUSOLVER_STATUS_SUCCESS)
+        fail(DMRG_ERR_CUDA, "syevd bufferSize failed");
+      double *wk = (double *)tmp.alloc(8 * (size_t)std::max(lw, 1));
+      if (cusolverDnDsyevd(C->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, (int)n,
+                           rho + roff[first], (int)n, eval + eoff[first], wk, lw, info + info_off) !=
+          CUSOLVER_STATUS_SUCCESS)
+        fail(DMRG_ERR_CUDA, "syevd failed");
+      info_of[first] = info_off++;
+    }
   }
-  double *wk = (double *)tmp.alloc(8 * (size_t)std::max(lwork_max, 1));
-  for (size_t i = 0; i < np; ++i)
-    if (cusolverDnDsyevd(C->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, dim[i],
-                         rho + roff[i], dim[i], eval + eoff[i], wk, lwork_max, info + i) !=
-        CUSOLVER_STATUS_SUCCESS)
-      fail(DMRG_ERR_CUDA, "syevd failed");
-  std::vector<double> ev(eo);
-  std::vector<int> hinfo(np);
-  CK(cudaMemcpyAsync(ev.data(), eval, 8 * eo, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(hinfo.data(), info, sizeof(int) * np, cudaMemcpyDeviceToHost, s));
+  std::vector<double> evp(eo);
+  std::vector<int> hinfo(std::max(info_off, 1));
+  CK(cudaMemcpyAsync(evp.data(), eval, 8 * eo, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(hinfo.data(), info, sizeof(int) * info_off, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  for (int i = 0; i < info_off; ++i)
+    if (hinfo[i] != 0) fail(DMRG_ERR_CUDA, "eigensolver info %d", hinfo[i]);
+  // genuine eigenvalues of block i: the last dim[i] of its npad[i] (ascending)
+  std::vector<double> ev(eo, 0.0);
   for (size_t i = 0; i < np; ++i)
-    if (hinfo[i] != 0) fail(DMRG_ERR_CUDA, "syevd info %d", hinfo[i]);
+    for (int k = 0; k < dim[i]; ++k) ev[eoff[i] + k] = evp[eoff[i] + npad[i] - dim[i] + k];
   // candidates: (-weight, sector, position in descending order)
   struct Cand {
     double v;
@@ -1957,9 +2015,9 @@ void truncate(dmrg_ctx *C, const double *psi, int side, int D, double *disc, dou
   for (size_t j = 0; j < order.size(); ++j) {
     int i = order[j].second;
     std::vector<int> colsel;
-    for (int k : kept[i]) colsel.push_back(dim[i] - 1 - k);
+    for (int k : kept[i]) colsel.push_back(npad[i] - 1 - k);
     int *dc = upload(tmp, colsel, s);
-    CK(launch_select_cols(rho + roff[i], dim[i], dim[i], dc, (int)colsel.size(), T.d + T.off[j], s));
+    CK(launch_select_cols(rho + roff[i], npad[i], dim[i], dc, (int)colsel.size(), T.d + T.off[j], s));
   }
   CK(cudaStreamSynchronize(s));
   C->prof[3] += now() - t0;
@@ -2306,6 +2364,7 @@ int dmrg_destroy(dmrg_ctx *ctx) {
   ctx->R.clear();
   ctx->partbuf.clear();
   ctx->dav.clear();
+  if (ctx->solver_params) cusolverDnDestroyParams(ctx->solver_params);
   if (ctx->solver) cusolverDnDestroy(ctx->solver);
   for (auto &e : ctx->ev)
     if (e) cudaEventDestroy(e);
