@@ -298,16 +298,18 @@ def main():
             serving_out["split"]["solves_per_s"] / max(serving_out["fp64"]["solves_per_s"], 1e-12))
     hbm, bf16, src = peaks()
     tf32_peak = bf16 * TF32_OVER_BF16
-    # roofline of the dominant kernel: the stage with the larger share
-    stA = {"stage1": st_split[1], "stage2": st_split[2]}
-    dom = max(stA, key=stA.get)
     si = g.heff_stage_info()
-    # algorithmic bytes per launch: operators read once (8 B/element as FP64 or
-    # TF32 hi+lo), psi read / sigma written once, the intermediate T written
-    # by stage 1 and read by stage 2 (8 B/element as TF32 hi+lo)
-    st_bytes = {"stage1": 8 * (si["nA"] + si["psi_len"] + si["nT"]),
-                "stage2": 8 * (si["nT"] + si["nB"] + si["psi_len"])}
-    st_flops = {"stage1": si["flops1"], "stage2": si["flops2"]}
+    plan = g.heff_split_plan()
+    # per-stage event marks: [psi split, stage 1, stage 2 + FP64 partial sum]
+    stA = {"stage1": st_split[1], "stage2": st_split[2]}
+    key = max(stA, key=stA.get)
+    dom, t_dom_ms = f"k_tf32_gemm {key}", stA[key]
+    # algorithmic bytes: operators read once (8 B/element as TF32 hi+lo), psi
+    # read once, the intermediate T written by stage 1 and read by stage 2
+    # (hi+lo), sigma written once
+    dom_bytes = {"stage1": 8 * (si["nA"] + si["psi_len"] + si["nT"]),
+                 "stage2": 8 * (si["nT"] + si["nB"] + si["psi_len"])}[key]
+    dom_flops = {"stage1": si["flops1"], "stage2": si["flops2"]}[key]
     line = {
         "metric": "H_eff*psi TFLOP/s", "value": job_value(flops, ms_split, world),
         "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -327,14 +329,15 @@ def main():
         "e2e": {"value": world * flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
                 "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n, "ms_per_step": e2e_ms},
         "clocks": clocks,
-        "gpu_launches": 8 * args.steps,   # per split apply: psi split, 3 + 3 GEMM launches, FP64 sum
-        "roofline": {"kernel": f"k_tf32_gemm {dom}", "bound": "tensor",
+        "split_plan": plan,
+        "gpu_launches": plan["launches"] * args.steps,
+        "roofline": {"kernel": dom, "bound": "tensor",
                      "achieved": None, "peak": tf32_peak, "unit": "TFLOP/s", "frac": None,
                      "peak_source": f"{src} bf16 x nominal tf32/bf16 ratio", "traffic": None},
     }
-    t_dom = stA[dom] * 1e-3
-    gbs = st_bytes[dom] / t_dom / 1e9
-    tfl = 4 * st_flops[dom] / t_dom / 1e12        # tensor work: 4 MMAs per product
+    t_dom = t_dom_ms * 1e-3
+    gbs = dom_bytes / t_dom / 1e9
+    tfl = 4 * dom_flops / t_dom / 1e12        # tensor work: 4 MMAs per product
     f_hbm, f_tc = gbs / hbm, tfl / tf32_peak
     if f_hbm >= f_tc:
         line["roofline"].update({"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
@@ -342,9 +345,9 @@ def main():
     else:
         line["roofline"].update({"achieved": tfl, "frac": f_tc})
     line["roofline"].update({"other": {"hbm_frac": f_hbm, "tensor_frac": f_tc,
-                                       "algorithmic_bytes": st_bytes[dom],
-                                       "tensor_flops_x4": 4 * st_flops[dom],
-                                       "ms_per_launch": stA[dom]}})
+                                       "algorithmic_bytes": dom_bytes,
+                                       "tensor_flops_x4": 4 * dom_flops,
+                                       "ms_per_launch": t_dom_ms}})
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

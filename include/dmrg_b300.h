@@ -227,6 +227,20 @@ int dmrg_heff_timing(dmrg_ctx *ctx, int enable, double *out4);
  * (may be NULL) receives up to max_entries pairs. */
 int dmrg_heff_tuning(dmrg_ctx *ctx, double *out, int max_entries, int *n_entries);
 
+/* Term structure of the window's H_eff: entry i couples input psi block
+ * out[3i] to output block out[3i+1] through out[3i+2] operator products (one
+ * class of terms with a common quantum-number shift).  Writes at most
+ * max_entries triples; *n_entries receives the total (out may be NULL to
+ * query it).  DMRG_ERR_STATE without a window. */
+int dmrg_heff_entries(dmrg_ctx *ctx, int *out, int max_entries, int *n_entries);
+
+/* Shape of the split-precision plan of the current window (built by the
+ * first split apply): out4[0] = kernel launches per apply, out4[1] = stage-1
+ * output tiles, out4[2] = stage-2 output tiles, out4[3] = split-K range of
+ * stage 2 (K elements per partial tile).  DMRG_ERR_STATE before the plan
+ * exists. */
+int dmrg_heff_split_plan(dmrg_ctx *ctx, double *out4);
+
 /* Replay the split-precision apply from captured CUDA graphs (default 1), one
  * graph per (psi, sigma) pointer pair; 0 launches the kernels directly. */
 int dmrg_set_graphs(dmrg_ctx *ctx, int enable);

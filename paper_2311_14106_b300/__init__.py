@@ -30,6 +30,7 @@ HEADER_FUNCTIONS = [
     "dmrg_heff_flops", "dmrg_davidson", "dmrg_truncate", "dmrg_sweep",
     "dmrg_heff_stage_info", "dmrg_heff_timing", "dmrg_profile",
     "dmrg_heff_apply_tf32_static", "dmrg_heff_tuning", "dmrg_set_graphs",
+    "dmrg_heff_split_plan", "dmrg_heff_entries",
 ]
 
 
@@ -73,6 +74,8 @@ _sig = {
     "dmrg_profile": (ctypes.c_int, [_P, _D]),
     "dmrg_heff_tuning": (ctypes.c_int, [_P, _D, ctypes.c_int, _I]),
     "dmrg_set_graphs": (ctypes.c_int, [_P, ctypes.c_int]),
+    "dmrg_heff_split_plan": (ctypes.c_int, [_P, _D]),
+    "dmrg_heff_entries": (ctypes.c_int, [_P, _I, ctypes.c_int, _I]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -256,6 +259,22 @@ class Dmrg:
         self._check(_lib.dmrg_heff_stage_info(self._h, _dptr(out)), "heff_stage_info")
         keys = ["flops1", "flops2", "nA", "nB", "nT", "psi_len"]
         return dict(zip(keys, out.tolist()))
+
+    def heff_entries(self):
+        """H_eff term structure: int array of (psi block in, psi block out, terms)."""
+        n = ctypes.c_int(0)
+        self._check(_lib.dmrg_heff_entries(self._h, None, 0, ctypes.byref(n)), "heff_entries")
+        out = np.zeros(3 * max(n.value, 1), dtype=np.int32)
+        self._check(_lib.dmrg_heff_entries(self._h, out.ctypes.data_as(_I), n.value,
+                                           ctypes.byref(n)), "heff_entries")
+        return out[:3 * n.value].reshape(-1, 3)
+
+    def heff_split_plan(self):
+        """Split-precision plan: launches per apply, stage-1 / stage-2 tiles, split-K range."""
+        out = np.zeros(4)
+        self._check(_lib.dmrg_heff_split_plan(self._h, _dptr(out)), "heff_split_plan")
+        return {"launches": int(out[0]), "tiles1": int(out[1]), "tiles2": int(out[2]),
+                "ksub": int(out[3])}
 
     def heff_timing(self, enable):
         """Start (1) / stop (0) per-stage event timing; returns accumulated

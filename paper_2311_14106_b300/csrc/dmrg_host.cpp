@@ -167,7 +167,7 @@ struct Window {
   void *tbl_ptr[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   size_t tbl_cap[6] = {0, 0, 0, 0, 0, 0};
   std::map<std::pair<const void *, const void *>, cudaGraphExec_t> graphs;
-  std::vector<long long> offA, offB, ldA, ldB;
+  std::vector<long long> offA, ldA, offBp, bpad;
   long long gen = 0;                 // build counter of this window
 };
 
@@ -1186,24 +1186,23 @@ Tf32Scratch tf32_scratch_sizes(const Window &w, int KSUB = KSUB_DEFAULT) {
     const HClass &h = w.hc[E[i].ci];
     const PsiBlk &p = w.psi[E[i].pi], &q = w.psi[E[i].po];
     const long long n = (long long)h.terms.size();
-    z.ldT[i] = r4(n * p.db);
+    z.ldT[i] = r4(p.db);   // T rows (a', k), b padded to 4 floats
     z.offT[i] = z.nT;
-    z.nT += a64(q.da * z.ldT[i]);
+    z.nT += a64(q.da * n * z.ldT[i]);
   }
   for (size_t i = 0; i < np; ++i) {
     z.ldP[i] = r4(w.psi[i].da);
     z.offP[i] = z.nP;
     z.nP += a64(w.psi[i].db * z.ldP[i]);
   }
-  std::vector<long long> Ksum(np, 0);
   for (size_t po = 0; po < np; ++po) {
     long long parts = 0;
     for (size_t i = 0; i < ne; ++i)
       if (E[i].po == (int)po) {
-        const long long K = (long long)w.hc[E[i].ci].terms.size() * w.psi[E[i].pi].db;
+        const long long K = (long long)w.hc[E[i].ci].terms.size() * r4(w.psi[E[i].pi].db);
         parts += (K + KSUB - 1) / KSUB;
       }
-    z.nws += parts * w.psi[po].da * w.psi[po].db;
+    z.nws += a64(parts * w.psi[po].da * r4(w.psi[po].db));
   }
   return z;
 }
@@ -1217,10 +1216,10 @@ void tf32_operator_copies(dmrg_ctx *C) {
   const auto &E = w.s1info;
   const size_t ne = E.size();
   w.offA.assign(ne, 0);
-  w.offB.assign(ne, 0);
   w.ldA.assign(ne, 0);
-  w.ldB.assign(ne, 0);
-  long long nA = 0, nB = 0;
+  w.offBp.assign(ne, 0);
+  w.bpad.assign(ne, 0);
+  long long nA = 0, nBp = 0;
   for (size_t i = 0; i < ne; ++i) {
     const HClass &h = w.hc[E[i].ci];
     const PsiBlk &p = w.psi[E[i].pi], &q = w.psi[E[i].po];
@@ -1228,13 +1227,18 @@ void tf32_operator_copies(dmrg_ctx *C) {
     w.ldA[i] = r4(p.da);
     w.offA[i] = nA;
     nA += a64(q.da * n * w.ldA[i]);
-    w.ldB[i] = r4(n * p.db);
-    w.offB[i] = nB;
-    nB += a64(q.db * w.ldB[i]);
+    w.bpad[i] = r4(p.db);
+    w.offBp[i] = nBp;
+    nBp += a64(q.db * n * w.bpad[i]);
   }
   auto fl = [&](long long n) { return (float *)w.buf.alloc(4 * std::max<long long>(n, 64)); };
   P.A_hi = fl(nA); P.A_lo = fl(nA);
-  P.B_hi = fl(nB); P.B_lo = fl(nB);
+  // B with every term's b segment padded to 4 floats (zeros), so that stage 2
+  // runs over K = (k, b) with b padded and each term starts 16-byte aligned
+  P.Bp_hi = fl(nBp);
+  P.Bp_lo = fl(nBp);
+  CK(cudaMemsetAsync(P.Bp_hi, 0, 4 * std::max<long long>(nBp, 64), s));
+  CK(cudaMemsetAsync(P.Bp_lo, 0, 4 * std::max<long long>(nBp, 64), s));
   std::vector<Split2D> sp;
   for (size_t i = 0; i < ne; ++i) {
     const HClass &h = w.hc[E[i].ci];
@@ -1250,15 +1254,16 @@ void tf32_operator_copies(dmrg_ctx *C) {
     a.lo = P.A_lo + w.offA[i];
     a.dst_ld = w.ldA[i];
     sp.push_back(a);
+    // rows (b', k) of the [b'][k][b] stack, each p.db long, re-strided to bpad
     Split2D b;
     memset(&b, 0, sizeof b);
     b.src = w.Bstack + h.b_off.at(E[i].pi);
-    b.src_ld = (long long)n * p.db;
-    b.rows = q.db;
-    b.cols = n * p.db;
-    b.hi = P.B_hi + w.offB[i];
-    b.lo = P.B_lo + w.offB[i];
-    b.dst_ld = w.ldB[i];
+    b.src_ld = p.db;
+    b.rows = q.db * n;
+    b.cols = p.db;
+    b.hi = P.Bp_hi + w.offBp[i];
+    b.lo = P.Bp_lo + w.offBp[i];
+    b.dst_ld = w.bpad[i];
     sp.push_back(b);
   }
   WinBuf tmp;
@@ -1268,13 +1273,11 @@ void tf32_operator_copies(dmrg_ctx *C) {
   w.tf_copies = true;
 }
 
-void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo, float *T_hi,
-                 float *T_lo, float *ws, Tf32Tables &out, int KSUB = KSUB_DEFAULT) {
-  const Tf32Plan &P = w.tf;
-  const auto &E = w.s1info;
-  const size_t ne = E.size(), np = w.psi.size();
-  out = Tf32Tables();
-  for (size_t i = 0; i < np; ++i) {
+// psi (FP64, [a][b] per sector block) -> TF32 hi/lo, transposed to [b][a]
+std::vector<Split2D> psi_split_descs(const Window &w, const Tf32Scratch &z, float *P_hi,
+                                     float *P_lo) {
+  std::vector<Split2D> out;
+  for (size_t i = 0; i < w.psi.size(); ++i) {
     Split2D d;
     memset(&d, 0, sizeof d);
     d.src = nullptr;
@@ -1286,8 +1289,18 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo
     d.hi = P_hi + z.offP[i];
     d.lo = P_lo + z.offP[i];
     d.dst_ld = z.ldP[i];
-    out.psi_split.push_back(d);
+    out.push_back(d);
   }
+  return out;
+}
+
+void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo, float *T_hi,
+                 float *T_lo, float *ws, Tf32Tables &out, int KSUB = KSUB_DEFAULT) {
+  const Tf32Plan &P = w.tf;
+  const auto &E = w.s1info;
+  const size_t ne = E.size(), np = w.psi.size();
+  out = Tf32Tables();
+  out.psi_split = psi_split_descs(w, z, P_hi, P_lo);
   auto &maps = out.maps;
   auto mk = [&](const float *base, long long rows, long long cols, long long ld, int box) {
     CUtensorMap m;
@@ -1308,17 +1321,31 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo
   auto &w2 = out.w2;
   std::vector<std::vector<int>> into(np);
   std::vector<int> mThi(ne), mTlo(ne), mBhi(ne), mBlo(ne);
+  auto mk3 = [&](const float *base, long long d0, long long d1, long long d2, long long s1,
+                 long long s2) {
+    CUtensorMap m;
+    int rc = encode_map3(&m, base, d0, d1, d2, s1, s2, 32, 32, 1);
+    if (rc != 0) fail(DMRG_ERR_CUDA, "cuTensorMapEncodeTiled (store) failed (%d)", rc);
+    maps.push_back(m);
+    return (int)maps.size() - 1;
+  };
   for (size_t i = 0; i < ne; ++i) {
     const HClass &h = w.hc[E[i].ci];
     const PsiBlk &p = w.psi[E[i].pi], &q = w.psi[E[i].po];
     const int n = (int)h.terms.size();
+    const long long bp = z.ldT[i];   // = r4(p.db)
     int ahi = mk(P.A_hi + w.offA[i], (long long)q.da * n, p.da, w.ldA[i], 128);
     int alo = mk(P.A_lo + w.offA[i], (long long)q.da * n, p.da, w.ldA[i], 128);
-    mThi[i] = mk(T_hi + z.offT[i], q.da, (long long)n * p.db, z.ldT[i], 128);
-    mTlo[i] = mk(T_lo + z.offT[i], q.da, (long long)n * p.db, z.ldT[i], 128);
+    // T as stage-1 output: rows (a', k), columns b (padded); as stage-2
+    // operand: rows a', K = (k, b)
+    const long long rowsT = (long long)q.da * n;
+    const int sThi = mk3(T_hi + z.offT[i], bp, rowsT, 1, bp, rowsT * bp);
+    const int sTlo = mk3(T_lo + z.offT[i], bp, rowsT, 1, bp, rowsT * bp);
+    mThi[i] = mk(T_hi + z.offT[i], q.da, (long long)n * bp, (long long)n * bp, 128);
+    mTlo[i] = mk(T_lo + z.offT[i], q.da, (long long)n * bp, (long long)n * bp, 128);
     int bbox = ntile_of(q.db);
-    mBhi[i] = mk(P.B_hi + w.offB[i], q.db, (long long)n * p.db, w.ldB[i], bbox);
-    mBlo[i] = mk(P.B_lo + w.offB[i], q.db, (long long)n * p.db, w.ldB[i], bbox);
+    mBhi[i] = mk(P.Bp_hi + w.offBp[i], q.db, (long long)n * w.bpad[i], (long long)n * w.bpad[i], bbox);
+    mBlo[i] = mk(P.Bp_lo + w.offBp[i], q.db, (long long)n * w.bpad[i], (long long)n * w.bpad[i], bbox);
     TSeg sg;
     sg.mA_hi = ahi; sg.mA_lo = alo; sg.mB_hi = mPhi[E[i].pi]; sg.mB_lo = mPlo[E[i].pi];
     sg.K = p.da;
@@ -1334,25 +1361,22 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo
         memset(&t, 0, sizeof t);
         t.seg0 = seg; t.nseg = 1;
         t.M = M; t.N = N; t.m0 = m0; t.n0 = n0; t.ntile = nt;
-        t.mode = 0; t.alpha = alpha;
-        t.out_hi = T_hi + z.offT[i];
-        t.out_lo = T_lo + z.offT[i];
-        t.nrep = n; t.rep = p.db; t.ld = z.ldT[i];
+        t.mode = TW_SPLIT; t.alpha = alpha;
+        t.mOut_hi = sThi; t.mOut_lo = sTlo; t.zout = 0;
         w1.push_back(t);
       }
     into[E[i].po].push_back((int)i);
   }
-  // stage 2: the long K (all terms x psi columns) is cut into ranges of at
-  // most KSUB; each range is one work item writing an FP32 partial tile, and
-  // the partials are summed in FP64 (fixed order).
+  // stage 2: the long K (all terms x padded psi columns) is cut into ranges
+  // of at most KSUB; each range is one work item writing an FP32 partial
+  // tile, and the partials are summed in FP64 (fixed order).
   long long wsn = 0;
   for (size_t po = 0; po < np; ++po) {
     const PsiBlk &q = w.psi[po];
     std::vector<TSeg> ranges;
     for (int i : into[po]) {
       const HClass &h = w.hc[E[i].ci];
-      const PsiBlk &p = w.psi[E[i].pi];
-      const int K = (int)h.terms.size() * p.db;
+      const int K = (int)(h.terms.size() * w.bpad[i]);
       for (int k0 = 0; k0 < K; k0 += KSUB) {
         TSeg sg;
         sg.mA_hi = mThi[i]; sg.mA_lo = mTlo[i]; sg.mB_hi = mBhi[i]; sg.mB_lo = mBlo[i];
@@ -1361,15 +1385,20 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo
         ranges.push_back(sg);
       }
     }
-    const long long blk = (long long)q.da * q.db;
+    const long long ldw = r4(q.db), blk = (long long)q.da * ldw;
     const int nparts = (int)ranges.size();
     PartialSum ps;
+    memset(&ps, 0, sizeof ps);
     ps.ws = ws + wsn;
     ps.stride = blk;
     ps.off = q.off;
-    ps.n = (int)blk;
-    ps.nparts = nparts;
+    ps.ld = ldw;
+    ps.n = q.da * q.db;
+    ps.cols = q.db;
+    ps.nparts = nparts;   // 0: no term reaches this block, sigma = 0
     out.psums.push_back(ps);
+    if (nparts == 0) continue;
+    const int mW = mk3(ws + wsn, q.db, q.da, nparts, ldw, blk);
     const int M = q.da, N = q.db, nt = ntile_of(N);
     for (int pi = 0; pi < nparts; ++pi) {
       int seg = (int)segs.size();
@@ -1380,13 +1409,12 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo
           memset(&t, 0, sizeof t);
           t.seg0 = seg; t.nseg = 1;
           t.M = M; t.N = N; t.m0 = m0; t.n0 = n0; t.ntile = nt;
-          t.mode = 2; t.alpha = 1.f;
-          t.ld = q.db;
-          t.out32 = ws + wsn + (long long)pi * blk;
+          t.mode = TW_PARTIAL; t.alpha = 1.f;
+          t.mOut_hi = mW; t.mOut_lo = mW; t.zout = pi;
           w2.push_back(t);
         }
     }
-    wsn += (long long)nparts * blk;
+    wsn += a64((long long)nparts * blk);
   }
   if (wsn > z.nws) fail(DMRG_ERR_STATE, "internal: partial-tile workspace size");
   // persistent CTAs take work items round-robin: order them by cost (K chunks
@@ -1519,9 +1547,9 @@ void launch_tf32(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s) 
   mark(C, 0, s);
   CK(launch_split2d((const Split2D *)P.psi_split, P.npsi, s, psi));
   mark(C, 1, s);
-  CK(tf32_gemm(P.work1, P.n1, P.seg, P.maps, nullptr, P.err, s));
+  CK(tf32_gemm(P.work1, P.n1, P.seg, P.maps, P.err, s));
   mark(C, 2, s);
-  CK(tf32_gemm(P.work2, P.n2, P.seg, P.maps, sigma, P.err, s));
+  CK(tf32_gemm(P.work2, P.n2, P.seg, P.maps, P.err, s));
   CK(sum_partials(P.psum, P.npsum, sigma, s));
   mark(C, 3, s);
 }
@@ -2700,9 +2728,9 @@ int dmrg_heff_apply_tf32_static(dmrg_ctx *C, const double *psi, double *sigma, v
     CK(cudaMemsetAsync(err, 0, sizeof(int), s));   // the only state that must start at zero
     CK(launch_split2d((const Split2D *)(b + ow.o_split), (int)t.psi_split.size(), s, psi));
     CK(tf32_gemm((const TWork *)(b + ow.o_w1), t.n1, (const TSeg *)(b + ow.o_seg),
-                 (const CUtensorMap *)(b + ow.o_maps), nullptr, err, s));
+                 (const CUtensorMap *)(b + ow.o_maps), err, s));
     CK(tf32_gemm((const TWork *)(b + ow.o_w2), t.n2, (const TSeg *)(b + ow.o_seg),
-                 (const CUtensorMap *)(b + ow.o_maps), sigma, err, s));
+                 (const CUtensorMap *)(b + ow.o_maps), err, s));
     CK(sum_partials((const PartialSum *)(b + ow.o_ps), (int)t.psums.size(), sigma, s));
   });
 }
@@ -2747,6 +2775,41 @@ int dmrg_heff_stage_info(dmrg_ctx *C, double *out6) {
   out6[3] = (double)w.nB;
   out6[4] = (double)w.nT;
   out6[5] = (double)w.psi_len;
+  return DMRG_OK;
+}
+
+int dmrg_heff_split_plan(dmrg_ctx *C, double *out4) {
+  if (!C || !out4) return DMRG_ERR_ARG;
+  const Window &w = C->win;
+  if (!w.valid || !w.tf_ready) {
+    C->err = "split plan not built: apply once with DMRG_SPLIT_TF32 first";
+    return DMRG_ERR_STATE;
+  }
+  const Tf32Plan &P = w.tf;
+  int launches = 1 + (P.npsum > 0 ? 1 : 0);
+  for (int i = 0; i < 3; ++i) launches += (P.n1[i] > 0) + (P.n2[i] > 0);
+  out4[0] = launches;
+  out4[1] = P.nwork1;
+  out4[2] = P.nwork2;
+  out4[3] = (double)w.ksub;
+  return DMRG_OK;
+}
+
+int dmrg_heff_entries(dmrg_ctx *C, int *out, int max_entries, int *n_entries) {
+  if (!C || !n_entries) return DMRG_ERR_ARG;
+  const Window &w = C->win;
+  if (!w.valid) {
+    C->err = "no window built";
+    return DMRG_ERR_STATE;
+  }
+  *n_entries = (int)w.s1info.size();
+  if (out)
+    for (int i = 0; i < std::min(max_entries, *n_entries); ++i) {
+      const S1 &e = w.s1info[i];
+      out[3 * i] = e.pi;
+      out[3 * i + 1] = e.po;
+      out[3 * i + 2] = (int)w.hc[e.ci].terms.size();
+    }
   return DMRG_OK;
 }
 

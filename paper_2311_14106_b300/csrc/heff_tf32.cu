@@ -25,7 +25,7 @@ constexpr int BK = 32;            // floats per 128-byte swizzle row
 constexpr int TILE_A = BM * BK * 4;          // 16 KB
 constexpr int MAX_SMEM = 232448;             // 227 KB per CTA
 constexpr int NACC = 4;                      // TMEM accumulators (4 x 128 columns)
-constexpr int STAGE_OUT = 4 * 32 * 33 * 4;   // epilogue transpose buffers
+constexpr int STAGE_OUT = 4 * 2 * 4096;      // epilogue staging: 4 warps x (hi, lo) 32 x 32
 
 // Pipeline geometry for a launch whose tiles are at most NT columns wide:
 // a stage holds A_hi, A_lo (128 x 32 each) and B_hi, B_lo (NT x 32 each).
@@ -121,6 +121,34 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void st_shared_v4(uint32_t a, float x, float y, float z, float w) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(x), "f"(y), "f"(z), "f"(w)
+               : "memory");
+}
+
+// shared -> global tile store through a 3-D tensor map (bulk async group)
+__device__ __forceinline__ void tma_store3d(const CUtensorMap *map, int x, int y, int z,
+                                            uint32_t src) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+          (uint64_t)map),
+      "r"(x), "r"(y), "r"(z), "r"(src)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// the staging buffer may be rewritten once the stores issued so far read it
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 __device__ __forceinline__ float tf32_round(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -157,16 +185,15 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t a, uint32_t parity, int *
 template <int NT>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__ segs,
-            const CUtensorMap *__restrict__ maps, double *__restrict__ out64,
-            int *__restrict__ err) {
+            const CUtensorMap *__restrict__ maps, int *__restrict__ err) {
   using G = Geo<NT>;
   constexpr int STAGES = G::STAGES;
   constexpr int STAGE_BYTES = G::STAGE_BYTES;
   constexpr int TILE_B = G::TILE_B;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  Shared *sh = (Shared *)(smem + STAGES * STAGE_BYTES);
-  float(*stage_out)[32][33] = (float(*)[32][33])(smem + STAGES * STAGE_BYTES + 512);
+  uint8_t *stage_out = smem + STAGES * STAGE_BYTES;      // 1024-byte aligned
+  Shared *sh = (Shared *)(stage_out + STAGE_OUT);
   volatile int *abort_flag = &sh->abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -263,7 +290,14 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
     }
   } else {
     // ---------------- epilogue (warps 2..5) ----------------
+    // Each lane holds one accumulator row.  Per 32-column block the warp
+    // stages its 32 x 32 sub-tile in shared memory in the 128-byte-swizzled
+    // box layout (16-byte chunk q of row r at position q ^ (r & 7)) and one
+    // lane stores it by TMA; the tensor map clips rows and columns outside
+    // the destination.
     const int quarter = warp & 3;            // TMEM lanes 32*quarter .. +31
+    const uint32_t stg_hi = smem_u32(stage_out + (warp - 2) * 8192), stg_lo = stg_hi + 4096;
+    const uint32_t rowoff = (uint32_t)lane * 128;
     int j = 0;
     for (int t = blockIdx.x; t < nwork; t += gridDim.x, ++j) {
       const TWork w = works[t];
@@ -271,65 +305,10 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
       const uint32_t aph = (j / NACC) & 1;
       if (!wait_or_abort(smem_u32(&sh->acc_full[acc]), aph, err, 4, abort_flag)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // Each lane holds one accumulator row.  When the warp's rows are one
-      // contiguous run of the output (all columns of the tile, one block row
-      // of T), they are staged in shared memory in destination order, R rows
-      // at a time (R x nt <= 1024 floats), and stored as a flat coalesced
-      // stream; otherwise each row's 32-column blocks are transposed through
-      // shared memory and stored as 128-byte runs.
       const int row0 = w.m0 + quarter * 32;
-      const int nt = min(w.ntile, w.N - w.n0);          // valid columns
-      const int rv = min(32, w.M - row0);               // valid rows
       const uint32_t tbase = tmem + acc * ACC_COLS + ((uint32_t)(quarter * 32) << 16);
-      float(*tile)[33] = stage_out[warp - 2];
-      float *flat = &tile[0][0];
-      bool contiguous = false;
-      long long base = 0;
-      if (w.n0 == 0 && rv > 0) {
-        if (w.mode == 0) {
-          const int a0 = row0 / w.nrep, k0 = row0 - a0 * w.nrep;
-          contiguous = (nt == w.rep && k0 + rv <= w.nrep);
-          base = (long long)a0 * w.ld + (long long)k0 * w.rep;
-        } else if (w.mode == 2) {
-          contiguous = (nt == w.ld);
-          base = (long long)row0 * w.ld;
-        }
-      }
-      if (contiguous) {
-        const int R = nt >= 32 ? 1024 / nt : 32;           // rows per phase
-        for (int r0 = 0; r0 < rv; r0 += R) {
-          const bool mine = lane >= r0 && lane < r0 + R;
-          for (int c0 = 0; c0 < w.ntile; c0 += 16) {
-            float v[16];
-            tmem_ld16(tbase + c0, v);
-            if (mine) {
-#pragma unroll
-              for (int i = 0; i < 16; ++i) {
-                const int c = c0 + i;
-                if (c < nt) {
-                  const int e = (lane - r0) * nt + c;
-                  flat[e + (e >> 5)] = w.alpha * v[i];
-                }
-              }
-            }
-          }
-          __syncwarp();
-          const int ne = min(R, rv - r0) * nt;
-          const long long b0 = base + (long long)r0 * nt;
-          if (w.mode == 0) {
-            for (int e = lane; e < ne; e += 32) {
-              const float x = flat[e + (e >> 5)];
-              const float h = tf32_round(x);
-              w.out_hi[b0 + e] = h;
-              w.out_lo[b0 + e] = tf32_round(x - h);
-            }
-          } else {
-            for (int e = lane; e < ne; e += 32) w.out32[b0 + e] = flat[e + (e >> 5)];
-          }
-          __syncwarp();
-        }
-      } else {
-        for (int c0 = 0; c0 < w.ntile; c0 += 32) {
+      if (row0 < w.M) {
+        for (int c0 = 0; c0 < w.ntile && w.n0 + c0 < w.N; c0 += 32) {
           float v[32];
           tmem_ld16(tbase + c0, v);
           if (c0 + 16 < w.ntile) {
@@ -338,37 +317,43 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
 #pragma unroll
             for (int i = 16; i < 32; ++i) v[i] = 0.f;
           }
-          const int ncol = min(32, nt - c0);
-          if (ncol > 0) {
-#pragma unroll
-            for (int i = 0; i < 32; ++i) tile[lane][i] = w.alpha * v[i];
-            __syncwarp();
-            const int col = w.n0 + c0 + lane;
-            const bool cok = lane < ncol;
-            for (int rr = 0; rr < rv; ++rr) {
-              const int row = row0 + rr;
-              if (!cok) continue;
-              const float x = tile[rr][lane];
-              if (w.mode == 0) {
-                const long long o = (long long)(row / w.nrep) * w.ld +
-                                    (long long)(row % w.nrep) * w.rep + col;
-                const float h = tf32_round(x);
-                w.out_hi[o] = h;
-                w.out_lo[o] = tf32_round(x - h);
-              } else if (w.mode == 1) {
-                out64[w.off64 + (long long)row * w.ld + col] = (double)x;
-              } else {
-                w.out32[(long long)row * w.ld + col] = x;
-              }
-            }
-          }
+          if (lane == 0) bulk_wait_read();
           __syncwarp();
+          if (w.mode == TW_SPLIT) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              float h[4], l[4];
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                const float x = w.alpha * v[4 * q + i];
+                h[i] = tf32_round(x);
+                l[i] = tf32_round(x - h[i]);
+              }
+              const uint32_t o = rowoff + ((uint32_t)(q ^ (lane & 7)) << 4);
+              st_shared_v4(stg_hi + o, h[0], h[1], h[2], h[3]);
+              st_shared_v4(stg_lo + o, l[0], l[1], l[2], l[3]);
+            }
+          } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+              st_shared_v4(stg_hi + rowoff + ((uint32_t)(q ^ (lane & 7)) << 4), v[4 * q],
+                           v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+          }
+          fence_async_shared();
+          __syncwarp();
+          if (lane == 0) {
+            tma_store3d(&maps[w.mOut_hi], w.n0 + c0, row0, w.zout, stg_hi);
+            if (w.mode == TW_SPLIT) tma_store3d(&maps[w.mOut_lo], w.n0 + c0, row0, w.zout, stg_lo);
+            bulk_commit();
+          }
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&sh->acc_empty[acc]))
                    : "memory");
     }
+    if (lane == 0) bulk_wait_all();
+    __syncwarp();
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -385,7 +370,9 @@ __global__ void k_sum_partials(const PartialSum *__restrict__ ps, double *__rest
   const PartialSum p = ps[blockIdx.y];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += gridDim.x * blockDim.x) {
     double acc = 0.0;
-    for (int k = 0; k < p.nparts; ++k) acc += (double)p.ws[k * p.stride + i];
+    const long long r = i / p.cols, c = i - r * p.cols;
+    const float *src = p.ws + r * p.ld + c;
+    for (int k = 0; k < p.nparts; ++k) acc += (double)src[k * p.stride];
     sigma[p.off + i] = acc;
   }
 }
@@ -413,6 +400,31 @@ int encode_map(CUtensorMap *out, const float *base, int rows, int cols, long lon
   cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : -3;
+}
+
+int encode_map3(CUtensorMap *out, const float *base, long long d0, long long d1, long long d2,
+                long long s1, long long s2, int box0, int box1, int box2) {
+  static const EncodeFn fn = [] {
+    cudaDriverEntryPointQueryResult q;
+    void *p = nullptr;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return (EncodeFn) nullptr;
+    return (EncodeFn)p;
+  }();
+  if (!fn) return -1;
+  if (((uintptr_t)base & 15) || (s1 & 3) || (s2 & 3) || d0 <= 0 || d1 <= 0 || d2 <= 0 ||
+      box0 * 4 > 128)
+    return -2;
+  cuuint64_t dims[3] = {(cuuint64_t)d0, (cuuint64_t)d1, (cuuint64_t)d2};
+  cuuint64_t strides[2] = {(cuuint64_t)s1 * 4, (cuuint64_t)s2 * 4};
+  cuuint32_t box[3] = {(cuuint32_t)box0, (cuuint32_t)box1, (cuuint32_t)box2};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)base, dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : -3;
@@ -451,22 +463,22 @@ int sm_count() {
 // (the shared-memory attributes are set by tf32_prepare, outside any capture)
 template <int NT>
 cudaError_t launch_nt(const TWork *work, int nwork, const TSeg *seg, const CUtensorMap *maps,
-                      double *out64, int *err, cudaStream_t s) {
+                      int *err, cudaStream_t s) {
   if (nwork <= 0) return cudaSuccess;
   const int nsm = sm_count();
   const int grid = nwork < nsm ? nwork : nsm;
-  k_tf32_gemm<NT><<<grid, NTHREADS, Geo<NT>::SMEM_BYTES, s>>>(work, nwork, seg, maps, out64, err);
+  k_tf32_gemm<NT><<<grid, NTHREADS, Geo<NT>::SMEM_BYTES, s>>>(work, nwork, seg, maps, err);
   return cudaGetLastError();
 }
 
 cudaError_t tf32_gemm(const TWork *work, const int *nwork3, const TSeg *seg,
-                      const CUtensorMap *maps, double *out64, int *err, cudaStream_t s) {
+                      const CUtensorMap *maps, int *err, cudaStream_t s) {
   // work items are grouped by tile width: [<= 32 | <= 64 | <= 128]
-  cudaError_t e = launch_nt<32>(work, nwork3[0], seg, maps, out64, err, s);
+  cudaError_t e = launch_nt<32>(work, nwork3[0], seg, maps, err, s);
   if (e != cudaSuccess) return e;
-  e = launch_nt<64>(work + nwork3[0], nwork3[1], seg, maps, out64, err, s);
+  e = launch_nt<64>(work + nwork3[0], nwork3[1], seg, maps, err, s);
   if (e != cudaSuccess) return e;
-  return launch_nt<128>(work + nwork3[0] + nwork3[1], nwork3[2], seg, maps, out64, err, s);
+  return launch_nt<128>(work + nwork3[0] + nwork3[1], nwork3[2], seg, maps, err, s);
 }
 
 }  // namespace dmrg

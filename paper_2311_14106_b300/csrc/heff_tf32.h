@@ -20,38 +20,42 @@ struct TSeg {
   int k0;            // first K index (multiple of 32)
 };
 
-// One 128 x ntile output tile.
+// Epilogue of a work item.
+enum { TW_SPLIT = 0,      // alpha * C split into TF32 (hi, lo), stored to T
+       TW_PARTIAL = 1 };  // C stored as an FP32 partial tile (split-K slot)
+
+// One 128 x ntile output tile.  The epilogue stores it by TMA through 3-D
+// tensor maps (x column, y row, z slot) with 32 x 32 boxes; the maps clip
+// rows and columns outside the destination.
 struct TWork {
   int seg0, nseg;
-  int M, N;          // full problem extent (for masking)
+  int M, N;          // full problem extent (rows, columns)
   int m0, n0;        // tile origin
   int ntile;         // UMMA N of this tile (multiple of 16, <= 128)
-  int mode;          // 0: write split TF32 (hi, lo) to T; 1: write FP64;
-                     // 2: write an FP32 partial tile (split-K)
+  int mode;          // TW_SPLIT or TW_PARTIAL
   float alpha;
-  // mode 0: element (r, c) -> base + (r / nrep) * ld + (r % nrep) * rep + c
-  float *out_hi, *out_lo;
-  int nrep, rep;
-  long long ld;
-  // mode 1: element (r, c) -> out64[off64 + r * ld + c] (bound sigma)
-  long long off64;
-  // mode 2: element (r, c) -> out32[r * ld + c]
-  float *out32;
+  int mOut_hi, mOut_lo;   // store maps (mOut_lo unused for TW_PARTIAL)
+  int zout;               // z coordinate of the destination (partial slot)
 };
 
-// FP64 sum of the split-K partial tiles of one sigma block:
-// sigma[off + i] = sum_p ws[p * stride + i], i < n (fixed order).
+// FP64 sum of the split-K partial tiles of one sigma block (rows x cols,
+// partial rows ld floats apart): sigma[off + r*cols + c] =
+// sum_p ws[p*stride + r*ld + c], summed in a fixed order.
 struct PartialSum {
   const float *ws;
   long long stride;
   long long off;
-  int n;
+  long long ld;
+  int n;             // rows * cols
+  int cols;
   int nparts;
+  int pad;
 };
 
 struct Tf32Plan {
   // split operand storage (float, padded rows)
-  float *A_hi = nullptr, *A_lo = nullptr, *B_hi = nullptr, *B_lo = nullptr;
+  float *A_hi = nullptr, *A_lo = nullptr;     // [a'][k][a], rows 16-byte aligned
+  float *Bp_hi = nullptr, *Bp_lo = nullptr;   // [b'][k][b], b padded to 4 floats
   float *P_hi = nullptr, *P_lo = nullptr, *T_hi = nullptr, *T_lo = nullptr;
   CUtensorMap *maps = nullptr;      // device copy of the tensor maps
   TSeg *seg = nullptr;
@@ -72,6 +76,11 @@ struct Tf32Plan {
 int encode_map(CUtensorMap *out, const float *base, int rows, int cols, long long ld,
                int box_rows);
 
+// Encode a 3-D tensor map (d0 innermost; strides s1, s2 in floats, multiples
+// of 4) with a (box0 x box1 x box2) box and 128-byte swizzle (box0 = 32).
+int encode_map3(CUtensorMap *out, const float *base, long long d0, long long d1, long long d2,
+                long long s1, long long s2, int box0, int box1, int box2);
+
 // Device address and size of the fixed scratch array (heff_static.cu); the
 // first call on a device looks the address up.
 cudaError_t static_scratch(void **ptr, size_t *bytes);
@@ -84,6 +93,6 @@ cudaError_t tf32_prepare();
 // work holds nwork3[0] items with ntile <= 32, then nwork3[1] with ntile <= 64,
 // then nwork3[2] with ntile <= 128 (one launch each, pipeline sized to the width).
 cudaError_t tf32_gemm(const TWork *work, const int *nwork3, const TSeg *seg,
-                      const CUtensorMap *maps, double *out64, int *err, cudaStream_t s);
+                      const CUtensorMap *maps, int *err, cudaStream_t s);
 
 }  // namespace dmrg

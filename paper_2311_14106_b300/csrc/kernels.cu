@@ -277,10 +277,14 @@ __global__ void k_split2d(const Split2D *__restrict__ ds, const double *__restri
 }
 
 cudaError_t launch_split2d(const Split2D *d, int n, cudaStream_t s, const double *bind) {
-  if (n <= 0) return cudaSuccess;
-  dim3 grid(128, 1, n), block(32, 8);
-  k_split2d<<<grid, block, 0, s>>>(d, bind);
-  return cudaGetLastError();
+  // grid.z is limited to 65535: launch in chunks of descriptors
+  for (int i0 = 0; i0 < n; i0 += 65535) {
+    dim3 grid(128, 1, n - i0 < 65535 ? n - i0 : 65535), block(32, 8);
+    k_split2d<<<grid, block, 0, s>>>(d + i0, bind);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 // ----------------------------------------------------------------------------

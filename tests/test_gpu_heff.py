@@ -89,6 +89,8 @@ def test_heff_fp64_and_split_vs_oracle(name, Lx, Ly, spinful, target, D, l):
     g.set_precision(lib.SPLIT_TF32)
     s32 = g.heff_apply_host(psi)
     assert rel(s32, ref) <= TOL_SPLIT, rel(s32, ref)
+    # repeated applies (graph replay) are bitwise reproducible
+    assert np.array_equal(g.heff_apply_host(psi), s32)
     # device-pointer entry point agrees with the host one
     x = torch.tensor(psi, device="cuda")
     y = torch.empty_like(x)
