@@ -4,8 +4,9 @@
 // Stage 1:  T[(a',k), b]  = sign * A_stack[(a',k), a] . psi[a, b]
 // Stage 2:  sigma[a', b'] = sum_segments T[a', (k,b)] . B_stack[b', (k,b)]^T
 // Both are C = A . B^T with K-major operands.  Each FP64 operand x is held as
-// x_hi + x_lo (TF32 each); the product uses all four cross terms
-// (lo.lo + lo.hi + hi.lo + hi.hi) with FP32 accumulation in tensor memory.  A work item is one 128 x ntile output tile;
+// x_hi + x_lo (TF32 each); a product is lo.hi + hi.lo + hi.hi (lo.lo, of
+// relative size 2^-22, is below the FP32 accumulation error) with FP32
+// accumulation in tensor memory.  A work item is one 128 x ntile output tile;
 // per 32-wide K chunk the producer loads A_hi, A_lo, B_hi, B_lo by TMA and the
 // MMA warp issues 4 k-steps x 4 tcgen05.mma.
 // Every mbarrier wait is bounded; on timeout the kernel records an error
@@ -261,7 +262,8 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
         const uint32_t d = tmem + acc * ACC_COLS;
         uint32_t accum = 0;
         for (int s = 0; s < w.nseg; ++s) {
-          const int nk = (segs[w.seg0 + s].K + BK - 1) / BK;
+          const int K = segs[w.seg0 + s].K;
+          const int nk = (K + BK - 1) / BK;
           for (int kc = 0; kc < nk; ++kc, ++it) {
             const int st = it % STAGES;
             const uint32_t ph = (it / STAGES) & 1;
@@ -271,13 +273,15 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
             const uint32_t a_lo = a_hi + TILE_A;
             const uint32_t b_hi = a_hi + 2 * TILE_A;
             const uint32_t b_lo = b_hi + TILE_B;
-#pragma unroll
-            for (int k = 0; k < BK / 8; ++k) {
+            // k-steps of 8 that hold data (the rest of a ragged chunk is zero fill)
+            const int rem = K - kc * BK;
+            const int nk8 = rem >= BK ? BK / 8 : (rem + 7) / 8;
+            for (int k = 0; k < nk8; ++k) {
               const uint32_t ko = k * 32;   // 8 tf32 = 32 bytes along the swizzled row
-              // small terms first: lo.lo, lo.hi, hi.lo, then hi.hi
-              mma_tf32(d, sdesc(a_lo + ko), sdesc(b_lo + ko), id, accum);
+              // small terms first: lo.hi, hi.lo, then hi.hi (lo.lo is below
+              // the FP32 accumulation error and is left out)
+              mma_tf32(d, sdesc(a_lo + ko), sdesc(b_hi + ko), id, accum);
               accum = 1;
-              mma_tf32(d, sdesc(a_lo + ko), sdesc(b_hi + ko), id, 1);
               mma_tf32(d, sdesc(a_hi + ko), sdesc(b_lo + ko), id, 1);
               mma_tf32(d, sdesc(a_hi + ko), sdesc(b_hi + ko), id, 1);
             }
@@ -366,13 +370,23 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
 
 }  // namespace
 
+// One thread per sigma element; the partials are added in slot order (eight
+// loads in flight per step), so the result does not depend on the launch.
 __global__ void k_sum_partials(const PartialSum *__restrict__ ps, double *__restrict__ sigma) {
   const PartialSum p = ps[blockIdx.y];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += gridDim.x * blockDim.x) {
-    double acc = 0.0;
     const long long r = i / p.cols, c = i - r * p.cols;
     const float *src = p.ws + r * p.ld + c;
-    for (int k = 0; k < p.nparts; ++k) acc += (double)src[k * p.stride];
+    double acc = 0.0;
+    int k = 0;
+    for (; k + 8 <= p.nparts; k += 8) {
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = __ldg(src + (long long)(k + j) * p.stride);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc += (double)v[j];
+    }
+    for (; k < p.nparts; ++k) acc += (double)src[(long long)k * p.stride];
     sigma[p.off + i] = acc;
   }
 }
@@ -432,7 +446,7 @@ int encode_map3(CUtensorMap *out, const float *base, long long d0, long long d1,
 
 cudaError_t sum_partials(const PartialSum *p, int n, double *sigma, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  dim3 grid(8, n);
+  dim3 grid(64, n);   // blocks beyond a block's elements exit at once
   k_sum_partials<<<grid, 256, 0, s>>>(p, sigma);
   return cudaGetLastError();
 }
