@@ -1377,6 +1377,13 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo
   // (fused blocks: A_k rows a' at stride n*ldA, B_k rows b' at stride n*bpad)
   std::vector<int> mThi(ne), mTlo(ne), mBhi(ne), mBlo(ne);
   std::vector<std::array<int, 4>> m3(ne);
+  // stage-2 packing of small sigma blocks: R segments per 128 x 128 tile
+  std::vector<int> Rq(np, 1);
+  for (size_t po = 0; po < np; ++po) {
+    const PsiBlk &q = w.psi[po];
+    if (fz && fused_block(q)) continue;
+    Rq[po] = (q.da <= 32 && q.db <= 32) ? 4 : ((q.da <= 64 && q.db <= 64) ? 2 : 1);
+  }
   std::vector<float> alpha(ne);
   for (size_t i = 0; i < ne; ++i) {
     const HClass &h = w.hc[E[i].ci];
@@ -1402,9 +1409,10 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo
     const long long rowsT = (long long)q.da * n;
     const int sThi = mk3(T_hi + z.offT[i], bp, rowsT, 1, bp, rowsT * bp, 32, 32, 1);
     const int sTlo = mk3(T_lo + z.offT[i], bp, rowsT, 1, bp, rowsT * bp, 32, 32, 1);
-    mThi[i] = mk(T_hi + z.offT[i], q.da, (long long)n * bp, (long long)n * bp, 128);
-    mTlo[i] = mk(T_lo + z.offT[i], q.da, (long long)n * bp, (long long)n * bp, 128);
-    int bbox = ntile_of(q.db);
+    const int R = Rq[E[i].po];
+    mThi[i] = mk(T_hi + z.offT[i], q.da, (long long)n * bp, (long long)n * bp, 128 / R);
+    mTlo[i] = mk(T_lo + z.offT[i], q.da, (long long)n * bp, (long long)n * bp, 128 / R);
+    int bbox = R > 1 ? 128 / R : ntile_of(q.db);
     mBhi[i] = mk(P.Bp_hi + w.offBp[i], q.db, (long long)n * w.bpad[i], (long long)n * w.bpad[i], bbox);
     mBlo[i] = mk(P.Bp_lo + w.offBp[i], q.db, (long long)n * w.bpad[i], (long long)n * w.bpad[i], bbox);
     TSeg sg;
@@ -1429,6 +1437,10 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo
   // tile; the partials are summed in FP64 in a fixed order.
   long long wsn = 0;
   std::vector<long long> fcost;
+  struct PackCand {
+    int seg, mOut, z, R, nchunk;
+  };
+  std::vector<PackCand> pk;
   for (size_t po = 0; po < np; ++po) {
     const PsiBlk &q = w.psi[po];
     const long long ldw = r4(q.db), blk = (long long)q.da * ldw;
@@ -1495,9 +1507,11 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo
       const int K = (int)(h.terms.size() * w.bpad[i]);
       for (int k0 = 0; k0 < K; k0 += KSUB) {
         TSeg sg;
+        memset(&sg, 0, sizeof sg);
         sg.mA_hi = mThi[i]; sg.mA_lo = mTlo[i]; sg.mB_hi = mBhi[i]; sg.mB_lo = mBlo[i];
         sg.k0 = k0;
         sg.K = std::min(KSUB, K - k0);
+        sg.xoob = (K + 31) / 32 * 32;
         ranges.push_back(sg);
       }
     }
@@ -1509,6 +1523,10 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo
     for (int pi = 0; pi < nparts; ++pi) {
       int seg = (int)segs.size();
       segs.push_back(ranges[pi]);
+      if (Rq[po] > 1) {
+        pk.push_back({seg, mW, pi, Rq[po], (ranges[pi].K + 31) / 32});
+        continue;
+      }
       for (int m0 = 0; m0 < M; m0 += 128)
         for (int n0 = 0; n0 < N; n0 += nt) {
           TWork t;
@@ -1523,9 +1541,35 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo
     wsn += a64((long long)nparts * blk);
   }
   if (wsn > z.nws) fail(DMRG_ERR_STATE, "internal: partial-tile workspace size");
+  // packed stage-2 tiles: segments of equal R, longest first, R per tile
+  std::stable_sort(pk.begin(), pk.end(), [](const PackCand &a, const PackCand &b) {
+    if (a.R != b.R) return a.R > b.R;
+    return a.nchunk > b.nchunk;
+  });
+  for (size_t i0 = 0; i0 < pk.size();) {
+    const int R = pk[i0].R;
+    TWork t;
+    memset(&t, 0, sizeof t);
+    t.M = 128; t.N = 128; t.ntile = 128;
+    t.mode = TW_PARTIAL; t.alpha = 1.f;
+    t.R = R;
+    for (int r = 0; r < 4; ++r) t.pseg[r] = -1;
+    size_t i = i0;
+    for (int r = 0; r < R && i < pk.size() && pk[i].R == R; ++r, ++i) {
+      t.pseg[r] = pk[i].seg;
+      t.pout[r] = pk[i].mOut;
+      t.pz[r] = pk[i].z;
+      t.nchunk = std::max(t.nchunk, pk[i].nchunk);
+    }
+    t.seg0 = t.pseg[0];
+    t.nseg = 1;
+    w2.push_back(t);
+    i0 = i;
+  }
   // persistent CTAs take work items round-robin: order them by cost (K chunks
   // x tile width), largest first
   auto cost = [&](const TWork &t) {
+    if (t.R > 1) return (long long)t.nchunk * t.ntile;
     long long k = 0;
     for (int i = 0; i < t.nseg; ++i) k += (segs[t.seg0 + i].K + 31) / 32;
     return k * t.ntile;

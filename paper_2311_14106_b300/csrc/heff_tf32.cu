@@ -229,6 +229,32 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
       for (int t = blockIdx.x; t < nwork && !*abort_flag; t += gridDim.x) {
         const TWork w = works[t];
         const uint32_t stage_tx = 2 * TILE_A + 2 * (uint32_t)w.ntile * BK * 4;
+        if (w.R > 1) {
+          // packed tile: per chunk, group r's rows of A and B from its own
+          // segment (a chunk past the segment's end loads zeros)
+          const uint32_t ga = (BM / w.R) * BK * 4, gb = (uint32_t)(w.ntile / w.R) * BK * 4;
+          uint32_t tx = 0;
+          for (int r = 0; r < w.R; ++r)
+            if (w.pseg[r] >= 0) tx += 2 * ga + 2 * gb;
+          for (int kc = 0; kc < w.nchunk; ++kc, ++it) {
+            const int st = it % STAGES;
+            const uint32_t ph = (it / STAGES) & 1;
+            if (!wait_or_abort(smem_u32(&sh->empty[st]), ph ^ 1, err, 1, abort_flag)) break;
+            uint8_t *base = smem + st * STAGE_BYTES;
+            const uint32_t fb = smem_u32(&sh->full[st]);
+            mbar_expect_tx(fb, tx);
+            for (int r = 0; r < w.R; ++r) {
+              if (w.pseg[r] < 0) continue;
+              const TSeg sg = segs[w.pseg[r]];
+              const int kx = kc * BK < sg.K ? sg.k0 + kc * BK : sg.xoob;
+              tma_load(smem_u32(base + r * ga), &maps[sg.mA_hi], kx, 0, fb);
+              tma_load(smem_u32(base + TILE_A + r * ga), &maps[sg.mA_lo], kx, 0, fb);
+              tma_load(smem_u32(base + 2 * TILE_A + r * gb), &maps[sg.mB_hi], kx, 0, fb);
+              tma_load(smem_u32(base + 2 * TILE_A + TILE_B + r * gb), &maps[sg.mB_lo], kx, 0, fb);
+            }
+          }
+          continue;
+        }
         for (int s = 0; s < w.nseg && !*abort_flag; ++s) {
           const TSeg sg = segs[w.seg0 + s];
           const int nk = (sg.K + BK - 1) / BK;
@@ -261,8 +287,11 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t d = tmem + acc * ACC_COLS;
         uint32_t accum = 0;
-        for (int s = 0; s < w.nseg; ++s) {
-          const int K = segs[w.seg0 + s].K;
+        const int nseg = w.R > 1 ? 1 : w.nseg;
+        for (int s = 0; s < nseg; ++s) {
+          // packed tiles run all their chunks without trimming (the groups'
+          // segments end at different K)
+          const int K = w.R > 1 ? w.nchunk * BK : segs[w.seg0 + s].K;
           const int nk = (K + BK - 1) / BK;
           for (int kc = 0; kc < nk; ++kc, ++it) {
             const int st = it % STAGES;
@@ -309,10 +338,24 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
       const uint32_t aph = (j / NACC) & 1;
       if (!wait_or_abort(smem_u32(&sh->acc_full[acc]), aph, err, 4, abort_flag)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int row0 = w.m0 + quarter * 32;
       const uint32_t tbase = tmem + acc * ACC_COLS + ((uint32_t)(quarter * 32) << 16);
-      if (row0 < w.M) {
-        for (int c0 = 0; c0 < w.ntile && w.n0 + c0 < w.N; c0 += 32) {
+      // destination of this warp's rows: a plain tile, or the diagonal block
+      // of its group in a packed tile
+      int row0 = w.m0 + quarter * 32, cbeg = 0, cend = w.ntile, xoff = w.n0, mo = w.mOut_hi,
+          zo = w.zout;
+      bool live = row0 < w.M;
+      if (w.R > 1) {
+        const int per = 4 / w.R, r = quarter / per, gw = w.ntile / w.R;
+        row0 = (quarter % per) * 32;
+        cbeg = r * gw;
+        cend = cbeg + gw;
+        xoff = -cbeg;
+        mo = w.pout[r];
+        zo = w.pz[r];
+        live = w.pseg[r] >= 0;
+      }
+      if (live) {
+        for (int c0 = cbeg; c0 < cend && (w.R > 1 || w.n0 + c0 < w.N); c0 += 32) {
           float v[32];
           tmem_ld16(tbase + c0, v);
           if (c0 + 16 < w.ntile) {
@@ -346,8 +389,8 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
           fence_async_shared();
           __syncwarp();
           if (lane == 0) {
-            tma_store3d(&maps[w.mOut_hi], w.n0 + c0, row0, w.zout, stg_hi);
-            if (w.mode == TW_SPLIT) tma_store3d(&maps[w.mOut_lo], w.n0 + c0, row0, w.zout, stg_lo);
+            tma_store3d(&maps[mo], xoff + c0, row0, zo, stg_hi);
+            if (w.mode == TW_SPLIT) tma_store3d(&maps[w.mOut_lo], xoff + c0, row0, zo, stg_lo);
             bulk_commit();
           }
         }

@@ -20,6 +20,8 @@ struct TSeg {
   int mA_hi, mA_lo, mB_hi, mB_lo;   // indices into the tensor-map table
   int K;             // length of this K range
   int k0;            // first K index (multiple of 32)
+  int xoob;          // a K coordinate past the maps' extent (loads read zeros)
+  int pad;
 };
 
 // Epilogue of a work item.
@@ -38,6 +40,14 @@ struct TWork {
   float alpha;
   int mOut_hi, mOut_lo;   // store maps (mOut_lo unused for TW_PARTIAL)
   int zout;               // z coordinate of the destination (partial slot)
+  // Packed partial tiles (R = 2 or 4; R = 1 otherwise): R independent
+  // segments, each with at most 128/R rows and columns, share one MMA
+  // tile: group r occupies rows and columns [r*128/R, (r+1)*128/R) and the
+  // diagonal block r of the product is its partial tile (the off-diagonal
+  // blocks are discarded).  One tensor instruction then advances R
+  // segments.  pseg[r] < 0 marks an unused group.
+  int R, nchunk;
+  int pseg[4], pout[4], pz[4];
 };
 
 // FP64 sum of the split-K partial tiles of one sigma block (rows x cols,
