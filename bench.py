@@ -241,7 +241,7 @@ def main():
                 g.heff_apply(psi, sig, stream)
             torch.cuda.synchronize()
             stages = g.heff_timing(0)
-        return ms, stages / max(stages[5], 1)
+        return ms, stages / max(stages[4], 1)
 
     # split path: the headline
     with Clocks(local) as clk:
@@ -300,19 +300,15 @@ def main():
     tf32_peak = bf16 * TF32_OVER_BF16
     si = g.heff_stage_info()
     plan = g.heff_split_plan()
-    # per-kernel event marks: [psi split, stage 1, stage 2, fused, partial sum]
+    # per-kernel event marks: [psi split, stage 1, stage 2, partial sum]
     # Algorithmic bytes: operators read once (8 B/element as TF32 hi+lo), psi
-    # read once; the two-stage kernels also write and read the intermediate
-    # T (hi+lo) of the blocks they serve.  The fused kernel keeps it on chip.
-    fa, fb, ft = plan["fused_nA"], plan["fused_nB"], plan["fused_nT"]
-    nT2 = si["nT"] - ft                 # intermediate of the two-stage blocks
+    # read once, the intermediate T written by stage 1 and read by stage 2
+    # (hi+lo), sigma partials written once
     kern = {
-        "k_tf32_gemm stage1": (st_split[1], 8 * (si["nA"] - fa + nT2) + 8 * si["psi_len"],
-                               si["flops1"] - plan["fused_flops1"]),
-        "k_tf32_gemm stage2": (st_split[2], 8 * (nT2 + si["nB"] - fb) + 4 * si["psi_len"],
-                               si["flops2"] - plan["fused_flops2"]),
-        "k_heff_fused": (st_split[3], 8 * (fa + fb) + 12 * si["psi_len"],
-                         plan["fused_flops1"] + plan["fused_flops2"]),
+        "k_tf32_gemm stage1": (st_split[1], 8 * (si["nA"] + si["nT"]) + 8 * si["psi_len"],
+                               si["flops1"]),
+        "k_tf32_gemm stage2": (st_split[2], 8 * (si["nT"] + si["nB"]) + 4 * si["psi_len"],
+                               si["flops2"]),
     }
     dom = max(kern, key=lambda k: kern[k][0])
     t_dom_ms, dom_bytes, dom_flops = kern[dom]
@@ -327,8 +323,8 @@ def main():
                    "parallelism": f"replicas x{world}", "block_build_seconds": t_build},
         "fp64": {"ms_per_step": ms_64, "tflops": flops / (ms_64 * 1e-3) / 1e12,
                  "stage_ms": st_64[1:3].tolist()},
-        "split_kernel_ms": dict(zip(["psi_split", "stage1", "stage2", "fused", "partial_sum"],
-                                    st_split[:5].tolist())),
+        "split_kernel_ms": dict(zip(["psi_split", "stage1", "stage2", "partial_sum"],
+                                    st_split[:4].tolist())),
         "autotuner": [{"ksub": k, "ms_per_apply": v} for k, v in g.heff_tuning()],
         "sigma_rel_diff_split_vs_fp64": err_sigma,
         "solve": solve,

@@ -216,13 +216,12 @@ int dmrg_heff_stage_info(dmrg_ctx *ctx, double *out6);
 
 /* Per-kernel timing of dmrg_heff_apply with CUDA events recorded on the
  * apply stream.  enable = 1 starts (and zeroes) the accumulation, 0 stops
- * it.  out6 (may be NULL) receives accumulated milliseconds of
- * [0] psi split (split path), [1] stage 1, [2] stage 2 (two-stage kernels;
- * the FP64 path's two stages), [3] fused kernel (split path, large sigma
- * blocks), [4] FP64 sum of the split-K partial tiles (split path), and
- * [5] the number of applies timed; reading synchronises the last timed
+ * it.  out5 (may be NULL) receives accumulated milliseconds of
+ * [0] psi split (split path), [1] stage 1, [2] stage 2, [3] FP64 sum of the
+ * split-K partial tiles (split path; the FP64 path sums inside stage 2),
+ * and [4] the number of applies timed; reading synchronises the last timed
  * apply. */
-int dmrg_heff_timing(dmrg_ctx *ctx, int enable, double *out6);
+int dmrg_heff_timing(dmrg_ctx *ctx, int enable, double *out5);
 
 /* Autotuner record of this context: *n_entries pairs (candidate split-K
  * range, milliseconds per split-precision apply) timed on the first large
@@ -237,22 +236,11 @@ int dmrg_heff_tuning(dmrg_ctx *ctx, double *out, int max_entries, int *n_entries
  * query it).  DMRG_ERR_STATE without a window. */
 int dmrg_heff_entries(dmrg_ctx *ctx, int *out, int max_entries, int *n_entries);
 
-/* Split-precision kernel choice: 1 sends sigma blocks with both extents
- * above 32 through the fused kernel (the intermediate A_k psi stays in
- * tensor memory); 0 (default) sends every block through the two-stage
- * kernels (intermediate written to and read back from device memory, fewer
- * tensor instructions per term; faster on the measured windows).  Takes
- * effect at the next split apply. */
-int dmrg_set_fused(dmrg_ctx *ctx, int enable);
-
 /* Shape of the split-precision plan of the current window (built by the
- * first split apply): out10[0] = kernel launches per apply, [1] stage-1
- * tiles, [2] stage-2 tiles (two-stage blocks), [3] split-K range (K
- * elements per partial tile), [4] fused tiles; for the fused blocks' terms:
- * [5] A-stack and [6] B-stack elements, [7] flops of A_k psi, [8] flops of
- * the second contraction, [9] elements of the intermediate A_k psi (kept
- * on chip).  DMRG_ERR_STATE before the plan exists. */
-int dmrg_heff_split_plan(dmrg_ctx *ctx, double *out10);
+ * first split apply): out4[0] = kernel launches per apply, [1] stage-1
+ * tiles, [2] stage-2 tiles, [3] split-K range of stage 2 (K elements per
+ * partial tile).  DMRG_ERR_STATE before the plan exists. */
+int dmrg_heff_split_plan(dmrg_ctx *ctx, double *out4);
 
 /* Replay the split-precision apply from captured CUDA graphs (default 1), one
  * graph per (psi, sigma) pointer pair; 0 launches the kernels directly. */

@@ -29,7 +29,7 @@ HEADER_FUNCTIONS = [
     "dmrg_set_precision", "dmrg_heff_apply", "dmrg_heff_apply_host",
     "dmrg_heff_flops", "dmrg_davidson", "dmrg_truncate", "dmrg_sweep",
     "dmrg_heff_stage_info", "dmrg_heff_timing", "dmrg_profile",
-    "dmrg_heff_apply_tf32_static", "dmrg_heff_tuning", "dmrg_set_graphs", "dmrg_set_fused",
+    "dmrg_heff_apply_tf32_static", "dmrg_heff_tuning", "dmrg_set_graphs",
     "dmrg_heff_split_plan", "dmrg_heff_entries",
 ]
 
@@ -75,7 +75,6 @@ _sig = {
     "dmrg_heff_tuning": (ctypes.c_int, [_P, _D, ctypes.c_int, _I]),
     "dmrg_set_graphs": (ctypes.c_int, [_P, ctypes.c_int]),
     "dmrg_heff_split_plan": (ctypes.c_int, [_P, _D]),
-    "dmrg_set_fused": (ctypes.c_int, [_P, ctypes.c_int]),
     "dmrg_heff_entries": (ctypes.c_int, [_P, _I, ctypes.c_int, _I]),
 }
 for _name, (_res, _args) in _sig.items():
@@ -271,23 +270,16 @@ class Dmrg:
         return out[:3 * n.value].reshape(-1, 3)
 
     def heff_split_plan(self):
-        """Split-precision plan: launches per apply, tiles per kernel, split-K
-        range, and the fused blocks' operator elements and flops."""
-        out = np.zeros(10)
+        """Split-precision plan: launches per apply, stage-1 / stage-2 tiles, split-K range."""
+        out = np.zeros(4)
         self._check(_lib.dmrg_heff_split_plan(self._h, _dptr(out)), "heff_split_plan")
         return {"launches": int(out[0]), "tiles1": int(out[1]), "tiles2": int(out[2]),
-                "ksub": int(out[3]), "tiles_fused": int(out[4]), "fused_nA": float(out[5]),
-                "fused_nB": float(out[6]), "fused_flops1": float(out[7]),
-                "fused_flops2": float(out[8]), "fused_nT": float(out[9])}
-
-    def set_fused(self, enable):
-        """Split path: large sigma blocks through the fused kernel (default False)."""
-        self._check(_lib.dmrg_set_fused(self._h, int(enable)), "set_fused")
+                "ksub": int(out[3])}
 
     def heff_timing(self, enable):
         """Start (1) / stop (0) per-kernel event timing; returns accumulated
-        [split_ms, stage1_ms, stage2_ms, fused_ms, partial_sum_ms, n_applies]."""
-        out = np.zeros(6)
+        [split_ms, stage1_ms, stage2_ms, partial_sum_ms, n_applies]."""
+        out = np.zeros(5)
         self._check(_lib.dmrg_heff_timing(self._h, enable, _dptr(out)), "heff_timing")
         return out
 

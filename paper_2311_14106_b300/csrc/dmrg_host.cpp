@@ -135,8 +135,6 @@ struct Tf32Tables {
   std::vector<TWork> w1, w2;      // grouped by tile width (<= 32, <= 64, <= 128)
   int n1[3] = {0, 0, 0}, n2[3] = {0, 0, 0};
   std::vector<PartialSum> psums;
-  std::vector<FUnit> units;       // fused path (large sigma blocks)
-  std::vector<FWork> fw;          // largest cost first
 };
 
 struct Window {
@@ -166,10 +164,9 @@ struct Window {
   Tf32Plan tf;           // split-precision plan (heff_tf32)
   bool tf_ready = false;
   bool tf_copies = false;            // TF32 copies of the operator stacks exist
-  bool tf_fused = false;             // plan built with the fused kernel
   int ksub = 0;                      // split-K range in use
-  void *tbl_ptr[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  size_t tbl_cap[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  void *tbl_ptr[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  size_t tbl_cap[6] = {0, 0, 0, 0, 0, 0};
   std::map<std::pair<const void *, const void *>, cudaGraphExec_t> graphs;
   std::vector<long long> offA, ldA, offBp, bpad;
   long long gen = 0;                 // build counter of this window
@@ -192,7 +189,6 @@ struct dmrg_ctx {
   std::map<BlockPart *, std::unique_ptr<WinBuf>> partbuf;
   Window win;
   Tf32Tables tables;     // host copy of the split-path tables of the window
-  bool use_fused = false; // large sigma blocks through the fused kernel
   cudaStream_t stream = nullptr;
   cusolverDnHandle_t solver = nullptr;
   cusolverDnParams_t solver_params = nullptr;
@@ -200,8 +196,8 @@ struct dmrg_ctx {
   double prof[7] = {0};
   // optional per-stage event timing of H_eff*psi
   bool timing = false;
-  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  double tacc[6] = {0, 0, 0, 0, 0, 0};
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  double tacc[5] = {0, 0, 0, 0, 0};
   bool pending = false;
   // Davidson scratch
   WinBuf dav;
@@ -854,7 +850,7 @@ void build_window(dmrg_ctx *C, int l) {
   w.tf_copies = false;
   for (auto &g : w.graphs) cudaGraphExecDestroy(g.second);
   w.graphs.clear();
-  for (int i = 0; i < 8; ++i) {
+  for (int i = 0; i < 6; ++i) {
     w.tbl_ptr[i] = nullptr;
     w.tbl_cap[i] = 0;
   }
@@ -1127,13 +1123,13 @@ void build_window(dmrg_ctx *C, int l) {
 
 void collect_timing(dmrg_ctx *C) {
   if (!C->pending) return;
-  CK(cudaEventSynchronize(C->ev[5]));
-  for (int i = 0; i < 5; ++i) {
+  CK(cudaEventSynchronize(C->ev[4]));
+  for (int i = 0; i < 4; ++i) {
     float ms = 0;
     CK(cudaEventElapsedTime(&ms, C->ev[i], C->ev[i + 1]));
     C->tacc[i] += ms;
   }
-  C->tacc[5] += 1;
+  C->tacc[4] += 1;
   C->pending = false;
 }
 
@@ -1141,7 +1137,7 @@ void mark(dmrg_ctx *C, int i, cudaStream_t s) {
   if (!C->timing) return;
   if (i == 0) collect_timing(C);
   CK(cudaEventRecord(C->ev[i], s));
-  if (i == 5) C->pending = true;
+  if (i == 4) C->pending = true;
 }
 
 void apply_fp64(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s) {
@@ -1154,7 +1150,6 @@ void apply_fp64(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s) {
   CK(launch_sum_partials64(w.d_ps64, (int)w.ps64.size(), sigma, s));
   mark(C, 3, s);
   mark(C, 4, s);
-  mark(C, 5, s);
 }
 
 }  // namespace
@@ -1179,42 +1174,13 @@ struct Tf32Scratch {
 const int KSUB_DEFAULT = 1024;   // longest K range of one stage-2 work item
 const int KSUB_CANDIDATES[3] = {512, 1024, 2048};
 
-// Sigma blocks with both extents above 32 take the fused kernel; smaller ones
-// (whose 128-row tiles are mostly padding) take the two-stage kernels.
-bool fused_block(const PsiBlk &q) { return q.da > 32 && q.db > 32; }
-constexpr int FUSED_NB = 128;   // psi columns per fused unit (MMA1 N <= 128)
-
-// Split-K ranges of a fused sigma block: units (entry, term, 128-column
-// chunk of psi) in entry / term / chunk order, cut so that a range holds at
-// most KSUB psi columns.  Calls f(entry, k, b0, nb, new_range) per unit.
-template <typename F>
-int fused_ranges(const Window &w, const std::vector<int> &entries, int KSUB, F &&f) {
-  int nr = 0, kacc = 0;
-  for (int i : entries) {
-    const HClass &h = w.hc[w.s1info[i].ci];
-    const PsiBlk &p = w.psi[w.s1info[i].pi];
-    for (int k = 0; k < (int)h.terms.size(); ++k)
-      for (int b0 = 0; b0 < p.db; b0 += FUSED_NB) {
-        const int nb = std::min(FUSED_NB, p.db - b0);
-        const bool fresh = nr == 0 || kacc + nb > KSUB;
-        if (fresh) {
-          ++nr;
-          kacc = 0;
-        }
-        kacc += nb;
-        f(i, k, b0, nb, fresh);
-      }
-  }
-  return nr;
-}
-
 std::vector<std::vector<int>> entries_into(const Window &w) {
   std::vector<std::vector<int>> into(w.psi.size());
   for (size_t i = 0; i < w.s1info.size(); ++i) into[w.s1info[i].po].push_back((int)i);
   return into;
 }
 
-Tf32Scratch tf32_scratch_sizes(const Window &w, int KSUB, bool fz) {
+Tf32Scratch tf32_scratch_sizes(const Window &w, int KSUB) {
   Tf32Scratch z;
   const auto &E = w.s1info;
   const size_t ne = E.size(), np = w.psi.size();
@@ -1227,7 +1193,6 @@ Tf32Scratch tf32_scratch_sizes(const Window &w, int KSUB, bool fz) {
     const PsiBlk &p = w.psi[E[i].pi], &q = w.psi[E[i].po];
     const long long n = (long long)h.terms.size();
     z.ldT[i] = r4(p.db);   // T rows (a', k), b padded to 4 floats
-    if (fz && fused_block(q)) continue;   // no intermediate in HBM
     z.offT[i] = z.nT;
     z.nT += a64(q.da * n * z.ldT[i]);
   }
@@ -1239,13 +1204,9 @@ Tf32Scratch tf32_scratch_sizes(const Window &w, int KSUB, bool fz) {
   const auto into = entries_into(w);
   for (size_t po = 0; po < np; ++po) {
     long long parts = 0;
-    if (fz && fused_block(w.psi[po])) {
-      parts = fused_ranges(w, into[po], KSUB, [](int, int, int, int, bool) {});
-    } else {
-      for (int i : into[po]) {
-        const long long K = (long long)w.hc[E[i].ci].terms.size() * r4(w.psi[E[i].pi].db);
-        parts += (K + KSUB - 1) / KSUB;
-      }
+    for (int i : into[po]) {
+      const long long K = (long long)w.hc[E[i].ci].terms.size() * r4(w.psi[E[i].pi].db);
+      parts += (K + KSUB - 1) / KSUB;
     }
     z.nws += a64(parts * w.psi[po].da * r4(w.psi[po].db));
   }
@@ -1340,7 +1301,7 @@ std::vector<Split2D> psi_split_descs(const Window &w, const Tf32Scratch &z, floa
 }
 
 void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo, float *T_hi,
-                 float *T_lo, float *ws, Tf32Tables &out, int KSUB, bool fz) {
+                 float *T_lo, float *ws, Tf32Tables &out, int KSUB) {
   const Tf32Plan &P = w.tf;
   const auto &E = w.s1info;
   const size_t ne = E.size(), np = w.psi.size();
@@ -1373,15 +1334,12 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo
   auto &w1 = out.w1;
   auto &w2 = out.w2;
   const auto into = entries_into(w);
-  // per entry: stage-1 / stage-2 maps (two-stage blocks) or 3-D operand maps
-  // (fused blocks: A_k rows a' at stride n*ldA, B_k rows b' at stride n*bpad)
+  // per entry: stage-1 tiles, and the maps stage 2 reads
   std::vector<int> mThi(ne), mTlo(ne), mBhi(ne), mBlo(ne);
-  std::vector<std::array<int, 4>> m3(ne);
   // stage-2 packing of small sigma blocks: R segments per 128 x 128 tile
   std::vector<int> Rq(np, 1);
   for (size_t po = 0; po < np; ++po) {
     const PsiBlk &q = w.psi[po];
-    if (fz && fused_block(q)) continue;
     Rq[po] = (q.da <= 32 && q.db <= 32) ? 4 : ((q.da <= 64 && q.db <= 64) ? 2 : 1);
   }
   std::vector<float> alpha(ne);
@@ -1391,16 +1349,6 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo
     const int n = (int)h.terms.size();
     const int nl = qnum(w.Ld.basis.qn[p.a]);
     alpha[i] = (h.pB && (nl & 1)) ? -1.f : 1.f;
-    if (fz && fused_block(q)) {
-      const long long nA = n * w.ldA[i], nB = n * w.bpad[i];
-      // A box: the block's a' rows (8-row swizzle groups), at most one tile
-      const int ra = q.da > 128 ? 128 : (q.da + 7) / 8 * 8;
-      m3[i][0] = mk3(P.A_hi + w.offA[i], p.da, n, q.da, w.ldA[i], nA, 32, 1, ra);
-      m3[i][1] = mk3(P.A_lo + w.offA[i], p.da, n, q.da, w.ldA[i], nA, 32, 1, ra);
-      m3[i][2] = mk3(P.Bp_hi + w.offBp[i], p.db, n, q.db, w.bpad[i], nB, 32, 1, ntile_of(q.db));
-      m3[i][3] = mk3(P.Bp_lo + w.offBp[i], p.db, n, q.db, w.bpad[i], nB, 32, 1, ntile_of(q.db));
-      continue;
-    }
     const long long bp = z.ldT[i];   // = r4(p.db)
     int ahi = mk(P.A_hi + w.offA[i], (long long)q.da * n, p.da, w.ldA[i], 128);
     int alo = mk(P.A_lo + w.offA[i], (long long)q.da * n, p.da, w.ldA[i], 128);
@@ -1436,7 +1384,6 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo
   // per sigma block: split-K ranges, each one FP32 partial tile per output
   // tile; the partials are summed in FP64 in a fixed order.
   long long wsn = 0;
-  std::vector<long long> fcost;
   struct PackCand {
     int seg, mOut, z, R, nchunk;
   };
@@ -1453,54 +1400,6 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo
     ps.ld = ldw;
     ps.n = q.da * q.db;
     ps.cols = q.db;
-    if (fz && fused_block(q)) {
-      // units (entry, term, psi chunk) grouped into ranges of <= KSUB columns
-      std::vector<std::pair<int, int>> ranges;
-      std::vector<long long> rcost;
-      const int nparts = fused_ranges(w, into[po], KSUB, [&](int i, int k, int b0, int nb, bool fresh) {
-        const PsiBlk &p = w.psi[E[i].pi];
-        if (fresh) {
-          ranges.push_back({(int)out.units.size(), 0});
-          rcost.push_back(0);
-        }
-        FUnit u;
-        u.mA_hi = m3[i][0]; u.mA_lo = m3[i][1];
-        u.mP_hi = mPhi[E[i].pi]; u.mP_lo = mPlo[E[i].pi];
-        u.mB_hi = m3[i][2]; u.mB_lo = m3[i][3];
-        u.k = k;
-        u.b0 = b0;
-        u.nb = nb;
-        u.n1 = (nb + 15) / 16 * 16;
-        u.ra = q.da > 128 ? 128 : (q.da + 7) / 8 * 8;
-        u.pbox = ntile_of(p.db);
-        u.ka = p.da;
-        u.nk1 = (p.da + 31) / 32;
-        u.alpha = alpha[i];
-        out.units.push_back(u);
-        ranges.back().second++;
-        // tensor-pipe work: MMA1 (K = psi rows, N = n1) + MMA2 (K = nb, N = tile)
-        rcost.back() += (long long)((p.da + 7) / 8) * u.n1 + (long long)((nb + 7) / 8) * nt;
-      });
-      ps.nparts = nparts;
-      out.psums.push_back(ps);
-      if (nparts == 0) continue;
-      const int mW = mk3(ws + wsn, q.db, q.da, nparts, ldw, blk, 32, 32, 1);
-      for (int r = 0; r < nparts; ++r)
-        for (int m0 = 0; m0 < M; m0 += 128)
-          for (int n0 = 0; n0 < N; n0 += nt) {
-            FWork t;
-            memset(&t, 0, sizeof t);
-            t.u0 = ranges[r].first;
-            t.nu = ranges[r].second;
-            t.M = M; t.N = N; t.m0 = m0; t.n0 = n0; t.ntile = nt;
-            t.mOut = mW;
-            t.zout = r;
-            out.fw.push_back(t);
-            fcost.push_back(rcost[r]);
-          }
-      wsn += a64((long long)nparts * blk);
-      continue;
-    }
     std::vector<TSeg> ranges;
     for (int i : into[po]) {
       const HClass &h = w.hc[E[i].ci];
@@ -1584,14 +1483,6 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo
   std::stable_sort(w2.begin(), w2.end(), order);
   for (const TWork &t : w1) out.n1[bucket(t)]++;
   for (const TWork &t : w2) out.n2[bucket(t)]++;
-  // fused tiles: one launch, largest cost first
-  std::vector<int> ord(out.fw.size());
-  for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int)i;
-  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return fcost[a] > fcost[b]; });
-  std::vector<FWork> sorted;
-  sorted.reserve(ord.size());
-  for (int i : ord) sorted.push_back(out.fw[i]);
-  out.fw.swap(sorted);
 }
 
 void upload_tables(dmrg_ctx *C, Tf32Tables &tb, cudaStream_t s);
@@ -1608,12 +1499,10 @@ void build_tf32(dmrg_ctx *C) {
   Tf32Plan &P = w.tf;
   if (!w.tf_copies) tf32_operator_copies(C);
   CK(tf32_prepare());
-  CK(fused_prepare());
-  const bool fz = C->use_fused;
   const bool tune = C->ksub_choice == 0 && (double)(w.nA + w.nB) * 8.0 > 256e6;
   int best = C->ksub_choice ? C->ksub_choice : KSUB_DEFAULT;
   // scratch sized for the smallest candidate (most partial tiles)
-  Tf32Scratch zmax = tf32_scratch_sizes(w, tune ? KSUB_CANDIDATES[0] : best, fz);
+  Tf32Scratch zmax = tf32_scratch_sizes(w, tune ? KSUB_CANDIDATES[0] : best);
   auto fl = [&](long long n) { return (float *)w.buf.alloc(4 * std::max<long long>(n, 64)); };
   P.P_hi = fl(zmax.nP); P.P_lo = fl(zmax.nP);
   P.T_hi = fl(zmax.nT); P.T_lo = fl(zmax.nT);
@@ -1630,8 +1519,8 @@ void build_tf32(dmrg_ctx *C) {
     CK(cudaEventCreate(&e1));
     float best_ms = 1e30f;
     for (int ks : KSUB_CANDIDATES) {
-      Tf32Scratch z = tf32_scratch_sizes(w, ks, fz);
-      tf32_tables(w, z, P.P_hi, P.P_lo, P.T_hi, P.T_lo, P.ws, C->tables, ks, fz);
+      Tf32Scratch z = tf32_scratch_sizes(w, ks);
+      tf32_tables(w, z, P.P_hi, P.P_lo, P.T_hi, P.T_lo, P.ws, C->tables, ks);
       upload_tables(C, C->tables, s);
       launch_tf32(C, x, y, s);   // warm
       CK(cudaEventRecord(e0, s));
@@ -1651,9 +1540,8 @@ void build_tf32(dmrg_ctx *C) {
     C->ksub_choice = best;
   }
   w.ksub = best;
-  Tf32Scratch z = tf32_scratch_sizes(w, best, fz);
-  tf32_tables(w, z, P.P_hi, P.P_lo, P.T_hi, P.T_lo, P.ws, C->tables, best, fz);
-  w.tf_fused = fz;
+  Tf32Scratch z = tf32_scratch_sizes(w, best);
+  tf32_tables(w, z, P.P_hi, P.P_lo, P.T_hi, P.T_lo, P.ws, C->tables, best);
   upload_tables(C, C->tables, s);
   CK(cudaStreamSynchronize(s));
   w.tf_ready = true;
@@ -1675,8 +1563,7 @@ void upload_tables(dmrg_ctx *C, Tf32Tables &tb, cudaStream_t s) {
   need(w.tbl_ptr[3], w.tbl_cap[3], std::max<size_t>(tb.w1.size(), 1) * sizeof(TWork));
   need(w.tbl_ptr[4], w.tbl_cap[4], std::max<size_t>(tb.w2.size(), 1) * sizeof(TWork));
   need(w.tbl_ptr[5], w.tbl_cap[5], std::max<size_t>(tb.psums.size(), 1) * sizeof(PartialSum));
-  need(w.tbl_ptr[6], w.tbl_cap[6], std::max<size_t>(tb.units.size(), 1) * sizeof(FUnit));
-  need(w.tbl_ptr[7], w.tbl_cap[7], std::max<size_t>(tb.fw.size(), 1) * sizeof(FWork));
+
   auto put = [&](void *dst, const void *src, size_t n) {
     if (n) CK(cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, s));
   };
@@ -1686,8 +1573,7 @@ void upload_tables(dmrg_ctx *C, Tf32Tables &tb, cudaStream_t s) {
   put(w.tbl_ptr[3], tb.w1.data(), tb.w1.size() * sizeof(TWork));
   put(w.tbl_ptr[4], tb.w2.data(), tb.w2.size() * sizeof(TWork));
   put(w.tbl_ptr[5], tb.psums.data(), tb.psums.size() * sizeof(PartialSum));
-  put(w.tbl_ptr[6], tb.units.data(), tb.units.size() * sizeof(FUnit));
-  put(w.tbl_ptr[7], tb.fw.data(), tb.fw.size() * sizeof(FWork));
+
   P.psi_split = w.tbl_ptr[0];
   P.npsi = (int)tb.psi_split.size();
   P.maps = (CUtensorMap *)w.tbl_ptr[1];
@@ -1698,9 +1584,6 @@ void upload_tables(dmrg_ctx *C, Tf32Tables &tb, cudaStream_t s) {
   P.nwork1 = (int)tb.w1.size();
   P.nwork2 = (int)tb.w2.size();
   P.npsum = (int)tb.psums.size();
-  P.units = (FUnit *)w.tbl_ptr[6];
-  P.fwork = (FWork *)w.tbl_ptr[7];
-  P.nfw = (int)tb.fw.size();
   for (int i = 0; i < 3; ++i) {
     P.n1[i] = tb.n1[i];
     P.n2[i] = tb.n2[i];
@@ -1719,10 +1602,8 @@ void launch_tf32(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s) 
   mark(C, 2, s);
   CK(tf32_gemm(P.work2, P.n2, P.seg, P.maps, P.err, s));
   mark(C, 3, s);
-  CK(fused_gemm(P.fwork, P.nfw, P.units, P.maps, P.err, s));
-  mark(C, 4, s);
   CK(sum_partials(P.psum, P.npsum, sigma, s));
-  mark(C, 5, s);
+  mark(C, 4, s);
 }
 
 // The split apply is 8 launches; it is captured once per (psi, sigma) pair
@@ -1730,7 +1611,7 @@ void launch_tf32(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s) 
 // With per-stage timing on, the launches go out directly.
 void apply_tf32(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s) {
   Window &w = C->win;
-  if (!w.tf_ready || w.tf_fused != C->use_fused) {
+  if (!w.tf_ready) {
     cudaStream_t save = C->stream;
     C->stream = s;
     build_tf32(C);
@@ -2844,9 +2725,8 @@ int dmrg_heff_apply_tf32_static(dmrg_ctx *C, const double *psi, double *sigma, v
     // layout: [error flag | tables | P hi, P lo | T hi, T lo | partial tiles]
     struct Owner {
       long long gen = -1;
-      bool fz = false;
       Tf32Tables tb;
-      size_t o_maps, o_seg, o_w1, o_w2, o_ps, o_split, o_units, o_fw;
+      size_t o_maps, o_seg, o_w1, o_w2, o_ps, o_split;
     };
     static std::mutex mu;
     static std::map<int, Owner> owners;
@@ -2855,13 +2735,11 @@ int dmrg_heff_apply_tf32_static(dmrg_ctx *C, const double *psi, double *sigma, v
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     unsigned char *b = (unsigned char *)base;
     const int ks = w.ksub ? w.ksub : KSUB_DEFAULT;
-    const bool fz = C->use_fused;
-    CK(fused_prepare());
-    if (ow.gen != w.gen || ow.fz != fz) {
-      Tf32Scratch z = tf32_scratch_sizes(w, ks, fz);
+    if (ow.gen != w.gen) {
+      Tf32Scratch z = tf32_scratch_sizes(w, ks);
       // table sizes do not depend on the pointers: size them with a dry run
       Tf32Tables probe;
-      tf32_tables(w, z, (float *)b, (float *)b, (float *)b, (float *)b, (float *)b, probe, ks, fz);
+      tf32_tables(w, z, (float *)b, (float *)b, (float *)b, (float *)b, (float *)b, probe, ks);
       size_t off = 256;
       ow.o_maps = off; off = al(off + probe.maps.size() * sizeof(CUtensorMap));
       ow.o_seg = off; off = al(off + probe.segs.size() * sizeof(TSeg));
@@ -2869,8 +2747,6 @@ int dmrg_heff_apply_tf32_static(dmrg_ctx *C, const double *psi, double *sigma, v
       ow.o_w2 = off; off = al(off + probe.w2.size() * sizeof(TWork));
       ow.o_ps = off; off = al(off + probe.psums.size() * sizeof(PartialSum));
       ow.o_split = off; off = al(off + probe.psi_split.size() * sizeof(Split2D));
-      ow.o_units = off; off = al(off + probe.units.size() * sizeof(FUnit));
-      ow.o_fw = off; off = al(off + probe.fw.size() * sizeof(FWork));
       const size_t oP = off;
       off = al(off + 4 * (size_t)z.nP);
       const size_t oP2 = off;
@@ -2886,7 +2762,7 @@ int dmrg_heff_apply_tf32_static(dmrg_ctx *C, const double *psi, double *sigma, v
                            "(use dmrg_heff_apply for larger windows)", off, cap);
       ow.gen = -1;
       tf32_tables(w, z, (float *)(b + oP), (float *)(b + oP2), (float *)(b + oT),
-                  (float *)(b + oT2), (float *)(b + oW), ow.tb, ks, fz);
+                  (float *)(b + oT2), (float *)(b + oW), ow.tb, ks);
       const Tf32Tables &t = ow.tb;
       auto put = [&](size_t o, const void *src, size_t n) {
         if (n) CK(cudaMemcpyAsync(b + o, src, n, cudaMemcpyHostToDevice, s));
@@ -2897,10 +2773,7 @@ int dmrg_heff_apply_tf32_static(dmrg_ctx *C, const double *psi, double *sigma, v
       put(ow.o_w2, t.w2.data(), t.w2.size() * sizeof(TWork));
       put(ow.o_ps, t.psums.data(), t.psums.size() * sizeof(PartialSum));
       put(ow.o_split, t.psi_split.data(), t.psi_split.size() * sizeof(Split2D));
-      put(ow.o_units, t.units.data(), t.units.size() * sizeof(FUnit));
-      put(ow.o_fw, t.fw.data(), t.fw.size() * sizeof(FWork));
       ow.gen = w.gen;
-      ow.fz = fz;
     }
     const Tf32Tables &t = ow.tb;
     int *err = (int *)b;
@@ -2910,8 +2783,6 @@ int dmrg_heff_apply_tf32_static(dmrg_ctx *C, const double *psi, double *sigma, v
                  (const CUtensorMap *)(b + ow.o_maps), err, s));
     CK(tf32_gemm((const TWork *)(b + ow.o_w2), t.n2, (const TSeg *)(b + ow.o_seg),
                  (const CUtensorMap *)(b + ow.o_maps), err, s));
-    CK(fused_gemm((const FWork *)(b + ow.o_fw), (int)t.fw.size(), (const FUnit *)(b + ow.o_units),
-                  (const CUtensorMap *)(b + ow.o_maps), err, s));
     CK(sum_partials((const PartialSum *)(b + ow.o_ps), (int)t.psums.size(), sigma, s));
   });
 }
@@ -2959,8 +2830,8 @@ int dmrg_heff_stage_info(dmrg_ctx *C, double *out6) {
   return DMRG_OK;
 }
 
-int dmrg_heff_split_plan(dmrg_ctx *C, double *out10) {
-  if (!C || !out10) return DMRG_ERR_ARG;
+int dmrg_heff_split_plan(dmrg_ctx *C, double *out4) {
+  if (!C || !out4) return DMRG_ERR_ARG;
   const Window &w = C->win;
   if (!w.valid || !w.tf_ready) {
     C->err = "split plan not built: apply once with DMRG_SPLIT_TF32 first";
@@ -2969,31 +2840,10 @@ int dmrg_heff_split_plan(dmrg_ctx *C, double *out10) {
   const Tf32Plan &P = w.tf;
   int launches = 1 + (P.npsum > 0 ? 1 : 0);
   for (int i = 0; i < 3; ++i) launches += (P.n1[i] > 0) + (P.n2[i] > 0);
-  launches += P.nfw > 0;
-  // operator elements and products of the fused sigma blocks
-  double fa = 0, fb = 0, f1 = 0, f2 = 0, ft = 0;
-  if (w.tf_fused)
-    for (const S1 &e : w.s1info) {
-      const PsiBlk &p = w.psi[e.pi], &q = w.psi[e.po];
-      if (!fused_block(q)) continue;
-      const double n = (double)w.hc[e.ci].terms.size();
-      fa += n * q.da * p.da;
-      fb += n * q.db * p.db;
-      ft += n * q.da * p.db;
-      f1 += 2.0 * n * q.da * p.da * p.db;
-      f2 += 2.0 * n * q.da * p.db * q.db;
-    }
-  double *o = out10;
-  o[0] = launches;
-  o[1] = P.nwork1;
-  o[2] = P.nwork2;
-  o[3] = (double)w.ksub;
-  o[4] = P.nfw;
-  o[5] = fa;
-  o[6] = fb;
-  o[7] = f1;
-  o[8] = f2;
-  o[9] = ft;
+  out4[0] = launches;
+  out4[1] = P.nwork1;
+  out4[2] = P.nwork2;
+  out4[3] = (double)w.ksub;
   return DMRG_OK;
 }
 
@@ -3015,14 +2865,14 @@ int dmrg_heff_entries(dmrg_ctx *C, int *out, int max_entries, int *n_entries) {
   return DMRG_OK;
 }
 
-int dmrg_heff_timing(dmrg_ctx *C, int enable, double *out6) {
+int dmrg_heff_timing(dmrg_ctx *C, int enable, double *out5) {
   if (!C) return DMRG_ERR_ARG;
   return guard(C, [&] {
     if (!C->ev[0])
       for (auto &e : C->ev) CK(cudaEventCreate(&e));
     collect_timing(C);
-    if (out6)
-      for (int i = 0; i < 6; ++i) out6[i] = C->tacc[i];
+    if (out5)
+      for (int i = 0; i < 5; ++i) out5[i] = C->tacc[i];
     if (enable && !C->timing)
       for (double &t : C->tacc) t = 0;
     C->timing = enable != 0;
@@ -3037,12 +2887,6 @@ int dmrg_heff_tuning(dmrg_ctx *C, double *out, int max_entries, int *n_entries) 
       out[2 * i] = C->tune_log[i][0];
       out[2 * i + 1] = C->tune_log[i][1];
     }
-  return DMRG_OK;
-}
-
-int dmrg_set_fused(dmrg_ctx *C, int enable) {
-  if (!C) return DMRG_ERR_ARG;
-  C->use_fused = enable != 0;
   return DMRG_OK;
 }
 

@@ -11,8 +11,6 @@
 
 #include <vector>
 
-#include "heff_fused.h"
-
 namespace dmrg {
 
 // One K-segment: A (M x K) and B (N x K), each as (hi, lo) tensor maps.
@@ -77,9 +75,6 @@ struct Tf32Plan {
   float *ws = nullptr;              // split-K partial tiles of stage 2
   PartialSum *psum = nullptr;
   int npsum = 0;
-  FUnit *units = nullptr;           // fused path (large sigma blocks)
-  FWork *fwork = nullptr;
-  int nfw = 0;
   void *psi_split = nullptr;        // SplitT descriptors (device), one per psi block
   int npsi = 0;
   int *err = nullptr;               // device error flag (bounded waits)

@@ -4,8 +4,8 @@ At the 6x6 Hubbard, D = 1024 window the FP64 oracle cannot build the block
 operators in reasonable time, so the reference here is the library's own
 FP64 path (pinned to the oracle at <= 1e-12 on the smaller windows of
 test_gpu_heff.py).  The window has sigma blocks wider than 128 (two MMA
-tiles, two psi chunks per fused unit) and terms whose psi chunk needs more
-K chunks than the operand ring holds, which the small windows do not reach.
+tiles per block), long split-K ranges and all packing classes of stage 2,
+which the small windows do not all reach.
 """
 import numpy as np
 import pytest
@@ -33,7 +33,7 @@ def build(D):
 
 
 @pytest.mark.parametrize("D", [1024])
-def test_split_paths_vs_fp64_full_size(D):
+def test_split_path_vs_fp64_full_size(D):
     g = build(D)
     n, layout = g.heff_layout()
     assert max(max(da, db) for _, _, da, db in layout) > 128
@@ -41,16 +41,13 @@ def test_split_paths_vs_fp64_full_size(D):
     g.set_precision(lib.FP64)
     ref = g.heff_apply_host(psi)
     g.set_precision(lib.SPLIT_TF32)
-    out = {}
-    for fused in (True, False):
-        g.set_fused(fused)
-        s = g.heff_apply_host(psi)      # raises if a kernel recorded an error
-        err = np.linalg.norm(s - ref) / np.linalg.norm(ref)
-        assert err <= TOL_SPLIT, (fused, err)
-        plan = g.heff_split_plan()
-        assert (plan["tiles_fused"] > 0) == fused
-        out[fused] = s
-    # the two split paths agree to the split-precision level as well
-    d = np.linalg.norm(out[True] - out[False]) / np.linalg.norm(ref)
-    assert d <= TOL_SPLIT
+    s = g.heff_apply_host(psi)      # raises if a kernel recorded an error
+    err = np.linalg.norm(s - ref) / np.linalg.norm(ref)
+    assert err <= TOL_SPLIT, err
+    # the sampled elements of the largest block agree elementwise too
+    big = max(range(len(layout)), key=lambda i: layout[i][2] * layout[i][3])
+    off = sum(da * db for _, _, da, db in layout[:big])
+    blk = slice(off, off + layout[big][2] * layout[big][3])
+    scale = np.abs(ref).max()
+    assert np.abs(s[blk] - ref[blk]).max() <= 1e-4 * scale
     g.close()
