@@ -301,13 +301,13 @@ def main():
     si = g.heff_stage_info()
     plan = g.heff_split_plan()
     # per-kernel event marks: [psi split, stage 1, stage 2, partial sum]
-    # Algorithmic bytes: operators read once (8 B/element as TF32 hi+lo), psi
-    # read once, the intermediate T written by stage 1 and read by stage 2
-    # (hi+lo), sigma partials written once
+    # Algorithmic bytes: operator stacks read once (FP32, 4 B/element), psi
+    # read once (TF32 hi+lo), the intermediate T written by stage 1 and read
+    # by stage 2 (FP32), sigma partials written once (FP32)
     kern = {
-        "k_tf32_gemm stage1": (st_split[1], 8 * (si["nA"] + si["nT"]) + 8 * si["psi_len"],
+        "k_tf32_gemm stage1": (st_split[1], 4 * (si["nA"] + si["nT"]) + 8 * si["psi_len"],
                                si["flops1"]),
-        "k_tf32_gemm stage2": (st_split[2], 8 * (si["nT"] + si["nB"]) + 4 * si["psi_len"],
+        "k_tf32_gemm stage2": (st_split[2], 4 * (si["nT"] + si["nB"]) + 4 * si["psi_len"],
                                si["flops2"]),
     }
     dom = max(kern, key=lambda k: kern[k][0])
@@ -316,7 +316,7 @@ def main():
         "metric": "H_eff*psi TFLOP/s", "value": job_value(flops, ms_split, world),
         "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_split, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "tf32 hi+lo split, 3 products (fp32 accumulate), fp64 in/out",
+        "vs_baseline": None, "dtype": "tf32 hi+lo split on chip from fp32 operands, 3 products (fp32 accumulate), fp64 in/out",
         "data": "synthetic",
         "config": {"workload": args.workload, "description": wl[6], "psi_len": n,
                    "algorithmic_flops_per_step": flops, "l2": "operator stacks >> L2; no flush",

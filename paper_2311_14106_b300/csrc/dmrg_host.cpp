@@ -1165,7 +1165,7 @@ long long a64(long long x) { return (x + 63) & ~63LL; }
 int ntile_of(int n) { return n > 128 ? 128 : ((n + 15) / 16) * 16; }
 
 // Sizes (floats) of the per-apply scratch of the split path: psi split
-// (P hi/lo), stage-1 intermediate (T hi/lo) and stage-2 partial tiles (ws).
+// (P hi/lo), stage-1 intermediate (T, FP32) and stage-2 partial tiles (ws).
 struct Tf32Scratch {
   long long nP = 0, nT = 0, nws = 0;
   std::vector<long long> offP, offT, ldP, ldT;
@@ -1213,8 +1213,9 @@ Tf32Scratch tf32_scratch_sizes(const Window &w, int KSUB) {
   return z;
 }
 
-// TF32 (hi, lo) copies of the operator stacks: built once per window and
-// owned by the context (they are inputs of every split-path apply).
+// FP32 copies of the operator stacks: built once per window and owned by the
+// context (they are inputs of every split-path apply; the kernels split
+// them into TF32 hi + lo on chip).
 void tf32_operator_copies(dmrg_ctx *C) {
   Window &w = C->win;
   cudaStream_t s = C->stream;
@@ -1238,13 +1239,11 @@ void tf32_operator_copies(dmrg_ctx *C) {
     nBp += a64(q.db * n * w.bpad[i]);
   }
   auto fl = [&](long long n) { return (float *)w.buf.alloc(4 * std::max<long long>(n, 64)); };
-  P.A_hi = fl(nA); P.A_lo = fl(nA);
+  P.A32 = fl(nA);
   // B with every term's b segment padded to 4 floats (zeros), so that stage 2
   // runs over K = (k, b) with b padded and each term starts 16-byte aligned
-  P.Bp_hi = fl(nBp);
-  P.Bp_lo = fl(nBp);
-  CK(cudaMemsetAsync(P.Bp_hi, 0, 4 * std::max<long long>(nBp, 64), s));
-  CK(cudaMemsetAsync(P.Bp_lo, 0, 4 * std::max<long long>(nBp, 64), s));
+  P.B32 = fl(nBp);
+  CK(cudaMemsetAsync(P.B32, 0, 4 * std::max<long long>(nBp, 64), s));
   std::vector<Split2D> sp;
   for (size_t i = 0; i < ne; ++i) {
     const HClass &h = w.hc[E[i].ci];
@@ -1256,8 +1255,8 @@ void tf32_operator_copies(dmrg_ctx *C) {
     a.src_ld = p.da;
     a.rows = q.da * n;
     a.cols = p.da;
-    a.hi = P.A_hi + w.offA[i];
-    a.lo = P.A_lo + w.offA[i];
+    a.hi = P.A32 + w.offA[i];
+    a.lo = nullptr;
     a.dst_ld = w.ldA[i];
     sp.push_back(a);
     // rows (b', k) of the [b'][k][b] stack, each p.db long, re-strided to bpad
@@ -1267,8 +1266,8 @@ void tf32_operator_copies(dmrg_ctx *C) {
     b.src_ld = p.db;
     b.rows = q.db * n;
     b.cols = p.db;
-    b.hi = P.Bp_hi + w.offBp[i];
-    b.lo = P.Bp_lo + w.offBp[i];
+    b.hi = P.B32 + w.offBp[i];
+    b.lo = nullptr;
     b.dst_ld = w.bpad[i];
     sp.push_back(b);
   }
@@ -1300,8 +1299,8 @@ std::vector<Split2D> psi_split_descs(const Window &w, const Tf32Scratch &z, floa
   return out;
 }
 
-void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo, float *T_hi,
-                 float *T_lo, float *ws, Tf32Tables &out, int KSUB) {
+void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo, float *T32,
+                 float *ws, Tf32Tables &out, int KSUB) {
   const Tf32Plan &P = w.tf;
   const auto &E = w.s1info;
   const size_t ne = E.size(), np = w.psi.size();
@@ -1350,21 +1349,20 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo
     const int nl = qnum(w.Ld.basis.qn[p.a]);
     alpha[i] = (h.pB && (nl & 1)) ? -1.f : 1.f;
     const long long bp = z.ldT[i];   // = r4(p.db)
-    int ahi = mk(P.A_hi + w.offA[i], (long long)q.da * n, p.da, w.ldA[i], 128);
-    int alo = mk(P.A_lo + w.offA[i], (long long)q.da * n, p.da, w.ldA[i], 128);
+    int ahi = mk(P.A32 + w.offA[i], (long long)q.da * n, p.da, w.ldA[i], 128);
     // T as stage-1 output: rows (a', k), columns b (padded); as stage-2
     // operand: rows a', K = (k, b)
     const long long rowsT = (long long)q.da * n;
-    const int sThi = mk3(T_hi + z.offT[i], bp, rowsT, 1, bp, rowsT * bp, 32, 32, 1);
-    const int sTlo = mk3(T_lo + z.offT[i], bp, rowsT, 1, bp, rowsT * bp, 32, 32, 1);
+    const int sT = mk3(T32 + z.offT[i], bp, rowsT, 1, bp, rowsT * bp, 32, 32, 1);
     const int R = Rq[E[i].po];
-    mThi[i] = mk(T_hi + z.offT[i], q.da, (long long)n * bp, (long long)n * bp, 128 / R);
-    mTlo[i] = mk(T_lo + z.offT[i], q.da, (long long)n * bp, (long long)n * bp, 128 / R);
+    mThi[i] = mk(T32 + z.offT[i], q.da, (long long)n * bp, (long long)n * bp, 128 / R);
+    mTlo[i] = -1;
     int bbox = R > 1 ? 128 / R : ntile_of(q.db);
-    mBhi[i] = mk(P.Bp_hi + w.offBp[i], q.db, (long long)n * w.bpad[i], (long long)n * w.bpad[i], bbox);
-    mBlo[i] = mk(P.Bp_lo + w.offBp[i], q.db, (long long)n * w.bpad[i], (long long)n * w.bpad[i], bbox);
+    mBhi[i] = mk(P.B32 + w.offBp[i], q.db, (long long)n * w.bpad[i], (long long)n * w.bpad[i], bbox);
+    mBlo[i] = -1;
     TSeg sg;
-    sg.mA_hi = ahi; sg.mA_lo = alo; sg.mB_hi = mPhi[E[i].pi]; sg.mB_lo = mPlo[E[i].pi];
+    memset(&sg, 0, sizeof sg);
+    sg.mA_hi = ahi; sg.mA_lo = -1; sg.mB_hi = mPhi[E[i].pi]; sg.mB_lo = mPlo[E[i].pi];
     sg.K = p.da;
     sg.k0 = 0;
     int seg = (int)segs.size();
@@ -1377,7 +1375,7 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo
         t.seg0 = seg; t.nseg = 1;
         t.M = M; t.N = N; t.m0 = m0; t.n0 = n0; t.ntile = nt;
         t.mode = TW_SPLIT; t.alpha = alpha[i];
-        t.mOut_hi = sThi; t.mOut_lo = sTlo; t.zout = 0;
+        t.mOut_hi = sT; t.mOut_lo = -1; t.zout = 0;
         w1.push_back(t);
       }
   }
@@ -1505,7 +1503,7 @@ void build_tf32(dmrg_ctx *C) {
   Tf32Scratch zmax = tf32_scratch_sizes(w, tune ? KSUB_CANDIDATES[0] : best);
   auto fl = [&](long long n) { return (float *)w.buf.alloc(4 * std::max<long long>(n, 64)); };
   P.P_hi = fl(zmax.nP); P.P_lo = fl(zmax.nP);
-  P.T_hi = fl(zmax.nT); P.T_lo = fl(zmax.nT);
+  P.T32 = fl(zmax.nT);
   P.ws = fl(zmax.nws);
   P.err = (int *)w.buf.alloc(sizeof(int));
   CK(cudaMemsetAsync(P.err, 0, sizeof(int), s));
@@ -1520,7 +1518,7 @@ void build_tf32(dmrg_ctx *C) {
     float best_ms = 1e30f;
     for (int ks : KSUB_CANDIDATES) {
       Tf32Scratch z = tf32_scratch_sizes(w, ks);
-      tf32_tables(w, z, P.P_hi, P.P_lo, P.T_hi, P.T_lo, P.ws, C->tables, ks);
+      tf32_tables(w, z, P.P_hi, P.P_lo, P.T32, P.ws, C->tables, ks);
       upload_tables(C, C->tables, s);
       launch_tf32(C, x, y, s);   // warm
       CK(cudaEventRecord(e0, s));
@@ -1541,7 +1539,7 @@ void build_tf32(dmrg_ctx *C) {
   }
   w.ksub = best;
   Tf32Scratch z = tf32_scratch_sizes(w, best);
-  tf32_tables(w, z, P.P_hi, P.P_lo, P.T_hi, P.T_lo, P.ws, C->tables, best);
+  tf32_tables(w, z, P.P_hi, P.P_lo, P.T32, P.ws, C->tables, best);
   upload_tables(C, C->tables, s);
   CK(cudaStreamSynchronize(s));
   w.tf_ready = true;
@@ -2722,7 +2720,7 @@ int dmrg_heff_apply_tf32_static(dmrg_ctx *C, const double *psi, double *sigma, v
     CK(tf32_prepare());
     int dev = 0;
     CK(cudaGetDevice(&dev));
-    // layout: [error flag | tables | P hi, P lo | T hi, T lo | partial tiles]
+    // layout: [error flag | tables | P hi, P lo | T | partial tiles]
     struct Owner {
       long long gen = -1;
       Tf32Tables tb;
@@ -2739,7 +2737,7 @@ int dmrg_heff_apply_tf32_static(dmrg_ctx *C, const double *psi, double *sigma, v
       Tf32Scratch z = tf32_scratch_sizes(w, ks);
       // table sizes do not depend on the pointers: size them with a dry run
       Tf32Tables probe;
-      tf32_tables(w, z, (float *)b, (float *)b, (float *)b, (float *)b, (float *)b, probe, ks);
+      tf32_tables(w, z, (float *)b, (float *)b, (float *)b, (float *)b, probe, ks);
       size_t off = 256;
       ow.o_maps = off; off = al(off + probe.maps.size() * sizeof(CUtensorMap));
       ow.o_seg = off; off = al(off + probe.segs.size() * sizeof(TSeg));
@@ -2753,8 +2751,6 @@ int dmrg_heff_apply_tf32_static(dmrg_ctx *C, const double *psi, double *sigma, v
       off = al(off + 4 * (size_t)z.nP);
       const size_t oT = off;
       off = al(off + 4 * (size_t)z.nT);
-      const size_t oT2 = off;
-      off = al(off + 4 * (size_t)z.nT);
       const size_t oW = off;
       off = al(off + 4 * (size_t)z.nws);
       if (off > cap)
@@ -2762,7 +2758,7 @@ int dmrg_heff_apply_tf32_static(dmrg_ctx *C, const double *psi, double *sigma, v
                            "(use dmrg_heff_apply for larger windows)", off, cap);
       ow.gen = -1;
       tf32_tables(w, z, (float *)(b + oP), (float *)(b + oP2), (float *)(b + oT),
-                  (float *)(b + oT2), (float *)(b + oW), ow.tb, ks);
+                  (float *)(b + oW), ow.tb, ks);
       const Tf32Tables &t = ow.tb;
       auto put = [&](size_t o, const void *src, size_t n) {
         if (n) CK(cudaMemcpyAsync(b + o, src, n, cudaMemcpyHostToDevice, s));

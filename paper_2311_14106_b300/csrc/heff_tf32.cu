@@ -3,12 +3,15 @@
 //
 // Stage 1:  T[(a',k), b]  = sign * A_stack[(a',k), a] . psi[a, b]
 // Stage 2:  sigma[a', b'] = sum_segments T[a', (k,b)] . B_stack[b', (k,b)]^T
-// Both are C = A . B^T with K-major operands.  Each FP64 operand x is held as
-// x_hi + x_lo (TF32 each); a product is lo.hi + hi.lo + hi.hi (lo.lo, of
-// relative size 2^-22, is below the FP32 accumulation error) with FP32
-// accumulation in tensor memory.  A work item is one 128 x ntile output tile;
-// per 32-wide K chunk the producer loads A_hi, A_lo, B_hi, B_lo by TMA and the
-// MMA warp issues 4 k-steps x 4 tcgen05.mma.
+// Both are C = A . B^T with K-major operands.  The operator stacks and T are
+// FP32 in device memory; psi^T comes split as TF32 (hi, lo).  Each FP32
+// operand chunk is split on chip: the tensor core reads the FP32 tile as the
+// high part (top 19 bits) and converter warps write the low part next to it.
+// A product is lo.hi + hi.lo + hi.hi (lo.lo, of relative size 2^-22, is
+// below the FP32 accumulation error) with FP32 accumulation in tensor
+// memory.  A work item is one 128 x ntile output tile; per 32-wide K chunk
+// the producer loads A and B (and psi^T's low part) by TMA, the converters
+// add the low parts and the MMA warp issues 4 k-steps x 3 tcgen05.mma.
 // Every mbarrier wait is bounded; on timeout the kernel records an error
 // code, skips the remaining work, frees its TMEM and returns.
 #include <cuda.h>
@@ -26,10 +29,10 @@ constexpr int BK = 32;            // floats per 128-byte swizzle row
 constexpr int TILE_A = BM * BK * 4;          // 16 KB
 constexpr int MAX_SMEM = 232448;             // 227 KB per CTA
 constexpr int NACC = 4;                      // TMEM accumulators (4 x 128 columns)
-constexpr int STAGE_OUT = 4 * 2 * 4096;      // epilogue staging: 4 warps x (hi, lo) 32 x 32
+constexpr int STAGE_OUT = 4 * 4096;          // epilogue staging: 4 warps x one 32 x 32 box
 
 // Pipeline geometry for a launch whose tiles are at most NT columns wide:
-// a stage holds A_hi, A_lo (128 x 32 each) and B_hi, B_lo (NT x 32 each).
+// a stage holds A, A_lo (128 x 32 each) and B, B_lo (NT x 32 each).
 template <int NT>
 struct Geo {
   static constexpr int TILE_B = NT * BK * 4;
@@ -156,16 +159,39 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(r);
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+
+// four FP32 values at src -> their low TF32 parts at dst
+__device__ __forceinline__ void lo_split4(uint32_t src, uint32_t dst) {
+  float x[4];
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3])
+               : "r"(src)
+               : "memory");
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float hi = __uint_as_float(__float_as_uint(x[i]) & 0xffffe000u);
+    x[i] = tf32_round(x[i] - hi);
+  }
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "f"(x[0]), "f"(x[1]),
+               "f"(x[2]), "f"(x[3])
+               : "memory");
+}
+
 // Persistent, warp-specialised 3xTF32 GEMM.  Each CTA walks the work list
 // with stride gridDim.x (the list is sorted by cost, largest first):
 //   warp 0, lane 0   TMA producer over all K chunks of all its tiles
-//   warp 1, lane 0   MMA issuer, alternating between two TMEM accumulators
+//   warp 1, lane 0   MMA issuer, rotating over four TMEM accumulators
 //   warps 2..5       epilogue: drain an accumulator while the next tile runs
-constexpr int NTHREADS = 192;
+//   warps 6..9       converters: split each FP32 operand chunk on chip
+constexpr int NTHREADS = 320;
+constexpr int NCONV = 128;
 constexpr int ACC_COLS = 128;
 
 struct Shared {
-  uint64_t full[8], empty[8], acc_full[NACC], acc_empty[NACC];
+  uint64_t full[8], conv[8], empty[8], acc_full[NACC], acc_empty[NACC];
   uint32_t tmem;
   int abort;
 };
@@ -201,6 +227,7 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
   if (threadIdx.x == 0) {
     for (int i = 0; i < STAGES; ++i) {
       mbar_init(smem_u32(&sh->full[i]), 1);
+      mbar_init(smem_u32(&sh->conv[i]), NCONV);
       mbar_init(smem_u32(&sh->empty[i]), 1);
     }
     for (int i = 0; i < NACC; ++i) {
@@ -228,14 +255,17 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
       int it = 0;
       for (int t = blockIdx.x; t < nwork && !*abort_flag; t += gridDim.x) {
         const TWork w = works[t];
-        const uint32_t stage_tx = 2 * TILE_A + 2 * (uint32_t)w.ntile * BK * 4;
+        // stage 2 (partial tiles) reads B as FP32 and splits it on chip;
+        // stage 1 reads psi^T already split (hi, lo)
+        const bool bsplit = w.mode == TW_PARTIAL;
+        const uint32_t stage_tx = TILE_A + (bsplit ? 1u : 2u) * (uint32_t)w.ntile * BK * 4;
         if (w.R > 1) {
           // packed tile: per chunk, group r's rows of A and B from its own
           // segment (a chunk past the segment's end loads zeros)
           const uint32_t ga = (BM / w.R) * BK * 4, gb = (uint32_t)(w.ntile / w.R) * BK * 4;
           uint32_t tx = 0;
           for (int r = 0; r < w.R; ++r)
-            if (w.pseg[r] >= 0) tx += 2 * ga + 2 * gb;
+            if (w.pseg[r] >= 0) tx += ga + gb;
           for (int kc = 0; kc < w.nchunk; ++kc, ++it) {
             const int st = it % STAGES;
             const uint32_t ph = (it / STAGES) & 1;
@@ -248,9 +278,7 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
               const TSeg sg = segs[w.pseg[r]];
               const int kx = kc * BK < sg.K ? sg.k0 + kc * BK : sg.xoob;
               tma_load(smem_u32(base + r * ga), &maps[sg.mA_hi], kx, 0, fb);
-              tma_load(smem_u32(base + TILE_A + r * ga), &maps[sg.mA_lo], kx, 0, fb);
               tma_load(smem_u32(base + 2 * TILE_A + r * gb), &maps[sg.mB_hi], kx, 0, fb);
-              tma_load(smem_u32(base + 2 * TILE_A + TILE_B + r * gb), &maps[sg.mB_lo], kx, 0, fb);
             }
           }
           continue;
@@ -267,9 +295,8 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
             mbar_expect_tx(fb, stage_tx);
             const int kx = sg.k0 + kc * BK;
             tma_load(smem_u32(base), &maps[sg.mA_hi], kx, w.m0, fb);
-            tma_load(smem_u32(base + TILE_A), &maps[sg.mA_lo], kx, w.m0, fb);
             tma_load(smem_u32(base + 2 * TILE_A), &maps[sg.mB_hi], kx, w.n0, fb);
-            tma_load(smem_u32(base + 2 * TILE_A + TILE_B), &maps[sg.mB_lo], kx, w.n0, fb);
+            if (!bsplit) tma_load(smem_u32(base + 2 * TILE_A + TILE_B), &maps[sg.mB_lo], kx, w.n0, fb);
           }
         }
       }
@@ -296,7 +323,7 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
           for (int kc = 0; kc < nk; ++kc, ++it) {
             const int st = it % STAGES;
             const uint32_t ph = (it / STAGES) & 1;
-            if (!wait_or_abort(smem_u32(&sh->full[st]), ph, err, 3, abort_flag)) break;
+            if (!wait_or_abort(smem_u32(&sh->conv[st]), ph, err, 3, abort_flag)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a_hi = smem_u32(smem + st * STAGE_BYTES);
             const uint32_t a_lo = a_hi + TILE_A;
@@ -321,6 +348,41 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
         mma_commit(smem_u32(&sh->acc_full[acc]));
       }
     }
+  } else if (warp >= 6) {
+    // ---------------- converters (warps 6..9) ----------------
+    // For every chunk (same order as the producer) write the low parts
+    // lo = rna_tf32(x - trunc_tf32(x)) of the FP32 operand tiles next to
+    // them; the tensor core reads the FP32 tile itself as the high part (it
+    // uses the top 19 bits), so hi + lo carries x to ~2^-22.  The layout is
+    // elementwise, so the swizzled tile maps to the same swizzled offsets.
+    const int tid = threadIdx.x - 6 * 32;
+    int it = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < nwork && ok; t += gridDim.x) {
+      const TWork w = works[t];
+      const bool bsplit = w.mode == TW_PARTIAL;
+      int nk = 0;
+      if (w.R > 1) {
+        nk = w.nchunk;
+      } else {
+        for (int s = 0; s < w.nseg; ++s) nk += (segs[w.seg0 + s].K + BK - 1) / BK;
+      }
+      const int nb4 = bsplit ? w.ntile * BK / 4 : 0;   // float4s of the B tile
+      for (int kc = 0; kc < nk; ++kc, ++it) {
+        const int st = it % STAGES;
+        if (!wait_or_abort(smem_u32(&sh->full[st]), (it / STAGES) & 1, err, 5, abort_flag)) {
+          ok = false;
+          break;
+        }
+        const uint32_t a = smem_u32(smem + st * STAGE_BYTES);
+#pragma unroll 4
+        for (int i = tid; i < TILE_A / 16; i += NCONV) lo_split4(a + 16 * i, a + TILE_A + 16 * i);
+        const uint32_t b = a + 2 * TILE_A;
+        for (int i = tid; i < nb4; i += NCONV) lo_split4(b + 16 * i, b + TILE_B + 16 * i);
+        fence_async_shared();
+        mbar_arrive(smem_u32(&sh->conv[st]));
+      }
+    }
   } else {
     // ---------------- epilogue (warps 2..5) ----------------
     // Each lane holds one accumulator row.  Per 32-column block the warp
@@ -329,7 +391,7 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
     // lane stores it by TMA; the tensor map clips rows and columns outside
     // the destination.
     const int quarter = warp & 3;            // TMEM lanes 32*quarter .. +31
-    const uint32_t stg_hi = smem_u32(stage_out + (warp - 2) * 8192), stg_lo = stg_hi + 4096;
+    const uint32_t stg = smem_u32(stage_out + (warp - 2) * 4096);
     const uint32_t rowoff = (uint32_t)lane * 128;
     int j = 0;
     for (int t = blockIdx.x; t < nwork; t += gridDim.x, ++j) {
@@ -366,31 +428,15 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
           }
           if (lane == 0) bulk_wait_read();
           __syncwarp();
-          if (w.mode == TW_SPLIT) {
+          const float al = w.mode == TW_SPLIT ? w.alpha : 1.f;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              float h[4], l[4];
-#pragma unroll
-              for (int i = 0; i < 4; ++i) {
-                const float x = w.alpha * v[4 * q + i];
-                h[i] = tf32_round(x);
-                l[i] = tf32_round(x - h[i]);
-              }
-              const uint32_t o = rowoff + ((uint32_t)(q ^ (lane & 7)) << 4);
-              st_shared_v4(stg_hi + o, h[0], h[1], h[2], h[3]);
-              st_shared_v4(stg_lo + o, l[0], l[1], l[2], l[3]);
-            }
-          } else {
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-              st_shared_v4(stg_hi + rowoff + ((uint32_t)(q ^ (lane & 7)) << 4), v[4 * q],
-                           v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-          }
+          for (int q = 0; q < 8; ++q)
+            st_shared_v4(stg + rowoff + ((uint32_t)(q ^ (lane & 7)) << 4), al * v[4 * q],
+                         al * v[4 * q + 1], al * v[4 * q + 2], al * v[4 * q + 3]);
           fence_async_shared();
           __syncwarp();
           if (lane == 0) {
-            tma_store3d(&maps[mo], xoff + c0, row0, zo, stg_hi);
-            if (w.mode == TW_SPLIT) tma_store3d(&maps[w.mOut_lo], xoff + c0, row0, zo, stg_lo);
+            tma_store3d(&maps[mo], xoff + c0, row0, zo, stg);
             bulk_commit();
           }
         }

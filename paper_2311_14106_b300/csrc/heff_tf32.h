@@ -15,7 +15,8 @@ namespace dmrg {
 
 // One K-segment: A (M x K) and B (N x K), each as (hi, lo) tensor maps.
 struct TSeg {
-  int mA_hi, mA_lo, mB_hi, mB_lo;   // indices into the tensor-map table
+  int mA_hi, mA_lo, mB_hi, mB_lo;   // indices into the tensor-map table (FP32
+                                    // operands use the _hi map only)
   int K;             // length of this K range
   int k0;            // first K index (multiple of 32)
   int xoob;          // a K coordinate past the maps' extent (loads read zeros)
@@ -23,8 +24,8 @@ struct TSeg {
 };
 
 // Epilogue of a work item.
-enum { TW_SPLIT = 0,      // alpha * C split into TF32 (hi, lo), stored to T
-       TW_PARTIAL = 1 };  // C stored as an FP32 partial tile (split-K slot)
+enum { TW_SPLIT = 0,      // stage 1: alpha * C stored to T (FP32)
+       TW_PARTIAL = 1 };  // stage 2: C stored as an FP32 partial tile (split-K slot)
 
 // One 128 x ntile output tile.  The epilogue stores it by TMA through 3-D
 // tensor maps (x column, y row, z slot) with 32 x 32 boxes; the maps clip
@@ -36,7 +37,7 @@ struct TWork {
   int ntile;         // UMMA N of this tile (multiple of 16, <= 128)
   int mode;          // TW_SPLIT or TW_PARTIAL
   float alpha;
-  int mOut_hi, mOut_lo;   // store maps (mOut_lo unused for TW_PARTIAL)
+  int mOut_hi, mOut_lo;   // store map (mOut_lo unused)
   int zout;               // z coordinate of the destination (partial slot)
   // Packed partial tiles (R = 2 or 4; R = 1 otherwise): R independent
   // segments, each with at most 128/R rows and columns, share one MMA
@@ -63,10 +64,12 @@ struct PartialSum {
 };
 
 struct Tf32Plan {
-  // split operand storage (float, padded rows)
-  float *A_hi = nullptr, *A_lo = nullptr;     // [a'][k][a], rows 16-byte aligned
-  float *Bp_hi = nullptr, *Bp_lo = nullptr;   // [b'][k][b], b padded to 4 floats
-  float *P_hi = nullptr, *P_lo = nullptr, *T_hi = nullptr, *T_lo = nullptr;
+  // operand storage (float, padded rows): operator stacks and the stage-1
+  // intermediate in FP32 (split on chip), psi^T split as TF32 (hi, lo)
+  float *A32 = nullptr;                // [a'][k][a], rows 16-byte aligned
+  float *B32 = nullptr;                // [b'][k][b], b padded to 4 floats
+  float *T32 = nullptr;                // [a'][k][b], b padded to 4 floats
+  float *P_hi = nullptr, *P_lo = nullptr;
   CUtensorMap *maps = nullptr;      // device copy of the tensor maps
   TSeg *seg = nullptr;
   TWork *work1 = nullptr, *work2 = nullptr;

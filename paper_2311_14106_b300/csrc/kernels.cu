@@ -259,16 +259,24 @@ __global__ void k_split2d(const Split2D *__restrict__ ds, const double *__restri
       if (d.trans) {
         int c = c0 + j, r = r0 + threadIdx.x;
         if (c < d.cols && r < d.rows) {
-          split1(tile[threadIdx.x][j], h, l);
-          d.hi[(long long)c * d.dst_ld + r] = h;
-          d.lo[(long long)c * d.dst_ld + r] = l;
+          if (d.lo) {
+            split1(tile[threadIdx.x][j], h, l);
+            d.hi[(long long)c * d.dst_ld + r] = h;
+            d.lo[(long long)c * d.dst_ld + r] = l;
+          } else {
+            d.hi[(long long)c * d.dst_ld + r] = (float)tile[threadIdx.x][j];
+          }
         }
       } else {
         int r = r0 + j, c = c0 + threadIdx.x;
         if (c < d.cols && r < d.rows) {
-          split1(tile[j][threadIdx.x], h, l);
-          d.hi[(long long)r * d.dst_ld + c] = h;
-          d.lo[(long long)r * d.dst_ld + c] = l;
+          if (d.lo) {
+            split1(tile[j][threadIdx.x], h, l);
+            d.hi[(long long)r * d.dst_ld + c] = h;
+            d.lo[(long long)r * d.dst_ld + c] = l;
+          } else {   // FP32 copy (round to nearest)
+            d.hi[(long long)r * d.dst_ld + c] = (float)tile[j][threadIdx.x];
+          }
         }
       }
     }

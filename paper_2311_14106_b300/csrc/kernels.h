@@ -75,7 +75,8 @@ struct SCopy {
 };
 
 // Split of an FP64 matrix into TF32 (hi, lo) float matrices with a padded
-// row stride; trans = 1 writes the transpose (cols x rows).
+// row stride (lo == NULL: an FP32 copy into hi, rounded to nearest);
+// trans = 1 writes the transpose (cols x rows).
 struct Split2D {
   const double *src;     // (rows x cols), row stride src_ld
   long long src_ld;
