@@ -302,10 +302,10 @@ def main():
     plan = g.heff_split_plan()
     # per-kernel event marks: [psi split, stage 1, stage 2, partial sum]
     # Algorithmic bytes: operator stacks read once (FP32, 4 B/element), psi
-    # read once (TF32 hi+lo), the intermediate T written by stage 1 and read
+    # read once (FP32), the intermediate T written by stage 1 and read
     # by stage 2 (FP32), sigma partials written once (FP32)
     kern = {
-        "k_tf32_gemm stage1": (st_split[1], 4 * (si["nA"] + si["nT"]) + 8 * si["psi_len"],
+        "k_tf32_gemm stage1": (st_split[1], 4 * (si["nA"] + si["nT"]) + 4 * si["psi_len"],
                                si["flops1"]),
         "k_tf32_gemm stage2": (st_split[2], 4 * (si["nT"] + si["nB"]) + 4 * si["psi_len"],
                                si["flops2"]),

@@ -1165,7 +1165,7 @@ long long a64(long long x) { return (x + 63) & ~63LL; }
 int ntile_of(int n) { return n > 128 ? 128 : ((n + 15) / 16) * 16; }
 
 // Sizes (floats) of the per-apply scratch of the split path: psi split
-// (P hi/lo), stage-1 intermediate (T, FP32) and stage-2 partial tiles (ws).
+// (P, FP32), stage-1 intermediate (T, FP32) and stage-2 partial tiles (ws).
 struct Tf32Scratch {
   long long nP = 0, nT = 0, nws = 0;
   std::vector<long long> offP, offT, ldP, ldT;
@@ -1278,9 +1278,8 @@ void tf32_operator_copies(dmrg_ctx *C) {
   w.tf_copies = true;
 }
 
-// psi (FP64, [a][b] per sector block) -> TF32 hi/lo, transposed to [b][a]
-std::vector<Split2D> psi_split_descs(const Window &w, const Tf32Scratch &z, float *P_hi,
-                                     float *P_lo) {
+// psi (FP64, [a][b] per sector block) -> FP32, transposed to [b][a]
+std::vector<Split2D> psi_split_descs(const Window &w, const Tf32Scratch &z, float *P32) {
   std::vector<Split2D> out;
   for (size_t i = 0; i < w.psi.size(); ++i) {
     Split2D d;
@@ -1291,21 +1290,21 @@ std::vector<Split2D> psi_split_descs(const Window &w, const Tf32Scratch &z, floa
     d.rows = w.psi[i].da;
     d.cols = w.psi[i].db;
     d.trans = 1;
-    d.hi = P_hi + z.offP[i];
-    d.lo = P_lo + z.offP[i];
+    d.hi = P32 + z.offP[i];
+    d.lo = nullptr;
     d.dst_ld = z.ldP[i];
     out.push_back(d);
   }
   return out;
 }
 
-void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo, float *T32,
-                 float *ws, Tf32Tables &out, int KSUB) {
+void tf32_tables(const Window &w, const Tf32Scratch &z, float *P32, float *T32, float *ws,
+                 Tf32Tables &out, int KSUB) {
   const Tf32Plan &P = w.tf;
   const auto &E = w.s1info;
   const size_t ne = E.size(), np = w.psi.size();
   out = Tf32Tables();
-  out.psi_split = psi_split_descs(w, z, P_hi, P_lo);
+  out.psi_split = psi_split_descs(w, z, P32);
   auto &maps = out.maps;
   auto mk = [&](const float *base, long long rows, long long cols, long long ld, int box) {
     CUtensorMap m;
@@ -1322,12 +1321,10 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo
     maps.push_back(m);
     return (int)maps.size() - 1;
   };
-  std::vector<int> mPhi(np), mPlo(np);
+  std::vector<int> mP(np);
   for (size_t i = 0; i < np; ++i) {
     const PsiBlk &p = w.psi[i];
-    int box = ntile_of(p.db);
-    mPhi[i] = mk(P_hi + z.offP[i], p.db, p.da, z.ldP[i], box);
-    mPlo[i] = mk(P_lo + z.offP[i], p.db, p.da, z.ldP[i], box);
+    mP[i] = mk(P32 + z.offP[i], p.db, p.da, z.ldP[i], ntile_of(p.db));
   }
   auto &segs = out.segs;
   auto &w1 = out.w1;
@@ -1362,7 +1359,7 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P_hi, float *P_lo
     mBlo[i] = -1;
     TSeg sg;
     memset(&sg, 0, sizeof sg);
-    sg.mA_hi = ahi; sg.mA_lo = -1; sg.mB_hi = mPhi[E[i].pi]; sg.mB_lo = mPlo[E[i].pi];
+    sg.mA_hi = ahi; sg.mA_lo = -1; sg.mB_hi = mP[E[i].pi]; sg.mB_lo = -1;
     sg.K = p.da;
     sg.k0 = 0;
     int seg = (int)segs.size();
@@ -1502,7 +1499,7 @@ void build_tf32(dmrg_ctx *C) {
   // scratch sized for the smallest candidate (most partial tiles)
   Tf32Scratch zmax = tf32_scratch_sizes(w, tune ? KSUB_CANDIDATES[0] : best);
   auto fl = [&](long long n) { return (float *)w.buf.alloc(4 * std::max<long long>(n, 64)); };
-  P.P_hi = fl(zmax.nP); P.P_lo = fl(zmax.nP);
+  P.P32 = fl(zmax.nP);
   P.T32 = fl(zmax.nT);
   P.ws = fl(zmax.nws);
   P.err = (int *)w.buf.alloc(sizeof(int));
@@ -1518,7 +1515,7 @@ void build_tf32(dmrg_ctx *C) {
     float best_ms = 1e30f;
     for (int ks : KSUB_CANDIDATES) {
       Tf32Scratch z = tf32_scratch_sizes(w, ks);
-      tf32_tables(w, z, P.P_hi, P.P_lo, P.T32, P.ws, C->tables, ks);
+      tf32_tables(w, z, P.P32, P.T32, P.ws, C->tables, ks);
       upload_tables(C, C->tables, s);
       launch_tf32(C, x, y, s);   // warm
       CK(cudaEventRecord(e0, s));
@@ -1539,7 +1536,7 @@ void build_tf32(dmrg_ctx *C) {
   }
   w.ksub = best;
   Tf32Scratch z = tf32_scratch_sizes(w, best);
-  tf32_tables(w, z, P.P_hi, P.P_lo, P.T32, P.ws, C->tables, best);
+  tf32_tables(w, z, P.P32, P.T32, P.ws, C->tables, best);
   upload_tables(C, C->tables, s);
   CK(cudaStreamSynchronize(s));
   w.tf_ready = true;
@@ -2720,7 +2717,7 @@ int dmrg_heff_apply_tf32_static(dmrg_ctx *C, const double *psi, double *sigma, v
     CK(tf32_prepare());
     int dev = 0;
     CK(cudaGetDevice(&dev));
-    // layout: [error flag | tables | P hi, P lo | T | partial tiles]
+    // layout: [error flag | tables | psi^T | T | partial tiles]
     struct Owner {
       long long gen = -1;
       Tf32Tables tb;
@@ -2737,7 +2734,7 @@ int dmrg_heff_apply_tf32_static(dmrg_ctx *C, const double *psi, double *sigma, v
       Tf32Scratch z = tf32_scratch_sizes(w, ks);
       // table sizes do not depend on the pointers: size them with a dry run
       Tf32Tables probe;
-      tf32_tables(w, z, (float *)b, (float *)b, (float *)b, (float *)b, probe, ks);
+      tf32_tables(w, z, (float *)b, (float *)b, (float *)b, probe, ks);
       size_t off = 256;
       ow.o_maps = off; off = al(off + probe.maps.size() * sizeof(CUtensorMap));
       ow.o_seg = off; off = al(off + probe.segs.size() * sizeof(TSeg));
@@ -2747,8 +2744,6 @@ int dmrg_heff_apply_tf32_static(dmrg_ctx *C, const double *psi, double *sigma, v
       ow.o_split = off; off = al(off + probe.psi_split.size() * sizeof(Split2D));
       const size_t oP = off;
       off = al(off + 4 * (size_t)z.nP);
-      const size_t oP2 = off;
-      off = al(off + 4 * (size_t)z.nP);
       const size_t oT = off;
       off = al(off + 4 * (size_t)z.nT);
       const size_t oW = off;
@@ -2757,8 +2752,7 @@ int dmrg_heff_apply_tf32_static(dmrg_ctx *C, const double *psi, double *sigma, v
         fail(DMRG_ERR_ARG, "window needs %zu bytes of scratch; the static scratch holds %zu bytes "
                            "(use dmrg_heff_apply for larger windows)", off, cap);
       ow.gen = -1;
-      tf32_tables(w, z, (float *)(b + oP), (float *)(b + oP2), (float *)(b + oT),
-                  (float *)(b + oW), ow.tb, ks);
+      tf32_tables(w, z, (float *)(b + oP), (float *)(b + oT), (float *)(b + oW), ow.tb, ks);
       const Tf32Tables &t = ow.tb;
       auto put = [&](size_t o, const void *src, size_t n) {
         if (n) CK(cudaMemcpyAsync(b + o, src, n, cudaMemcpyHostToDevice, s));

@@ -32,16 +32,20 @@ constexpr int NACC = 4;                      // TMEM accumulators (4 x 128 colum
 constexpr int STAGE_OUT = 4 * 4096;          // epilogue staging: 4 warps x one 32 x 32 box
 
 // Pipeline geometry for a launch whose tiles are at most NT columns wide:
-// a stage holds A, A_lo (128 x 32 each) and B, B_lo (NT x 32 each).
+// a TMA stage holds the FP32 chunks A (128 x 32) and B (NT x 32); a low-part
+// slot holds A_lo and B_lo.  The FP32 chunks stay until the MMAs that read
+// them as high parts complete; the low parts need only LO slots.
+constexpr int LO = 2;
 template <int NT>
 struct Geo {
   static constexpr int TILE_B = NT * BK * 4;
-  static constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;
-  static constexpr int STAGES_RAW = (MAX_SMEM - 1024 - 512 - STAGE_OUT) / STAGE_BYTES;
-  static constexpr int STAGES = STAGES_RAW > 6 ? 6 : STAGES_RAW;
-  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 512 + STAGE_OUT;
+  static constexpr int STAGE_BYTES = TILE_A + TILE_B;
+  static constexpr int STAGES_RAW =
+      (MAX_SMEM - 1024 - 512 - STAGE_OUT - LO * STAGE_BYTES) / STAGE_BYTES;
+  static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
+  static constexpr int SMEM_BYTES = (STAGES + LO) * STAGE_BYTES + 1024 + 512 + STAGE_OUT;
 };
-static_assert(Geo<128>::STAGES >= 3, "pipeline too shallow");
+static_assert(Geo<128>::STAGES >= 4, "pipeline too shallow");
 constexpr long long WAIT_LIMIT = 1LL << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -185,13 +189,13 @@ __device__ __forceinline__ void lo_split4(uint32_t src, uint32_t dst) {
 //   warp 0, lane 0   TMA producer over all K chunks of all its tiles
 //   warp 1, lane 0   MMA issuer, rotating over four TMEM accumulators
 //   warps 2..5       epilogue: drain an accumulator while the next tile runs
-//   warps 6..9       converters: split each FP32 operand chunk on chip
-constexpr int NTHREADS = 320;
-constexpr int NCONV = 128;
+//   warps 6..13      converters: split each FP32 operand chunk on chip
+constexpr int NTHREADS = 448;
+constexpr int NCONV = 256;
 constexpr int ACC_COLS = 128;
 
 struct Shared {
-  uint64_t full[8], conv[8], empty[8], acc_full[NACC], acc_empty[NACC];
+  uint64_t full[8], empty[8], lo_full[LO], lo_empty[LO], acc_full[NACC], acc_empty[NACC];
   uint32_t tmem;
   int abort;
 };
@@ -219,7 +223,8 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
   constexpr int TILE_B = G::TILE_B;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t *stage_out = smem + STAGES * STAGE_BYTES;      // 1024-byte aligned
+  uint8_t *lo_ring = smem + STAGES * STAGE_BYTES;        // low parts
+  uint8_t *stage_out = lo_ring + LO * STAGE_BYTES;       // 1024-byte aligned
   Shared *sh = (Shared *)(stage_out + STAGE_OUT);
   volatile int *abort_flag = &sh->abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -227,8 +232,11 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
   if (threadIdx.x == 0) {
     for (int i = 0; i < STAGES; ++i) {
       mbar_init(smem_u32(&sh->full[i]), 1);
-      mbar_init(smem_u32(&sh->conv[i]), NCONV);
       mbar_init(smem_u32(&sh->empty[i]), 1);
+    }
+    for (int i = 0; i < LO; ++i) {
+      mbar_init(smem_u32(&sh->lo_full[i]), NCONV);
+      mbar_init(smem_u32(&sh->lo_empty[i]), 1);
     }
     for (int i = 0; i < NACC; ++i) {
       mbar_init(smem_u32(&sh->acc_full[i]), 1);
@@ -255,10 +263,7 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
       int it = 0;
       for (int t = blockIdx.x; t < nwork && !*abort_flag; t += gridDim.x) {
         const TWork w = works[t];
-        // stage 2 (partial tiles) reads B as FP32 and splits it on chip;
-        // stage 1 reads psi^T already split (hi, lo)
-        const bool bsplit = w.mode == TW_PARTIAL;
-        const uint32_t stage_tx = TILE_A + (bsplit ? 1u : 2u) * (uint32_t)w.ntile * BK * 4;
+        const uint32_t stage_tx = TILE_A + (uint32_t)w.ntile * BK * 4;
         if (w.R > 1) {
           // packed tile: per chunk, group r's rows of A and B from its own
           // segment (a chunk past the segment's end loads zeros)
@@ -278,7 +283,7 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
               const TSeg sg = segs[w.pseg[r]];
               const int kx = kc * BK < sg.K ? sg.k0 + kc * BK : sg.xoob;
               tma_load(smem_u32(base + r * ga), &maps[sg.mA_hi], kx, 0, fb);
-              tma_load(smem_u32(base + 2 * TILE_A + r * gb), &maps[sg.mB_hi], kx, 0, fb);
+              tma_load(smem_u32(base + TILE_A + r * gb), &maps[sg.mB_hi], kx, 0, fb);
             }
           }
           continue;
@@ -295,8 +300,7 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
             mbar_expect_tx(fb, stage_tx);
             const int kx = sg.k0 + kc * BK;
             tma_load(smem_u32(base), &maps[sg.mA_hi], kx, w.m0, fb);
-            tma_load(smem_u32(base + 2 * TILE_A), &maps[sg.mB_hi], kx, w.n0, fb);
-            if (!bsplit) tma_load(smem_u32(base + 2 * TILE_A + TILE_B), &maps[sg.mB_lo], kx, w.n0, fb);
+            tma_load(smem_u32(base + TILE_A), &maps[sg.mB_hi], kx, w.n0, fb);
           }
         }
       }
@@ -323,12 +327,15 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
           for (int kc = 0; kc < nk; ++kc, ++it) {
             const int st = it % STAGES;
             const uint32_t ph = (it / STAGES) & 1;
-            if (!wait_or_abort(smem_u32(&sh->conv[st]), ph, err, 3, abort_flag)) break;
+            // the low parts of chunk `it` are ready (its FP32 chunk too)
+            const int ls = it % LO;
+            if (!wait_or_abort(smem_u32(&sh->lo_full[ls]), (it / LO) & 1, err, 3, abort_flag))
+              break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a_hi = smem_u32(smem + st * STAGE_BYTES);
-            const uint32_t a_lo = a_hi + TILE_A;
-            const uint32_t b_hi = a_hi + 2 * TILE_A;
-            const uint32_t b_lo = b_hi + TILE_B;
+            const uint32_t b_hi = a_hi + TILE_A;
+            const uint32_t a_lo = smem_u32(lo_ring + ls * STAGE_BYTES);
+            const uint32_t b_lo = a_lo + TILE_A;
             // k-steps of 8 that hold data (the rest of a ragged chunk is zero fill)
             const int rem = K - kc * BK;
             const int nk8 = rem >= BK ? BK / 8 : (rem + 7) / 8;
@@ -342,6 +349,7 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
               mma_tf32(d, sdesc(a_hi + ko), sdesc(b_hi + ko), id, 1);
             }
             mma_commit(smem_u32(&sh->empty[st]));
+            mma_commit(smem_u32(&sh->lo_empty[ls]));
           }
         }
         // every work item has K >= 1, so the accumulator always holds data
@@ -349,7 +357,7 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
       }
     }
   } else if (warp >= 6) {
-    // ---------------- converters (warps 6..9) ----------------
+    // ---------------- converters (warps 6..13) ----------------
     // For every chunk (same order as the producer) write the low parts
     // lo = rna_tf32(x - trunc_tf32(x)) of the FP32 operand tiles next to
     // them; the tensor core reads the FP32 tile itself as the high part (it
@@ -360,27 +368,27 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
     bool ok = true;
     for (int t = blockIdx.x; t < nwork && ok; t += gridDim.x) {
       const TWork w = works[t];
-      const bool bsplit = w.mode == TW_PARTIAL;
       int nk = 0;
       if (w.R > 1) {
         nk = w.nchunk;
       } else {
         for (int s = 0; s < w.nseg; ++s) nk += (segs[w.seg0 + s].K + BK - 1) / BK;
       }
-      const int nb4 = bsplit ? w.ntile * BK / 4 : 0;   // float4s of the B tile
+      const int n4 = (TILE_A + w.ntile * BK * 4) / 16;   // float4s of the A and B chunks
       for (int kc = 0; kc < nk; ++kc, ++it) {
-        const int st = it % STAGES;
-        if (!wait_or_abort(smem_u32(&sh->full[st]), (it / STAGES) & 1, err, 5, abort_flag)) {
+        const int st = it % STAGES, ls = it % LO;
+        if (!wait_or_abort(smem_u32(&sh->full[st]), (it / STAGES) & 1, err, 5, abort_flag) ||
+            !wait_or_abort(smem_u32(&sh->lo_empty[ls]), ((it / LO) & 1) ^ 1, err, 6, abort_flag)) {
           ok = false;
           break;
         }
-        const uint32_t a = smem_u32(smem + st * STAGE_BYTES);
+        // A (16 KB) and B (ntile rows) are contiguous in both slots
+        const uint32_t src = smem_u32(smem + st * STAGE_BYTES);
+        const uint32_t dst = smem_u32(lo_ring + ls * STAGE_BYTES);
 #pragma unroll 4
-        for (int i = tid; i < TILE_A / 16; i += NCONV) lo_split4(a + 16 * i, a + TILE_A + 16 * i);
-        const uint32_t b = a + 2 * TILE_A;
-        for (int i = tid; i < nb4; i += NCONV) lo_split4(b + 16 * i, b + TILE_B + 16 * i);
+        for (int i = tid; i < n4; i += NCONV) lo_split4(src + 16 * i, dst + 16 * i);
         fence_async_shared();
-        mbar_arrive(smem_u32(&sh->conv[st]));
+        mbar_arrive(smem_u32(&sh->lo_full[ls]));
       }
     }
   } else {

@@ -64,12 +64,11 @@ struct PartialSum {
 };
 
 struct Tf32Plan {
-  // operand storage (float, padded rows): operator stacks and the stage-1
-  // intermediate in FP32 (split on chip), psi^T split as TF32 (hi, lo)
+  // operand storage (FP32, padded rows; the kernels split it on chip)
   float *A32 = nullptr;                // [a'][k][a], rows 16-byte aligned
   float *B32 = nullptr;                // [b'][k][b], b padded to 4 floats
   float *T32 = nullptr;                // [a'][k][b], b padded to 4 floats
-  float *P_hi = nullptr, *P_lo = nullptr;
+  float *P32 = nullptr;                // psi^T per block, [b][a]
   CUtensorMap *maps = nullptr;      // device copy of the tensor maps
   TSeg *seg = nullptr;
   TWork *work1 = nullptr, *work2 = nullptr;
