@@ -1172,7 +1172,7 @@ struct Tf32Scratch {
 };
 
 const int KSUB_DEFAULT = 1024;   // longest K range of one stage-2 work item
-const int KSUB_CANDIDATES[3] = {512, 1024, 2048};
+const int KSUB_CANDIDATES[3] = {1024, 2048, 4096};
 
 std::vector<std::vector<int>> entries_into(const Window &w) {
   std::vector<std::vector<int>> into(w.psi.size());
@@ -1524,7 +1524,9 @@ void build_tf32(dmrg_ctx *C) {
       CK(cudaEventSynchronize(e1));
       float ms = 0;
       CK(cudaEventElapsedTime(&ms, e0, e1));
-      if (ms < best_ms) {
+      // candidates run smallest range first; a longer range (longer FP32
+      // accumulation) must win by more than 1.5% to be taken
+      if (ms < best_ms * 0.985f) {
         best_ms = ms;
         best = ks;
       }

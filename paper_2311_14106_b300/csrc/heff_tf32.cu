@@ -339,14 +339,18 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
             // k-steps of 8 that hold data (the rest of a ragged chunk is zero fill)
             const int rem = K - kc * BK;
             const int nk8 = rem >= BK ? BK / 8 : (rem + 7) / 8;
+            // descriptors of the chunk's tiles; a k-step of 8 tf32 (32 bytes
+            // along the swizzled row) adds 2 to the encoded start address
+            const uint64_t dah = sdesc(a_hi), dal = sdesc(a_lo), dbh = sdesc(b_hi),
+                           dbl = sdesc(b_lo);
             for (int k = 0; k < nk8; ++k) {
-              const uint32_t ko = k * 32;   // 8 tf32 = 32 bytes along the swizzled row
+              const uint64_t ko = 2 * k;
               // small terms first: lo.hi, hi.lo, then hi.hi (lo.lo is below
               // the FP32 accumulation error and is left out)
-              mma_tf32(d, sdesc(a_lo + ko), sdesc(b_hi + ko), id, accum);
+              mma_tf32(d, dal + ko, dbh + ko, id, accum);
               accum = 1;
-              mma_tf32(d, sdesc(a_hi + ko), sdesc(b_lo + ko), id, 1);
-              mma_tf32(d, sdesc(a_hi + ko), sdesc(b_hi + ko), id, 1);
+              mma_tf32(d, dah + ko, dbl + ko, id, 1);
+              mma_tf32(d, dah + ko, dbh + ko, id, 1);
             }
             mma_commit(smem_u32(&sh->empty[st]));
             mma_commit(smem_u32(&sh->lo_empty[ls]));
@@ -467,24 +471,55 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
 
 }  // namespace
 
-// One thread per sigma element; the partials are added in slot order (eight
-// loads in flight per step), so the result does not depend on the launch.
+// s + c += x with the rounding error of the add kept in c (Knuth's
+// branch-free two-sum): the sum of a few hundred FP32 partials stays accurate
+// to about 2^-24 of the total while using only FP32 arithmetic (FP64 units
+// are scarce on this part).
+__device__ __forceinline__ void two_sum_add(float &s, float &c, float x) {
+  const float t = s + x;
+  const float z = t - s;
+  c += (s - (t - z)) + (x - z);
+  s = t;
+}
+
+// One thread per four consecutive elements of a sigma row (partial rows are
+// 16-byte aligned: ld is a multiple of 4 floats); the partials are added in
+// slot order, eight float4 loads in flight per step, so the result does not
+// depend on the launch.
 __global__ void k_sum_partials(const PartialSum *__restrict__ ps, double *__restrict__ sigma) {
   const PartialSum p = ps[blockIdx.y];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += gridDim.x * blockDim.x) {
-    const long long r = i / p.cols, c = i - r * p.cols;
-    const float *src = p.ws + r * p.ld + c;
-    double acc = 0.0;
+  const int c4n = (p.cols + 3) / 4, rows = p.cols > 0 ? p.n / p.cols : 0;
+  const int n4 = rows * c4n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += gridDim.x * blockDim.x) {
+    const int r = i / c4n, c = (i - r * c4n) * 4;
+    const float4 *src = (const float4 *)(p.ws + (long long)r * p.ld + c);
+    const long long st4 = p.stride / 4;
+    float s0 = 0, s1 = 0, s2 = 0, s3 = 0, e0 = 0, e1 = 0, e2 = 0, e3 = 0;
     int k = 0;
     for (; k + 8 <= p.nparts; k += 8) {
-      float v[8];
+      float4 v[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = __ldg(src + (long long)(k + j) * p.stride);
+      for (int j = 0; j < 8; ++j) v[j] = __ldg(src + (long long)(k + j) * st4);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) acc += (double)v[j];
+      for (int j = 0; j < 8; ++j) {
+        two_sum_add(s0, e0, v[j].x);
+        two_sum_add(s1, e1, v[j].y);
+        two_sum_add(s2, e2, v[j].z);
+        two_sum_add(s3, e3, v[j].w);
+      }
     }
-    for (; k < p.nparts; ++k) acc += (double)src[(long long)k * p.stride];
-    sigma[p.off + i] = acc;
+    for (; k < p.nparts; ++k) {
+      const float4 v = __ldg(src + (long long)k * st4);
+      two_sum_add(s0, e0, v.x);
+      two_sum_add(s1, e1, v.y);
+      two_sum_add(s2, e2, v.z);
+      two_sum_add(s3, e3, v.w);
+    }
+    double *out = sigma + p.off + (long long)r * p.cols + c;
+    out[0] = (double)s0 + (double)e0;
+    if (c + 1 < p.cols) out[1] = (double)s1 + (double)e1;
+    if (c + 2 < p.cols) out[2] = (double)s2 + (double)e2;
+    if (c + 3 < p.cols) out[3] = (double)s3 + (double)e3;
   }
 }
 
@@ -543,7 +578,7 @@ int encode_map3(CUtensorMap *out, const float *base, long long d0, long long d1,
 
 cudaError_t sum_partials(const PartialSum *p, int n, double *sigma, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  dim3 grid(64, n);   // blocks beyond a block's elements exit at once
+  dim3 grid(32, n);   // blocks beyond a block's elements exit at once
   k_sum_partials<<<grid, 256, 0, s>>>(p, sigma);
   return cudaGetLastError();
 }

@@ -50,8 +50,9 @@ struct TWork {
 };
 
 // FP64 sum of the split-K partial tiles of one sigma block (rows x cols,
-// partial rows ld floats apart): sigma[off + r*cols + c] =
-// sum_p ws[p*stride + r*ld + c], summed in a fixed order.
+// partial rows ld floats apart, ld and stride multiples of 4, ws 16-byte
+// aligned): sigma[off + r*cols + c] = sum_p ws[p*stride + r*ld + c],
+// summed in a fixed order.
 struct PartialSum {
   const float *ws;
   long long stride;
