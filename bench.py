@@ -40,6 +40,22 @@ WORKLOADS = {
 CPU_SAMPLE = ("hubbard", 4, 4, (8, 8), 4.0, 64)
 
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# DRAM traffic per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, one
+# pass on the full window; profiles/launches_hubbard6x6_D1024.md), valid only for
+# the kernel source it was taken with: reported as null once that file changes.
+TRAFFIC_SOURCE = os.path.join(ROOT, "paper_2311_14106_b300", "csrc", "heff_tf32.cu")
+TRAFFIC_SHA = "c23e8b98166adb6b"
+TRAFFIC = {("hubbard6x6_D1024", "k_tf32_gemm stage1"): 4.987e9,
+           ("hubbard6x6_D1024", "k_tf32_gemm stage2"): 5.514e9}
+
+
+def traffic_of(workload, kernel):
+    import hashlib
+    try:
+        sha = hashlib.sha256(open(TRAFFIC_SOURCE, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return TRAFFIC.get((workload, kernel)) if sha == TRAFFIC_SHA else None
 TF32_OVER_BF16 = 1.1 / 2.25        # nominal dense tf32 / bf16 tensor ratio
 
 
@@ -189,7 +205,7 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="hubbard6x6_D1024", choices=sorted(WORKLOADS))
@@ -336,7 +352,8 @@ def main():
         "gpu_launches": plan["launches"] * args.steps,
         "roofline": {"kernel": dom, "bound": "tensor",
                      "achieved": None, "peak": tf32_peak, "unit": "TFLOP/s", "frac": None,
-                     "peak_source": f"{src} bf16 x nominal tf32/bf16 ratio", "traffic": None},
+                     "peak_source": f"{src} bf16 x nominal tf32/bf16 ratio",
+                     "traffic": traffic_of(args.workload, dom)},
     }
     t_dom = t_dom_ms * 1e-3
     gbs = dom_bytes / t_dom / 1e9
