@@ -150,14 +150,14 @@ int dmrg_heff_apply(dmrg_ctx *ctx, const double *psi, double *sigma,
  * cannot let the library allocate device memory on the call path (for
  * example code running under another framework's memory pool, or code that
  * must not trigger the implicit synchronisation of cudaMalloc / cudaFree).
- * The per-call scratch of the split path (psi as TF32 hi/lo, the stage-1
+ * The per-call scratch of the split path (psi^T in FP32, the stage-1
  * intermediate, the stage-2 partial tiles and the work tables) is taken from
  * a fixed 64 MiB array that every GPU loading this library holds until the
  * process exits; the call itself makes no cudaMalloc, cudaFree or other
  * allocating device call.
  *   - psi, sigma: device pointers as for dmrg_heff_apply; sigma is
  *     overwritten.  The result equals dmrg_heff_apply's split result.
- *   - Needs the window's TF32 operator copies, which the first
+ *   - Needs the window's FP32 operator copies, which the first
  *     dmrg_heff_apply with DMRG_SPLIT_TF32 creates (Errors: STATE if absent).
  *   - A window whose scratch exceeds 64 MiB is rejected with DMRG_ERR_ARG and
  *     a message giving the size it needs.
@@ -217,7 +217,7 @@ int dmrg_heff_stage_info(dmrg_ctx *ctx, double *out6);
 /* Per-kernel timing of dmrg_heff_apply with CUDA events recorded on the
  * apply stream.  enable = 1 starts (and zeroes) the accumulation, 0 stops
  * it.  out5 (may be NULL) receives accumulated milliseconds of
- * [0] psi split (split path), [1] stage 1, [2] stage 2, [3] FP64 sum of the
+ * [0] psi split (split path), [1] stage 1, [2] stage 2, [3] sum of the
  * split-K partial tiles (split path; the FP64 path sums inside stage 2),
  * and [4] the number of applies timed; reading synchronises the last timed
  * apply. */

@@ -2711,7 +2711,7 @@ int dmrg_heff_apply_tf32_static(dmrg_ctx *C, const double *psi, double *sigma, v
     Window &w = C->win;
     cudaStream_t s = (cudaStream_t)stream;
     if (!w.tf_copies)
-      fail(DMRG_ERR_STATE, "TF32 operator copies not built: call dmrg_heff_apply once with "
+      fail(DMRG_ERR_STATE, "FP32 operator copies not built: call dmrg_heff_apply once with "
                            "DMRG_SPLIT_TF32 after dmrg_build_block_ops");
     void *base = nullptr;
     size_t cap = 0;
