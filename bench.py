@@ -306,6 +306,10 @@ def main():
         serving_out = {"stream": "12 requests, exponential inter-arrival mean 0.1 s (seed 3); "
                                  "spinless 4x4 V~U[0,4] and Hubbard 4x4 U~U[0,8], D in {64,128}, "
                                  "2 sweeps each, 4 slots"}
+        # untimed warm-up: loads the solver and kernel modules once per process,
+        # so that neither arm pays it
+        for prec in (lib.SPLIT_TF32, lib.FP64):
+            srvmod.run_one(srvmod.Request(-1, "spinless", 3, 3, 1.0, 16, 1, 0.0, seed=1), prec)
         for name, prec in (("split", lib.SPLIT_TF32), ("fp64", lib.FP64)):
             reqs = srvmod.poisson_stream(12, 0.1, 3, mix, sweeps=2)
             srv = srvmod.Server(precision=prec, slots=4, hbm_budget=200e9, davidson_tol=1e-7)
