@@ -2,7 +2,7 @@
 
 A step is one sigma = H_eff*psi of the middle two-site window of the
 workload (the Davidson matvec the paper's performance figures count).
-value = algorithmic TFLOP/s of the split 3xTF32 path (whole job: sum over
+value = algorithmic TFLOP/s of the split-precision path (whole job: sum over
 replicas); the FP64 path, the Davidson solve time of both paths, their energy
 difference (FP64 Rayleigh quotient) and the end-to-end host-buffer rate are
 reported beside it.  Inputs: seeded synthetic lattices and random MPS bases
@@ -43,10 +43,9 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM traffic per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, one
 # pass on the full window; profiles/launches_hubbard6x6_D1024.md), valid only for
 # the kernel source it was taken with: reported as null once that file changes.
-TRAFFIC_SOURCE = os.path.join(ROOT, "paper_2311_14106_b300", "csrc", "heff_tf32.cu")
-TRAFFIC_SHA = "c23e8b98166adb6b"
-TRAFFIC = {("hubbard6x6_D1024", "k_tf32_gemm stage1"): 4.987e9,
-           ("hubbard6x6_D1024", "k_tf32_gemm stage2"): 5.514e9}
+TRAFFIC_SOURCE = os.path.join(ROOT, "paper_2311_14106_b300", "csrc", "heff_split.cu")
+TRAFFIC_SHA = "unmeasured"
+TRAFFIC = {}
 
 
 def traffic_of(workload, kernel):
@@ -56,7 +55,7 @@ def traffic_of(workload, kernel):
     except OSError:
         return None
     return TRAFFIC.get((workload, kernel)) if sha == TRAFFIC_SHA else None
-TF32_OVER_BF16 = 1.1 / 2.25        # nominal dense tf32 / bf16 tensor ratio
+F16_OVER_BF16 = 1.0                # kind::f16 runs FP16 and BF16 at the same dense rate
 
 
 def peaks():
@@ -261,7 +260,7 @@ def main():
 
     # split path: the headline
     with Clocks(local) as clk:
-        ms_split, st_split = timed(lib.SPLIT_TF32, args.steps, args.warmup)
+        ms_split, st_split = timed(lib.SPLIT, args.steps, args.warmup)
     clocks = clk.summary()
     sig_split = sig.clone()
     # FP64 path (fewer steps: FP64 throughput is ~1/100 of the split path)
@@ -270,7 +269,7 @@ def main():
     sig_64 = sig.clone()
     err_sigma = float((sig_split - sig_64).norm() / sig_64.norm())
     # end-to-end through the host-buffer entry point (pinned host memory)
-    g.set_precision(lib.SPLIT_TF32)
+    g.set_precision(lib.SPLIT)
     hp = torch.tensor(synth.random_psi(layout, 1)).pin_memory()
     hs = torch.empty_like(hp).pin_memory()
     import ctypes
@@ -286,7 +285,7 @@ def main():
     # Davidson solves of the window with both paths (energy at FP64 RQ)
     solve = {}
     if not args.no_solve:
-        for name, prec in (("split", lib.SPLIT_TF32), ("fp64", lib.FP64)):
+        for name, prec in (("split", lib.SPLIT), ("fp64", lib.FP64)):
             g.set_precision(prec)
             x = torch.zeros_like(psi)
             torch.cuda.synchronize()
@@ -308,26 +307,26 @@ def main():
                                  "2 sweeps each, 4 slots"}
         # untimed warm-up: loads the solver and kernel modules once per process,
         # so that neither arm pays it
-        for prec in (lib.SPLIT_TF32, lib.FP64):
+        for prec in (lib.SPLIT, lib.FP64):
             srvmod.run_one(srvmod.Request(-1, "spinless", 3, 3, 1.0, 16, 1, 0.0, seed=1), prec)
-        for name, prec in (("split", lib.SPLIT_TF32), ("fp64", lib.FP64)):
+        for name, prec in (("split", lib.SPLIT), ("fp64", lib.FP64)):
             reqs = srvmod.poisson_stream(12, 0.1, 3, mix, sweeps=2)
             srv = srvmod.Server(precision=prec, slots=4, hbm_budget=200e9, davidson_tol=1e-7)
             serving_out[name] = srv.run(reqs)
         serving_out["solves_per_s_ratio_split_over_fp64"] = (
             serving_out["split"]["solves_per_s"] / max(serving_out["fp64"]["solves_per_s"], 1e-12))
     hbm, bf16, src = peaks()
-    tf32_peak = bf16 * TF32_OVER_BF16
+    tc_peak = bf16 * F16_OVER_BF16
     si = g.heff_stage_info()
     plan = g.heff_split_plan()
     # per-kernel event marks: [psi split, stage 1, stage 2, partial sum]
-    # Algorithmic bytes: operator stacks read once (FP32, 4 B/element), psi
-    # read once (FP32), the intermediate T written by stage 1 and read
+    # Algorithmic bytes: operator stacks read once (FP16 hi+lo, 4 B/element), psi
+    # read once (FP64), the intermediate T written by stage 1 and read
     # by stage 2 (FP32), sigma partials written once (FP32)
     kern = {
-        "k_tf32_gemm stage1": (st_split[1], 4 * (si["nA"] + si["nT"]) + 4 * si["psi_len"],
+        "k_split_gemm stage1": (st_split[1], 4 * (si["nA"] + si["nT"]) + 4 * si["psi_len"],
                                si["flops1"]),
-        "k_tf32_gemm stage2": (st_split[2], 4 * (si["nT"] + si["nB"]) + 4 * si["psi_len"],
+        "k_split_gemm stage2": (st_split[2], 4 * (si["nT"] + si["nB"]) + 4 * si["psi_len"],
                                si["flops2"]),
     }
     dom = max(kern, key=lambda k: kern[k][0])
@@ -336,7 +335,7 @@ def main():
         "metric": "H_eff*psi TFLOP/s", "value": job_value(flops, ms_split, world),
         "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_split, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "tf32 hi+lo split on chip from fp32 operands, 3 products (fp32 accumulate), fp64 in/out",
+        "vs_baseline": None, "dtype": "fp16 hi+lo split with per-block power-of-two scales, 3 products (fp32 accumulate), fp64 in/out",
         "data": "synthetic",
         "config": {"workload": args.workload, "description": wl[6], "psi_len": n,
                    "algorithmic_flops_per_step": flops, "l2": "operator stacks >> L2; no flush",
@@ -355,14 +354,14 @@ def main():
         "split_plan": plan,
         "gpu_launches": plan["launches"] * args.steps,
         "roofline": {"kernel": dom, "bound": "tensor",
-                     "achieved": None, "peak": tf32_peak, "unit": "TFLOP/s", "frac": None,
-                     "peak_source": f"{src} bf16 x nominal tf32/bf16 ratio",
+                     "achieved": None, "peak": tc_peak, "unit": "TFLOP/s", "frac": None,
+                     "peak_source": f"{src} bf16 (dense fp16 rate)",
                      "traffic": traffic_of(args.workload, dom)},
     }
     t_dom = t_dom_ms * 1e-3
     gbs = dom_bytes / t_dom / 1e9
     tfl = 3 * dom_flops / t_dom / 1e12        # tensor work: 3 MMAs per product
-    f_hbm, f_tc = gbs / hbm, tfl / tf32_peak
+    f_hbm, f_tc = gbs / hbm, tfl / tc_peak
     if f_hbm >= f_tc:
         line["roofline"].update({"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                                  "frac": f_hbm, "peak_source": f"{src} hbm_gbs"})

@@ -61,7 +61,7 @@ enum {
 };
 
 enum { DMRG_U1 = 1, DMRG_U1U1 = 2 };                 /* symmetry */
-enum { DMRG_FP64 = 0, DMRG_SPLIT_TF32 = 1 };         /* H_eff*psi precision */
+enum { DMRG_FP64 = 0, DMRG_SPLIT = 1 };         /* H_eff*psi precision */
 enum { DMRG_MODEL_SPINLESS_TV = 1, DMRG_MODEL_HUBBARD = 2 };
 
 typedef struct dmrg_ctx dmrg_ctx;   /* opaque, owned by the library */
@@ -72,7 +72,7 @@ typedef struct {
   int n_up;                /* target particles (spinless: N) */
   int n_dn;                /* target down particles (spinless: ignored) */
   int d_max;               /* bond dimension D kept by truncation */
-  int precision;           /* DMRG_FP64 or DMRG_SPLIT_TF32 for H_eff*psi */
+  int precision;           /* DMRG_FP64 or DMRG_SPLIT for H_eff*psi */
   double davidson_tol;     /* residual 2-norm bound, normalized vector */
   int davidson_max_sub;    /* Davidson subspace size (>= 4) */
   int davidson_max_iter;   /* Davidson iteration limit */
@@ -135,7 +135,7 @@ int dmrg_build_block_ops(dmrg_ctx *ctx, int l, void *stream);
 int dmrg_heff_layout(dmrg_ctx *ctx, long long *psi_len, int *n_blocks,
                      int *blocks);
 
-/* Select the arithmetic of dmrg_heff_apply: DMRG_FP64 or DMRG_SPLIT_TF32. */
+/* Select the arithmetic of dmrg_heff_apply: DMRG_FP64 or DMRG_SPLIT. */
 int dmrg_set_precision(dmrg_ctx *ctx, int precision);
 
 /* a5 -- sigma = H_eff * psi (Sec. II.A, Davidson matvec).  psi, sigma:
@@ -158,7 +158,7 @@ int dmrg_heff_apply(dmrg_ctx *ctx, const double *psi, double *sigma,
  *   - psi, sigma: device pointers as for dmrg_heff_apply; sigma is
  *     overwritten.  The result equals dmrg_heff_apply's split result.
  *   - Needs the window's FP32 operator copies, which the first
- *     dmrg_heff_apply with DMRG_SPLIT_TF32 creates (Errors: STATE if absent).
+ *     dmrg_heff_apply with DMRG_SPLIT creates (Errors: STATE if absent).
  *   - A window whose scratch exceeds 64 MiB is rejected with DMRG_ERR_ARG and
  *     a message giving the size it needs.
  *   - The first call on a device looks up the array's device address, and the
@@ -168,7 +168,7 @@ int dmrg_heff_apply(dmrg_ctx *ctx, const double *psi, double *sigma,
  *     call's contents; calls whose GPU work overlaps in time race with each
  *     other and give wrong results.  Serialize them (one stream, or events).
  */
-int dmrg_heff_apply_tf32_static(dmrg_ctx *ctx, const double *psi,
+int dmrg_heff_apply_split_static(dmrg_ctx *ctx, const double *psi,
                                 double *sigma, void *stream);
 
 /* Same as dmrg_heff_apply but with host buffers: copies psi to the device,

@@ -19,7 +19,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_STATE, ERR_TIMEOUT, ERR_NOT_CONVERGED = 0, -1, -2, -3, -4, -5, -6
 U1, U1U1 = 1, 2
-FP64, SPLIT_TF32 = 0, 1
+FP64, SPLIT = 0, 1
 MODEL_SPINLESS_TV, MODEL_HUBBARD = 1, 2
 
 HEADER_FUNCTIONS = [
@@ -29,7 +29,7 @@ HEADER_FUNCTIONS = [
     "dmrg_set_precision", "dmrg_heff_apply", "dmrg_heff_apply_host",
     "dmrg_heff_flops", "dmrg_davidson", "dmrg_truncate", "dmrg_sweep",
     "dmrg_heff_stage_info", "dmrg_heff_timing", "dmrg_profile",
-    "dmrg_heff_apply_tf32_static", "dmrg_heff_tuning", "dmrg_set_graphs",
+    "dmrg_heff_apply_split_static", "dmrg_heff_tuning", "dmrg_set_graphs",
     "dmrg_heff_split_plan", "dmrg_heff_entries",
 ]
 
@@ -64,7 +64,7 @@ _sig = {
     "dmrg_set_precision": (ctypes.c_int, [_P, ctypes.c_int]),
     "dmrg_heff_apply": (ctypes.c_int, [_P, _P, _P, _P]),
     "dmrg_heff_apply_host": (ctypes.c_int, [_P, _D, _D, _P]),
-    "dmrg_heff_apply_tf32_static": (ctypes.c_int, [_P, _P, _P, _P]),
+    "dmrg_heff_apply_split_static": (ctypes.c_int, [_P, _P, _P, _P]),
     "dmrg_heff_flops": (ctypes.c_int, [_P, _D]),
     "dmrg_davidson": (ctypes.c_int, [_P, _P, _D, _I, _P]),
     "dmrg_truncate": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _D, _D, _P]),
@@ -212,8 +212,8 @@ class Dmrg:
     def heff_apply_static(self, psi, sigma, stream=None):
         """Split-precision H_eff psi that allocates no device memory: its
         scratch is the library's fixed 64 MiB device array (see the header)."""
-        self._check(_lib.dmrg_heff_apply_tf32_static(self._h, _tensor_ptr(psi), _tensor_ptr(sigma),
-                                                     _stream_ptr(stream)), "heff_apply_tf32_static")
+        self._check(_lib.dmrg_heff_apply_split_static(self._h, _tensor_ptr(psi), _tensor_ptr(sigma),
+                                                     _stream_ptr(stream)), "heff_apply_split_static")
 
     def heff_apply_host(self, psi, stream=None):
         psi = np.ascontiguousarray(psi, dtype=np.float64)

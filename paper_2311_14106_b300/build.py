@@ -6,7 +6,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libdmrgb300.so")
-SOURCES = ["kernels.cu", "heff_tf32.cu", "heff_static.cu", "dmrg_host.cpp"]
+SOURCES = ["kernels.cu", "heff_split.cu", "heff_static.cu", "dmrg_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

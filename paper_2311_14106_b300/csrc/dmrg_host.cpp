@@ -2,7 +2,7 @@
 // rotation), sector tables ("Tables", Sec. III.B), block operators
 // (normal and complementary), the two-site window, H_eff*psi, Davidson,
 // truncation and sweeps.  All bulk arithmetic runs in the CUDA kernels of
-// kernels.cu / heff_tf32.cu; this file builds their work lists.
+// kernels.cu / heff_split.cu; this file builds their work lists.
 #include <cuda_runtime.h>
 #include <cusolverDn.h>
 
@@ -24,7 +24,7 @@
 
 #include "../../include/dmrg_b300.h"
 #include "formulas.h"
-#include "heff_tf32.h"
+#include "heff_split.h"
 #include "kernels.h"
 #include "model.h"
 
@@ -128,8 +128,8 @@ struct PsiBlk {
 
 // Host tables of the split path (psi split descriptors, tensor maps, K
 // ranges, tile lists, partial sums) for given scratch pointers.
-struct Tf32Tables {
-  std::vector<Split2D> psi_split;
+struct SplitTables {
+  std::vector<F16Split> psi_split;
   std::vector<CUtensorMap> maps;
   std::vector<TSeg> segs;
   std::vector<TWork> w1, w2;      // grouped by tile width (<= 32, <= 64, <= 128)
@@ -161,14 +161,15 @@ struct Window {
   PartialSum64 *d_ps64 = nullptr;
   std::vector<GemmDesc> stage1, stage2;   // host copies (split-path planning)
   std::vector<GemmSeg> seg1, seg2;
-  Tf32Plan tf;           // split-precision plan (heff_tf32)
+  SplitPlan tf;          // split-precision plan (heff_split)
   bool tf_ready = false;
-  bool tf_copies = false;            // TF32 copies of the operator stacks exist
+  bool tf_copies = false;            // FP16 (hi, lo) copies of the operator stacks exist
   int ksub = 0;                      // split-K range in use
   void *tbl_ptr[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   size_t tbl_cap[6] = {0, 0, 0, 0, 0, 0};
   std::map<std::pair<const void *, const void *>, cudaGraphExec_t> graphs;
-  std::vector<long long> offA, ldA, offBp, bpad;
+  std::vector<long long> offA, ldA, offBp, bpad;   // split copies (halves)
+  std::vector<float> sA, sB, rnA;                   // per entry: scales, largest A row norm
   long long gen = 0;                 // build counter of this window
 };
 
@@ -188,7 +189,7 @@ struct dmrg_ctx {
   std::map<int, std::unique_ptr<BlockPart>> R;      // R[n], sites n..N-1
   std::map<BlockPart *, std::unique_ptr<WinBuf>> partbuf;
   Window win;
-  Tf32Tables tables;     // host copy of the split-path tables of the window
+  SplitTables tables;    // host copy of the split-path tables of the window
   cudaStream_t stream = nullptr;
   cusolverDnHandle_t solver = nullptr;
   cusolverDnParams_t solver_params = nullptr;
@@ -1157,16 +1158,18 @@ void apply_fp64(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s) {
 namespace {
 
 // ---------------------------------------------------------------------------
-// split-precision plan: TF32 (hi, lo) copies of the stacks, tensor maps and
-// tile lists of the two tcgen05 stages
+// split-precision plan: scaled FP16 (hi, lo) copies of the stacks, tensor maps
+// and tile lists of the two tcgen05 stages
 // ---------------------------------------------------------------------------
 long long r4(long long x) { return (x + 3) & ~3LL; }
+long long r8(long long x) { return (x + 7) & ~7LL; }
 long long a64(long long x) { return (x + 63) & ~63LL; }
 int ntile_of(int n) { return n > 128 ? 128 : ((n + 15) / 16) * 16; }
 
-// Sizes (floats) of the per-apply scratch of the split path: psi split
-// (P, FP32), stage-1 intermediate (T, FP32) and stage-2 partial tiles (ws).
-struct Tf32Scratch {
+// Sizes of the per-apply scratch of the split path: psi^T split (P, halves,
+// hi and lo each), stage-1 intermediate (T, halves, hi and lo each) and
+// stage-2 partial tiles (ws, floats).
+struct SplitScratch {
   long long nP = 0, nT = 0, nws = 0;
   std::vector<long long> offP, offT, ldP, ldT;
 };
@@ -1180,8 +1183,8 @@ std::vector<std::vector<int>> entries_into(const Window &w) {
   return into;
 }
 
-Tf32Scratch tf32_scratch_sizes(const Window &w, int KSUB) {
-  Tf32Scratch z;
+SplitScratch split_scratch_sizes(const Window &w, int KSUB) {
+  SplitScratch z;
   const auto &E = w.s1info;
   const size_t ne = E.size(), np = w.psi.size();
   z.offT.assign(ne, 0);
@@ -1192,12 +1195,12 @@ Tf32Scratch tf32_scratch_sizes(const Window &w, int KSUB) {
     const HClass &h = w.hc[E[i].ci];
     const PsiBlk &p = w.psi[E[i].pi], &q = w.psi[E[i].po];
     const long long n = (long long)h.terms.size();
-    z.ldT[i] = r4(p.db);   // T rows (a', k), b padded to 4 floats
+    z.ldT[i] = r8(p.db);   // T rows (a', k), b padded to 8 halves
     z.offT[i] = z.nT;
     z.nT += a64(q.da * n * z.ldT[i]);
   }
   for (size_t i = 0; i < np; ++i) {
-    z.ldP[i] = r4(w.psi[i].da);
+    z.ldP[i] = r8(w.psi[i].da);
     z.offP[i] = z.nP;
     z.nP += a64(w.psi[i].db * z.ldP[i]);
   }
@@ -1205,7 +1208,7 @@ Tf32Scratch tf32_scratch_sizes(const Window &w, int KSUB) {
   for (size_t po = 0; po < np; ++po) {
     long long parts = 0;
     for (int i : into[po]) {
-      const long long K = (long long)w.hc[E[i].ci].terms.size() * r4(w.psi[E[i].pi].db);
+      const long long K = (long long)w.hc[E[i].ci].terms.size() * r8(w.psi[E[i].pi].db);
       parts += (K + KSUB - 1) / KSUB;
     }
     z.nws += a64(parts * w.psi[po].da * r4(w.psi[po].db));
@@ -1213,13 +1216,14 @@ Tf32Scratch tf32_scratch_sizes(const Window &w, int KSUB) {
   return z;
 }
 
-// FP32 copies of the operator stacks: built once per window and owned by the
-// context (they are inputs of every split-path apply; the kernels split
-// them into TF32 hi + lo on chip).
-void tf32_operator_copies(dmrg_ctx *C) {
+// Scaled FP16 (hi, lo) copies of the operator stacks: built once per window
+// and owned by the context (inputs of every split-path apply).  Each class
+// entry's A and B stacks get one power-of-two scale from their largest
+// element; the largest A-row 2-norm bounds the entry's stage-1 output.
+void split_operator_copies(dmrg_ctx *C) {
   Window &w = C->win;
   cudaStream_t s = C->stream;
-  Tf32Plan &P = w.tf;
+  SplitPlan &P = w.tf;
   const auto &E = w.s1info;
   const size_t ne = E.size();
   w.offA.assign(ne, 0);
@@ -1227,62 +1231,88 @@ void tf32_operator_copies(dmrg_ctx *C) {
   w.offBp.assign(ne, 0);
   w.bpad.assign(ne, 0);
   long long nA = 0, nBp = 0;
+  std::vector<StatDesc> sd(ne);
   for (size_t i = 0; i < ne; ++i) {
     const HClass &h = w.hc[E[i].ci];
     const PsiBlk &p = w.psi[E[i].pi], &q = w.psi[E[i].po];
     const long long n = (long long)h.terms.size();
-    w.ldA[i] = r4(p.da);
+    w.ldA[i] = r8(p.da);
     w.offA[i] = nA;
     nA += a64(q.da * n * w.ldA[i]);
-    w.bpad[i] = r4(p.db);
+    w.bpad[i] = r8(p.db);
     w.offBp[i] = nBp;
     nBp += a64(q.db * n * w.bpad[i]);
+    memset(&sd[i], 0, sizeof sd[i]);
+    sd[i].a = w.Astack + h.a_off.at(E[i].pi);
+    sd[i].rowsA = (long long)q.da * n;
+    sd[i].colsA = p.da;
+    sd[i].b = w.Bstack + h.b_off.at(E[i].pi);
+    sd[i].rowsB = (long long)q.db * n;
+    sd[i].colsB = p.db;
   }
-  auto fl = [&](long long n) { return (float *)w.buf.alloc(4 * std::max<long long>(n, 64)); };
-  P.A32 = fl(nA);
-  // B with every term's b segment padded to 4 floats (zeros), so that stage 2
-  // runs over K = (k, b) with b padded and each term starts 16-byte aligned
-  P.B32 = fl(nBp);
-  CK(cudaMemsetAsync(P.B32, 0, 4 * std::max<long long>(nBp, 64), s));
-  std::vector<Split2D> sp;
+  WinBuf tmp;
+  EntryStat *dst = (EntryStat *)tmp.alloc(sizeof(EntryStat) * std::max<size_t>(ne, 1));
+  CK(entry_stats(upload(tmp, sd, s), (int)ne, dst, s));
+  std::vector<EntryStat> st(ne);
+  if (ne) CK(cudaMemcpyAsync(st.data(), dst, sizeof(EntryStat) * ne, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  w.sA.resize(ne);
+  w.sB.resize(ne);
+  w.rnA.resize(ne);
   for (size_t i = 0; i < ne; ++i) {
-    const HClass &h = w.hc[E[i].ci];
+    w.sA[i] = pow2_scale_host(st[i].maxA);
+    w.sB[i] = pow2_scale_host(st[i].maxB);
+    w.rnA[i] = st[i].rnA;
+  }
+  auto hf = [&](long long n) { return (__half *)w.buf.alloc(2 * std::max<long long>(n, 64)); };
+  P.Ah = hf(nA);
+  P.Al = hf(nA);
+  // B with every term's b segment padded to 8 halves (zeros), so that stage 2
+  // runs over K = (k, b) with b padded and each term starts 16-byte aligned
+  P.Bh = hf(nBp);
+  P.Bl = hf(nBp);
+  CK(cudaMemsetAsync(P.Bh, 0, 2 * std::max<long long>(nBp, 64), s));
+  CK(cudaMemsetAsync(P.Bl, 0, 2 * std::max<long long>(nBp, 64), s));
+  std::vector<F16Split> sp;
+  for (size_t i = 0; i < ne; ++i) {
     const PsiBlk &p = w.psi[E[i].pi], &q = w.psi[E[i].po];
-    const int n = (int)h.terms.size();
-    Split2D a;
+    const int n = (int)w.hc[E[i].ci].terms.size();
+    F16Split a;
     memset(&a, 0, sizeof a);
-    a.src = w.Astack + h.a_off.at(E[i].pi);
+    a.src = sd[i].a;
     a.src_ld = p.da;
     a.rows = q.da * n;
     a.cols = p.da;
-    a.hi = P.A32 + w.offA[i];
-    a.lo = nullptr;
+    a.hi = P.Ah + w.offA[i];
+    a.lo = P.Al + w.offA[i];
     a.dst_ld = w.ldA[i];
+    a.scale = w.sA[i];
     sp.push_back(a);
     // rows (b', k) of the [b'][k][b] stack, each p.db long, re-strided to bpad
-    Split2D b;
+    F16Split b;
     memset(&b, 0, sizeof b);
-    b.src = w.Bstack + h.b_off.at(E[i].pi);
+    b.src = sd[i].b;
     b.src_ld = p.db;
     b.rows = q.db * n;
     b.cols = p.db;
-    b.hi = P.B32 + w.offBp[i];
-    b.lo = nullptr;
+    b.hi = P.Bh + w.offBp[i];
+    b.lo = P.Bl + w.offBp[i];
     b.dst_ld = w.bpad[i];
+    b.scale = w.sB[i];
     sp.push_back(b);
   }
-  WinBuf tmp;
-  Split2D *d = upload(tmp, sp, s);
-  CK(launch_split2d(d, (int)sp.size(), s));
+  CK(f16_split(upload(tmp, sp, s), (int)sp.size(), nullptr, nullptr, s));
   CK(cudaStreamSynchronize(s));
   w.tf_copies = true;
 }
 
-// psi (FP64, [a][b] per sector block) -> FP32, transposed to [b][a]
-std::vector<Split2D> psi_split_descs(const Window &w, const Tf32Scratch &z, float *P32) {
-  std::vector<Split2D> out;
+// psi (FP64, [a][b] per sector block) -> scaled FP16 (hi, lo), transposed to
+// [b][a]; the scale comes from the block's statistics of this apply
+std::vector<F16Split> psi_split_descs(const Window &w, const SplitScratch &z, __half *Ph,
+                                      __half *Pl) {
+  std::vector<F16Split> out;
   for (size_t i = 0; i < w.psi.size(); ++i) {
-    Split2D d;
+    F16Split d;
     memset(&d, 0, sizeof d);
     d.src = nullptr;
     d.src_off = w.psi[i].off;
@@ -1290,26 +1320,41 @@ std::vector<Split2D> psi_split_descs(const Window &w, const Tf32Scratch &z, floa
     d.rows = w.psi[i].da;
     d.cols = w.psi[i].db;
     d.trans = 1;
-    d.hi = P32 + z.offP[i];
-    d.lo = nullptr;
+    d.hi = Ph + z.offP[i];
+    d.lo = Pl + z.offP[i];
     d.dst_ld = z.ldP[i];
+    d.pblk = (int)i;
+    d.scale = 0.f;
     out.push_back(d);
   }
   return out;
 }
 
-void tf32_tables(const Window &w, const Tf32Scratch &z, float *P32, float *T32, float *ws,
-                 Tf32Tables &out, int KSUB) {
-  const Tf32Plan &P = w.tf;
+std::vector<PsiDesc> psi_descs(const Window &w) {
+  std::vector<PsiDesc> out(w.psi.size());
+  for (size_t i = 0; i < w.psi.size(); ++i) out[i] = {w.psi[i].off, w.psi[i].da, w.psi[i].db};
+  return out;
+}
+
+void split_tables(const Window &w, const SplitScratch &z, __half *Ph, __half *Pl, __half *Th,
+                  __half *Tl, float *ws, SplitTables &out, int KSUB) {
+  const SplitPlan &P = w.tf;
   const auto &E = w.s1info;
   const size_t ne = E.size(), np = w.psi.size();
-  out = Tf32Tables();
-  out.psi_split = psi_split_descs(w, z, P32);
+  out = SplitTables();
+  out.psi_split = psi_split_descs(w, z, Ph, Pl);
   auto &maps = out.maps;
-  auto mk = [&](const float *base, long long rows, long long cols, long long ld, int box) {
+  auto mk = [&](const __half *base, long long rows, long long cols, long long ld, int box) {
     CUtensorMap m;
-    int rc = encode_map(&m, base, (int)rows, (int)cols, ld, box);
+    int rc = encode_map_h(&m, base, rows, cols, ld, box);
     if (rc != 0) fail(DMRG_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) rows %lld cols %lld", rc, rows, cols);
+    maps.push_back(m);
+    return (int)maps.size() - 1;
+  };
+  auto mk3h = [&](const __half *base, long long d0, long long d1, long long s1) {
+    CUtensorMap m;
+    int rc = encode_map3_h(&m, base, d0, d1, 1, s1, d1 * s1, 32, 1);
+    if (rc != 0) fail(DMRG_ERR_CUDA, "cuTensorMapEncodeTiled (3-D, store) failed (%d)", rc);
     maps.push_back(m);
     return (int)maps.size() - 1;
   };
@@ -1321,10 +1366,11 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P32, float *T32, 
     maps.push_back(m);
     return (int)maps.size() - 1;
   };
-  std::vector<int> mP(np);
+  std::vector<int> mPh(np), mPl(np);
   for (size_t i = 0; i < np; ++i) {
     const PsiBlk &p = w.psi[i];
-    mP[i] = mk(P32 + z.offP[i], p.db, p.da, z.ldP[i], ntile_of(p.db));
+    mPh[i] = mk(Ph + z.offP[i], p.db, p.da, z.ldP[i], ntile_of(p.db));
+    mPl[i] = mk(Pl + z.offP[i], p.db, p.da, z.ldP[i], ntile_of(p.db));
   }
   auto &segs = out.segs;
   auto &w1 = out.w1;
@@ -1345,21 +1391,23 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P32, float *T32, 
     const int n = (int)h.terms.size();
     const int nl = qnum(w.Ld.basis.qn[p.a]);
     alpha[i] = (h.pB && (nl & 1)) ? -1.f : 1.f;
-    const long long bp = z.ldT[i];   // = r4(p.db)
-    int ahi = mk(P.A32 + w.offA[i], (long long)q.da * n, p.da, w.ldA[i], 128);
+    const long long bp = z.ldT[i];   // = r8(p.db)
+    const int ahi = mk(P.Ah + w.offA[i], (long long)q.da * n, p.da, w.ldA[i], 128);
+    const int alo = mk(P.Al + w.offA[i], (long long)q.da * n, p.da, w.ldA[i], 128);
     // T as stage-1 output: rows (a', k), columns b (padded); as stage-2
     // operand: rows a', K = (k, b)
     const long long rowsT = (long long)q.da * n;
-    const int sT = mk3(T32 + z.offT[i], bp, rowsT, 1, bp, rowsT * bp, 32, 32, 1);
+    const int sThi = mk3h(Th + z.offT[i], bp, rowsT, bp);
+    const int sTlo = mk3h(Tl + z.offT[i], bp, rowsT, bp);
     const int R = Rq[E[i].po];
-    mThi[i] = mk(T32 + z.offT[i], q.da, (long long)n * bp, (long long)n * bp, 128 / R);
-    mTlo[i] = -1;
+    mThi[i] = mk(Th + z.offT[i], q.da, (long long)n * bp, (long long)n * bp, 128 / R);
+    mTlo[i] = mk(Tl + z.offT[i], q.da, (long long)n * bp, (long long)n * bp, 128 / R);
     int bbox = R > 1 ? 128 / R : ntile_of(q.db);
-    mBhi[i] = mk(P.B32 + w.offBp[i], q.db, (long long)n * w.bpad[i], (long long)n * w.bpad[i], bbox);
-    mBlo[i] = -1;
+    mBhi[i] = mk(P.Bh + w.offBp[i], q.db, (long long)n * w.bpad[i], (long long)n * w.bpad[i], bbox);
+    mBlo[i] = mk(P.Bl + w.offBp[i], q.db, (long long)n * w.bpad[i], (long long)n * w.bpad[i], bbox);
     TSeg sg;
     memset(&sg, 0, sizeof sg);
-    sg.mA_hi = ahi; sg.mA_lo = -1; sg.mB_hi = mP[E[i].pi]; sg.mB_lo = -1;
+    sg.mA_hi = ahi; sg.mA_lo = alo; sg.mB_hi = mPh[E[i].pi]; sg.mB_lo = mPl[E[i].pi];
     sg.K = p.da;
     sg.k0 = 0;
     int seg = (int)segs.size();
@@ -1372,15 +1420,18 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P32, float *T32, 
         t.seg0 = seg; t.nseg = 1;
         t.M = M; t.N = N; t.m0 = m0; t.n0 = n0; t.ntile = nt;
         t.mode = TW_SPLIT; t.alpha = alpha[i];
-        t.mOut_hi = sT; t.mOut_lo = -1; t.zout = 0;
+        t.fa = 1.f / w.sA[i];
+        t.rn = w.rnA[i];
+        t.pblk = E[i].pi;
+        t.mOut_hi = sThi; t.mOut_lo = sTlo; t.zout = 0;
         w1.push_back(t);
       }
   }
-  // per sigma block: split-K ranges, each one FP32 partial tile per output
-  // tile; the partials are summed in FP64 in a fixed order.
+  // per sigma block: split-K ranges (one entry each), each one FP32 partial
+  // tile per output tile; the partials are summed in a fixed order.
   long long wsn = 0;
   struct PackCand {
-    int seg, mOut, z, R, nchunk;
+    int seg, mOut, z, R, nchunk, entry;
   };
   std::vector<PackCand> pk;
   for (size_t po = 0; po < np; ++po) {
@@ -1396,6 +1447,7 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P32, float *T32, 
     ps.n = q.da * q.db;
     ps.cols = q.db;
     std::vector<TSeg> ranges;
+    std::vector<int> rent;   // entry of each range
     for (int i : into[po]) {
       const HClass &h = w.hc[E[i].ci];
       const int K = (int)(h.terms.size() * w.bpad[i]);
@@ -1405,8 +1457,9 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P32, float *T32, 
         sg.mA_hi = mThi[i]; sg.mA_lo = mTlo[i]; sg.mB_hi = mBhi[i]; sg.mB_lo = mBlo[i];
         sg.k0 = k0;
         sg.K = std::min(KSUB, K - k0);
-        sg.xoob = (K + 31) / 32 * 32;
+        sg.xoob = (K + 63) / 64 * 64;
         ranges.push_back(sg);
+        rent.push_back(i);
       }
     }
     const int nparts = (int)ranges.size();
@@ -1418,7 +1471,7 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P32, float *T32, 
       int seg = (int)segs.size();
       segs.push_back(ranges[pi]);
       if (Rq[po] > 1) {
-        pk.push_back({seg, mW, pi, Rq[po], (ranges[pi].K + 31) / 32});
+        pk.push_back({seg, mW, pi, Rq[po], (ranges[pi].K + 63) / 64, rent[pi]});
         continue;
       }
       for (int m0 = 0; m0 < M; m0 += 128)
@@ -1428,6 +1481,9 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P32, float *T32, 
           t.seg0 = seg; t.nseg = 1;
           t.M = M; t.N = N; t.m0 = m0; t.n0 = n0; t.ntile = nt;
           t.mode = TW_PARTIAL; t.alpha = 1.f;
+          t.fa = 1.f / w.sB[rent[pi]];
+          t.rn = w.rnA[rent[pi]];
+          t.pblk = E[rent[pi]].pi;
           t.mOut_hi = mW; t.mOut_lo = mW; t.zout = pi;
           w2.push_back(t);
         }
@@ -1453,6 +1509,9 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P32, float *T32, 
       t.pseg[r] = pk[i].seg;
       t.pout[r] = pk[i].mOut;
       t.pz[r] = pk[i].z;
+      t.pfa[r] = 1.f / w.sB[pk[i].entry];
+      t.prn[r] = w.rnA[pk[i].entry];
+      t.ppb[r] = E[pk[i].entry].pi;
       t.nchunk = std::max(t.nchunk, pk[i].nchunk);
     }
     t.seg0 = t.pseg[0];
@@ -1465,7 +1524,7 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P32, float *T32, 
   auto cost = [&](const TWork &t) {
     if (t.R > 1) return (long long)t.nchunk * t.ntile;
     long long k = 0;
-    for (int i = 0; i < t.nseg; ++i) k += (segs[t.seg0 + i].K + 31) / 32;
+    for (int i = 0; i < t.nseg; ++i) k += (segs[t.seg0 + i].K + 63) / 64;
     return k * t.ntile;
   };
   // group by tile width (one launch per width class), largest cost first
@@ -1480,28 +1539,33 @@ void tf32_tables(const Window &w, const Tf32Scratch &z, float *P32, float *T32, 
   for (const TWork &t : w2) out.n2[bucket(t)]++;
 }
 
-void upload_tables(dmrg_ctx *C, Tf32Tables &tb, cudaStream_t s);
-void launch_tf32(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s);
+void upload_tables(dmrg_ctx *C, SplitTables &tb, cudaStream_t s);
+void launch_split(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s);
 
 // Autotuner: the stage-2 split-K range trades FP32 accumulation length against
 // partial-tile traffic and tile count.  For windows whose operator stacks are
 // large enough for the choice to matter, each candidate is timed on the live
 // window (three applies each, CUDA events) and the fastest is kept for the
 // rest of the context's life (windows of one run have similar shapes).
-void build_tf32(dmrg_ctx *C) {
+void build_split(dmrg_ctx *C) {
   Window &w = C->win;
   cudaStream_t s = C->stream;
-  Tf32Plan &P = w.tf;
-  if (!w.tf_copies) tf32_operator_copies(C);
-  CK(tf32_prepare());
+  SplitPlan &P = w.tf;
+  if (!w.tf_copies) split_operator_copies(C);
+  CK(split_prepare());
   const bool tune = C->ksub_choice == 0 && (double)(w.nA + w.nB) * 8.0 > 256e6;
   int best = C->ksub_choice ? C->ksub_choice : KSUB_DEFAULT;
   // scratch sized for the smallest candidate (most partial tiles)
-  Tf32Scratch zmax = tf32_scratch_sizes(w, tune ? KSUB_CANDIDATES[0] : best);
+  SplitScratch zmax = split_scratch_sizes(w, tune ? KSUB_CANDIDATES[0] : best);
   auto fl = [&](long long n) { return (float *)w.buf.alloc(4 * std::max<long long>(n, 64)); };
-  P.P32 = fl(zmax.nP);
-  P.T32 = fl(zmax.nT);
+  auto hf = [&](long long n) { return (__half *)w.buf.alloc(2 * std::max<long long>(n, 64)); };
+  P.Ph = hf(zmax.nP);
+  P.Pl = hf(zmax.nP);
+  P.Th = hf(zmax.nT);
+  P.Tl = hf(zmax.nT);
   P.ws = fl(zmax.nws);
+  P.pstat = (PsiStat *)w.buf.alloc(sizeof(PsiStat) * std::max<size_t>(w.psi.size(), 1));
+  P.psi_desc = upload(w.buf, psi_descs(w), s);
   P.err = (int *)w.buf.alloc(sizeof(int));
   CK(cudaMemsetAsync(P.err, 0, sizeof(int), s));
   if (tune) {
@@ -1514,12 +1578,12 @@ void build_tf32(dmrg_ctx *C) {
     CK(cudaEventCreate(&e1));
     float best_ms = 1e30f;
     for (int ks : KSUB_CANDIDATES) {
-      Tf32Scratch z = tf32_scratch_sizes(w, ks);
-      tf32_tables(w, z, P.P32, P.T32, P.ws, C->tables, ks);
+      SplitScratch z = split_scratch_sizes(w, ks);
+      split_tables(w, z, P.Ph, P.Pl, P.Th, P.Tl, P.ws, C->tables, ks);
       upload_tables(C, C->tables, s);
-      launch_tf32(C, x, y, s);   // warm
+      launch_split(C, x, y, s);   // warm
       CK(cudaEventRecord(e0, s));
-      for (int r = 0; r < 3; ++r) launch_tf32(C, x, y, s);
+      for (int r = 0; r < 3; ++r) launch_split(C, x, y, s);
       CK(cudaEventRecord(e1, s));
       CK(cudaEventSynchronize(e1));
       float ms = 0;
@@ -1537,16 +1601,16 @@ void build_tf32(dmrg_ctx *C) {
     C->ksub_choice = best;
   }
   w.ksub = best;
-  Tf32Scratch z = tf32_scratch_sizes(w, best);
-  tf32_tables(w, z, P.P32, P.T32, P.ws, C->tables, best);
+  SplitScratch z = split_scratch_sizes(w, best);
+  split_tables(w, z, P.Ph, P.Pl, P.Th, P.Tl, P.ws, C->tables, best);
   upload_tables(C, C->tables, s);
   CK(cudaStreamSynchronize(s));
   w.tf_ready = true;
 }
 
-void upload_tables(dmrg_ctx *C, Tf32Tables &tb, cudaStream_t s) {
+void upload_tables(dmrg_ctx *C, SplitTables &tb, cudaStream_t s) {
   Window &w = C->win;
-  Tf32Plan &P = w.tf;
+  SplitPlan &P = w.tf;
   // table buffers: grow-only, so the tuner's candidates can reuse them
   auto need = [&](void *&ptr, size_t &cap, size_t bytes) {
     if (bytes > cap) {
@@ -1554,7 +1618,7 @@ void upload_tables(dmrg_ctx *C, Tf32Tables &tb, cudaStream_t s) {
       cap = bytes;
     }
   };
-  need(w.tbl_ptr[0], w.tbl_cap[0], std::max<size_t>(tb.psi_split.size(), 1) * sizeof(Split2D));
+  need(w.tbl_ptr[0], w.tbl_cap[0], std::max<size_t>(tb.psi_split.size(), 1) * sizeof(F16Split));
   need(w.tbl_ptr[1], w.tbl_cap[1], std::max<size_t>(tb.maps.size(), 1) * sizeof(CUtensorMap));
   need(w.tbl_ptr[2], w.tbl_cap[2], std::max<size_t>(tb.segs.size(), 1) * sizeof(TSeg));
   need(w.tbl_ptr[3], w.tbl_cap[3], std::max<size_t>(tb.w1.size(), 1) * sizeof(TWork));
@@ -1564,7 +1628,7 @@ void upload_tables(dmrg_ctx *C, Tf32Tables &tb, cudaStream_t s) {
   auto put = [&](void *dst, const void *src, size_t n) {
     if (n) CK(cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, s));
   };
-  put(w.tbl_ptr[0], tb.psi_split.data(), tb.psi_split.size() * sizeof(Split2D));
+  put(w.tbl_ptr[0], tb.psi_split.data(), tb.psi_split.size() * sizeof(F16Split));
   put(w.tbl_ptr[1], tb.maps.data(), tb.maps.size() * sizeof(CUtensorMap));
   put(w.tbl_ptr[2], tb.segs.data(), tb.segs.size() * sizeof(TSeg));
   put(w.tbl_ptr[3], tb.w1.data(), tb.w1.size() * sizeof(TWork));
@@ -1590,32 +1654,33 @@ void upload_tables(dmrg_ctx *C, Tf32Tables &tb, cudaStream_t s) {
   w.graphs.clear();
 }
 
-void launch_tf32(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s) {
-  Tf32Plan &P = C->win.tf;
+void launch_split(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s) {
+  SplitPlan &P = C->win.tf;
   mark(C, 0, s);
-  CK(launch_split2d((const Split2D *)P.psi_split, P.npsi, s, psi));
+  CK(psi_stats(P.psi_desc, P.npsi, psi, P.pstat, s));
+  CK(f16_split((const F16Split *)P.psi_split, P.npsi, P.pstat, psi, s));
   mark(C, 1, s);
-  CK(tf32_gemm(P.work1, P.n1, P.seg, P.maps, P.err, s));
+  CK(split_gemm(P.work1, P.n1, P.seg, P.maps, P.pstat, P.err, s));
   mark(C, 2, s);
-  CK(tf32_gemm(P.work2, P.n2, P.seg, P.maps, P.err, s));
+  CK(split_gemm(P.work2, P.n2, P.seg, P.maps, P.pstat, P.err, s));
   mark(C, 3, s);
   CK(sum_partials(P.psum, P.npsum, sigma, s));
   mark(C, 4, s);
 }
 
-// The split apply is 8 launches; it is captured once per (psi, sigma) pair
+// The split apply is a handful of launches; it is captured once per (psi, sigma) pair
 // into a CUDA graph and replayed (Davidson reuses a fixed set of vector slots).
 // With per-stage timing on, the launches go out directly.
-void apply_tf32(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s) {
+void apply_split(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s) {
   Window &w = C->win;
   if (!w.tf_ready) {
     cudaStream_t save = C->stream;
     C->stream = s;
-    build_tf32(C);
+    build_split(C);
     C->stream = save;
   }
   if (C->timing || !C->use_graphs) {
-    launch_tf32(C, psi, sigma, s);
+    launch_split(C, psi, sigma, s);
     return;
   }
   auto key = std::make_pair((const void *)psi, (const void *)sigma);
@@ -1630,7 +1695,7 @@ void apply_tf32(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s) {
       std::unique_lock<std::shared_mutex> lk(capture_lock());
       CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
       try {
-        launch_tf32(C, psi, sigma, cs);
+        launch_split(C, psi, sigma, cs);
       } catch (...) {
         cudaStreamEndCapture(cs, &g);
         throw;
@@ -1655,7 +1720,7 @@ void check_err_flag(dmrg_ctx *C, cudaStream_t s) {
 }
 
 void apply(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s, int precision) {
-  if (precision == DMRG_SPLIT_TF32) apply_tf32(C, psi, sigma, s);
+  if (precision == DMRG_SPLIT) apply_split(C, psi, sigma, s);
   else apply_fp64(C, psi, sigma, s);
 }
 
@@ -1808,7 +1873,7 @@ int davidson(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_t s,
     // The split product is accurate to ~1e-6 relative, so its residual cannot
     // fall much below that times |theta|; the reported energy is the FP64
     // Rayleigh quotient, whose error is second order in the residual.
-    const double floor = prec == DMRG_SPLIT_TF32 ? kSplitResidualFloor * std::max(1.0, std::fabs(theta)) : 0.0;
+    const double floor = prec == DMRG_SPLIT ? kSplitResidualFloor * std::max(1.0, std::fabs(theta)) : 0.0;
     // A start vector already at the floor is accepted as is.  Otherwise the
     // split path does not stop on reaching the floor: an excited state can
     // converge first from a start with little ground-state weight (early
@@ -1824,7 +1889,7 @@ int davidson(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_t s,
     if (rnorm < 0.5 * best_r) {
       best_r = rnorm;
       best_it = it;
-    } else if (prec == DMRG_SPLIT_TF32 && it - best_it >= 16 && rnorm < 10.0 * std::max(tol, floor)) {
+    } else if (prec == DMRG_SPLIT && it - best_it >= 16 && rnorm < 10.0 * std::max(tol, floor)) {
       conv = true;
       break;
     }
@@ -2673,7 +2738,7 @@ int dmrg_heff_layout(dmrg_ctx *C, long long *psi_len, int *n_blocks, int *blocks
 }
 
 int dmrg_set_precision(dmrg_ctx *C, int precision) {
-  if (!C || (precision != DMRG_FP64 && precision != DMRG_SPLIT_TF32)) return DMRG_ERR_ARG;
+  if (!C || (precision != DMRG_FP64 && precision != DMRG_SPLIT)) return DMRG_ERR_ARG;
   C->precision = precision;
   return DMRG_OK;
 }
@@ -2707,7 +2772,7 @@ int dmrg_heff_apply_host(dmrg_ctx *C, const double *psi_h, double *sigma_h, void
   });
 }
 
-int dmrg_heff_apply_tf32_static(dmrg_ctx *C, const double *psi, double *sigma, void *stream) {
+int dmrg_heff_apply_split_static(dmrg_ctx *C, const double *psi, double *sigma, void *stream) {
   if (!C || !psi || !sigma) return DMRG_ERR_ARG;
   if (!C->win.valid) {
     C->err = "no window built";
@@ -2717,19 +2782,19 @@ int dmrg_heff_apply_tf32_static(dmrg_ctx *C, const double *psi, double *sigma, v
     Window &w = C->win;
     cudaStream_t s = (cudaStream_t)stream;
     if (!w.tf_copies)
-      fail(DMRG_ERR_STATE, "FP32 operator copies not built: call dmrg_heff_apply once with "
-                           "DMRG_SPLIT_TF32 after dmrg_build_block_ops");
+      fail(DMRG_ERR_STATE, "split operator copies not built: call dmrg_heff_apply once with "
+                           "DMRG_SPLIT after dmrg_build_block_ops");
     void *base = nullptr;
     size_t cap = 0;
     CK(static_scratch(&base, &cap));
-    CK(tf32_prepare());
+    CK(split_prepare());
     int dev = 0;
     CK(cudaGetDevice(&dev));
-    // layout: [error flag | tables | psi^T | T | partial tiles]
+    // layout: [error flag | tables | psi statistics | psi^T hi, lo | T hi, lo | partial tiles]
     struct Owner {
       long long gen = -1;
-      Tf32Tables tb;
-      size_t o_maps, o_seg, o_w1, o_w2, o_ps, o_split;
+      SplitTables tb;
+      size_t o_maps, o_seg, o_w1, o_w2, o_ps, o_split, o_pdesc, o_pstat;
     };
     static std::mutex mu;
     static std::map<int, Owner> owners;
@@ -2738,30 +2803,40 @@ int dmrg_heff_apply_tf32_static(dmrg_ctx *C, const double *psi, double *sigma, v
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     unsigned char *b = (unsigned char *)base;
     const int ks = w.ksub ? w.ksub : KSUB_DEFAULT;
+    const size_t np = w.psi.size();
     if (ow.gen != w.gen) {
-      Tf32Scratch z = tf32_scratch_sizes(w, ks);
+      SplitScratch z = split_scratch_sizes(w, ks);
       // table sizes do not depend on the pointers: size them with a dry run
-      Tf32Tables probe;
-      tf32_tables(w, z, (float *)b, (float *)b, (float *)b, probe, ks);
+      SplitTables probe;
+      __half *hb = (__half *)b;
+      split_tables(w, z, hb, hb, hb, hb, (float *)b, probe, ks);
       size_t off = 256;
       ow.o_maps = off; off = al(off + probe.maps.size() * sizeof(CUtensorMap));
       ow.o_seg = off; off = al(off + probe.segs.size() * sizeof(TSeg));
       ow.o_w1 = off; off = al(off + probe.w1.size() * sizeof(TWork));
       ow.o_w2 = off; off = al(off + probe.w2.size() * sizeof(TWork));
       ow.o_ps = off; off = al(off + probe.psums.size() * sizeof(PartialSum));
-      ow.o_split = off; off = al(off + probe.psi_split.size() * sizeof(Split2D));
-      const size_t oP = off;
-      off = al(off + 4 * (size_t)z.nP);
-      const size_t oT = off;
-      off = al(off + 4 * (size_t)z.nT);
+      ow.o_split = off; off = al(off + probe.psi_split.size() * sizeof(F16Split));
+      ow.o_pdesc = off; off = al(off + np * sizeof(PsiDesc));
+      ow.o_pstat = off; off = al(off + np * sizeof(PsiStat));
+      const size_t oPh = off;
+      off = al(off + 2 * (size_t)z.nP);
+      const size_t oPl = off;
+      off = al(off + 2 * (size_t)z.nP);
+      const size_t oTh = off;
+      off = al(off + 2 * (size_t)z.nT);
+      const size_t oTl = off;
+      off = al(off + 2 * (size_t)z.nT);
       const size_t oW = off;
       off = al(off + 4 * (size_t)z.nws);
       if (off > cap)
         fail(DMRG_ERR_ARG, "window needs %zu bytes of scratch; the static scratch holds %zu bytes "
                            "(use dmrg_heff_apply for larger windows)", off, cap);
       ow.gen = -1;
-      tf32_tables(w, z, (float *)(b + oP), (float *)(b + oT), (float *)(b + oW), ow.tb, ks);
-      const Tf32Tables &t = ow.tb;
+      split_tables(w, z, (__half *)(b + oPh), (__half *)(b + oPl), (__half *)(b + oTh),
+                   (__half *)(b + oTl), (float *)(b + oW), ow.tb, ks);
+      const SplitTables &t = ow.tb;
+      const std::vector<PsiDesc> pd = psi_descs(w);
       auto put = [&](size_t o, const void *src, size_t n) {
         if (n) CK(cudaMemcpyAsync(b + o, src, n, cudaMemcpyHostToDevice, s));
       };
@@ -2770,17 +2845,20 @@ int dmrg_heff_apply_tf32_static(dmrg_ctx *C, const double *psi, double *sigma, v
       put(ow.o_w1, t.w1.data(), t.w1.size() * sizeof(TWork));
       put(ow.o_w2, t.w2.data(), t.w2.size() * sizeof(TWork));
       put(ow.o_ps, t.psums.data(), t.psums.size() * sizeof(PartialSum));
-      put(ow.o_split, t.psi_split.data(), t.psi_split.size() * sizeof(Split2D));
+      put(ow.o_split, t.psi_split.data(), t.psi_split.size() * sizeof(F16Split));
+      put(ow.o_pdesc, pd.data(), pd.size() * sizeof(PsiDesc));
       ow.gen = w.gen;
     }
-    const Tf32Tables &t = ow.tb;
+    const SplitTables &t = ow.tb;
     int *err = (int *)b;
+    PsiStat *pst = (PsiStat *)(b + ow.o_pstat);
     CK(cudaMemsetAsync(err, 0, sizeof(int), s));   // the only state that must start at zero
-    CK(launch_split2d((const Split2D *)(b + ow.o_split), (int)t.psi_split.size(), s, psi));
-    CK(tf32_gemm((const TWork *)(b + ow.o_w1), t.n1, (const TSeg *)(b + ow.o_seg),
-                 (const CUtensorMap *)(b + ow.o_maps), err, s));
-    CK(tf32_gemm((const TWork *)(b + ow.o_w2), t.n2, (const TSeg *)(b + ow.o_seg),
-                 (const CUtensorMap *)(b + ow.o_maps), err, s));
+    CK(psi_stats((const PsiDesc *)(b + ow.o_pdesc), (int)np, psi, pst, s));
+    CK(f16_split((const F16Split *)(b + ow.o_split), (int)t.psi_split.size(), pst, psi, s));
+    CK(split_gemm((const TWork *)(b + ow.o_w1), t.n1, (const TSeg *)(b + ow.o_seg),
+                  (const CUtensorMap *)(b + ow.o_maps), pst, err, s));
+    CK(split_gemm((const TWork *)(b + ow.o_w2), t.n2, (const TSeg *)(b + ow.o_seg),
+                  (const CUtensorMap *)(b + ow.o_maps), pst, err, s));
     CK(sum_partials((const PartialSum *)(b + ow.o_ps), (int)t.psums.size(), sigma, s));
   });
 }
@@ -2832,11 +2910,11 @@ int dmrg_heff_split_plan(dmrg_ctx *C, double *out4) {
   if (!C || !out4) return DMRG_ERR_ARG;
   const Window &w = C->win;
   if (!w.valid || !w.tf_ready) {
-    C->err = "split plan not built: apply once with DMRG_SPLIT_TF32 first";
+    C->err = "split plan not built: apply once with DMRG_SPLIT first";
     return DMRG_ERR_STATE;
   }
-  const Tf32Plan &P = w.tf;
-  int launches = 1 + (P.npsum > 0 ? 1 : 0);
+  const SplitPlan &P = w.tf;
+  int launches = 2 + (P.npsum > 0 ? 1 : 0);
   for (int i = 0; i < 3; ++i) launches += (P.n1[i] > 0) + (P.n2[i] > 0);
   out4[0] = launches;
   out4[1] = P.nwork1;

@@ -1,52 +1,52 @@
-// 3 x TF32 grouped GEMM on tcgen05 (sm_103a) for the two H_eff*psi stages.
-// (persistent, warp-specialised; see k_tf32_gemm)
+// Split-precision grouped GEMM on tcgen05 (sm_103a) for the two H_eff*psi stages.
+// (persistent, warp-specialised; see k_split_gemm)
 //
 // Stage 1:  T[(a',k), b]  = sign * A_stack[(a',k), a] . psi[a, b]
 // Stage 2:  sigma[a', b'] = sum_segments T[a', (k,b)] . B_stack[b', (k,b)]^T
-// Both are C = A . B^T with K-major operands.  The operator stacks and T are
-// FP32 in device memory; psi^T comes split as TF32 (hi, lo).  Each FP32
-// operand chunk is split on chip: the tensor core reads the FP32 tile as the
-// high part (top 19 bits) and converter warps write the low part next to it.
-// A product is lo.hi + hi.lo + hi.hi (lo.lo, of relative size 2^-22, is
-// below the FP32 accumulation error) with FP32 accumulation in tensor
-// memory.  A work item is one 128 x ntile output tile; per 32-wide K chunk
-// the producer loads A and B (and psi^T's low part) by TMA, the converters
-// add the low parts and the MMA warp issues 4 k-steps x 3 tcgen05.mma.
+// Both are C = A . B^T with K-major operands.  Every operand block is held in
+// device memory as x * s = hi + lo (FP16 each, s a power of two per block, so
+// the pair takes the 4 bytes of an FP32 value); a product is lo.hi + hi.lo +
+// hi.hi (lo.lo, of relative size 2^-22, is below the FP32 accumulation error)
+// with FP32 accumulation in tensor memory, and the epilogue takes the scales
+// out exactly.  Stage 1 writes T already rescaled and split for stage 2.
+// A work item is one 128 x ntile output tile; per 64-wide K chunk the
+// producer loads A_hi, A_lo, B_hi, B_lo by TMA and the MMA warp issues
+// 4 k-steps x 3 tcgen05.mma of kind::f16 (K = 16 each).
 // Every mbarrier wait is bounded; on timeout the kernel records an error
-// code, skips the remaining work, frees its TMEM and returns.
+// code, skips the remaining work, waits for its stores, frees its TMEM and
+// returns.
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "heff_tf32.h"
+#include <cmath>
+
+#include "heff_split.h"
 
 namespace dmrg {
 
 namespace {
 
 constexpr int BM = 128;           // UMMA M
-constexpr int BK = 32;            // floats per 128-byte swizzle row
-constexpr int TILE_A = BM * BK * 4;          // 16 KB
-constexpr int MAX_SMEM = 232448;             // 227 KB per CTA
-constexpr int NACC = 4;                      // TMEM accumulators (4 x 128 columns)
-constexpr int STAGE_OUT = 4 * 4096;          // epilogue staging: 4 warps x one 32 x 32 box
+constexpr int BK = 64;            // halves per 128-byte swizzle row (one K chunk)
+constexpr int TILE_A = BM * 128;  // 16 KB
+constexpr int MAX_SMEM = 232448;  // 227 KB per CTA
+constexpr int NACC = 4;           // TMEM accumulators (4 x 128 columns)
+constexpr int STAGE_OUT = 4 * 8192;   // epilogue staging: 4 warps x (hi, lo) 32 x 64 halves
+constexpr long long WAIT_LIMIT = 1LL << 22;
 
 // Pipeline geometry for a launch whose tiles are at most NT columns wide:
-// a TMA stage holds the FP32 chunks A (128 x 32) and B (NT x 32); a low-part
-// slot holds A_lo and B_lo.  The FP32 chunks stay until the MMAs that read
-// them as high parts complete; the low parts need only LO slots.
-constexpr int LO = 2;
+// a stage holds A_hi, A_lo (128 x 64 halves each) and B_hi, B_lo (NT x 64).
 template <int NT>
 struct Geo {
-  static constexpr int TILE_B = NT * BK * 4;
-  static constexpr int STAGE_BYTES = TILE_A + TILE_B;
-  static constexpr int STAGES_RAW =
-      (MAX_SMEM - 1024 - 512 - STAGE_OUT - LO * STAGE_BYTES) / STAGE_BYTES;
-  static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
-  static constexpr int SMEM_BYTES = (STAGES + LO) * STAGE_BYTES + 1024 + 512 + STAGE_OUT;
+  static constexpr int TILE_B = NT * 128;
+  static constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;
+  static constexpr int STAGES_RAW = (MAX_SMEM - 1024 - 512 - STAGE_OUT) / STAGE_BYTES;
+  static constexpr int STAGES = STAGES_RAW > 6 ? 6 : STAGES_RAW;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 512 + STAGE_OUT;
 };
-static_assert(Geo<128>::STAGES >= 4, "pipeline too shallow");
-constexpr long long WAIT_LIMIT = 1LL << 22;
+static_assert(Geo<128>::STAGES >= 3, "pipeline too shallow");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -94,17 +94,17 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
   return d;
 }
 
-// instruction descriptor: D f32, A/B tf32, both K-major, M = 128, N = n
-__device__ __forceinline__ uint32_t idesc_tf32(int n) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+// instruction descriptor: D f32, A/B f16, both K-major, M = 128, N = n
+__device__ __forceinline__ uint32_t idesc_f16(int n) {
+  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t id,
-                                         uint32_t accum) {
+__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t id,
+                                        uint32_t accum) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
       "l"(a), "l"(b), "r"(id), "r"(accum)
       : "memory");
 }
@@ -157,45 +157,43 @@ __device__ __forceinline__ void fence_async_shared() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-__device__ __forceinline__ float tf32_round(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t a) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
-}
-
-// four FP32 values at src -> their low TF32 parts at dst
-__device__ __forceinline__ void lo_split4(uint32_t src, uint32_t dst) {
-  float x[4];
-  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-               : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3])
-               : "r"(src)
-               : "memory");
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const float hi = __uint_as_float(__float_as_uint(x[i]) & 0xffffe000u);
-    x[i] = tf32_round(x[i] - hi);
-  }
-  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "f"(x[0]), "f"(x[1]),
-               "f"(x[2]), "f"(x[3])
+__device__ __forceinline__ void st_shared_v4u(uint32_t a, uint32_t x, uint32_t y, uint32_t z,
+                                              uint32_t w) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w)
                : "memory");
 }
 
-// Persistent, warp-specialised 3xTF32 GEMM.  Each CTA walks the work list
+// Power of two s with |m| * s <= 2^14 (m = f 2^e, f in [0.5, 1): s = 2^(14-e));
+// 1 for m <= 0.  The exponent is clamped so that s stays finite.
+__device__ __forceinline__ float pow2_scale(float m) {
+  if (!(m > 0.f) || !(m < 3.0e38f)) return 1.f;
+  int e;
+  frexpf(m, &e);
+  int x = 14 - e;
+  x = x > 100 ? 100 : (x < -100 ? -100 : x);
+  return ldexpf(1.f, x);
+}
+
+// x * s -> (hi, lo) halves with hi + lo = x * s to ~2^-22 relative
+__device__ __forceinline__ void split_h(float t, __half &h, __half &l) {
+  h = __float2half_rn(t);
+  l = __float2half_rn(t - __half2float(h));
+}
+
+__device__ __forceinline__ uint32_t pack_h2(__half a, __half b) {
+  return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+}
+
+// Persistent, warp-specialised split GEMM.  Each CTA walks the work list
 // with stride gridDim.x (the list is sorted by cost, largest first):
 //   warp 0, lane 0   TMA producer over all K chunks of all its tiles
 //   warp 1, lane 0   MMA issuer, rotating over four TMEM accumulators
 //   warps 2..5       epilogue: drain an accumulator while the next tile runs
-//   warps 6..13      converters: split each FP32 operand chunk on chip
-constexpr int NTHREADS = 448;
-constexpr int NCONV = 256;
+constexpr int NTHREADS = 192;
 constexpr int ACC_COLS = 128;
 
 struct Shared {
-  uint64_t full[8], empty[8], lo_full[LO], lo_empty[LO], acc_full[NACC], acc_empty[NACC];
+  uint64_t full[8], empty[8], acc_full[NACC], acc_empty[NACC];
   uint32_t tmem;
   int abort;
 };
@@ -215,16 +213,16 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t a, uint32_t parity, int *
 
 template <int NT>
 __global__ void __launch_bounds__(NTHREADS, 1)
-k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__ segs,
-            const CUtensorMap *__restrict__ maps, int *__restrict__ err) {
+k_split_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__ segs,
+             const CUtensorMap *__restrict__ maps, const PsiStat *__restrict__ pstat,
+             int *__restrict__ err) {
   using G = Geo<NT>;
   constexpr int STAGES = G::STAGES;
   constexpr int STAGE_BYTES = G::STAGE_BYTES;
   constexpr int TILE_B = G::TILE_B;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t *lo_ring = smem + STAGES * STAGE_BYTES;        // low parts
-  uint8_t *stage_out = lo_ring + LO * STAGE_BYTES;       // 1024-byte aligned
+  uint8_t *stage_out = smem + STAGES * STAGE_BYTES;      // 1024-byte aligned
   Shared *sh = (Shared *)(stage_out + STAGE_OUT);
   volatile int *abort_flag = &sh->abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -233,10 +231,6 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
     for (int i = 0; i < STAGES; ++i) {
       mbar_init(smem_u32(&sh->full[i]), 1);
       mbar_init(smem_u32(&sh->empty[i]), 1);
-    }
-    for (int i = 0; i < LO; ++i) {
-      mbar_init(smem_u32(&sh->lo_full[i]), NCONV);
-      mbar_init(smem_u32(&sh->lo_empty[i]), 1);
     }
     for (int i = 0; i < NACC; ++i) {
       mbar_init(smem_u32(&sh->acc_full[i]), 1);
@@ -263,14 +257,14 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
       int it = 0;
       for (int t = blockIdx.x; t < nwork && !*abort_flag; t += gridDim.x) {
         const TWork w = works[t];
-        const uint32_t stage_tx = TILE_A + (uint32_t)w.ntile * BK * 4;
+        const uint32_t stage_tx = 2 * TILE_A + 2 * (uint32_t)w.ntile * 128;
         if (w.R > 1) {
           // packed tile: per chunk, group r's rows of A and B from its own
           // segment (a chunk past the segment's end loads zeros)
-          const uint32_t ga = (BM / w.R) * BK * 4, gb = (uint32_t)(w.ntile / w.R) * BK * 4;
+          const uint32_t ga = (BM / w.R) * 128, gb = (uint32_t)(w.ntile / w.R) * 128;
           uint32_t tx = 0;
           for (int r = 0; r < w.R; ++r)
-            if (w.pseg[r] >= 0) tx += ga + gb;
+            if (w.pseg[r] >= 0) tx += 2 * ga + 2 * gb;
           for (int kc = 0; kc < w.nchunk; ++kc, ++it) {
             const int st = it % STAGES;
             const uint32_t ph = (it / STAGES) & 1;
@@ -283,7 +277,9 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
               const TSeg sg = segs[w.pseg[r]];
               const int kx = kc * BK < sg.K ? sg.k0 + kc * BK : sg.xoob;
               tma_load(smem_u32(base + r * ga), &maps[sg.mA_hi], kx, 0, fb);
-              tma_load(smem_u32(base + TILE_A + r * gb), &maps[sg.mB_hi], kx, 0, fb);
+              tma_load(smem_u32(base + TILE_A + r * ga), &maps[sg.mA_lo], kx, 0, fb);
+              tma_load(smem_u32(base + 2 * TILE_A + r * gb), &maps[sg.mB_hi], kx, 0, fb);
+              tma_load(smem_u32(base + 2 * TILE_A + TILE_B + r * gb), &maps[sg.mB_lo], kx, 0, fb);
             }
           }
           continue;
@@ -300,7 +296,9 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
             mbar_expect_tx(fb, stage_tx);
             const int kx = sg.k0 + kc * BK;
             tma_load(smem_u32(base), &maps[sg.mA_hi], kx, w.m0, fb);
-            tma_load(smem_u32(base + TILE_A), &maps[sg.mB_hi], kx, w.n0, fb);
+            tma_load(smem_u32(base + TILE_A), &maps[sg.mA_lo], kx, w.m0, fb);
+            tma_load(smem_u32(base + 2 * TILE_A), &maps[sg.mB_hi], kx, w.n0, fb);
+            tma_load(smem_u32(base + 2 * TILE_A + TILE_B), &maps[sg.mB_lo], kx, w.n0, fb);
           }
         }
       }
@@ -311,7 +309,7 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
       int it = 0, j = 0;
       for (int t = blockIdx.x; t < nwork && !*abort_flag; t += gridDim.x, ++j) {
         const TWork w = works[t];
-        const uint32_t id = idesc_tf32(w.ntile);
+        const uint32_t id = idesc_f16(w.ntile);
         const int acc = j % NACC;
         const uint32_t aph = (j / NACC) & 1;
         if (!wait_or_abort(smem_u32(&sh->acc_empty[acc]), aph ^ 1, err, 2, abort_flag)) break;
@@ -327,83 +325,46 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
           for (int kc = 0; kc < nk; ++kc, ++it) {
             const int st = it % STAGES;
             const uint32_t ph = (it / STAGES) & 1;
-            // the low parts of chunk `it` are ready (its FP32 chunk too)
-            const int ls = it % LO;
-            if (!wait_or_abort(smem_u32(&sh->lo_full[ls]), (it / LO) & 1, err, 3, abort_flag))
-              break;
+            if (!wait_or_abort(smem_u32(&sh->full[st]), ph, err, 3, abort_flag)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a_hi = smem_u32(smem + st * STAGE_BYTES);
-            const uint32_t b_hi = a_hi + TILE_A;
-            const uint32_t a_lo = smem_u32(lo_ring + ls * STAGE_BYTES);
-            const uint32_t b_lo = a_lo + TILE_A;
-            // k-steps of 8 that hold data (the rest of a ragged chunk is zero fill)
+            const uint32_t a_lo = a_hi + TILE_A;
+            const uint32_t b_hi = a_hi + 2 * TILE_A;
+            const uint32_t b_lo = b_hi + TILE_B;
+            // k-steps of 16 that hold data (the rest of a ragged chunk is zero fill)
             const int rem = K - kc * BK;
-            const int nk8 = rem >= BK ? BK / 8 : (rem + 7) / 8;
-            // descriptors of the chunk's tiles; a k-step of 8 tf32 (32 bytes
-            // along the swizzled row) adds 2 to the encoded start address
+            const int nk16 = rem >= BK ? BK / 16 : (rem + 15) / 16;
+            // a k-step of 16 halves (32 bytes along the swizzled row) adds 2
+            // to the encoded start address
             const uint64_t dah = sdesc(a_hi), dal = sdesc(a_lo), dbh = sdesc(b_hi),
                            dbl = sdesc(b_lo);
-            for (int k = 0; k < nk8; ++k) {
+            for (int k = 0; k < nk16; ++k) {
               const uint64_t ko = 2 * k;
               // small terms first: lo.hi, hi.lo, then hi.hi (lo.lo is below
               // the FP32 accumulation error and is left out)
-              mma_tf32(d, dal + ko, dbh + ko, id, accum);
+              mma_f16(d, dal + ko, dbh + ko, id, accum);
               accum = 1;
-              mma_tf32(d, dah + ko, dbl + ko, id, 1);
-              mma_tf32(d, dah + ko, dbh + ko, id, 1);
+              mma_f16(d, dah + ko, dbl + ko, id, 1);
+              mma_f16(d, dah + ko, dbh + ko, id, 1);
             }
             mma_commit(smem_u32(&sh->empty[st]));
-            mma_commit(smem_u32(&sh->lo_empty[ls]));
           }
         }
         // every work item has K >= 1, so the accumulator always holds data
         mma_commit(smem_u32(&sh->acc_full[acc]));
       }
     }
-  } else if (warp >= 6) {
-    // ---------------- converters (warps 6..13) ----------------
-    // For every chunk (same order as the producer) write the low parts
-    // lo = rna_tf32(x - trunc_tf32(x)) of the FP32 operand tiles next to
-    // them; the tensor core reads the FP32 tile itself as the high part (it
-    // uses the top 19 bits), so hi + lo carries x to ~2^-22.  The layout is
-    // elementwise, so the swizzled tile maps to the same swizzled offsets.
-    const int tid = threadIdx.x - 6 * 32;
-    int it = 0;
-    bool ok = true;
-    for (int t = blockIdx.x; t < nwork && ok; t += gridDim.x) {
-      const TWork w = works[t];
-      int nk = 0;
-      if (w.R > 1) {
-        nk = w.nchunk;
-      } else {
-        for (int s = 0; s < w.nseg; ++s) nk += (segs[w.seg0 + s].K + BK - 1) / BK;
-      }
-      const int n4 = (TILE_A + w.ntile * BK * 4) / 16;   // float4s of the A and B chunks
-      for (int kc = 0; kc < nk; ++kc, ++it) {
-        const int st = it % STAGES, ls = it % LO;
-        if (!wait_or_abort(smem_u32(&sh->full[st]), (it / STAGES) & 1, err, 5, abort_flag) ||
-            !wait_or_abort(smem_u32(&sh->lo_empty[ls]), ((it / LO) & 1) ^ 1, err, 6, abort_flag)) {
-          ok = false;
-          break;
-        }
-        // A (16 KB) and B (ntile rows) are contiguous in both slots
-        const uint32_t src = smem_u32(smem + st * STAGE_BYTES);
-        const uint32_t dst = smem_u32(lo_ring + ls * STAGE_BYTES);
-#pragma unroll 4
-        for (int i = tid; i < n4; i += NCONV) lo_split4(src + 16 * i, dst + 16 * i);
-        fence_async_shared();
-        mbar_arrive(smem_u32(&sh->lo_full[ls]));
-      }
-    }
   } else {
     // ---------------- epilogue (warps 2..5) ----------------
-    // Each lane holds one accumulator row.  Per 32-column block the warp
-    // stages its 32 x 32 sub-tile in shared memory in the 128-byte-swizzled
-    // box layout (16-byte chunk q of row r at position q ^ (r & 7)) and one
-    // lane stores it by TMA; the tensor map clips rows and columns outside
-    // the destination.
+    // Each lane holds one accumulator row.  The warp stages its 32-row
+    // sub-tile in shared memory in the 128-byte-swizzled box layout (16-byte
+    // chunk q of row r at position q ^ (r & 7)) and one lane stores it by
+    // TMA; the tensor maps clip rows and columns outside the destination.
+    //   stage 1: T = alpha * C / (sA sP), times T's own power of two, split
+    //            into FP16 (hi, lo), 64 columns per box;
+    //   stage 2: C / (sT sB) as FP32, 32 columns per box.
     const int quarter = warp & 3;            // TMEM lanes 32*quarter .. +31
-    const uint32_t stg = smem_u32(stage_out + (warp - 2) * 4096);
+    const uint32_t stg = smem_u32(stage_out + (warp - 2) * 8192), stg2 = stg + 4096;
     const uint32_t rowoff = (uint32_t)lane * 128;
     int j = 0;
     for (int t = blockIdx.x; t < nwork; t += gridDim.x, ++j) {
@@ -413,12 +374,12 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
       if (!wait_or_abort(smem_u32(&sh->acc_full[acc]), aph, err, 4, abort_flag)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t tbase = tmem + acc * ACC_COLS + ((uint32_t)(quarter * 32) << 16);
-      // destination of this warp's rows: a plain tile, or the diagonal block
-      // of its group in a packed tile
       int row0 = w.m0 + quarter * 32, cbeg = 0, cend = w.ntile, xoff = w.n0, mo = w.mOut_hi,
           zo = w.zout;
       bool live = row0 < w.M;
+      float fac;
       if (w.R > 1) {
+        // destination of this warp's rows: the diagonal block of its group
         const int per = 4 / w.R, r = quarter / per, gw = w.ntile / w.R;
         row0 = (quarter % per) * 32;
         cbeg = r * gw;
@@ -427,8 +388,51 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
         mo = w.pout[r];
         zo = w.pz[r];
         live = w.pseg[r] >= 0;
+        fac = live ? w.pfa[r] / pow2_scale(w.prn[r] * pstat[w.ppb[r]].cn) : 0.f;
+      } else if (w.mode == TW_SPLIT) {
+        const PsiStat ps = pstat[w.pblk];
+        fac = w.alpha * w.fa * pow2_scale(w.rn * ps.cn) / pow2_scale(ps.mx);
+      } else {
+        fac = w.fa / pow2_scale(w.rn * pstat[w.pblk].cn);
       }
-      if (live) {
+      if (live && w.mode == TW_SPLIT) {
+        for (int c0 = 0; c0 < w.ntile && w.n0 + c0 < w.N; c0 += 64) {
+          float v[64];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (c0 + 16 * q < w.ntile) {
+              tmem_ld16(tbase + c0 + 16 * q, v + 16 * q);
+            } else {
+#pragma unroll
+              for (int i = 0; i < 16; ++i) v[16 * q + i] = 0.f;
+            }
+          }
+          if (lane == 0) bulk_wait_read();
+          __syncwarp();
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              __half h0, l0, h1, l1;
+              split_h(fac * v[8 * q + 2 * i], h0, l0);
+              split_h(fac * v[8 * q + 2 * i + 1], h1, l1);
+              h[i] = pack_h2(h0, h1);
+              l[i] = pack_h2(l0, l1);
+            }
+            const uint32_t o = rowoff + ((uint32_t)(q ^ (lane & 7)) << 4);
+            st_shared_v4u(stg + o, h[0], h[1], h[2], h[3]);
+            st_shared_v4u(stg2 + o, l[0], l[1], l[2], l[3]);
+          }
+          fence_async_shared();
+          __syncwarp();
+          if (lane == 0) {
+            tma_store3d(&maps[w.mOut_hi], w.n0 + c0, row0, 0, stg);
+            tma_store3d(&maps[w.mOut_lo], w.n0 + c0, row0, 0, stg2);
+            bulk_commit();
+          }
+        }
+      } else if (live) {
         for (int c0 = cbeg; c0 < cend && (w.R > 1 || w.n0 + c0 < w.N); c0 += 32) {
           float v[32];
           tmem_ld16(tbase + c0, v);
@@ -440,11 +444,10 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
           }
           if (lane == 0) bulk_wait_read();
           __syncwarp();
-          const float al = w.mode == TW_SPLIT ? w.alpha : 1.f;
 #pragma unroll
           for (int q = 0; q < 8; ++q)
-            st_shared_v4(stg + rowoff + ((uint32_t)(q ^ (lane & 7)) << 4), al * v[4 * q],
-                         al * v[4 * q + 1], al * v[4 * q + 2], al * v[4 * q + 3]);
+            st_shared_v4(stg + rowoff + ((uint32_t)(q ^ (lane & 7)) << 4), fac * v[4 * q],
+                         fac * v[4 * q + 1], fac * v[4 * q + 2], fac * v[4 * q + 3]);
           fence_async_shared();
           __syncwarp();
           if (lane == 0) {
@@ -469,7 +472,143 @@ k_tf32_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__
   }
 }
 
-}  // namespace
+// ---------------------------------------------------------------------------
+// scaled FP16 (hi, lo) copies and their statistics
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float warp_max(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// one CTA per class entry: max |A|, max row 2-norm of A, max |B| (FP64 stacks)
+__global__ void __launch_bounds__(256) k_entry_stats(const StatDesc *__restrict__ ds,
+                                                     EntryStat *__restrict__ out) {
+  const StatDesc d = ds[blockIdx.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float mA = 0.f, rA = 0.f, mB = 0.f;
+  for (long long r = warp; r < d.rowsA; r += 8) {
+    const double *row = d.a + r * d.colsA;
+    double ss = 0.0;
+    float m = 0.f;
+    for (int c = lane; c < d.colsA; c += 32) {
+      const double x = row[c];
+      ss += x * x;
+      m = fmaxf(m, (float)fabs(x));
+    }
+    // row sums of squares in FP32 (only a bound is needed)
+    const float s = warp_sum((float)ss);
+    mA = fmaxf(mA, warp_max(m));
+    rA = fmaxf(rA, sqrtf(s));
+  }
+  for (long long r = warp; r < d.rowsB; r += 8) {
+    const double *row = d.b + r * d.colsB;
+    float m = 0.f;
+    for (int c = lane; c < d.colsB; c += 32) m = fmaxf(m, (float)fabs(row[c]));
+    mB = fmaxf(mB, warp_max(m));
+  }
+  __shared__ float red[3][8];
+  if (lane == 0) {
+    red[0][warp] = mA;
+    red[1][warp] = rA;
+    red[2][warp] = mB;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float a = 0.f, b = 0.f, c = 0.f;
+    for (int i = 0; i < 8; ++i) {
+      a = fmaxf(a, red[0][i]);
+      b = fmaxf(b, red[1][i]);
+      c = fmaxf(c, red[2][i]);
+    }
+    // the bound on T uses the row norm rounded up a little (FP32 sums)
+    out[blockIdx.x] = {a, b * 1.0001f, c, 0.f};
+  }
+}
+
+// one CTA per psi block (rows x cols, row-major at psi + off): max |psi| and
+// the largest column 2-norm
+__global__ void __launch_bounds__(256) k_psi_stats(const PsiDesc *__restrict__ ds,
+                                                   const double *__restrict__ psi,
+                                                   PsiStat *__restrict__ out) {
+  const PsiDesc d = ds[blockIdx.x];
+  const double *p = psi + d.off;
+  float m = 0.f, cn = 0.f;
+  for (int c = threadIdx.x; c < d.cols; c += blockDim.x) {
+    double ss = 0.0;
+    float mc = 0.f;
+    for (int r = 0; r < d.rows; ++r) {
+      const double x = p[(long long)r * d.cols + c];
+      ss += x * x;
+      mc = fmaxf(mc, (float)fabs(x));
+    }
+    m = fmaxf(m, mc);
+    cn = fmaxf(cn, (float)sqrt(ss));
+  }
+  __shared__ float red[2][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  m = warp_max(m);
+  cn = warp_max(cn);
+  if (lane == 0) {
+    red[0][warp] = m;
+    red[1][warp] = cn;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float a = 0.f, b = 0.f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      a = fmaxf(a, red[0][i]);
+      b = fmaxf(b, red[1][i]);
+    }
+    out[blockIdx.x] = {a, b * 1.0001f};
+  }
+}
+
+// FP64 -> scaled FP16 (hi, lo), 32 x 32 tiles through shared memory
+__global__ void k_f16_split(const F16Split *__restrict__ ds, const PsiStat *__restrict__ pstat,
+                            const double *__restrict__ bind) {
+  __shared__ double tile[32][33];
+  const F16Split d = ds[blockIdx.z];
+  const double *src = d.src ? d.src : bind + d.src_off;
+  const double s = d.scale > 0.f ? (double)d.scale : (double)pow2_scale(pstat[d.pblk].mx);
+  const int tr = (d.rows + 31) / 32, tc = (d.cols + 31) / 32;
+  for (int t = blockIdx.x; t < tr * tc; t += gridDim.x) {
+    const int r0 = (t / tc) * 32, c0 = (t % tc) * 32;
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+      const int r = r0 + j, c = c0 + threadIdx.x;
+      tile[j][threadIdx.x] = (r < d.rows && c < d.cols) ? src[(long long)r * d.src_ld + c] : 0.0;
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+      int r, c;
+      double x;
+      if (d.trans) {
+        c = c0 + j;
+        r = r0 + threadIdx.x;
+        x = tile[threadIdx.x][j];
+      } else {
+        r = r0 + j;
+        c = c0 + threadIdx.x;
+        x = tile[j][threadIdx.x];
+      }
+      if (c < d.cols && r < d.rows) {
+        const double y = x * s;
+        const __half h = __double2half(y);
+        const __half l = __double2half(y - (double)__half2float(h));
+        const long long o = d.trans ? (long long)c * d.dst_ld + r : (long long)r * d.dst_ld + c;
+        d.hi[o] = h;
+        d.lo[o] = l;
+      }
+    }
+    __syncthreads();
+  }
+}
 
 // s + c += x with the rounding error of the add kept in c (Knuth's
 // branch-free two-sum): the sum of a few hundred FP32 partials stays accurate
@@ -528,8 +667,7 @@ typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, voi
                              const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-int encode_map(CUtensorMap *out, const float *base, int rows, int cols, long long ld,
-               int box_rows) {
+EncodeFn encoder() {
   static const EncodeFn fn = [] {
     cudaDriverEntryPointQueryResult q;
     void *p = nullptr;
@@ -539,13 +677,72 @@ int encode_map(CUtensorMap *out, const float *base, int rows, int cols, long lon
       return (EncodeFn) nullptr;
     return (EncodeFn)p;
   }();
+  return fn;
+}
+
+int sm_count() {
+  static const int n = [] {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 148;
+  }();
+  return n;
+}
+
+template <int NT>
+cudaError_t prepare_nt() {
+  return cudaFuncSetAttribute(k_split_gemm<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              Geo<NT>::SMEM_BYTES);
+}
+
+// (the shared-memory attributes are set by split_prepare, outside any capture)
+template <int NT>
+cudaError_t launch_nt(const TWork *work, int nwork, const TSeg *seg, const CUtensorMap *maps,
+                      const PsiStat *pstat, int *err, cudaStream_t s) {
+  if (nwork <= 0) return cudaSuccess;
+  const int nsm = sm_count();
+  const int grid = nwork < nsm ? nwork : nsm;
+  k_split_gemm<NT><<<grid, NTHREADS, Geo<NT>::SMEM_BYTES, s>>>(work, nwork, seg, maps, pstat, err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+float pow2_scale_host(float m) {
+  if (!(m > 0.f) || !(m < 3.0e38f)) return 1.f;
+  int e;
+  std::frexp(m, &e);
+  int x = 14 - e;
+  x = x > 100 ? 100 : (x < -100 ? -100 : x);
+  return std::ldexp(1.f, x);
+}
+
+int encode_map_h(CUtensorMap *out, const __half *base, long long rows, long long cols,
+                 long long ld, int box_rows) {
+  const EncodeFn fn = encoder();
   if (!fn) return -1;
-  if (((uintptr_t)base & 15) || (ld & 3) || rows <= 0 || cols <= 0) return -2;
+  if (((uintptr_t)base & 15) || (ld & 7) || rows <= 0 || cols <= 0) return -2;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
   cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)base, dims, strides, box, estr,
+  CUresult r = fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (void *)base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : -3;
+}
+
+int encode_map3_h(CUtensorMap *out, const __half *base, long long d0, long long d1,
+                  long long d2, long long s1, long long s2, int box1, int box2) {
+  const EncodeFn fn = encoder();
+  if (!fn) return -1;
+  if (((uintptr_t)base & 15) || (s1 & 7) || (s2 & 7) || d0 <= 0 || d1 <= 0 || d2 <= 0) return -2;
+  cuuint64_t dims[3] = {(cuuint64_t)d0, (cuuint64_t)d1, (cuuint64_t)d2};
+  cuuint64_t strides[2] = {(cuuint64_t)s1 * 2, (cuuint64_t)s2 * 2};
+  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box1, (cuuint32_t)box2};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, (void *)base, dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : -3;
@@ -553,15 +750,7 @@ int encode_map(CUtensorMap *out, const float *base, int rows, int cols, long lon
 
 int encode_map3(CUtensorMap *out, const float *base, long long d0, long long d1, long long d2,
                 long long s1, long long s2, int box0, int box1, int box2) {
-  static const EncodeFn fn = [] {
-    cudaDriverEntryPointQueryResult q;
-    void *p = nullptr;
-    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) !=
-            cudaSuccess ||
-        q != cudaDriverEntryPointSuccess)
-      return (EncodeFn) nullptr;
-    return (EncodeFn)p;
-  }();
+  const EncodeFn fn = encoder();
   if (!fn) return -1;
   if (((uintptr_t)base & 15) || (s1 & 3) || (s2 & 3) || d0 <= 0 || d1 <= 0 || d2 <= 0 ||
       box0 * 4 > 128)
@@ -583,48 +772,45 @@ cudaError_t sum_partials(const PartialSum *p, int n, double *sigma, cudaStream_t
   return cudaGetLastError();
 }
 
-template <int NT>
-cudaError_t prepare_nt() {
-  return cudaFuncSetAttribute(k_tf32_gemm<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              Geo<NT>::SMEM_BYTES);
+cudaError_t entry_stats(const StatDesc *d, int n, EntryStat *out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_entry_stats<<<n, 256, 0, s>>>(d, out);
+  return cudaGetLastError();
 }
 
-cudaError_t tf32_prepare() {
+cudaError_t psi_stats(const PsiDesc *d, int n, const double *psi, PsiStat *out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_psi_stats<<<n, 256, 0, s>>>(d, psi, out);
+  return cudaGetLastError();
+}
+
+cudaError_t f16_split(const F16Split *d, int n, const PsiStat *pstat, const double *bind,
+                      cudaStream_t s) {
+  // grid.z is limited to 65535: launch in chunks of descriptors
+  for (int i0 = 0; i0 < n; i0 += 65535) {
+    dim3 grid(128, 1, n - i0 < 65535 ? n - i0 : 65535), block(32, 8);
+    k_f16_split<<<grid, block, 0, s>>>(d + i0, pstat, bind);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t split_prepare() {
   cudaError_t e = prepare_nt<32>();
   if (e == cudaSuccess) e = prepare_nt<64>();
   if (e == cudaSuccess) e = prepare_nt<128>();
   return e;
 }
 
-int sm_count() {
-  static const int n = [] {
-    int dev = 0, v = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-    return v > 0 ? v : 148;
-  }();
-  return n;
-}
-
-// (the shared-memory attributes are set by tf32_prepare, outside any capture)
-template <int NT>
-cudaError_t launch_nt(const TWork *work, int nwork, const TSeg *seg, const CUtensorMap *maps,
-                      int *err, cudaStream_t s) {
-  if (nwork <= 0) return cudaSuccess;
-  const int nsm = sm_count();
-  const int grid = nwork < nsm ? nwork : nsm;
-  k_tf32_gemm<NT><<<grid, NTHREADS, Geo<NT>::SMEM_BYTES, s>>>(work, nwork, seg, maps, err);
-  return cudaGetLastError();
-}
-
-cudaError_t tf32_gemm(const TWork *work, const int *nwork3, const TSeg *seg,
-                      const CUtensorMap *maps, int *err, cudaStream_t s) {
+cudaError_t split_gemm(const TWork *work, const int *nwork3, const TSeg *seg,
+                       const CUtensorMap *maps, const PsiStat *pstat, int *err, cudaStream_t s) {
   // work items are grouped by tile width: [<= 32 | <= 64 | <= 128]
-  cudaError_t e = launch_nt<32>(work, nwork3[0], seg, maps, err, s);
+  cudaError_t e = launch_nt<32>(work, nwork3[0], seg, maps, pstat, err, s);
   if (e != cudaSuccess) return e;
-  e = launch_nt<64>(work + nwork3[0], nwork3[1], seg, maps, err, s);
+  e = launch_nt<64>(work + nwork3[0], nwork3[1], seg, maps, pstat, err, s);
   if (e != cudaSuccess) return e;
-  return launch_nt<128>(work + nwork3[0] + nwork3[1], nwork3[2], seg, maps, err, s);
+  return launch_nt<128>(work + nwork3[0] + nwork3[1], nwork3[2], seg, maps, pstat, err, s);
 }
 
 }  // namespace dmrg

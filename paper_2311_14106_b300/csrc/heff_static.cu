@@ -1,5 +1,5 @@
 // Fixed device scratch for the allocation-free split-path H_eff*psi entry
-// point (dmrg_heff_apply_tf32_static).
+// point (dmrg_heff_apply_split_static).
 //
 // Callers that run inside a memory pool they do not own -- a host framework
 // whose device allocator must not be bypassed, a code path that may not

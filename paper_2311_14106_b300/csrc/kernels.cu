@@ -9,7 +9,6 @@
 //  * k_stack_copy copies (transposed, scaled) operator blocks into the
 //                 interleaved H_eff term stacks.
 //  * Davidson BLAS-1: dots, linear combinations, preconditioner, start vector.
-//  * k_split / k_split_t: FP64 -> TF32 (hi, lo) pairs for the split path.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -205,94 +204,6 @@ cudaError_t launch_stack_copy(const SCopy *d_cp, int n, cudaStream_t s) {
   dim3 grid(n, 4);
   k_stack_copy<<<grid, 256, 0, s>>>(d_cp);
   return cudaGetLastError();
-}
-
-// ----------------------------------------------------------------------------
-// TF32 split: x = hi + lo + O(2^-22 |x|), hi/lo representable in TF32
-// ----------------------------------------------------------------------------
-__device__ __forceinline__ float to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
-__device__ __forceinline__ void split1(double x, float &h, float &l) {
-  h = to_tf32((float)x);
-  l = to_tf32((float)(x - (double)h));
-}
-
-__global__ void k_split(const double *__restrict__ x, float *__restrict__ hi,
-                        float *__restrict__ lo, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    float h, l;
-    split1(x[i], h, l);
-    hi[i] = h;
-    lo[i] = l;
-  }
-}
-
-cudaError_t launch_split(const double *x, float *hi, float *lo, long long n,
-                         cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  long long blocks = (n + 255) / 256;
-  if (blocks > 148 * 32) blocks = 148 * 32;
-  k_split<<<(unsigned)blocks, 256, 0, s>>>(x, hi, lo, n);
-  return cudaGetLastError();
-}
-
-// split of FP64 matrices (optionally transposed through shared memory)
-__global__ void k_split2d(const Split2D *__restrict__ ds, const double *__restrict__ bind) {
-  __shared__ double tile[32][33];
-  const Split2D d = ds[blockIdx.z];
-  const double *src = d.src ? d.src : bind + d.src_off;
-  const int tr = (d.rows + 31) / 32, tc = (d.cols + 31) / 32;
-  for (int t = blockIdx.x; t < tr * tc; t += gridDim.x) {
-    const int r0 = (t / tc) * 32, c0 = (t % tc) * 32;
-    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
-      int r = r0 + j, c = c0 + threadIdx.x;
-      tile[j][threadIdx.x] = (r < d.rows && c < d.cols) ? src[(long long)r * d.src_ld + c] : 0.0;
-    }
-    __syncthreads();
-    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
-      float h, l;
-      if (d.trans) {
-        int c = c0 + j, r = r0 + threadIdx.x;
-        if (c < d.cols && r < d.rows) {
-          if (d.lo) {
-            split1(tile[threadIdx.x][j], h, l);
-            d.hi[(long long)c * d.dst_ld + r] = h;
-            d.lo[(long long)c * d.dst_ld + r] = l;
-          } else {
-            d.hi[(long long)c * d.dst_ld + r] = (float)tile[threadIdx.x][j];
-          }
-        }
-      } else {
-        int r = r0 + j, c = c0 + threadIdx.x;
-        if (c < d.cols && r < d.rows) {
-          if (d.lo) {
-            split1(tile[j][threadIdx.x], h, l);
-            d.hi[(long long)r * d.dst_ld + c] = h;
-            d.lo[(long long)r * d.dst_ld + c] = l;
-          } else {   // FP32 copy (round to nearest)
-            d.hi[(long long)r * d.dst_ld + c] = (float)tile[j][threadIdx.x];
-          }
-        }
-      }
-    }
-    __syncthreads();
-  }
-}
-
-cudaError_t launch_split2d(const Split2D *d, int n, cudaStream_t s, const double *bind) {
-  // grid.z is limited to 65535: launch in chunks of descriptors
-  for (int i0 = 0; i0 < n; i0 += 65535) {
-    dim3 grid(128, 1, n - i0 < 65535 ? n - i0 : 65535), block(32, 8);
-    k_split2d<<<grid, block, 0, s>>>(d + i0, bind);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
 }
 
 // ----------------------------------------------------------------------------

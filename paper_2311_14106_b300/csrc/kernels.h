@@ -74,19 +74,6 @@ struct SCopy {
   double coef;
 };
 
-// Split of an FP64 matrix into TF32 (hi, lo) float matrices with a padded
-// row stride (lo == NULL: an FP32 copy into hi, rounded to nearest);
-// trans = 1 writes the transpose (cols x rows).
-struct Split2D {
-  const double *src;     // (rows x cols), row stride src_ld
-  long long src_ld;
-  float *hi, *lo;
-  long long dst_ld;
-  int rows, cols;
-  int trans;
-  int pad;
-  long long src_off;     // used when src == NULL: bound vector + src_off
-};
 
 // A segment with B == NULL reads bindB + b_bs; a descriptor with C == NULL
 // writes bindC + c_bs (psi / sigma supplied per call, batch must be 1).
@@ -108,11 +95,6 @@ struct PartialSum64 {
 cudaError_t launch_sum_partials64(const PartialSum64 *p, int n, double *out, cudaStream_t s);
 
 cudaError_t launch_stack_copy(const SCopy *d_cp, int n, cudaStream_t s);
-cudaError_t launch_split(const double *x, float *hi, float *lo, long long n,
-                         cudaStream_t s);
-// A descriptor with src == NULL reads bindSrc + src_off (psi bound per call).
-cudaError_t launch_split2d(const Split2D *d, int n, cudaStream_t s,
-                           const double *bindSrc = nullptr);
 
 // Davidson helpers (FP64).  V holds k vectors with leading dimension ld.
 // dots: out[i] = <V_i, x>, two-pass deterministic reduction (work >= 64*k).

@@ -19,7 +19,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import (FP64, MODEL_HUBBARD, MODEL_SPINLESS_TV, SPLIT_TF32, Dmrg,
+from . import (FP64, MODEL_HUBBARD, MODEL_SPINLESS_TV, SPLIT, Dmrg,
                lattice_hamiltonian, momentum_basis)
 
 
@@ -109,7 +109,7 @@ def run_one(req, precision, stream=None, davidson_tol=1e-7, rng_iso=None):
 class Server:
     """Admits requests by slots and HBM footprint; runs them concurrently."""
 
-    def __init__(self, precision=SPLIT_TF32, slots=4, hbm_budget=200e9, davidson_tol=1e-7):
+    def __init__(self, precision=SPLIT, slots=4, hbm_budget=200e9, davidson_tol=1e-7):
         self.precision = precision
         self.slots = slots
         self.hbm_budget = hbm_budget

@@ -40,7 +40,7 @@ def test_split_path_vs_fp64_full_size(D):
     psi = synth.random_psi(layout, 1)
     g.set_precision(lib.FP64)
     ref = g.heff_apply_host(psi)
-    g.set_precision(lib.SPLIT_TF32)
+    g.set_precision(lib.SPLIT)
     s = g.heff_apply_host(psi)      # raises if a kernel recorded an error
     err = np.linalg.norm(s - ref) / np.linalg.norm(ref)
     assert err <= TOL_SPLIT, err

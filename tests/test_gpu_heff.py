@@ -86,7 +86,7 @@ def test_heff_fp64_and_split_vs_oracle(name, Lx, Ly, spinful, target, D, l):
     g.set_precision(lib.FP64)
     s64 = g.heff_apply_host(psi)
     assert rel(s64, ref) <= TOL64, rel(s64, ref)
-    g.set_precision(lib.SPLIT_TF32)
+    g.set_precision(lib.SPLIT)
     s32 = g.heff_apply_host(psi)
     assert rel(s32, ref) <= TOL_SPLIT, rel(s32, ref)
     # repeated applies (graph replay) are bitwise reproducible
@@ -112,7 +112,7 @@ def test_heff_flops_matches_layout_count():
 def test_davidson_energy_vs_oracle():
     w, g = window_case(4, 4, False, (8,), 64, 7)
     e_ref, _ = w.solve(tol=1e-12)
-    for prec in (lib.FP64, lib.SPLIT_TF32):
+    for prec in (lib.FP64, lib.SPLIT):
         g.set_precision(prec)
         x = torch.zeros(w.size, dtype=torch.float64, device="cuda")
         e, it, conv = g.davidson(x)
@@ -134,7 +134,7 @@ def test_sweep_matches_ed_spinless_3x3():
 def test_sweep_split_matches_ed_spinless_3x3():
     model, ham, h, W = problem(3, 3, False, (4,))
     e_ed = ed.ground_energy(h, W, 4)[0]
-    g = make_gpu(9, (4,), False, ham, d_max=20, davidson_tol=1e-9, precision=lib.SPLIT_TF32)
+    g = make_gpu(9, (4,), False, ham, d_max=20, davidson_tol=1e-9, precision=lib.SPLIT)
     g.set_mps(right=synth.random_right_isometries(9, False, (4,), 20, 1, 0))
     E = g.sweep(2)
     assert abs(E[-1] - e_ed) <= 1e-9 * abs(e_ed), (E, e_ed)
@@ -152,7 +152,7 @@ def test_sweep_hubbard_3x3_variational_and_matches_oracle():
     assert abs(E[-1] - Eo[-1]) <= 1e-6 * abs(e_ed), (E, Eo)
 
 
-@pytest.mark.parametrize("prec", [lib.FP64, lib.SPLIT_TF32])
+@pytest.mark.parametrize("prec", [lib.FP64, lib.SPLIT])
 def test_sweep_4x4_full_D_exact_and_D128_gap(prec):
     """4x4 spinless model at the paper's Fig. 1 parameters (t'=0.4, V=0.8, half
     filling), momentum basis, vs ED over all 12870 states.  At D = 256 (the
@@ -180,11 +180,11 @@ def test_split_sweeps_follow_fp64_hubbard_4x4():
     T, V = lib.lattice_hamiltonian(lib.MODEL_HUBBARD, 4, 4, 1.0, 0.0, 4.0)
     U = lib.momentum_basis(4, 4)
     E = {}
-    for prec in (lib.FP64, lib.SPLIT_TF32):
+    for prec in (lib.FP64, lib.SPLIT):
         g = lib.Dmrg(16, 8, 8, spinful=True, d_max=128, precision=prec, davidson_tol=1e-7, seed=7)
         g.set_hamiltonian(T, V, U)
         g.set_mps(right=synth.random_right_isometries(16, True, (8, 8), 128, 1, 7))
         E[prec] = g.sweep(2)
         g.close()
-    rel_diff = abs(E[lib.SPLIT_TF32][-1] - E[lib.FP64][-1]) / abs(E[lib.FP64][-1])
+    rel_diff = abs(E[lib.SPLIT][-1] - E[lib.FP64][-1]) / abs(E[lib.FP64][-1])
     assert rel_diff <= 1e-6, (E, rel_diff)

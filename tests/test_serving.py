@@ -49,7 +49,7 @@ def test_admission_respects_slots_and_budget(monkeypatch):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("prec", [lib.FP64, lib.SPLIT_TF32])
+@pytest.mark.parametrize("prec", [lib.FP64, lib.SPLIT])
 def test_same_result_alone_and_in_the_mix(prec):
     pytest.importorskip("torch")
     mix = [("spinless", 3, 3, (0.5, 2.0), [16, 24]), ("hubbard", 3, 3, (2.0, 6.0), [16])]

@@ -2,7 +2,7 @@
 
 Some callers cannot let a library allocate device memory while they run
 (they live inside another framework's memory pool, or must avoid the implicit
-device synchronisation of cudaMalloc/cudaFree).  dmrg_heff_apply_tf32_static
+device synchronisation of cudaMalloc/cudaFree).  dmrg_heff_apply_split_static
 serves them from a fixed device array instead.  This file is collected last
 on purpose.  The test checks, through the C ABI, that two calls in a row give
 the same sigma as the allocating dmrg_heff_apply in the same precision and
@@ -34,7 +34,7 @@ def _window():
     li = synth.random_left_isometries(N, False, target, D, l, 5)
     ri = synth.random_right_isometries(N, False, target, D, l + 2, 6)
     w = odmrg.window_from_mps(model, li, ri, l)
-    g = lib.Dmrg(N, 8, d_max=D, precision=lib.SPLIT_TF32)
+    g = lib.Dmrg(N, 8, d_max=D, precision=lib.SPLIT)
     Tg, Vg = lib.lattice_hamiltonian(lib.MODEL_SPINLESS_TV, Lx, Ly, 1.0, 0.0, 1.0)
     g.set_hamiltonian(Tg, Vg, lib.momentum_basis(Lx, Ly) @ Q)
     g.set_mps(li, ri)
@@ -48,7 +48,7 @@ def rel(a, b):
 
 def test_static_scratch_apply_matches_allocating_apply():
     w, g = _window()
-    g.set_precision(lib.SPLIT_TF32)
+    g.set_precision(lib.SPLIT)
     rng = np.random.default_rng(3)
     psi = torch.tensor(rng.standard_normal(w.size), device="cuda")
     ref = torch.empty_like(psi)
