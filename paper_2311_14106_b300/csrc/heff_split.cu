@@ -157,6 +157,20 @@ __device__ __forceinline__ void fence_async_shared() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// tcgen05.ld of 16 columns without the wait (issue several, then one wait)
+__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t *r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void st_shared_v4u(uint32_t a, uint32_t x, uint32_t y, uint32_t z,
                                               uint32_t w) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w)
@@ -172,16 +186,6 @@ __device__ __forceinline__ float pow2_scale(float m) {
   int x = 14 - e;
   x = x > 100 ? 100 : (x < -100 ? -100 : x);
   return ldexpf(1.f, x);
-}
-
-// x * s -> (hi, lo) halves with hi + lo = x * s to ~2^-22 relative
-__device__ __forceinline__ void split_h(float t, __half &h, __half &l) {
-  h = __float2half_rn(t);
-  l = __float2half_rn(t - __half2float(h));
-}
-
-__device__ __forceinline__ uint32_t pack_h2(__half a, __half b) {
-  return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
 }
 
 // Persistent, warp-specialised split GEMM.  Each CTA walks the work list
@@ -397,32 +401,37 @@ k_split_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict_
       }
       if (live && w.mode == TW_SPLIT) {
         for (int c0 = 0; c0 < w.ntile && w.n0 + c0 < w.N; c0 += 64) {
-          float v[64];
+          uint32_t v[64];
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             if (c0 + 16 * q < w.ntile) {
-              tmem_ld16(tbase + c0 + 16 * q, v + 16 * q);
+              tmem_ld16_nw(tbase + c0 + 16 * q, v + 16 * q);
             } else {
 #pragma unroll
-              for (int i = 0; i < 16; ++i) v[16 * q + i] = 0.f;
+              for (int i = 0; i < 16; ++i) v[16 * q + i] = 0u;
             }
+          }
+          tmem_ld_wait();
+          // split pairs of columns with packed conversions, then store once
+          // the previous box has left the staging buffer
+          uint32_t h[32], l[32];
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const float2 t = make_float2(fac * __uint_as_float(v[2 * i]),
+                                         fac * __uint_as_float(v[2 * i + 1]));
+            const __half2 h2 = __float22half2_rn(t);
+            const float2 hb = __half22float2(h2);
+            const __half2 l2 = __float22half2_rn(make_float2(t.x - hb.x, t.y - hb.y));
+            h[i] = *reinterpret_cast<const uint32_t *>(&h2);
+            l[i] = *reinterpret_cast<const uint32_t *>(&l2);
           }
           if (lane == 0) bulk_wait_read();
           __syncwarp();
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
-            uint32_t h[4], l[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              __half h0, l0, h1, l1;
-              split_h(fac * v[8 * q + 2 * i], h0, l0);
-              split_h(fac * v[8 * q + 2 * i + 1], h1, l1);
-              h[i] = pack_h2(h0, h1);
-              l[i] = pack_h2(l0, l1);
-            }
             const uint32_t o = rowoff + ((uint32_t)(q ^ (lane & 7)) << 4);
-            st_shared_v4u(stg + o, h[0], h[1], h[2], h[3]);
-            st_shared_v4u(stg2 + o, l[0], l[1], l[2], l[3]);
+            st_shared_v4u(stg + o, h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
+            st_shared_v4u(stg2 + o, l[4 * q], l[4 * q + 1], l[4 * q + 2], l[4 * q + 3]);
           }
           fence_async_shared();
           __syncwarp();
