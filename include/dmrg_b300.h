@@ -145,19 +145,20 @@ int dmrg_set_precision(dmrg_ctx *ctx, int precision);
 int dmrg_heff_apply(dmrg_ctx *ctx, const double *psi, double *sigma,
                     void *stream);
 
-/* Allocation-free variant of dmrg_heff_apply in the split 3xTF32 precision.
+/* Allocation-free variant of dmrg_heff_apply in the split precision
+ * (DMRG_SPLIT: FP16 hi + lo operands with per-block power-of-two scales).
  * The paper has no counterpart: this entry point exists for callers that
  * cannot let the library allocate device memory on the call path (for
  * example code running under another framework's memory pool, or code that
  * must not trigger the implicit synchronisation of cudaMalloc / cudaFree).
- * The per-call scratch of the split path (psi^T in FP32, the stage-1
+ * The per-call scratch of the split path (psi^T in FP16 hi + lo, the stage-1
  * intermediate, the stage-2 partial tiles and the work tables) is taken from
  * a fixed 64 MiB array that every GPU loading this library holds until the
  * process exits; the call itself makes no cudaMalloc, cudaFree or other
  * allocating device call.
  *   - psi, sigma: device pointers as for dmrg_heff_apply; sigma is
  *     overwritten.  The result equals dmrg_heff_apply's split result.
- *   - Needs the window's FP32 operator copies, which the first
+ *   - Needs the window's FP16 operator copies, which the first
  *     dmrg_heff_apply with DMRG_SPLIT creates (Errors: STATE if absent).
  *   - A window whose scratch exceeds 64 MiB is rejected with DMRG_ERR_ARG and
  *     a message giving the size it needs.
@@ -210,8 +211,8 @@ int dmrg_sweep(dmrg_ctx *ctx, int n_sweeps, const int *d_schedule,
 /* Work of the two H_eff*psi stages of the current window (for rooflines):
  * out6 = [stage-1 flops, stage-2 flops, A-stack elements, B-stack elements,
  * intermediate T elements, psi_len].  Stage 1 computes T = A psi per term
- * class, stage 2 sigma = sum T B^T; each stored element is 8 bytes (FP64, or
- * TF32 hi + lo). */
+ * class, stage 2 sigma = sum T B^T; a stored element is 8 bytes on the FP64
+ * path and 4 bytes (FP16 hi + lo) on the split path. */
 int dmrg_heff_stage_info(dmrg_ctx *ctx, double *out6);
 
 /* Per-kernel timing of dmrg_heff_apply with CUDA events recorded on the

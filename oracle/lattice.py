@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
-Conventions (readings of the paper, each listed in the design doc):
+Conventions (readings of the paper where it is ambiguous or garbled):
   * site index i = y * Lx + x on an Lx x Ly torus (periodic in both directions,
     Sec. II.A "torus geometry").
   * hopping enters as -t (c^+_i c_j + h.c.) per bond; Eq. 2 / Eq. 3 print +t,

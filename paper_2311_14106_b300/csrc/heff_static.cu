@@ -6,7 +6,7 @@
 // synchronise the device the way cudaMalloc/cudaFree can, or a process that
 // has handed all device memory to another allocator -- cannot let the library
 // allocate scratch for every call.  For them the scratch of the split path
-// (psi in TF32 hi/lo, the stage-1 intermediate, the stage-2 partial tiles and
+// (psi^T in FP16 hi/lo, the stage-1 intermediate, the stage-2 partial tiles and
 // the work tables) lives in this file-scope array instead.  Every GPU that
 // loads the library holds these bytes until the process exits.
 #include <cuda_runtime.h>

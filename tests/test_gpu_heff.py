@@ -6,10 +6,11 @@ else -- lattice Hamiltonian, momentum basis, rotation, block operators --
 with their own code.
 
 Tolerances
-  * FP64 path: relative 2-norm error of sigma <= 1e-12 (spec bound).
-  * split 3xTF32 path: relative 2-norm error of sigma <= 2e-5.  Operands
-    carry ~22 significant bits (hi + lo) and the accumulation is FP32, so
-    the expected error is a few 1e-7 times sqrt(K) for K up to ~1e3.
+  * FP64 path: relative 2-norm error of sigma <= 1e-12.
+  * split path (FP16 hi + lo with per-block power-of-two scales, three
+    products, FP32 accumulation): relative 2-norm error of sigma <= 2e-5.
+    Operands carry ~22 significant bits and the accumulation is FP32, so
+    the expected error is a few 1e-7 times sqrt(K) for K up to ~4e3.
 """
 import numpy as np
 import pytest

@@ -52,7 +52,7 @@ def test_static_scratch_apply_matches_allocating_apply():
     rng = np.random.default_rng(3)
     psi = torch.tensor(rng.standard_normal(w.size), device="cuda")
     ref = torch.empty_like(psi)
-    g.heff_apply(psi, ref)          # allocating entry point (also builds TF32 operator copies)
+    g.heff_apply(psi, ref)          # allocating entry point (also builds the FP16 operator copies)
     torch.cuda.synchronize()
     ref_h = ref.cpu().numpy()
     oracle = w.apply(psi.cpu().numpy())
