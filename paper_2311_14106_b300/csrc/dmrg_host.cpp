@@ -1417,7 +1417,7 @@ void split_tables(const Window &w, const SplitScratch &z, __half *Ph, __half *Pl
       for (int n0 = 0; n0 < N; n0 += nt) {
         TWork t;
         memset(&t, 0, sizeof t);
-        t.seg0 = seg; t.nseg = 1;
+        t.s = segs[seg];
         t.M = M; t.N = N; t.m0 = m0; t.n0 = n0; t.ntile = nt;
         t.mode = TW_SPLIT; t.alpha = alpha[i];
         t.fa = 1.f / w.sA[i];
@@ -1478,7 +1478,7 @@ void split_tables(const Window &w, const SplitScratch &z, __half *Ph, __half *Pl
         for (int n0 = 0; n0 < N; n0 += nt) {
           TWork t;
           memset(&t, 0, sizeof t);
-          t.seg0 = seg; t.nseg = 1;
+          t.s = segs[seg];
           t.M = M; t.N = N; t.m0 = m0; t.n0 = n0; t.ntile = nt;
           t.mode = TW_PARTIAL; t.alpha = 1.f;
           t.fa = 1.f / w.sB[rent[pi]];
@@ -1514,8 +1514,7 @@ void split_tables(const Window &w, const SplitScratch &z, __half *Ph, __half *Pl
       t.ppb[r] = E[pk[i].entry].pi;
       t.nchunk = std::max(t.nchunk, pk[i].nchunk);
     }
-    t.seg0 = t.pseg[0];
-    t.nseg = 1;
+    t.s = segs[t.pseg[0]];
     w2.push_back(t);
     i0 = i;
   }
@@ -1523,9 +1522,7 @@ void split_tables(const Window &w, const SplitScratch &z, __half *Ph, __half *Pl
   // x tile width), largest first
   auto cost = [&](const TWork &t) {
     if (t.R > 1) return (long long)t.nchunk * t.ntile;
-    long long k = 0;
-    for (int i = 0; i < t.nseg; ++i) k += (segs[t.seg0 + i].K + 63) / 64;
-    return k * t.ntile;
+    return (long long)((t.s.K + 63) / 64) * t.ntile;
   };
   // group by tile width (one launch per width class), largest cost first
   auto bucket = [](const TWork &t) { return t.ntile <= 32 ? 0 : (t.ntile <= 64 ? 1 : 2); };

@@ -35,6 +35,9 @@ constexpr int MAX_SMEM = 232448;  // 227 KB per CTA
 constexpr int NACC = 4;           // TMEM accumulators (4 x 128 columns)
 constexpr int STAGE_OUT = 4 * 8192;   // epilogue staging: 4 warps x (hi, lo) 32 x 64 halves
 constexpr long long WAIT_LIMIT = 1LL << 22;
+constexpr int ND = 8;             // work-item descriptor slots in shared memory
+constexpr int DPRE = 3;           // descriptors fetched ahead of the producer
+constexpr int DESC_BYTES = ND * (int)sizeof(TWork);
 
 // Pipeline geometry for a launch whose tiles are at most NT columns wide:
 // a stage holds A_hi, A_lo (128 x 64 halves each) and B_hi, B_lo (NT x 64).
@@ -42,11 +45,13 @@ template <int NT>
 struct Geo {
   static constexpr int TILE_B = NT * 128;
   static constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;
-  static constexpr int STAGES_RAW = (MAX_SMEM - 1024 - 512 - STAGE_OUT) / STAGE_BYTES;
+  static constexpr int STAGES_RAW =
+      (MAX_SMEM - 1024 - 512 - STAGE_OUT - DESC_BYTES) / STAGE_BYTES;
   static constexpr int STAGES = STAGES_RAW > 6 ? 6 : STAGES_RAW;
-  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 512 + STAGE_OUT;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 512 + STAGE_OUT + DESC_BYTES;
 };
 static_assert(Geo<128>::STAGES >= 3, "pipeline too shallow");
+static_assert(Geo<128>::SMEM_BYTES <= MAX_SMEM, "shared memory");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -156,6 +161,18 @@ __device__ __forceinline__ void bulk_wait_all() {
 __device__ __forceinline__ void fence_async_shared() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
+                                         uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(mbar)
+      : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
 
 // tcgen05.ld of 16 columns without the wait (issue several, then one wait)
 __device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t *r) {
@@ -190,14 +207,19 @@ __device__ __forceinline__ float pow2_scale(float m) {
 
 // Persistent, warp-specialised split GEMM.  Each CTA walks the work list
 // with stride gridDim.x (the list is sorted by cost, largest first):
-//   warp 0, lane 0   TMA producer over all K chunks of all its tiles
+//   warp 0, lane 0   TMA producer over all K chunks of all its tiles; it also
+//                    bulk-copies the work descriptors DPRE items ahead into a
+//                    ring of ND shared-memory slots, so no role waits on a
+//                    global load at a tile boundary
 //   warp 1, lane 0   MMA issuer, rotating over four TMEM accumulators
 //   warps 2..5       epilogue: drain an accumulator while the next tile runs
+// A descriptor slot is refilled after its six readers (producer, MMA issuer,
+// four epilogue warps) have copied it to registers.
 constexpr int NTHREADS = 192;
 constexpr int ACC_COLS = 128;
 
 struct Shared {
-  uint64_t full[8], empty[8], acc_full[NACC], acc_empty[NACC];
+  uint64_t full[8], empty[8], acc_full[NACC], acc_empty[NACC], dfull[ND], dempty[ND];
   uint32_t tmem;
   int abort;
 };
@@ -227,7 +249,8 @@ k_split_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict_
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t *stage_out = smem + STAGES * STAGE_BYTES;      // 1024-byte aligned
-  Shared *sh = (Shared *)(stage_out + STAGE_OUT);
+  TWork *desc = (TWork *)(stage_out + STAGE_OUT);         // ND slots, 16-byte aligned
+  Shared *sh = (Shared *)(stage_out + STAGE_OUT + DESC_BYTES);
   volatile int *abort_flag = &sh->abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -239,6 +262,10 @@ k_split_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict_
     for (int i = 0; i < NACC; ++i) {
       mbar_init(smem_u32(&sh->acc_full[i]), 1);
       mbar_init(smem_u32(&sh->acc_empty[i]), 128);
+    }
+    for (int i = 0; i < ND; ++i) {
+      mbar_init(smem_u32(&sh->dfull[i]), 1);
+      mbar_init(smem_u32(&sh->dempty[i]), 6);
     }
     sh->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -254,13 +281,35 @@ k_split_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict_
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = sh->tmem;
+  // this CTA's items: blockIdx.x + i * gridDim.x, i < nmine
+  const int nmine = (int)blockIdx.x < nwork ? (nwork - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer ----------------
+      auto fetch = [&](int i) -> bool {
+        const int sl = i % ND;
+        if (!wait_or_abort(smem_u32(&sh->dempty[sl]), ((i / ND) & 1) ^ 1, err, 5, abort_flag))
+          return false;
+        const uint32_t fb = smem_u32(&sh->dfull[sl]);
+        mbar_expect_tx(fb, (uint32_t)sizeof(TWork));
+        bulk_g2s(smem_u32(desc + sl), works + blockIdx.x + (size_t)i * gridDim.x,
+                 (uint32_t)sizeof(TWork), fb);
+        return true;
+      };
+      bool ok = true;
+      int nfetch = 0;
+      for (int i = 0; i < DPRE && i < nmine && ok; ++i) nfetch += (ok = fetch(i)) ? 1 : 0;
       int it = 0;
-      for (int t = blockIdx.x; t < nwork && !*abort_flag; t += gridDim.x) {
-        const TWork w = works[t];
+      for (int i = 0; i < nmine && ok && !*abort_flag; ++i) {
+        if (i + DPRE < nmine) {
+          if (!fetch(i + DPRE)) break;
+          ++nfetch;
+        }
+        const int sl = i % ND;
+        if (!wait_or_abort(smem_u32(&sh->dfull[sl]), (i / ND) & 1, err, 6, abort_flag)) break;
+        // read in place; the slot is released once this item's loads are issued
+        const TWork &w = desc[sl];
         const uint32_t stage_tx = 2 * TILE_A + 2 * (uint32_t)w.ntile * 128;
         if (w.R > 1) {
           // packed tile: per chunk, group r's rows of A and B from its own
@@ -286,45 +335,60 @@ k_split_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict_
               tma_load(smem_u32(base + 2 * TILE_A + TILE_B + r * gb), &maps[sg.mB_lo], kx, 0, fb);
             }
           }
+          mbar_arrive(smem_u32(&sh->dempty[sl]));
           continue;
         }
-        for (int s = 0; s < w.nseg && !*abort_flag; ++s) {
-          const TSeg sg = segs[w.seg0 + s];
-          const int nk = (sg.K + BK - 1) / BK;
-          for (int kc = 0; kc < nk; ++kc, ++it) {
-            const int st = it % STAGES;
-            const uint32_t ph = (it / STAGES) & 1;
-            if (!wait_or_abort(smem_u32(&sh->empty[st]), ph ^ 1, err, 1, abort_flag)) break;
-            uint8_t *base = smem + st * STAGE_BYTES;
-            const uint32_t fb = smem_u32(&sh->full[st]);
-            mbar_expect_tx(fb, stage_tx);
-            const int kx = sg.k0 + kc * BK;
-            tma_load(smem_u32(base), &maps[sg.mA_hi], kx, w.m0, fb);
-            tma_load(smem_u32(base + TILE_A), &maps[sg.mA_lo], kx, w.m0, fb);
-            tma_load(smem_u32(base + 2 * TILE_A), &maps[sg.mB_hi], kx, w.n0, fb);
-            tma_load(smem_u32(base + 2 * TILE_A + TILE_B), &maps[sg.mB_lo], kx, w.n0, fb);
-          }
+        const TSeg sg = w.s;
+        const int m0 = w.m0, n0 = w.n0;
+        mbar_arrive(smem_u32(&sh->dempty[sl]));
+        const int nk = (sg.K + BK - 1) / BK;
+        for (int kc = 0; kc < nk; ++kc, ++it) {
+          const int st = it % STAGES;
+          const uint32_t ph = (it / STAGES) & 1;
+          if (!wait_or_abort(smem_u32(&sh->empty[st]), ph ^ 1, err, 1, abort_flag)) break;
+          uint8_t *base = smem + st * STAGE_BYTES;
+          const uint32_t fb = smem_u32(&sh->full[st]);
+          mbar_expect_tx(fb, stage_tx);
+          const int kx = sg.k0 + kc * BK;
+          tma_load(smem_u32(base), &maps[sg.mA_hi], kx, m0, fb);
+          tma_load(smem_u32(base + TILE_A), &maps[sg.mA_lo], kx, m0, fb);
+          tma_load(smem_u32(base + 2 * TILE_A), &maps[sg.mB_hi], kx, n0, fb);
+          tma_load(smem_u32(base + 2 * TILE_A + TILE_B), &maps[sg.mB_lo], kx, n0, fb);
         }
+      }
+      if (*abort_flag) {
+        // a wait gave up somewhere: let this CTA's copies in flight land
+        // before it exits (bounded; a completed phase returns at once)
+        for (int c = it > STAGES ? it - STAGES : 0; c < it; ++c)
+          for (long long k = 0; k < WAIT_LIMIT && !mbar_try(smem_u32(&sh->full[c % STAGES]),
+                                                           (c / STAGES) & 1); ++k)
+            __nanosleep(64);
+        for (int i = nfetch > ND ? nfetch - ND : 0; i < nfetch; ++i)
+          for (long long k = 0; k < WAIT_LIMIT && !mbar_try(smem_u32(&sh->dfull[i % ND]),
+                                                           (i / ND) & 1); ++k)
+            __nanosleep(64);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer ----------------
-      int it = 0, j = 0;
-      for (int t = blockIdx.x; t < nwork && !*abort_flag; t += gridDim.x, ++j) {
-        const TWork w = works[t];
-        const uint32_t id = idesc_f16(w.ntile);
+      int it = 0;
+      for (int j = 0; j < nmine && !*abort_flag; ++j) {
+        const int sl = j % ND;
+        if (!wait_or_abort(smem_u32(&sh->dfull[sl]), (j / ND) & 1, err, 6, abort_flag)) break;
+        const int ntile = desc[sl].ntile;
+        // packed tiles run all their chunks without trimming (the groups'
+        // segments end at different K)
+        const int K = desc[sl].R > 1 ? desc[sl].nchunk * BK : desc[sl].s.K;
+        mbar_arrive(smem_u32(&sh->dempty[sl]));
+        const uint32_t id = idesc_f16(ntile);
         const int acc = j % NACC;
         const uint32_t aph = (j / NACC) & 1;
         if (!wait_or_abort(smem_u32(&sh->acc_empty[acc]), aph ^ 1, err, 2, abort_flag)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t d = tmem + acc * ACC_COLS;
         uint32_t accum = 0;
-        const int nseg = w.R > 1 ? 1 : w.nseg;
-        for (int s = 0; s < nseg; ++s) {
-          // packed tiles run all their chunks without trimming (the groups'
-          // segments end at different K)
-          const int K = w.R > 1 ? w.nchunk * BK : segs[w.seg0 + s].K;
+        {
           const int nk = (K + BK - 1) / BK;
           for (int kc = 0; kc < nk; ++kc, ++it) {
             const int st = it % STAGES;
@@ -370,41 +434,63 @@ k_split_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict_
     const int quarter = warp & 3;            // TMEM lanes 32*quarter .. +31
     const uint32_t stg = smem_u32(stage_out + (warp - 2) * 8192), stg2 = stg + 4096;
     const uint32_t rowoff = (uint32_t)lane * 128;
-    int j = 0;
-    for (int t = blockIdx.x; t < nwork; t += gridDim.x, ++j) {
-      const TWork w = works[t];
+    for (int j = 0; j < nmine; ++j) {
+      const int sl = j % ND;
+      if (!wait_or_abort(smem_u32(&sh->dfull[sl]), (j / ND) & 1, err, 6, abort_flag)) break;
+      // this warp's share of the item, read from the slot, then the slot is released
+      const TWork &d = desc[sl];
+      const int R = d.R, mode = d.mode, ntile = d.ntile, M = d.M, N = d.N, n0 = d.n0;
+      const int mOut_lo = d.mOut_lo;
+      int row0 = d.m0 + quarter * 32, cbeg = 0, cend = ntile, xoff = n0, mo = d.mOut_hi,
+          zo = d.zout;
+      bool live = row0 < M;
+      float fa = d.fa, rn = d.rn, alpha = d.alpha;
+      int pb = d.pblk;
+      if (R > 1) {
+        // destination of this warp's rows: the diagonal block of its group
+        const int per = 4 / R, r = quarter / per, gw = ntile / R;
+        row0 = (quarter % per) * 32;
+        cbeg = r * gw;
+        cend = cbeg + gw;
+        xoff = -cbeg;
+        mo = d.pout[r];
+        zo = d.pz[r];
+        live = d.pseg[r] >= 0;
+        fa = d.pfa[r];
+        rn = d.prn[r];
+        pb = live ? d.ppb[r] : 0;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&sh->dempty[sl]));
+      // scale statistics of the psi block: loaded before the accumulator wait
+      const PsiStat ps = pstat[pb];
       const int acc = j % NACC;
       const uint32_t aph = (j / NACC) & 1;
       if (!wait_or_abort(smem_u32(&sh->acc_full[acc]), aph, err, 4, abort_flag)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t tbase = tmem + acc * ACC_COLS + ((uint32_t)(quarter * 32) << 16);
-      int row0 = w.m0 + quarter * 32, cbeg = 0, cend = w.ntile, xoff = w.n0, mo = w.mOut_hi,
-          zo = w.zout;
-      bool live = row0 < w.M;
       float fac;
-      if (w.R > 1) {
-        // destination of this warp's rows: the diagonal block of its group
-        const int per = 4 / w.R, r = quarter / per, gw = w.ntile / w.R;
-        row0 = (quarter % per) * 32;
-        cbeg = r * gw;
-        cend = cbeg + gw;
-        xoff = -cbeg;
-        mo = w.pout[r];
-        zo = w.pz[r];
-        live = w.pseg[r] >= 0;
-        fac = live ? w.pfa[r] / pow2_scale(w.prn[r] * pstat[w.ppb[r]].cn) : 0.f;
-      } else if (w.mode == TW_SPLIT) {
-        const PsiStat ps = pstat[w.pblk];
-        fac = w.alpha * w.fa * pow2_scale(w.rn * ps.cn) / pow2_scale(ps.mx);
+      if (R > 1) {
+        fac = live ? fa / pow2_scale(rn * ps.cn) : 0.f;
+      } else if (mode == TW_SPLIT) {
+        fac = alpha * fa * pow2_scale(rn * ps.cn) / pow2_scale(ps.mx);
       } else {
-        fac = w.fa / pow2_scale(w.rn * pstat[w.pblk].cn);
+        fac = fa / pow2_scale(rn * ps.cn);
       }
-      if (live && w.mode == TW_SPLIT) {
-        for (int c0 = 0; c0 < w.ntile && w.n0 + c0 < w.N; c0 += 64) {
+      // the accumulator is handed back to the MMA issuer as soon as its last
+      // columns are in registers
+      bool released = false;
+      auto release = [&]() {
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(smem_u32(&sh->acc_empty[acc]));
+        released = true;
+      };
+      if (live && mode == TW_SPLIT) {
+        for (int c0 = 0; c0 < ntile && n0 + c0 < N; c0 += 64) {
           uint32_t v[64];
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            if (c0 + 16 * q < w.ntile) {
+            if (c0 + 16 * q < ntile) {
               tmem_ld16_nw(tbase + c0 + 16 * q, v + 16 * q);
             } else {
 #pragma unroll
@@ -412,6 +498,7 @@ k_split_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict_
             }
           }
           tmem_ld_wait();
+          if (!(c0 + 64 < ntile && n0 + c0 + 64 < N)) release();
           // split pairs of columns with packed conversions, then store once
           // the previous box has left the staging buffer
           uint32_t h[32], l[32];
@@ -436,21 +523,22 @@ k_split_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict_
           fence_async_shared();
           __syncwarp();
           if (lane == 0) {
-            tma_store3d(&maps[w.mOut_hi], w.n0 + c0, row0, 0, stg);
-            tma_store3d(&maps[w.mOut_lo], w.n0 + c0, row0, 0, stg2);
+            tma_store3d(&maps[mo], n0 + c0, row0, 0, stg);
+            tma_store3d(&maps[mOut_lo], n0 + c0, row0, 0, stg2);
             bulk_commit();
           }
         }
       } else if (live) {
-        for (int c0 = cbeg; c0 < cend && (w.R > 1 || w.n0 + c0 < w.N); c0 += 32) {
+        for (int c0 = cbeg; c0 < cend && (R > 1 || n0 + c0 < N); c0 += 32) {
           float v[32];
           tmem_ld16(tbase + c0, v);
-          if (c0 + 16 < w.ntile) {
+          if (c0 + 16 < ntile) {
             tmem_ld16(tbase + c0 + 16, v + 16);
           } else {
 #pragma unroll
             for (int i = 16; i < 32; ++i) v[i] = 0.f;
           }
+          if (!(c0 + 32 < cend && (R > 1 || n0 + c0 + 32 < N))) release();
           if (lane == 0) bulk_wait_read();
           __syncwarp();
 #pragma unroll
@@ -465,9 +553,7 @@ k_split_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict_
           }
         }
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&sh->acc_empty[acc]))
-                   : "memory");
+      if (!released) release();
     }
     if (lane == 0) bulk_wait_all();
     __syncwarp();

@@ -34,9 +34,11 @@ enum { TW_SPLIT = 0,      // stage 1: T = alpha * C, rescaled and split (hi, lo)
 
 // One 128 x ntile output tile.  The epilogue stores it by TMA through 3-D
 // tensor maps (x column, y row, z slot); the maps clip rows and columns
-// outside the destination.
+// outside the destination.  Each CTA copies its work items into shared
+// memory with bulk copies a few items ahead, so the size is a multiple of
+// 16 bytes.
 struct TWork {
-  int seg0, nseg;
+  TSeg s;            // the item's K range (packed tiles: that of group 0)
   int M, N;          // full problem extent (rows, columns)
   int m0, n0;        // tile origin
   int ntile;         // UMMA N of this tile (multiple of 16, <= 128)
@@ -56,7 +58,9 @@ struct TWork {
   int R, nchunk;
   int pseg[4], pout[4], pz[4], ppb[4];
   float pfa[4], prn[4];
+  int pad;
 };
+static_assert(sizeof(TWork) == 192, "TWork is copied in 16-byte units");
 
 // Sum of the split-K partial tiles of one sigma block (rows x cols, partial
 // rows ld floats apart, ld and stride multiples of 4, ws 16-byte aligned):
