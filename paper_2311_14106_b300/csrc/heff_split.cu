@@ -33,7 +33,7 @@ constexpr int BK = 64;            // halves per 128-byte swizzle row (one K chun
 constexpr int TILE_A = BM * 128;  // 16 KB
 constexpr int MAX_SMEM = 232448;  // 227 KB per CTA
 constexpr int NACC = 4;           // TMEM accumulators (4 x 128 columns)
-constexpr int STAGE_OUT = 4 * 8192;   // epilogue staging: 4 warps x (hi, lo) 32 x 64 halves
+constexpr int WARP_OUT = 8192;    // epilogue staging per warp: (hi, lo) 32 x 64 halves
 constexpr long long WAIT_LIMIT = 1LL << 22;
 constexpr int ND = 8;             // work-item descriptor slots in shared memory
 constexpr int DPRE = 3;           // descriptors fetched ahead of the producer
@@ -41,8 +41,14 @@ constexpr int DESC_BYTES = ND * (int)sizeof(TWork);
 
 // Pipeline geometry for a launch whose tiles are at most NT columns wide:
 // a stage holds A_hi, A_lo (128 x 64 halves each) and B_hi, B_lo (NT x 64).
+// Narrow tiles carry little work per tile, so their epilogue runs as two
+// groups of four warps that take alternate tiles; 128-wide tiles keep the
+// shared memory for a deeper operand ring and use one group.
 template <int NT>
 struct Geo {
+  static constexpr int EPI_GROUPS = NT <= 64 ? 2 : 1;
+  static constexpr int NTHREADS = 64 + 128 * EPI_GROUPS;
+  static constexpr int STAGE_OUT = 4 * EPI_GROUPS * WARP_OUT;
   static constexpr int TILE_B = NT * 128;
   static constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;
   static constexpr int STAGES_RAW =
@@ -51,7 +57,10 @@ struct Geo {
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 512 + STAGE_OUT + DESC_BYTES;
 };
 static_assert(Geo<128>::STAGES >= 3, "pipeline too shallow");
-static_assert(Geo<128>::SMEM_BYTES <= MAX_SMEM, "shared memory");
+static_assert(Geo<128>::SMEM_BYTES <= MAX_SMEM && Geo<64>::SMEM_BYTES <= MAX_SMEM &&
+                  Geo<32>::SMEM_BYTES <= MAX_SMEM,
+              "shared memory");
+static_assert(Geo<64>::STAGES >= 3 && Geo<32>::STAGES >= 4, "pipeline too shallow");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -212,10 +221,11 @@ __device__ __forceinline__ float pow2_scale(float m) {
 //                    ring of ND shared-memory slots, so no role waits on a
 //                    global load at a tile boundary
 //   warp 1, lane 0   MMA issuer, rotating over four TMEM accumulators
-//   warps 2..5       epilogue: drain an accumulator while the next tile runs
+//   warps 2..       epilogue: drain an accumulator while the next tile runs
+//                    (one or two groups of four warps; group g takes the
+//                    CTA's items g, g + groups, ...)
 // A descriptor slot is refilled after its six readers (producer, MMA issuer,
 // four epilogue warps) have copied it to registers.
-constexpr int NTHREADS = 192;
 constexpr int ACC_COLS = 128;
 
 struct Shared {
@@ -238,7 +248,7 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t a, uint32_t parity, int *
 }
 
 template <int NT>
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __launch_bounds__(Geo<NT>::NTHREADS, 1)
 k_split_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__ segs,
              const CUtensorMap *__restrict__ maps, const PsiStat *__restrict__ pstat,
              int *__restrict__ err) {
@@ -246,6 +256,8 @@ k_split_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict_
   constexpr int STAGES = G::STAGES;
   constexpr int STAGE_BYTES = G::STAGE_BYTES;
   constexpr int TILE_B = G::TILE_B;
+  constexpr int STAGE_OUT = G::STAGE_OUT;
+  constexpr int GROUPS = G::EPI_GROUPS;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t *stage_out = smem + STAGES * STAGE_BYTES;      // 1024-byte aligned
@@ -432,9 +444,10 @@ k_split_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict_
     //            into FP16 (hi, lo), 64 columns per box;
     //   stage 2: C / (sT sB) as FP32, 32 columns per box.
     const int quarter = warp & 3;            // TMEM lanes 32*quarter .. +31
-    const uint32_t stg = smem_u32(stage_out + (warp - 2) * 8192), stg2 = stg + 4096;
+    const int group = (warp - 2) >> 2;
+    const uint32_t stg = smem_u32(stage_out + (warp - 2) * WARP_OUT), stg2 = stg + WARP_OUT / 2;
     const uint32_t rowoff = (uint32_t)lane * 128;
-    for (int j = 0; j < nmine; ++j) {
+    for (int j = group; j < nmine; j += GROUPS) {
       const int sl = j % ND;
       if (!wait_or_abort(smem_u32(&sh->dfull[sl]), (j / ND) & 1, err, 6, abort_flag)) break;
       // this warp's share of the item, read from the slot, then the slot is released
@@ -798,7 +811,8 @@ cudaError_t launch_nt(const TWork *work, int nwork, const TSeg *seg, const CUten
   if (nwork <= 0) return cudaSuccess;
   const int nsm = sm_count();
   const int grid = nwork < nsm ? nwork : nsm;
-  k_split_gemm<NT><<<grid, NTHREADS, Geo<NT>::SMEM_BYTES, s>>>(work, nwork, seg, maps, pstat, err);
+  k_split_gemm<NT><<<grid, Geo<NT>::NTHREADS, Geo<NT>::SMEM_BYTES, s>>>(work, nwork, seg, maps,
+                                                                        pstat, err);
   return cudaGetLastError();
 }
 
