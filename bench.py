@@ -307,10 +307,12 @@ def main():
         serving_out = {"stream": "12 requests, exponential inter-arrival mean 0.1 s (seed 3); "
                                  "spinless 4x4 V~U[0,4] and Hubbard 4x4 U~U[0,8], D in {64,128}, "
                                  "2 sweeps each, 4 slots"}
-        # untimed warm-up: loads the solver and kernel modules once per process,
-        # so that neither arm pays it
+        # untimed warm-up with the stream's own shapes: loads the eigensolver and
+        # kernel modules (lazily, per kernel) once per process, so that neither
+        # arm pays it
         for prec in (lib.SPLIT, lib.FP64):
-            srvmod.run_one(srvmod.Request(-1, "spinless", 3, 3, 1.0, 16, 1, 0.0, seed=1), prec)
+            for model in ("spinless", "hubbard"):
+                srvmod.run_one(srvmod.Request(-1, model, 4, 4, 2.0, 128, 1, 0.0, seed=1), prec)
         for name, prec in (("split", lib.SPLIT), ("fp64", lib.FP64)):
             reqs = srvmod.poisson_stream(12, 0.1, 3, mix, sweeps=2)
             srv = srvmod.Server(precision=prec, slots=4, hbm_budget=200e9, davidson_tol=1e-7)

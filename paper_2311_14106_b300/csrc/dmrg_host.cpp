@@ -74,12 +74,19 @@ std::shared_mutex &capture_lock() {
   return mu;
 }
 
-// Device buffers that live for one H_eff window.
+// Device buffers that live together (one H_eff window, one block, one
+// call's work lists) and are released together.  Requests of up to 64 KB
+// (descriptor tables, small work lists: hundreds per window) are carved from
+// 1 MB chunks, so they cost no cudaMalloc / cudaFree of their own (cudaFree
+// synchronises the whole device, which stalls concurrent solves).  Every
+// returned pointer is 256-byte aligned, as cudaMalloc's are.
 struct WinBuf {
+  static constexpr size_t kChunk = 1 << 20, kSmall = 64 << 10;
   std::vector<void *> ptrs;
-  void *alloc(size_t bytes) {
+  char *cur = nullptr;   // free part of the current small-request chunk
+  size_t left = 0;
+  void *raw(size_t bytes) {
     void *p = nullptr;
-    if (bytes == 0) bytes = 8;
     std::shared_lock<std::shared_mutex> lk(capture_lock());
     if (cudaMalloc(&p, bytes) != cudaSuccess) {
       cudaGetLastError();
@@ -88,7 +95,21 @@ struct WinBuf {
     ptrs.push_back(p);
     return p;
   }
+  void *alloc(size_t bytes) {
+    bytes = (std::max<size_t>(bytes, 8) + 255) & ~(size_t)255;
+    if (bytes > kSmall) return raw(bytes);
+    if (bytes > left) {
+      cur = (char *)raw(kChunk);
+      left = kChunk;
+    }
+    void *p = cur;
+    cur += bytes;
+    left -= bytes;
+    return p;
+  }
   void clear() {
+    cur = nullptr;
+    left = 0;
     if (ptrs.empty()) return;
     std::shared_lock<std::shared_mutex> lk(capture_lock());
     for (void *p : ptrs) cudaFree(p);
