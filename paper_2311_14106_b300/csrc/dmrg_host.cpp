@@ -17,6 +17,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <set>
 #include <shared_mutex>
 #include <numeric>
 #include <string>
@@ -80,15 +81,41 @@ std::shared_mutex &capture_lock() {
 // 1 MB chunks, so they cost no cudaMalloc / cudaFree of their own (cudaFree
 // synchronises the whole device, which stalls concurrent solves).  Every
 // returned pointer is 256-byte aligned, as cudaMalloc's are.
+//
+// A buffer set bound to a stream (the temporaries of one call, all used on
+// that stream) allocates and frees stream-ordered from the device's memory
+// pool instead: no device-wide synchronisation, and the pool reuses the
+// memory once the stream has passed the free.
+void keep_pool_memory() {
+  // the pool keeps up to 8 GB of freed memory for reuse (a property of this
+  // process's pool object only)
+  static std::mutex mu;
+  static std::set<int> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!done.insert(dev).second) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = 8ull << 30;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+}
+
 struct WinBuf {
   static constexpr size_t kChunk = 1 << 20, kSmall = 64 << 10;
   std::vector<void *> ptrs;
   char *cur = nullptr;   // free part of the current small-request chunk
   size_t left = 0;
+  cudaStream_t st = nullptr;
+  bool ordered = false;  // stream-ordered (pool) allocation on st
+  WinBuf() = default;
+  explicit WinBuf(cudaStream_t s) : st(s), ordered(true) {}
   void *raw(size_t bytes) {
     void *p = nullptr;
     std::shared_lock<std::shared_mutex> lk(capture_lock());
-    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    if (ordered) keep_pool_memory();
+    if ((ordered ? cudaMallocAsync(&p, bytes, st) : cudaMalloc(&p, bytes)) != cudaSuccess) {
       cudaGetLastError();
       fail(DMRG_ERR_OOM, "cudaMalloc(%zu) failed", bytes);
     }
@@ -112,7 +139,12 @@ struct WinBuf {
     left = 0;
     if (ptrs.empty()) return;
     std::shared_lock<std::shared_mutex> lk(capture_lock());
-    for (void *p : ptrs) cudaFree(p);
+    for (void *p : ptrs) {
+      if (ordered)
+        cudaFreeAsync(p, st);
+      else
+        cudaFree(p);
+    }
     ptrs.clear();
   }
   ~WinBuf() { clear(); }
@@ -625,7 +657,7 @@ void enlarge(dmrg_ctx *C, const BlockPart &X, const SitePart &st, bool site_firs
       ptr[ci].push_back((int)all.size());
     }
   }
-  WinBuf tmp;   // work lists, released once the gather has run
+  WinBuf tmp(s);   // work lists, released once the gather has run
   GTerm *d_terms = upload(tmp, all, s);
   std::vector<int *> d_ptr(U.cls.size());
   for (size_t ci = 0; ci < U.cls.size(); ++ci) d_ptr[ci] = upload(tmp, ptr[ci], s);
@@ -713,7 +745,7 @@ void renormalize(dmrg_ctx *C, const BlockPart &U, const Iso &T, BlockPart &B, Wi
       tmp_total += (long long)ob.nops * U.basis.dim[u_of[ko]] * T.cols[ki];
     }
   }
-  WinBuf work;   // intermediate products and work lists of this call
+  WinBuf work(s);   // intermediate products and work lists of this call
   double *tmp = (double *)work.alloc(sizeof(double) * std::max<long long>(tmp_total, 1));
   long long t1 = 0, t2 = 0;
   for (const Job &j : jobs) {
@@ -810,7 +842,7 @@ void upload_iso(dmrg_ctx *C, Iso &T) {
 void grow_left(dmrg_ctx *C, int n, const Iso &T) {
   SitePart st = make_site(C, n - 1);
   BlockPart U;
-  WinBuf ub;
+  WinBuf ub(C->stream);
   enlarge(C, *C->L[n - 1], st, false, C->N - n, U, ub);
   std::unique_ptr<BlockPart> B(new BlockPart());
   renormalize(C, U, T, *B, buf_of(C, B.get()));
@@ -823,7 +855,7 @@ void grow_left(dmrg_ctx *C, int n, const Iso &T) {
 void grow_right(dmrg_ctx *C, int n, const Iso &T) {
   SitePart st = make_site(C, n);
   BlockPart U;
-  WinBuf ub;
+  WinBuf ub(C->stream);
   enlarge(C, *C->R[n + 1], st, true, n, U, ub);
   std::unique_ptr<BlockPart> B(new BlockPart());
   renormalize(C, U, T, *B, buf_of(C, B.get()));
@@ -980,7 +1012,7 @@ void build_window(dmrg_ctx *C, int l) {
     }
   }
   {
-    WinBuf tmp;
+    WinBuf tmp(s);
     SCopy *d = upload(tmp, cps, s);
     CK(launch_stack_copy(d, (int)cps.size(), s));
     CK(cudaStreamSynchronize(s));
@@ -1132,7 +1164,7 @@ void build_window(dmrg_ctx *C, int l) {
       }
     }
     if (!dd.empty()) {
-      WinBuf tmp;
+      WinBuf tmp(s);
       GemmDesc *a = upload(tmp, dd, s);
       GemmSeg *b = upload(tmp, gg, s);
       CK(launch_gemm_f64(a, (int)dd.size(), b, tt, s));
@@ -1271,7 +1303,7 @@ void split_operator_copies(dmrg_ctx *C) {
     sd[i].rowsB = (long long)q.db * n;
     sd[i].colsB = p.db;
   }
-  WinBuf tmp;
+  WinBuf tmp(s);
   EntryStat *dst = (EntryStat *)tmp.alloc(sizeof(EntryStat) * std::max<size_t>(ne, 1));
   CK(entry_stats(upload(tmp, sd, s), (int)ne, dst, s));
   std::vector<EntryStat> st(ne);
@@ -1587,7 +1619,7 @@ void build_split(dmrg_ctx *C) {
   P.err = (int *)w.buf.alloc(sizeof(int));
   CK(cudaMemsetAsync(P.err, 0, sizeof(int), s));
   if (tune) {
-    WinBuf tb;
+    WinBuf tb(s);
     double *x = (double *)tb.alloc(8 * std::max<long long>(w.psi_len, 1));
     double *y = (double *)tb.alloc(8 * std::max<long long>(w.psi_len, 1));
     CK(launch_random(x, w.psi_len, 12345, s));
@@ -2024,7 +2056,7 @@ void truncate(dmrg_ctx *C, const double *psi, int side, int D, double *disc, dou
       eoff[i] = eo;
       eo += npad[i];
     }
-  WinBuf tmp;
+  WinBuf tmp(s);
   double *rho = (double *)tmp.alloc(8 * std::max<long long>(tot, 1));
   double *eval = (double *)tmp.alloc(8 * std::max<long long>(eo, 1));
   CK(cudaMemsetAsync(rho, 0, 8 * std::max<long long>(tot, 1), s));
@@ -2263,7 +2295,7 @@ void push_gemm(std::vector<GemmDesc> &dd, std::vector<GemmSeg> &gg, long long &t
 
 void run_gemms(std::vector<GemmDesc> &dd, std::vector<GemmSeg> &gg, long long tt, cudaStream_t s) {
   if (dd.empty()) return;
-  WinBuf tmp;
+  WinBuf tmp(s);
   GemmDesc *a = upload(tmp, dd, s);
   GemmSeg *b = upload(tmp, gg, s);
   CK(launch_gemm_f64(a, (int)dd.size(), b, tt, s));
@@ -2279,7 +2311,7 @@ void stvec(dmrg_ctx *C, const WinMeta &old, const double *psi_old, int side, dou
   Window &w = C->win;
   double t0 = now();
   CK(cudaMemsetAsync(psi_new, 0, 8 * std::max<long long>(w.psi_len, 1), s));
-  WinBuf tmp;
+  WinBuf tmp(s);
   std::vector<GemmDesc> dd;
   std::vector<GemmSeg> gg;
   long long tt = 0;
@@ -2435,7 +2467,7 @@ void sweep_impl(dmrg_ctx *C, int nsw, const int *dsched, double *E, cudaStream_t
   C->Lmap.clear();
   C->Rmap.clear();
   for (int n = 2; n <= N - 1; ++n) C->Rmap[n] = C->riso[n];
-  WinBuf xb[2];
+  WinBuf xb[2] = {WinBuf(s), WinBuf(s)};
   int cur = 0;
   double *prev = nullptr;
   WinMeta pm;
