@@ -1850,9 +1850,15 @@ void dots(dmrg_ctx *C, const double *V, int k, long long n, const double *x, Dav
   CK(cudaStreamSynchronize(s));
 }
 
-// out = a*out + sum c_i V_i
+// out = a*out + sum c_i V_i (coefficients by value: no copy, no host wait)
 void lincomb(double *out, const double *V, const std::vector<double> &c, double a, long long n,
              DavBuf &B, cudaStream_t s) {
+  if (c.size() <= (size_t)kLincombMax) {
+    LincombCoef h;
+    for (size_t i = 0; i < c.size(); ++i) h.c[i] = c[i];
+    CK(launch_lincomb_v(out, V, (int)c.size(), n, h, a, n, s));
+    return;
+  }
   std::vector<double> h(c);
   h.push_back(a);
   CK(cudaMemcpyAsync(B.coef, h.data(), 8 * h.size(), cudaMemcpyHostToDevice, s));
@@ -1981,11 +1987,10 @@ int davidson(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_t s,
     // (a caller's start vector, e.g. the StVec guess of a sweep, is already
     // close to the ground state and is preconditioned from the first step)
     if (!random_start || it >= kKrylovWarmup) CK(launch_precond(B.t, w.diag, th, n, s));
+    // classical Gram-Schmidt, twice: t -= V (V^T t), coefficients kept on the device
     for (int pass = 0; pass < 2; ++pass) {
-      std::vector<double> c;
-      dots(C, B.V, k, n, B.t, B, c, s);
-      for (auto &v : c) v = -v;
-      lincomb(B.t, B.V, c, 1.0, n, B, s);
+      CK(launch_dots(B.V, k, n, B.t, n, B.work, B.dots, s));
+      CK(launch_lincomb_d(B.t, B.V, k, n, B.dots, -1.0, 1.0, n, s));
     }
     double nt = std::sqrt(std::max(0.0, dot1(C, B.t, B.t, n, B, s)));
     if (!(nt > 1e-14)) {

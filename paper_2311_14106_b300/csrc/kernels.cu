@@ -279,6 +279,47 @@ cudaError_t launch_lincomb(double *out, const double *V, int k, long long ld,
   return cudaGetLastError();
 }
 
+__global__ void k_lincomb_v(double *__restrict__ out, const double *__restrict__ V, int k,
+                            long long ld, const __grid_constant__ LincombCoef c, double a,
+                            long long n) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+       j += (long long)gridDim.x * blockDim.x) {
+    double v = (a != 0.0) ? a * out[j] : 0.0;
+    for (int i = 0; i < k; ++i) v = fma(c.c[i], V[i * ld + j], v);
+    out[j] = v;
+  }
+}
+
+cudaError_t launch_lincomb_v(double *out, const double *V, int k, long long ld,
+                             const LincombCoef &c, double a, long long n, cudaStream_t s) {
+  if (k < 0 || k > kLincombMax) return cudaErrorInvalidValue;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 148 * 16) blocks = 148 * 16;
+  if (blocks < 1) blocks = 1;
+  k_lincomb_v<<<(unsigned)blocks, 256, 0, s>>>(out, V, k, ld, c, a, n);
+  return cudaGetLastError();
+}
+
+__global__ void k_lincomb_d(double *__restrict__ out, const double *__restrict__ V, int k,
+                            long long ld, const double *__restrict__ c, double cs, double a,
+                            long long n) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+       j += (long long)gridDim.x * blockDim.x) {
+    double v = (a != 0.0) ? a * out[j] : 0.0;
+    for (int i = 0; i < k; ++i) v = fma(cs * c[i], V[i * ld + j], v);
+    out[j] = v;
+  }
+}
+
+cudaError_t launch_lincomb_d(double *out, const double *V, int k, long long ld,
+                             const double *c, double cs, double a, long long n, cudaStream_t s) {
+  long long blocks = (n + 255) / 256;
+  if (blocks > 148 * 16) blocks = 148 * 16;
+  if (blocks < 1) blocks = 1;
+  k_lincomb_d<<<(unsigned)blocks, 256, 0, s>>>(out, V, k, ld, c, cs, a, n);
+  return cudaGetLastError();
+}
+
 __global__ void k_precond(double *__restrict__ r, const double *__restrict__ diag,
                           const double *__restrict__ theta, long long n) {
   const double th = *theta;

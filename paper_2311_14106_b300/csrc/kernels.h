@@ -105,6 +105,18 @@ cudaError_t launch_dots(const double *V, int k, long long ld,
 cudaError_t launch_lincomb(double *out, const double *V, int k, long long ld,
                            const double *coef, const double *a, long long n,
                            cudaStream_t s);
+// The same with the coefficients passed by value (k <= kLincombMax): no copy
+// to the device and nothing for the host to wait on.
+constexpr int kLincombMax = 64;
+struct LincombCoef {
+  double c[kLincombMax];
+};
+cudaError_t launch_lincomb_v(double *out, const double *V, int k, long long ld,
+                             const LincombCoef &c, double a, long long n, cudaStream_t s);
+// out = a * out + cs * sum_i c[i] V_i with c on the device (e.g. the result of
+// launch_dots, cs = -1 for a projection step)
+cudaError_t launch_lincomb_d(double *out, const double *V, int k, long long ld,
+                             const double *c, double cs, double a, long long n, cudaStream_t s);
 // r = (r) / (diag - theta) with clamping; diag may be NULL (no-op scale 1)
 cudaError_t launch_precond(double *r, const double *diag, const double *theta,
                            long long n, cudaStream_t s);
