@@ -1869,8 +1869,10 @@ void lincomb(double *out, const double *V, const std::vector<double> &c, double 
 constexpr double kSplitResidualFloor = 4e-6;
 constexpr int kKrylovWarmup = 12;
 
+// patience: split path only, iterations without halving the best residual
+// before a residual near the noise floor is accepted
 int davidson(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_t s,
-             bool fp64_rq = true) {
+             bool fp64_rq = true, int patience = 16) {
   Window &w = C->win;
   const long long n = w.psi_len;
   const int m = std::max(4, std::min(C->cfg.davidson_max_sub, 64));
@@ -1941,11 +1943,12 @@ int davidson(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_t s,
       break;
     }
     // stagnation near the split product's noise floor: stop if the best
-    // residual has not halved over the last 16 iterations
+    // residual has not halved over the last `patience` iterations
     if (rnorm < 0.5 * best_r) {
       best_r = rnorm;
       best_it = it;
-    } else if (prec == DMRG_SPLIT && it - best_it >= 16 && rnorm < 10.0 * std::max(tol, floor)) {
+    } else if (prec == DMRG_SPLIT && it - best_it >= patience &&
+               rnorm < 10.0 * std::max(tol, floor)) {
       conv = true;
       break;
     }
@@ -2479,6 +2482,7 @@ void sweep_impl(dmrg_ctx *C, int nsw, const int *dsched, double *E, cudaStream_t
   int prev_trunc = -1;   // -1 none, 0 left, 1 right, 2 same window follows
   double e = 0;
   int it;
+  int patience = 16;
   auto step = [&](int l, int trunc_side, int D, bool last) {
     build_window(C, l);
     const long long n = C->win.psi_len;
@@ -2492,7 +2496,7 @@ void sweep_impl(dmrg_ctx *C, int nsw, const int *dsched, double *E, cudaStream_t
       CK(cudaMemsetAsync(x, 0, 8 * std::max<long long>(n, 1), s));
     }
     // the FP64 Rayleigh quotient is only needed for the reported energy
-    int rc = davidson(C, x, &e, &it, s, last);
+    int rc = davidson(C, x, &e, &it, s, last, patience);
     (void)rc;
     pm = meta_of(C->win);
     if (trunc_side >= 0) truncate(C, x, trunc_side, D, nullptr, nullptr, s);
@@ -2502,6 +2506,10 @@ void sweep_impl(dmrg_ctx *C, int nsw, const int *dsched, double *E, cudaStream_t
   };
   for (int sw = 0; sw < nsw; ++sw) {
     const int D = dsched ? dsched[sw] : C->cfg.d_max;
+    // the first sweep starts from a random MPS: an excited state of an early
+    // window can reach the noise floor before the ground state shows up, so
+    // the split Davidson waits longer there before it accepts stagnation
+    patience = sw == 0 ? 16 : 4;
     for (int l = 0; l <= N - 2; ++l) step(l, l < N - 2 ? 0 : -1, D, false);
     for (int l = N - 2; l >= 0; --l) step(l, l > 0 ? 1 : -1, D, l == 0);
     if (E) E[sw] = e;
