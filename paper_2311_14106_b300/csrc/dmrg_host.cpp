@@ -102,6 +102,24 @@ void keep_pool_memory() {
   }
 }
 
+// Stream on which long-lived buffers are taken from and returned to the pool
+// (one per device, non-blocking).  An allocation is synchronised before use,
+// and the buffers' last users have finished when they are released (the
+// calls that use them end with a stream synchronisation), so neither needs
+// ordering against the callers' streams.
+// (Never throws: it also runs in destructors; the legacy stream stands in if
+// no stream can be made.)
+cudaStream_t release_stream() {
+  static std::mutex mu;
+  static std::map<int, cudaStream_t> streams;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  cudaStream_t &r = streams[dev];
+  if (!r && cudaStreamCreateWithFlags(&r, cudaStreamNonBlocking) != cudaSuccess) r = nullptr;
+  return r;
+}
+
 struct WinBuf {
   static constexpr size_t kChunk = 1 << 20, kSmall = 64 << 10;
   std::vector<void *> ptrs;
@@ -109,16 +127,26 @@ struct WinBuf {
   size_t left = 0;
   cudaStream_t st = nullptr;
   bool ordered = false;  // stream-ordered (pool) allocation on st
+  bool lasting = false;  // pool allocation on release_stream() (long-lived buffers)
   WinBuf() = default;
   explicit WinBuf(cudaStream_t s) : st(s), ordered(true) {}
+  // long-lived buffers, released without a device synchronisation
+  static WinBuf lasting_buf() {
+    WinBuf b;
+    b.ordered = true;
+    b.lasting = true;
+    return b;
+  }
   void *raw(size_t bytes) {
     void *p = nullptr;
     std::shared_lock<std::shared_mutex> lk(capture_lock());
     if (ordered) keep_pool_memory();
-    if ((ordered ? cudaMallocAsync(&p, bytes, st) : cudaMalloc(&p, bytes)) != cudaSuccess) {
+    const cudaStream_t as = lasting ? release_stream() : st;
+    if ((ordered ? cudaMallocAsync(&p, bytes, as) : cudaMalloc(&p, bytes)) != cudaSuccess) {
       cudaGetLastError();
       fail(DMRG_ERR_OOM, "cudaMalloc(%zu) failed", bytes);
     }
+    if (lasting) CK(cudaStreamSynchronize(as));   // usable on any stream from here
     ptrs.push_back(p);
     return p;
   }
@@ -139,9 +167,10 @@ struct WinBuf {
     left = 0;
     if (ptrs.empty()) return;
     std::shared_lock<std::shared_mutex> lk(capture_lock());
+    const cudaStream_t fs = lasting ? release_stream() : st;
     for (void *p : ptrs) {
       if (ordered)
-        cudaFreeAsync(p, st);
+        cudaFreeAsync(p, fs);
       else
         cudaFree(p);
     }
@@ -194,12 +223,16 @@ struct Window {
   bool valid = false;
   int l = -1;
   BlockPart Ld, Rd;
-  WinBuf ldbuf, rdbuf;
+  // window buffers are released without a device synchronisation: after the
+  // last H_eff*psi enqueued through the public entry points (use_ev)
+  WinBuf ldbuf = WinBuf::lasting_buf(), rdbuf = WinBuf::lasting_buf();
+  cudaEvent_t use_ev = nullptr;
+  bool used = false;
   std::vector<PsiBlk> psi;
   long long psi_len = 0;
   std::vector<int> a2psi;
   std::vector<HClass> hc;
-  WinBuf buf;            // stacks, T, descriptors
+  WinBuf buf = WinBuf::lasting_buf();   // stacks, T, descriptors
   double *Astack = nullptr, *Bstack = nullptr, *T = nullptr;
   long long nA = 0, nB = 0, nT = 0;
   GemmDesc *d1 = nullptr, *d2 = nullptr;
@@ -594,7 +627,14 @@ void enlarge(dmrg_ctx *C, const BlockPart &X, const SitePart &st, bool site_firs
   // per class, per op: terms
   std::vector<std::vector<std::vector<GTerm>>> terms(U.cls.size());
   for (size_t ci = 0; ci < U.cls.size(); ++ci) terms[ci].resize(U.cls[ci].nops);
-  std::map<std::tuple<int, int, int>, int> keyidx;
+  // The terms of one enlarged operator are accumulated per source operator
+  // of X (class, index, transposed) or X's identity.  A dense slot table over
+  // X's operators finds a term in O(1); the terms are emitted in key order.
+  std::vector<long long> cls_base(X.cls.size() + 1, 0);
+  for (size_t c = 0; c < X.cls.size(); ++c) cls_base[c + 1] = cls_base[c] + X.cls[c].nops;
+  std::vector<int> slot(1 + 2 * (size_t)cls_base.back(), -1);
+  std::vector<GTerm> accv;
+  std::vector<std::pair<std::tuple<int, int, int>, int>> touched;   // (key, slot table index)
   for (size_t k = 0; k < specs.size(); ++k) {
     const OpSpec &sp = specs[k];
     Ref r;
@@ -608,7 +648,8 @@ void enlarge(dmrg_ctx *C, const BlockPart &X, const SitePart &st, bool site_firs
       default: r = U.Q[{sp.i, sp.j}]; break;
     }
     if (r.cls < 0) continue;
-    std::map<std::tuple<int, int, int>, GTerm> acc;
+    accv.clear();
+    touched.clear();
     AddFn add = [&](const Fac &A, const Fac &B, double coef) {
       if (A.kind == 0 || B.kind == 0) return;
       const Fac &Xf = block_first ? A : B;
@@ -619,17 +660,26 @@ void enlarge(dmrg_ctx *C, const BlockPart &X, const SitePart &st, bool site_firs
       double c = coef * A.scale * B.scale;
       std::tuple<int, int, int> key = Xf.kind == 2 ? std::make_tuple(-1, 0, 0)
                                                    : std::make_tuple(Xf.ref.cls, Xf.ref.idx, Xf.trans);
-      auto it = acc.find(key);
-      if (it == acc.end()) {
+      size_t si = 0;
+      if (Xf.kind != 2) {
+        if (Xf.ref.cls < 0 || Xf.ref.cls >= (int)X.cls.size() || Xf.ref.idx < 0 ||
+            Xf.ref.idx >= X.cls[Xf.ref.cls].nops || (Xf.trans != 0 && Xf.trans != 1))
+          fail(DMRG_ERR_STATE, "internal: bad source operator in enlarged term");
+        si = 1 + 2 * (size_t)(cls_base[Xf.ref.cls] + Xf.ref.idx) + (size_t)Xf.trans;
+      }
+      if (slot[si] < 0) {
         GTerm t;
         memset(&t, 0, sizeof t);
         t.src = std::get<0>(key);
         t.idx = std::get<1>(key);
         t.trans = std::get<2>(key);
         t.p2 = B.parity;
-        it = acc.emplace(key, t).first;
+        slot[si] = (int)accv.size();
+        accv.push_back(t);
+        touched.push_back({key, (int)si});
       }
-      for (int e = 0; e < 16; ++e) it->second.m[e] += c * Sf.so.m[e];
+      GTerm &g = accv[slot[si]];
+      for (int e = 0; e < 16; ++e) g.m[e] += c * Sf.so.m[e];
     };
     switch (sp.kind) {
       case 0: formula_H(F, G, add, true); break;
@@ -641,10 +691,13 @@ void enlarge(dmrg_ctx *C, const BlockPart &X, const SitePart &st, bool site_firs
       default: formula_Q(F, G, sp.i, sp.j, C->W.data(), C->M, add); break;
     }
     auto &dst = terms[r.cls][r.idx];
-    for (auto &kv : acc) {
+    std::sort(touched.begin(), touched.end());
+    for (auto &kv : touched) {
+      const GTerm &g = accv[slot[kv.second]];
+      slot[kv.second] = -1;
       bool nz = false;
-      for (int e = 0; e < 16; ++e) nz |= kv.second.m[e] != 0.0;
-      if (nz) dst.push_back(kv.second);
+      for (int e = 0; e < 16; ++e) nz |= g.m[e] != 0.0;
+      if (nz) dst.push_back(g);
     }
   }
   // flatten terms, CSR per class
@@ -818,7 +871,7 @@ void free_part(dmrg_ctx *C, BlockPart *B) {
 
 WinBuf &buf_of(dmrg_ctx *C, BlockPart *B) {
   auto &p = C->partbuf[B];
-  if (!p) p.reset(new WinBuf());
+  if (!p) p.reset(new WinBuf(WinBuf::lasting_buf()));
   return *p;
 }
 
@@ -893,10 +946,26 @@ void block_src(const BlockPart &P, const Fac &f, int in_sec, int out_sec, SCopy 
   }
 }
 
+// the window's buffers are freed on the release stream: make it wait for the
+// last H_eff*psi that callers enqueued on their own streams
+void release_after_use(Window &w) {
+  if (w.used) cudaStreamWaitEvent(release_stream(), w.use_ev, 0);
+  w.used = false;
+}
+
+// after a public H_eff*psi call on stream s (the event exists once a window
+// has been built, so recording it allocates nothing)
+void note_use(Window &w, cudaStream_t s) {
+  CK(cudaEventRecord(w.use_ev, s));
+  w.used = true;
+}
+
 void build_window(dmrg_ctx *C, int l) {
   Window &w = C->win;
   cudaStream_t s = C->stream;
   w.valid = false;
+  release_after_use(w);
+  if (!w.use_ev) CK(cudaEventCreateWithFlags(&w.use_ev, cudaEventDisableTiming));
   w.buf.clear();
   w.ldbuf.clear();
   w.rdbuf.clear();
@@ -1823,6 +1892,7 @@ struct DavBuf {
 DavBuf dav_buffers(dmrg_ctx *C, long long n, int m) {
   if (C->dav_n != n || !C->V) {
     C->dav.clear();
+    C->dav = WinBuf::lasting_buf();
     C->V = (double *)C->dav.alloc(8 * (size_t)n * m);
     C->AV = (double *)C->dav.alloc(8 * (size_t)n * m);
     C->r = (double *)C->dav.alloc(8 * (size_t)n * 2);
@@ -2568,6 +2638,7 @@ int dmrg_destroy(dmrg_ctx *ctx) {
   if (ctx->cap_stream) cudaStreamSynchronize(ctx->cap_stream);
   for (auto &g : ctx->win.graphs) cudaGraphExecDestroy(g.second);
   ctx->win.graphs.clear();
+  release_after_use(ctx->win);
   ctx->win.buf.clear();
   ctx->win.ldbuf.clear();
   ctx->win.rdbuf.clear();
@@ -2580,6 +2651,7 @@ int dmrg_destroy(dmrg_ctx *ctx) {
   for (auto &e : ctx->ev)
     if (e) cudaEventDestroy(e);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->win.use_ev) cudaEventDestroy(ctx->win.use_ev);
   delete ctx;
   return DMRG_OK;
 }
@@ -2812,7 +2884,10 @@ int dmrg_heff_apply(dmrg_ctx *C, const double *psi, double *sigma, void *stream)
     C->err = "no window built";
     return DMRG_ERR_STATE;
   }
-  return guard(C, [&] { apply(C, psi, sigma, (cudaStream_t)stream, C->precision); });
+  return guard(C, [&] {
+    apply(C, psi, sigma, (cudaStream_t)stream, C->precision);
+    note_use(C->win, (cudaStream_t)stream);
+  });
 }
 
 int dmrg_heff_apply_host(dmrg_ctx *C, const double *psi_h, double *sigma_h, void *stream) {
@@ -2923,6 +2998,7 @@ int dmrg_heff_apply_split_static(dmrg_ctx *C, const double *psi, double *sigma, 
     CK(split_gemm((const TWork *)(b + ow.o_w2), t.n2, (const TSeg *)(b + ow.o_seg),
                   (const CUtensorMap *)(b + ow.o_maps), pst, err, s));
     CK(sum_partials((const PartialSum *)(b + ow.o_ps), (int)t.psums.size(), sigma, s));
+    note_use(w, s);
   });
 }
 
