@@ -189,3 +189,32 @@ def test_split_sweeps_follow_fp64_hubbard_4x4():
         g.close()
     rel_diff = abs(E[lib.SPLIT][-1] - E[lib.FP64][-1]) / abs(E[lib.FP64][-1])
     assert rel_diff <= 1e-6, (E, rel_diff)
+
+
+@pytest.mark.parametrize("prec", [lib.FP64, lib.SPLIT])
+def test_window_rebuild_while_apply_in_flight(prec):
+    """The window is rebuilt (new couplings, same sizes) while an H_eff*psi
+    enqueued on another stream has not started yet.  The old window's
+    buffers go back to the memory pool without a device synchronisation, but
+    only after that apply, so it still computes the old operator exactly."""
+    w, g = window_case(4, 4, False, (8,), 64, 7)
+    g.set_precision(prec)
+    psi = torch.tensor(np.random.default_rng(3).standard_normal(w.size), device="cuda")
+    ref = torch.empty_like(psi)
+    g.heff_apply(psi, ref)
+    torch.cuda.synchronize()
+    side, other = torch.cuda.Stream(), torch.cuda.Stream()
+    sig = torch.zeros_like(psi)
+    with torch.cuda.stream(side):
+        torch.cuda._sleep(200_000_000)   # about 0.1 s: the apply below waits behind it
+    g.heff_apply(psi, sig, stream=side)
+    _, ham, _, _ = problem(4, 4, False, (8,), V=2.5)
+    g.set_hamiltonian(*ham)
+    g.build_block_ops(7, stream=other)
+    side.synchronize()
+    assert torch.equal(sig, ref)
+    new = torch.empty_like(psi)
+    g.heff_apply(psi, new, stream=other)
+    other.synchronize()
+    assert rel(new.cpu().numpy(), ref.cpu().numpy()) > 1e-3
+    g.close()
