@@ -247,6 +247,16 @@ int dmrg_heff_split_plan(dmrg_ctx *ctx, double *out4);
  * graph per (psi, sigma) pointer pair; 0 launches the kernels directly. */
 int dmrg_set_graphs(dmrg_ctx *ctx, int enable);
 
+/* Self-test of the tcgen05 kernels' bounded waits (no counterpart in the
+ * paper): one device thread waits on a shared-memory barrier that nothing
+ * completes, with the same wait the H_eff*psi kernels use.  The wait gives up
+ * after about one second (2^31 SM cycles) and reports it; nothing faults and
+ * the context stays usable.  stream: CUDA stream or NULL.  Returns
+ * DMRG_ERR_TIMEOUT when the wait gave up as designed (the expected result),
+ * DMRG_ERR_CUDA if it did not or a CUDA call failed, DMRG_ERR_OOM if the
+ * 4-byte flag could not be allocated. */
+int dmrg_selftest_bounded_wait(void *stream);
+
 /* Timing breakdown of the last sweep in seconds, Sec. III.B categories:
  * out[0] Diag_H, [1] Ren (block ops), [2] Tables, [3] Diag_D, [4] StVec,
  * [5] Other; out[6] = number of H_eff*psi calls. */

@@ -30,7 +30,7 @@ HEADER_FUNCTIONS = [
     "dmrg_heff_flops", "dmrg_davidson", "dmrg_truncate", "dmrg_sweep",
     "dmrg_heff_stage_info", "dmrg_heff_timing", "dmrg_profile",
     "dmrg_heff_apply_split_static", "dmrg_heff_tuning", "dmrg_set_graphs",
-    "dmrg_heff_split_plan", "dmrg_heff_entries",
+    "dmrg_heff_split_plan", "dmrg_heff_entries", "dmrg_selftest_bounded_wait",
 ]
 
 
@@ -76,6 +76,7 @@ _sig = {
     "dmrg_set_graphs": (ctypes.c_int, [_P, ctypes.c_int]),
     "dmrg_heff_split_plan": (ctypes.c_int, [_P, _D]),
     "dmrg_heff_entries": (ctypes.c_int, [_P, _I, ctypes.c_int, _I]),
+    "dmrg_selftest_bounded_wait": (ctypes.c_int, [_P]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -111,6 +112,12 @@ def _tensor_ptr(t):
             raise ValueError("expected a contiguous float64 CUDA tensor")
         return t.data_ptr()
     return int(t)
+
+
+def selftest_bounded_wait(stream=None):
+    """Status of the bounded-wait self-test (ERR_TIMEOUT is the expected,
+    passing result: the device wait gave up after about a second)."""
+    return _lib.dmrg_selftest_bounded_wait(_stream_ptr(stream))
 
 
 def lattice_hamiltonian(model, Lx, Ly, t=1.0, tp=0.0, v=1.0):

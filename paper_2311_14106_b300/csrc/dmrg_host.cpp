@@ -3002,6 +3002,25 @@ int dmrg_heff_apply_split_static(dmrg_ctx *C, const double *psi, double *sigma, 
   });
 }
 
+int dmrg_selftest_bounded_wait(void *stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  int *d = nullptr, h = 0;
+  if (cudaMallocAsync(&d, sizeof(int), s) != cudaSuccess) {
+    cudaGetLastError();
+    return DMRG_ERR_OOM;
+  }
+  cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = wait_selftest(d, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFreeAsync(d, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return DMRG_ERR_CUDA;
+  }
+  return h == 7 ? DMRG_ERR_TIMEOUT : DMRG_ERR_CUDA;
+}
+
 int dmrg_heff_flops(dmrg_ctx *C, double *flops) {
   if (!C || !flops) return DMRG_ERR_ARG;
   if (!C->win.valid) return DMRG_ERR_STATE;

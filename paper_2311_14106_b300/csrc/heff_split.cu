@@ -34,7 +34,9 @@ constexpr int TILE_A = BM * 128;  // 16 KB
 constexpr int MAX_SMEM = 232448;  // 227 KB per CTA
 constexpr int NACC = 4;           // TMEM accumulators (4 x 128 columns)
 constexpr int WARP_OUT = 8192;    // epilogue staging per warp: (hi, lo) 32 x 64 halves
-constexpr long long WAIT_LIMIT = 1LL << 22;
+constexpr long long WAIT_LIMIT = 1LL << 22;      // polls (drain after an abort)
+constexpr long long WAIT_CYCLES = 1LL << 31;     // ~1 s at 2 GHz: a pipeline wait gives up
+constexpr uint32_t SUSPEND_NS = 100000;          // try_wait suspend-time hint
 constexpr int ND = 8;             // work-item descriptor slots in shared memory
 constexpr int DPRE = 3;           // descriptors fetched ahead of the producer
 constexpr int DESC_BYTES = ND * (int)sizeof(TWork);
@@ -235,12 +237,29 @@ struct Shared {
 };
 static_assert(sizeof(Shared) <= 512, "barrier area");
 
+// try_wait with a suspend-time hint: a waiting thread sleeps in hardware and
+// wakes when the phase completes (no polling delay at hand-offs)
+__device__ __forceinline__ bool mbar_try_suspend(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(a), "r"(parity), "r"(SUSPEND_NS)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded pipeline wait: gives up after WAIT_CYCLES (or when another role
+// has given up), records `code` and raises the CTA's abort flag.
 __device__ __forceinline__ bool wait_or_abort(uint32_t a, uint32_t parity, int *err, int code,
                                               volatile int *abort) {
-  for (long long i = 0; i < WAIT_LIMIT; ++i) {
-    if (mbar_try(a, parity)) return true;
+  const long long t0 = clock64();
+  for (;;) {
+    if (mbar_try_suspend(a, parity)) return true;
     if (*abort) return false;
-    if (i > 64) __nanosleep(64);
+    if (clock64() - t0 > WAIT_CYCLES) break;
   }
   atomicCAS(err, 0, code);
   *abort = 1;
@@ -580,6 +599,19 @@ k_split_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict_
   }
 }
 
+// Self-test of the bounded waits: one thread waits on a shared-memory barrier
+// that nothing completes; wait_or_abort must give up after WAIT_CYCLES and
+// record its code.  No memory operation is left in flight.
+__global__ void k_wait_selftest(int *err) {
+  __shared__ uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x != 0) return;
+  mbar_init(smem_u32(&bar), 1);
+  abort_flag = 0;
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (wait_or_abort(smem_u32(&bar), 0, err, 7, &abort_flag)) atomicExch(err, -1);
+}
+
 // ---------------------------------------------------------------------------
 // scaled FP16 (hi, lo) copies and their statistics
 // ---------------------------------------------------------------------------
@@ -910,6 +942,11 @@ cudaError_t split_prepare() {
   if (e == cudaSuccess) e = prepare_nt<64>();
   if (e == cudaSuccess) e = prepare_nt<128>();
   return e;
+}
+
+cudaError_t wait_selftest(int *err, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(err);
+  return cudaGetLastError();
 }
 
 cudaError_t split_gemm(const TWork *work, const int *nwork3, const TSeg *seg,

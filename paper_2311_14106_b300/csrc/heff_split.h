@@ -166,6 +166,11 @@ cudaError_t psi_stats(const PsiDesc *d, int n, const double *psi, PsiStat *out, 
 cudaError_t f16_split(const F16Split *d, int n, const PsiStat *pstat, const double *bind,
                       cudaStream_t s);
 
+// One thread waits on a barrier nothing completes; *err (zeroed by the
+// caller) receives 7 when the bounded wait gave up as designed, -1 if the
+// wait returned success.
+cudaError_t wait_selftest(int *err, cudaStream_t s);
+
 // Sets the kernels' shared-memory attributes (call before any stream capture).
 cudaError_t split_prepare();
 
