@@ -38,7 +38,6 @@ constexpr long long WAIT_LIMIT = 1LL << 22;      // polls (drain after an abort)
 constexpr long long WAIT_CYCLES = 1LL << 31;     // ~1 s at 2 GHz: a pipeline wait gives up
 constexpr uint32_t SUSPEND_NS = 100000;          // try_wait suspend-time hint
 constexpr int ND = 8;             // work-item descriptor slots in shared memory
-constexpr int DPRE = 3;           // descriptors fetched ahead of the producer
 constexpr int DESC_BYTES = ND * (int)sizeof(TWork);
 
 // Pipeline geometry for a launch whose tiles are at most NT columns wide:
@@ -49,7 +48,7 @@ constexpr int DESC_BYTES = ND * (int)sizeof(TWork);
 template <int NT>
 struct Geo {
   static constexpr int EPI_GROUPS = NT <= 64 ? 2 : 1;
-  static constexpr int NTHREADS = 64 + 128 * EPI_GROUPS;
+  static constexpr int NTHREADS = 96 + 128 * EPI_GROUPS;   // + descriptor warp
   static constexpr int STAGE_OUT = 4 * EPI_GROUPS * WARP_OUT;
   static constexpr int TILE_B = NT * 128;
   static constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;
@@ -172,15 +171,6 @@ __device__ __forceinline__ void bulk_wait_all() {
 __device__ __forceinline__ void fence_async_shared() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
-// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16)
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
-                                         uint32_t mbar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          dst),
-      "l"(src), "r"(bytes), "r"(mbar)
-      : "memory");
-}
 __device__ __forceinline__ void mbar_arrive(uint32_t a) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
 }
@@ -218,16 +208,18 @@ __device__ __forceinline__ float pow2_scale(float m) {
 
 // Persistent, warp-specialised split GEMM.  Each CTA walks the work list
 // with stride gridDim.x (the list is sorted by cost, largest first):
-//   warp 0, lane 0   TMA producer over all K chunks of all its tiles; it also
-//                    bulk-copies the work descriptors DPRE items ahead into a
-//                    ring of ND shared-memory slots, so no role waits on a
-//                    global load at a tile boundary
+//   warp 0, lane 0   TMA producer over all K chunks of all its tiles
 //   warp 1, lane 0   MMA issuer, rotating over four TMEM accumulators
-//   warps 2..       epilogue: drain an accumulator while the next tile runs
+//   warps 2..        epilogue: drain an accumulator while the next tile runs
 //                    (one or two groups of four warps; group g takes the
 //                    CTA's items g, g + groups, ...)
+//   last warp        copies the work descriptors with plain loads into a
+//                    ring of ND shared-memory slots, as far ahead as the ring
+//                    allows, so no role waits on a global load at a tile
+//                    boundary (and the copies do not queue behind tile loads
+//                    in the TMA unit)
 // A descriptor slot is refilled after its six readers (producer, MMA issuer,
-// four epilogue warps) have copied it to registers.
+// four epilogue warps) have released it.
 constexpr int ACC_COLS = 128;
 
 struct Shared {
@@ -318,25 +310,8 @@ k_split_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict_
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer ----------------
-      auto fetch = [&](int i) -> bool {
-        const int sl = i % ND;
-        if (!wait_or_abort(smem_u32(&sh->dempty[sl]), ((i / ND) & 1) ^ 1, err, 5, abort_flag))
-          return false;
-        const uint32_t fb = smem_u32(&sh->dfull[sl]);
-        mbar_expect_tx(fb, (uint32_t)sizeof(TWork));
-        bulk_g2s(smem_u32(desc + sl), works + blockIdx.x + (size_t)i * gridDim.x,
-                 (uint32_t)sizeof(TWork), fb);
-        return true;
-      };
-      bool ok = true;
-      int nfetch = 0;
-      for (int i = 0; i < DPRE && i < nmine && ok; ++i) nfetch += (ok = fetch(i)) ? 1 : 0;
       int it = 0;
-      for (int i = 0; i < nmine && ok && !*abort_flag; ++i) {
-        if (i + DPRE < nmine) {
-          if (!fetch(i + DPRE)) break;
-          ++nfetch;
-        }
+      for (int i = 0; i < nmine && !*abort_flag; ++i) {
         const int sl = i % ND;
         if (!wait_or_abort(smem_u32(&sh->dfull[sl]), (i / ND) & 1, err, 6, abort_flag)) break;
         // read in place; the slot is released once this item's loads are issued
@@ -394,10 +369,6 @@ k_split_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict_
           for (long long k = 0; k < WAIT_LIMIT && !mbar_try(smem_u32(&sh->full[c % STAGES]),
                                                            (c / STAGES) & 1); ++k)
             __nanosleep(64);
-        for (int i = nfetch > ND ? nfetch - ND : 0; i < nfetch; ++i)
-          for (long long k = 0; k < WAIT_LIMIT && !mbar_try(smem_u32(&sh->dfull[i % ND]),
-                                                           (i / ND) & 1); ++k)
-            __nanosleep(64);
       }
     }
   } else if (warp == 1) {
@@ -452,6 +423,20 @@ k_split_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict_
         // every work item has K >= 1, so the accumulator always holds data
         mma_commit(smem_u32(&sh->acc_full[acc]));
       }
+    }
+  } else if (warp == 2 + 4 * GROUPS) {
+    // ---------------- descriptor loader ----------------
+    // 12 lanes copy one 192-byte item (16 bytes each); lane 0 then arrives
+    // on the slot's barrier (release: the warp's stores are ordered before
+    // it by __syncwarp)
+    for (int i = 0; i < nmine; ++i) {
+      const int sl = i % ND;
+      if (!wait_or_abort(smem_u32(&sh->dempty[sl]), ((i / ND) & 1) ^ 1, err, 5, abort_flag)) break;
+      const uint4 *src = reinterpret_cast<const uint4 *>(works + blockIdx.x + (size_t)i * gridDim.x);
+      if (lane < (int)(sizeof(TWork) / 16)) reinterpret_cast<uint4 *>(desc + sl)[lane] = src[lane];
+      __threadfence_block();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&sh->dfull[sl]));
     }
   } else {
     // ---------------- epilogue (warps 2..5) ----------------
