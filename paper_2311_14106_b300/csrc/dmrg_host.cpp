@@ -1652,10 +1652,39 @@ void split_tables(const Window &w, const SplitScratch &z, __half *Ph, __half *Pl
     if (bucket(a) != bucket(b)) return bucket(a) < bucket(b);
     return cost(a) > cost(b);
   };
-  std::stable_sort(w1.begin(), w1.end(), order);
   std::stable_sort(w2.begin(), w2.end(), order);
-  for (const TWork &t : w1) out.n1[bucket(t)]++;
   for (const TWork &t : w2) out.n2[bucket(t)]++;
+  // Stage 1 runs as one launch of the 128-wide kernel (it takes any tile
+  // width).  Narrow tiles are bound by per-tile latency and wide ones by HBM
+  // bandwidth, so they should run at the same time: the items, sorted by
+  // cost, are dealt in rounds of one item per CTA, heavy and light rounds
+  // alternating, which gives every CTA a mix of widths and about the same
+  // total cost.
+  std::stable_sort(w1.begin(), w1.end(), [&](const TWork &a, const TWork &b) {
+    return cost(a) > cost(b);
+  });
+  {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+      nsm = 148;
+    // full rounds interleaved; the lightest remainder (a partial round) last,
+    // so every round stays aligned with the CTAs
+    const size_t n = w1.size(), G = (size_t)nsm, rounds = n / G;
+    std::vector<TWork> mixed;
+    mixed.reserve(n);
+    for (size_t lo = 0, hi = rounds; lo < hi;) {
+      for (size_t k = lo * G; k < (lo + 1) * G; ++k) mixed.push_back(w1[k]);
+      ++lo;
+      if (lo < hi) {
+        --hi;
+        for (size_t k = hi * G; k < (hi + 1) * G; ++k) mixed.push_back(w1[k]);
+      }
+    }
+    for (size_t k = rounds * G; k < n; ++k) mixed.push_back(w1[k]);
+    w1.swap(mixed);
+  }
+  out.n1[2] = (int)w1.size();
 }
 
 void upload_tables(dmrg_ctx *C, SplitTables &tb, cudaStream_t s);
