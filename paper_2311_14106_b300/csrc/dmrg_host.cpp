@@ -1756,6 +1756,13 @@ void build_split(dmrg_ctx *C) {
   w.tf_ready = true;
 }
 
+// most 32 x 32 tiles of one psi-split descriptor (CTAs per descriptor worth launching)
+int psi_tile_count(const std::vector<F16Split> &v) {
+  int m = 1;
+  for (const F16Split &d : v) m = std::max(m, ((d.rows + 31) / 32) * ((d.cols + 31) / 32));
+  return m;
+}
+
 void upload_tables(dmrg_ctx *C, SplitTables &tb, cudaStream_t s) {
   Window &w = C->win;
   SplitPlan &P = w.tf;
@@ -1785,6 +1792,7 @@ void upload_tables(dmrg_ctx *C, SplitTables &tb, cudaStream_t s) {
 
   P.psi_split = w.tbl_ptr[0];
   P.npsi = (int)tb.psi_split.size();
+  P.psi_tiles = psi_tile_count(tb.psi_split);
   P.maps = (CUtensorMap *)w.tbl_ptr[1];
   P.seg = (TSeg *)w.tbl_ptr[2];
   P.work1 = (TWork *)w.tbl_ptr[3];
@@ -1806,7 +1814,7 @@ void launch_split(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s)
   SplitPlan &P = C->win.tf;
   mark(C, 0, s);
   CK(psi_stats(P.psi_desc, P.npsi, psi, P.pstat, s));
-  CK(f16_split((const F16Split *)P.psi_split, P.npsi, P.pstat, psi, s));
+  CK(f16_split((const F16Split *)P.psi_split, P.npsi, P.pstat, psi, s, P.psi_tiles));
   mark(C, 1, s);
   CK(split_gemm(P.work1, P.n1, P.seg, P.maps, P.pstat, P.err, s));
   mark(C, 2, s);
@@ -3021,7 +3029,8 @@ int dmrg_heff_apply_split_static(dmrg_ctx *C, const double *psi, double *sigma, 
     PsiStat *pst = (PsiStat *)(b + ow.o_pstat);
     CK(cudaMemsetAsync(err, 0, sizeof(int), s));   // the only state that must start at zero
     CK(psi_stats((const PsiDesc *)(b + ow.o_pdesc), (int)np, psi, pst, s));
-    CK(f16_split((const F16Split *)(b + ow.o_split), (int)t.psi_split.size(), pst, psi, s));
+    CK(f16_split((const F16Split *)(b + ow.o_split), (int)t.psi_split.size(), pst, psi, s,
+                 psi_tile_count(t.psi_split)));
     CK(split_gemm((const TWork *)(b + ow.o_w1), t.n1, (const TSeg *)(b + ow.o_seg),
                   (const CUtensorMap *)(b + ow.o_maps), pst, err, s));
     CK(split_gemm((const TWork *)(b + ow.o_w2), t.n2, (const TSeg *)(b + ow.o_seg),

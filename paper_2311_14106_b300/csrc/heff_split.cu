@@ -668,7 +668,19 @@ __global__ void __launch_bounds__(256) k_psi_stats(const PsiDesc *__restrict__ d
   for (int c = threadIdx.x; c < d.cols; c += blockDim.x) {
     double ss = 0.0;
     float mc = 0.f;
-    for (int r = 0; r < d.rows; ++r) {
+    int r = 0;
+    // eight loads in flight, then added in row order
+    for (; r + 8 <= d.rows; r += 8) {
+      double x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) x[u] = p[(long long)(r + u) * d.cols + c];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        ss += x[u] * x[u];
+        mc = fmaxf(mc, (float)fabs(x[u]));
+      }
+    }
+    for (; r < d.rows; ++r) {
       const double x = p[(long long)r * d.cols + c];
       ss += x * x;
       mc = fmaxf(mc, (float)fabs(x));
@@ -911,10 +923,11 @@ cudaError_t psi_stats(const PsiDesc *d, int n, const double *psi, PsiStat *out, 
 }
 
 cudaError_t f16_split(const F16Split *d, int n, const PsiStat *pstat, const double *bind,
-                      cudaStream_t s) {
+                      cudaStream_t s, int grid_tiles) {
+  const unsigned gx = grid_tiles < 1 ? 1u : (grid_tiles > 128 ? 128u : (unsigned)grid_tiles);
   // grid.z is limited to 65535: launch in chunks of descriptors
   for (int i0 = 0; i0 < n; i0 += 65535) {
-    dim3 grid(128, 1, n - i0 < 65535 ? n - i0 : 65535), block(32, 8);
+    dim3 grid(gx, 1, n - i0 < 65535 ? n - i0 : 65535), block(32, 8);
     k_f16_split<<<grid, block, 0, s>>>(d + i0, pstat, bind);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

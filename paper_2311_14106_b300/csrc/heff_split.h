@@ -135,6 +135,7 @@ struct SplitPlan {
   int npsum = 0;
   void *psi_split = nullptr;        // F16Split descriptors (device), one per psi block
   int npsi = 0;
+  int psi_tiles = 1;                // most 32 x 32 tiles of one psi block
   PsiDesc *psi_desc = nullptr;      // psi block extents (device)
   int *err = nullptr;               // device error flag (bounded waits)
 };
@@ -163,8 +164,10 @@ cudaError_t static_scratch(void **ptr, size_t *bytes);
 cudaError_t sum_partials(const PartialSum *p, int n, double *sigma, cudaStream_t s);
 cudaError_t entry_stats(const StatDesc *d, int n, EntryStat *out, cudaStream_t s);
 cudaError_t psi_stats(const PsiDesc *d, int n, const double *psi, PsiStat *out, cudaStream_t s);
+// grid_tiles: CTAs per descriptor (each walks the descriptor's 32 x 32 tiles
+// with that stride); no more than its tile count is useful.
 cudaError_t f16_split(const F16Split *d, int n, const PsiStat *pstat, const double *bind,
-                      cudaStream_t s);
+                      cudaStream_t s, int grid_tiles = 128);
 
 // One thread waits on a barrier nothing completes; *err (zeroed by the
 // caller) receives 7 when the bounded wait gave up as designed, -1 if the
