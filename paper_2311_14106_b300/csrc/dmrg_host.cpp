@@ -1715,6 +1715,7 @@ void build_split(dmrg_ctx *C) {
   P.pstat = (PsiStat *)w.buf.alloc(sizeof(PsiStat) * std::max<size_t>(w.psi.size(), 1));
   P.psi_desc = upload(w.buf, psi_descs(w), s);
   P.err = (int *)w.buf.alloc(sizeof(int));
+  P.next = (int *)w.buf.alloc(6 * sizeof(int));
   CK(cudaMemsetAsync(P.err, 0, sizeof(int), s));
   if (tune) {
     WinBuf tb(s);
@@ -1816,9 +1817,9 @@ void launch_split(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s)
   CK(psi_stats(P.psi_desc, P.npsi, psi, P.pstat, s));
   CK(f16_split((const F16Split *)P.psi_split, P.npsi, P.pstat, psi, s, P.psi_tiles));
   mark(C, 1, s);
-  CK(split_gemm(P.work1, P.n1, P.seg, P.maps, P.pstat, P.err, s));
+  CK(split_gemm(P.work1, P.n1, P.next, P.seg, P.maps, P.pstat, P.err, s));
   mark(C, 2, s);
-  CK(split_gemm(P.work2, P.n2, P.seg, P.maps, P.pstat, P.err, s));
+  CK(split_gemm(P.work2, P.n2, P.next + 3, P.seg, P.maps, P.pstat, P.err, s));
   mark(C, 3, s);
   CK(sum_partials(P.psum, P.npsum, sigma, s));
   mark(C, 4, s);
@@ -2965,7 +2966,8 @@ int dmrg_heff_apply_split_static(dmrg_ctx *C, const double *psi, double *sigma, 
     CK(split_prepare());
     int dev = 0;
     CK(cudaGetDevice(&dev));
-    // layout: [error flag | tables | psi statistics | psi^T hi, lo | T hi, lo | partial tiles]
+    // layout: [error flag, item counters (bytes 16..39) | tables | psi statistics |
+    //          psi^T hi, lo | T hi, lo | partial tiles]
     struct Owner {
       long long gen = -1;
       SplitTables tb;
@@ -3027,13 +3029,13 @@ int dmrg_heff_apply_split_static(dmrg_ctx *C, const double *psi, double *sigma, 
     const SplitTables &t = ow.tb;
     int *err = (int *)b;
     PsiStat *pst = (PsiStat *)(b + ow.o_pstat);
-    CK(cudaMemsetAsync(err, 0, sizeof(int), s));   // the only state that must start at zero
+    CK(cudaMemsetAsync(err, 0, sizeof(int), s));   // must start at zero (split_gemm zeroes its counters)
     CK(psi_stats((const PsiDesc *)(b + ow.o_pdesc), (int)np, psi, pst, s));
     CK(f16_split((const F16Split *)(b + ow.o_split), (int)t.psi_split.size(), pst, psi, s,
                  psi_tile_count(t.psi_split)));
-    CK(split_gemm((const TWork *)(b + ow.o_w1), t.n1, (const TSeg *)(b + ow.o_seg),
+    CK(split_gemm((const TWork *)(b + ow.o_w1), t.n1, (int *)(b + 16), (const TSeg *)(b + ow.o_seg),
                   (const CUtensorMap *)(b + ow.o_maps), pst, err, s));
-    CK(split_gemm((const TWork *)(b + ow.o_w2), t.n2, (const TSeg *)(b + ow.o_seg),
+    CK(split_gemm((const TWork *)(b + ow.o_w2), t.n2, (int *)(b + 32), (const TSeg *)(b + ow.o_seg),
                   (const CUtensorMap *)(b + ow.o_maps), pst, err, s));
     CK(sum_partials((const PartialSum *)(b + ow.o_ps), (int)t.psums.size(), sigma, s));
     note_use(w, s);

@@ -262,7 +262,7 @@ template <int NT>
 __global__ void __launch_bounds__(Geo<NT>::NTHREADS, 1)
 k_split_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict__ segs,
              const CUtensorMap *__restrict__ maps, const PsiStat *__restrict__ pstat,
-             int *__restrict__ err) {
+             int *__restrict__ err, int *__restrict__ next_item) {
   using G = Geo<NT>;
   constexpr int STAGES = G::STAGES;
   constexpr int STAGE_BYTES = G::STAGE_BYTES;
@@ -304,18 +304,17 @@ k_split_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict_
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = sh->tmem;
-  // this CTA's items: blockIdx.x + i * gridDim.x, i < nmine
-  const int nmine = (int)blockIdx.x < nwork ? (nwork - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer ----------------
       int it = 0;
-      for (int i = 0; i < nmine && !*abort_flag; ++i) {
+      for (int i = 0; !*abort_flag; ++i) {
         const int sl = i % ND;
         if (!wait_or_abort(smem_u32(&sh->dfull[sl]), (i / ND) & 1, err, 6, abort_flag)) break;
         // read in place; the slot is released once this item's loads are issued
         const TWork &w = desc[sl];
+        if (w.mode < 0) break;   // no more items
         const uint32_t stage_tx = 2 * TILE_A + 2 * (uint32_t)w.ntile * 128;
         if (w.R > 1) {
           // packed tile: per chunk, group r's rows of A and B from its own
@@ -375,9 +374,10 @@ k_split_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict_
     if (lane == 0) {
       // ---------------- MMA issuer ----------------
       int it = 0;
-      for (int j = 0; j < nmine && !*abort_flag; ++j) {
+      for (int j = 0; !*abort_flag; ++j) {
         const int sl = j % ND;
         if (!wait_or_abort(smem_u32(&sh->dfull[sl]), (j / ND) & 1, err, 6, abort_flag)) break;
+        if (desc[sl].mode < 0) break;
         const int ntile = desc[sl].ntile;
         // packed tiles run all their chunks without trimming (the groups'
         // segments end at different K)
@@ -426,17 +426,41 @@ k_split_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict_
     }
   } else if (warp == 2 + 4 * GROUPS) {
     // ---------------- descriptor loader ----------------
-    // 12 lanes copy one 192-byte item (16 bytes each); lane 0 then arrives
-    // on the slot's barrier (release: the warp's stores are ordered before
-    // it by __syncwarp)
-    for (int i = 0; i < nmine; ++i) {
+    // Items are claimed from the launch's counter (list order: the CTAs
+    // share the work dynamically); 12 lanes copy a 192-byte item (16 bytes
+    // each), lane 0 then arrives on the slot's barrier (release: the warp's
+    // stores are ordered before it by the fence and __syncwarp).  When the
+    // list is exhausted, the next slot of every epilogue group gets an end
+    // mark (mode < 0).
+    int i = 0;
+    bool ok = true;
+    for (;; ++i) {
       const int sl = i % ND;
-      if (!wait_or_abort(smem_u32(&sh->dempty[sl]), ((i / ND) & 1) ^ 1, err, 5, abort_flag)) break;
-      const uint4 *src = reinterpret_cast<const uint4 *>(works + blockIdx.x + (size_t)i * gridDim.x);
+      if (!wait_or_abort(smem_u32(&sh->dempty[sl]), ((i / ND) & 1) ^ 1, err, 5, abort_flag)) {
+        ok = false;
+        break;
+      }
+      int idx = 0;
+      if (lane == 0) idx = atomicAdd(next_item, 1);
+      idx = __shfl_sync(0xffffffffu, idx, 0);
+      if (idx >= nwork) break;
+      const uint4 *src = reinterpret_cast<const uint4 *>(works + idx);
       if (lane < (int)(sizeof(TWork) / 16)) reinterpret_cast<uint4 *>(desc + sl)[lane] = src[lane];
       __threadfence_block();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&sh->dfull[sl]));
+    }
+    for (int k = 0; ok && k < GROUPS; ++k, ++i) {
+      const int sl = i % ND;
+      if (k > 0 &&
+          !wait_or_abort(smem_u32(&sh->dempty[sl]), ((i / ND) & 1) ^ 1, err, 5, abort_flag))
+        break;
+      if (lane == 0) {
+        desc[sl].mode = -1;
+        __threadfence_block();
+        mbar_arrive(smem_u32(&sh->dfull[sl]));
+      }
+      __syncwarp();
     }
   } else {
     // ---------------- epilogue (warps 2..5) ----------------
@@ -451,11 +475,12 @@ k_split_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict_
     const int group = (warp - 2) >> 2;
     const uint32_t stg = smem_u32(stage_out + (warp - 2) * WARP_OUT), stg2 = stg + WARP_OUT / 2;
     const uint32_t rowoff = (uint32_t)lane * 128;
-    for (int j = group; j < nmine; j += GROUPS) {
+    for (int j = group;; j += GROUPS) {
       const int sl = j % ND;
       if (!wait_or_abort(smem_u32(&sh->dfull[sl]), (j / ND) & 1, err, 6, abort_flag)) break;
       // this warp's share of the item, read from the slot, then the slot is released
       const TWork &d = desc[sl];
+      if (d.mode < 0) break;
       const int R = d.R, mode = d.mode, ntile = d.ntile, M = d.M, N = d.N, n0 = d.n0;
       const int mOut_lo = d.mOut_lo;
       int row0 = d.m0 + quarter * 32, cbeg = 0, cend = ntile, xoff = n0, mo = d.mOut_hi,
@@ -835,13 +860,14 @@ cudaError_t prepare_nt() {
 
 // (the shared-memory attributes are set by split_prepare, outside any capture)
 template <int NT>
-cudaError_t launch_nt(const TWork *work, int nwork, const TSeg *seg, const CUtensorMap *maps,
+cudaError_t launch_nt(const TWork *work, int nwork, int *next_item, const TSeg *seg,
+                      const CUtensorMap *maps,
                       const PsiStat *pstat, int *err, cudaStream_t s) {
   if (nwork <= 0) return cudaSuccess;
   const int nsm = sm_count();
   const int grid = nwork < nsm ? nwork : nsm;
   k_split_gemm<NT><<<grid, Geo<NT>::NTHREADS, Geo<NT>::SMEM_BYTES, s>>>(work, nwork, seg, maps,
-                                                                        pstat, err);
+                                                                        pstat, err, next_item);
   return cudaGetLastError();
 }
 
@@ -947,14 +973,18 @@ cudaError_t wait_selftest(int *err, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t split_gemm(const TWork *work, const int *nwork3, const TSeg *seg,
+cudaError_t split_gemm(const TWork *work, const int *nwork3, int *next3, const TSeg *seg,
                        const CUtensorMap *maps, const PsiStat *pstat, int *err, cudaStream_t s) {
-  // work items are grouped by tile width: [<= 32 | <= 64 | <= 128]
-  cudaError_t e = launch_nt<32>(work, nwork3[0], seg, maps, pstat, err, s);
+  // work items are grouped by tile width: [<= 32 | <= 64 | <= 128]; the
+  // launches' item counters start at zero
+  cudaError_t e = cudaMemsetAsync(next3, 0, 3 * sizeof(int), s);
   if (e != cudaSuccess) return e;
-  e = launch_nt<64>(work + nwork3[0], nwork3[1], seg, maps, pstat, err, s);
+  e = launch_nt<32>(work, nwork3[0], next3, seg, maps, pstat, err, s);
   if (e != cudaSuccess) return e;
-  return launch_nt<128>(work + nwork3[0] + nwork3[1], nwork3[2], seg, maps, pstat, err, s);
+  e = launch_nt<64>(work + nwork3[0], nwork3[1], next3 + 1, seg, maps, pstat, err, s);
+  if (e != cudaSuccess) return e;
+  return launch_nt<128>(work + nwork3[0] + nwork3[1], nwork3[2], next3 + 2, seg, maps, pstat,
+                        err, s);
 }
 
 }  // namespace dmrg

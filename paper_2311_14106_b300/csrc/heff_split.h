@@ -138,6 +138,7 @@ struct SplitPlan {
   int psi_tiles = 1;                // most 32 x 32 tiles of one psi block
   PsiDesc *psi_desc = nullptr;      // psi block extents (device)
   int *err = nullptr;               // device error flag (bounded waits)
+  int *next = nullptr;              // device item counters: 3 for stage 1, 3 for stage 2
 };
 
 // Power of two s with |m| * s <= 2^14 (1 for m <= 0); host and device agree.
@@ -179,7 +180,9 @@ cudaError_t split_prepare();
 
 // work holds nwork3[0] items with ntile <= 32, then nwork3[1] with ntile <= 64,
 // then nwork3[2] with ntile <= 128 (one launch each, pipeline sized to the width).
-cudaError_t split_gemm(const TWork *work, const int *nwork3, const TSeg *seg,
+// The CTAs of a launch claim items in list order from a device counter;
+// next3 (3 ints, device) holds the counters and is zeroed here first.
+cudaError_t split_gemm(const TWork *work, const int *nwork3, int *next3, const TSeg *seg,
                        const CUtensorMap *maps, const PsiStat *pstat, int *err, cudaStream_t s);
 
 }  // namespace dmrg
