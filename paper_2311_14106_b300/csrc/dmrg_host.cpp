@@ -1640,7 +1640,7 @@ void split_tables(const Window &w, const SplitScratch &z, __half *Ph, __half *Pl
     w2.push_back(t);
     i0 = i;
   }
-  // persistent CTAs take work items round-robin: order them by cost (K chunks
+  // persistent CTAs claim work items in list order: order them by cost (K chunks
   // x tile width), largest first
   auto cost = [&](const TWork &t) {
     if (t.R > 1) return (long long)t.nchunk * t.ntile;
@@ -1657,9 +1657,9 @@ void split_tables(const Window &w, const SplitScratch &z, __half *Ph, __half *Pl
   // Stage 1 runs as one launch of the 128-wide kernel (it takes any tile
   // width).  Narrow tiles are bound by per-tile latency and wide ones by HBM
   // bandwidth, so they should run at the same time: the items, sorted by
-  // cost, are dealt in rounds of one item per CTA, heavy and light rounds
-  // alternating, which gives every CTA a mix of widths and about the same
-  // total cost.
+  // cost, are arranged in rounds of one item per SM, heavy and light rounds
+  // alternating; claimed in that order, they give every CTA a mix of widths
+  // and about the same total cost.
   std::stable_sort(w1.begin(), w1.end(), [&](const TWork &a, const TWork &b) {
     return cost(a) > cost(b);
   });
@@ -1843,6 +1843,13 @@ void apply_split(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s) 
   auto key = std::make_pair((const void *)psi, (const void *)sigma);
   auto it = w.graphs.find(key);
   if (it == w.graphs.end()) {
+    // callers that pass ever new buffers would grow the cache without bound:
+    // keep at most 64 graphs per window (a destroyed graph still in flight
+    // completes first)
+    if (w.graphs.size() >= 64) {
+      for (auto &g : w.graphs) cudaGraphExecDestroy(g.second);
+      w.graphs.clear();
+    }
     // record on a private stream (the caller's may be the legacy default
     // stream, which cannot be captured); the graph is launched on `s`
     if (!C->cap_stream) CK(cudaStreamCreateWithFlags(&C->cap_stream, cudaStreamNonBlocking));
@@ -2937,7 +2944,7 @@ int dmrg_heff_apply_host(dmrg_ctx *C, const double *psi_h, double *sigma_h, void
   return guard(C, [&] {
     cudaStream_t s = (cudaStream_t)stream;
     const long long n = C->win.psi_len;
-    WinBuf b;
+    WinBuf b(s);   // stream-ordered from the pool: no device synchronisation
     double *dp = (double *)b.alloc(8 * std::max<long long>(n, 1));
     double *ds = (double *)b.alloc(8 * std::max<long long>(n, 1));
     CK(cudaMemcpyAsync(dp, psi_h, 8 * n, cudaMemcpyHostToDevice, s));

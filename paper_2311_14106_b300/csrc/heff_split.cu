@@ -206,18 +206,18 @@ __device__ __forceinline__ float pow2_scale(float m) {
   return ldexpf(1.f, x);
 }
 
-// Persistent, warp-specialised split GEMM.  Each CTA walks the work list
-// with stride gridDim.x (the list is sorted by cost, largest first):
+// Persistent, warp-specialised split GEMM.  The CTAs claim the items of the
+// work list in order from a device counter (the host orders the list):
 //   warp 0, lane 0   TMA producer over all K chunks of all its tiles
 //   warp 1, lane 0   MMA issuer, rotating over four TMEM accumulators
 //   warps 2..        epilogue: drain an accumulator while the next tile runs
 //                    (one or two groups of four warps; group g takes the
 //                    CTA's items g, g + groups, ...)
-//   last warp        copies the work descriptors with plain loads into a
-//                    ring of ND shared-memory slots, as far ahead as the ring
-//                    allows, so no role waits on a global load at a tile
-//                    boundary (and the copies do not queue behind tile loads
-//                    in the TMA unit)
+//   last warp        claims items and copies their descriptors with plain
+//                    loads into a ring of ND shared-memory slots, as far
+//                    ahead as the ring allows, so no role waits on a global
+//                    load at a tile boundary (and the copies do not queue
+//                    behind tile loads in the TMA unit)
 // A descriptor slot is refilled after its six readers (producer, MMA issuer,
 // four epilogue warps) have released it.
 constexpr int ACC_COLS = 128;
