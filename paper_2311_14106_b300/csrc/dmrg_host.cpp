@@ -130,6 +130,28 @@ struct WinBuf {
   bool lasting = false;  // pool allocation on release_stream() (long-lived buffers)
   WinBuf() = default;
   explicit WinBuf(cudaStream_t s) : st(s), ordered(true) {}
+  // owns its allocations: movable, not copyable
+  WinBuf(const WinBuf &) = delete;
+  WinBuf &operator=(const WinBuf &) = delete;
+  WinBuf(WinBuf &&o) noexcept { take(o); }
+  WinBuf &operator=(WinBuf &&o) noexcept {
+    if (this != &o) {
+      clear();
+      take(o);
+    }
+    return *this;
+  }
+  void take(WinBuf &o) {
+    ptrs.swap(o.ptrs);
+    cur = o.cur;
+    left = o.left;
+    st = o.st;
+    ordered = o.ordered;
+    lasting = o.lasting;
+    o.ptrs.clear();
+    o.cur = nullptr;
+    o.left = 0;
+  }
   // long-lived buffers, released without a device synchronisation
   static WinBuf lasting_buf() {
     WinBuf b;
@@ -1657,9 +1679,9 @@ void split_tables(const Window &w, const SplitScratch &z, __half *Ph, __half *Pl
   // Stage 1 runs as one launch of the 128-wide kernel (it takes any tile
   // width).  Narrow tiles are bound by per-tile latency and wide ones by HBM
   // bandwidth, so they should run at the same time: the items, sorted by
-  // cost, are arranged in rounds of one item per SM, heavy and light rounds
-  // alternating; claimed in that order, they give every CTA a mix of widths
-  // and about the same total cost.
+  // cost, are arranged in rounds of one item per SM, and rounds from the
+  // heavy, light and middle thirds follow each other; claimed in that order,
+  // they give every CTA a mix of widths and about the same total cost.
   std::stable_sort(w1.begin(), w1.end(), [&](const TWork &a, const TWork &b) {
     return cost(a) > cost(b);
   });
@@ -1673,13 +1695,15 @@ void split_tables(const Window &w, const SplitScratch &z, __half *Ph, __half *Pl
     const size_t n = w1.size(), G = (size_t)nsm, rounds = n / G;
     std::vector<TWork> mixed;
     mixed.reserve(n);
-    for (size_t lo = 0, hi = rounds; lo < hi;) {
-      for (size_t k = lo * G; k < (lo + 1) * G; ++k) mixed.push_back(w1[k]);
-      ++lo;
-      if (lo < hi) {
-        --hi;
-        for (size_t k = hi * G; k < (hi + 1) * G; ++k) mixed.push_back(w1[k]);
-      }
+    // heavy, light and middle thirds of the rounds taken in turn
+    const size_t t1 = rounds / 3, t2 = 2 * rounds / 3;
+    auto put_round = [&](size_t r) {
+      for (size_t k = r * G; k < (r + 1) * G; ++k) mixed.push_back(w1[k]);
+    };
+    for (size_t h = 0, m = t1, l = rounds; h < t1 || m < t2 || l > t2;) {
+      if (h < t1) put_round(h++);
+      if (l > t2) put_round(--l);
+      if (m < t2) put_round(m++);
     }
     for (size_t k = rounds * G; k < n; ++k) mixed.push_back(w1[k]);
     w1.swap(mixed);
