@@ -218,3 +218,21 @@ def test_window_rebuild_while_apply_in_flight(prec):
     other.synchronize()
     assert rel(new.cpu().numpy(), ref.cpu().numpy()) > 1e-3
     g.close()
+
+
+def test_graph_cache_many_buffer_pairs():
+    """The split apply replays a captured graph per (psi, sigma) pointer pair
+    and keeps at most 64 of them per window: 70 different output buffers
+    (the cache is flushed once on the way) all give the same sigma."""
+    w, g = window_case(4, 4, False, (8,), 64, 7)
+    g.set_precision(lib.SPLIT)
+    psi = torch.tensor(np.random.default_rng(4).standard_normal(w.size), device="cuda")
+    ref = torch.empty_like(psi)
+    g.heff_apply(psi, ref)
+    outs = [torch.empty_like(psi) for _ in range(70)]
+    for o in outs:
+        g.heff_apply(psi, o)
+    torch.cuda.synchronize()
+    for o in outs:
+        assert torch.equal(o, ref)
+    g.close()
