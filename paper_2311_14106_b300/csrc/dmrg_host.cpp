@@ -1360,6 +1360,13 @@ SplitScratch split_scratch_sizes(const Window &w, int KSUB) {
   return z;
 }
 
+// most 32 x 32 tiles of one F16Split descriptor (CTAs per descriptor worth launching)
+int split_tile_count(const std::vector<F16Split> &v) {
+  int m = 1;
+  for (const F16Split &d : v) m = std::max(m, ((d.rows + 31) / 32) * ((d.cols + 31) / 32));
+  return m;
+}
+
 // Scaled FP16 (hi, lo) copies of the operator stacks: built once per window
 // and owned by the context (inputs of every split-path apply).  Each class
 // entry's A and B stacks get one power-of-two scale from their largest
@@ -1445,7 +1452,7 @@ void split_operator_copies(dmrg_ctx *C) {
     b.scale = w.sB[i];
     sp.push_back(b);
   }
-  CK(f16_split(upload(tmp, sp, s), (int)sp.size(), nullptr, nullptr, s));
+  CK(f16_split(upload(tmp, sp, s), (int)sp.size(), nullptr, nullptr, s, split_tile_count(sp)));
   CK(cudaStreamSynchronize(s));
   w.tf_copies = true;
 }
@@ -1668,14 +1675,12 @@ void split_tables(const Window &w, const SplitScratch &z, __half *Ph, __half *Pl
     if (t.R > 1) return (long long)t.nchunk * t.ntile;
     return (long long)((t.s.K + 63) / 64) * t.ntile;
   };
-  // group by tile width (one launch per width class), largest cost first
-  auto bucket = [](const TWork &t) { return t.ntile <= 32 ? 0 : (t.ntile <= 64 ? 1 : 2); };
-  auto order = [&](const TWork &a, const TWork &b) {
-    if (bucket(a) != bucket(b)) return bucket(a) < bucket(b);
+  // stage 2 runs as one launch of the 128-wide kernel (it takes any tile
+  // width), largest cost first
+  std::stable_sort(w2.begin(), w2.end(), [&](const TWork &a, const TWork &b) {
     return cost(a) > cost(b);
-  };
-  std::stable_sort(w2.begin(), w2.end(), order);
-  for (const TWork &t : w2) out.n2[bucket(t)]++;
+  });
+  out.n2[2] = (int)w2.size();
   // Stage 1 runs as one launch of the 128-wide kernel (it takes any tile
   // width).  Narrow tiles are bound by per-tile latency and wide ones by HBM
   // bandwidth, so they should run at the same time: the items, sorted by
@@ -1781,13 +1786,6 @@ void build_split(dmrg_ctx *C) {
   w.tf_ready = true;
 }
 
-// most 32 x 32 tiles of one psi-split descriptor (CTAs per descriptor worth launching)
-int psi_tile_count(const std::vector<F16Split> &v) {
-  int m = 1;
-  for (const F16Split &d : v) m = std::max(m, ((d.rows + 31) / 32) * ((d.cols + 31) / 32));
-  return m;
-}
-
 void upload_tables(dmrg_ctx *C, SplitTables &tb, cudaStream_t s) {
   Window &w = C->win;
   SplitPlan &P = w.tf;
@@ -1817,7 +1815,7 @@ void upload_tables(dmrg_ctx *C, SplitTables &tb, cudaStream_t s) {
 
   P.psi_split = w.tbl_ptr[0];
   P.npsi = (int)tb.psi_split.size();
-  P.psi_tiles = psi_tile_count(tb.psi_split);
+  P.psi_tiles = split_tile_count(tb.psi_split);
   P.maps = (CUtensorMap *)w.tbl_ptr[1];
   P.seg = (TSeg *)w.tbl_ptr[2];
   P.work1 = (TWork *)w.tbl_ptr[3];
@@ -3063,7 +3061,7 @@ int dmrg_heff_apply_split_static(dmrg_ctx *C, const double *psi, double *sigma, 
     CK(cudaMemsetAsync(err, 0, sizeof(int), s));   // must start at zero (split_gemm zeroes its counters)
     CK(psi_stats((const PsiDesc *)(b + ow.o_pdesc), (int)np, psi, pst, s));
     CK(f16_split((const F16Split *)(b + ow.o_split), (int)t.psi_split.size(), pst, psi, s,
-                 psi_tile_count(t.psi_split)));
+                 split_tile_count(t.psi_split)));
     CK(split_gemm((const TWork *)(b + ow.o_w1), t.n1, (int *)(b + 16), (const TSeg *)(b + ow.o_seg),
                   (const CUtensorMap *)(b + ow.o_maps), pst, err, s));
     CK(split_gemm((const TWork *)(b + ow.o_w2), t.n2, (int *)(b + 32), (const TSeg *)(b + ow.o_seg),
