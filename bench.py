@@ -44,9 +44,9 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # pass on the full window; profiles/launches_hubbard6x6_D1024.md), valid only for
 # the kernel source it was taken with: reported as null once that file changes.
 TRAFFIC_SOURCE = os.path.join(ROOT, "paper_2311_14106_b300", "csrc", "heff_split.cu")
-TRAFFIC_SHA = "2fd35b853be18eef"
+TRAFFIC_SHA = "986c6afcb7e53341"
 TRAFFIC = {("hubbard6x6_D1024", "k_split_gemm stage1"): 5.180e9,
-           ("hubbard6x6_D1024", "k_split_gemm stage2"): 5.724e9}
+           ("hubbard6x6_D1024", "k_split_gemm stage2"): 5.715e9}
 
 
 def traffic_of(workload, kernel):

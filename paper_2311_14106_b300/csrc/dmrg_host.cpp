@@ -236,8 +236,7 @@ struct SplitTables {
   std::vector<F16Split> psi_split;
   std::vector<CUtensorMap> maps;
   std::vector<TSeg> segs;
-  std::vector<TWork> w1, w2;      // grouped by tile width (<= 32, <= 64, <= 128)
-  int n1[3] = {0, 0, 0}, n2[3] = {0, 0, 0};
+  std::vector<TWork> w1, w2;      // stage-1 and stage-2 items, in launch order
   std::vector<PartialSum> psums;
 };
 
@@ -1680,7 +1679,6 @@ void split_tables(const Window &w, const SplitScratch &z, __half *Ph, __half *Pl
   std::stable_sort(w2.begin(), w2.end(), [&](const TWork &a, const TWork &b) {
     return cost(a) > cost(b);
   });
-  out.n2[2] = (int)w2.size();
   // Stage 1 runs as one launch of the 128-wide kernel (it takes any tile
   // width).  Narrow tiles are bound by per-tile latency and wide ones by HBM
   // bandwidth, so they should run at the same time: the items, sorted by
@@ -1713,7 +1711,6 @@ void split_tables(const Window &w, const SplitScratch &z, __half *Ph, __half *Pl
     for (size_t k = rounds * G; k < n; ++k) mixed.push_back(w1[k]);
     w1.swap(mixed);
   }
-  out.n1[2] = (int)w1.size();
 }
 
 void upload_tables(dmrg_ctx *C, SplitTables &tb, cudaStream_t s);
@@ -1744,7 +1741,7 @@ void build_split(dmrg_ctx *C) {
   P.pstat = (PsiStat *)w.buf.alloc(sizeof(PsiStat) * std::max<size_t>(w.psi.size(), 1));
   P.psi_desc = upload(w.buf, psi_descs(w), s);
   P.err = (int *)w.buf.alloc(sizeof(int));
-  P.next = (int *)w.buf.alloc(6 * sizeof(int));
+  P.next = (int *)w.buf.alloc(2 * sizeof(int));
   CK(cudaMemsetAsync(P.err, 0, sizeof(int), s));
   if (tune) {
     WinBuf tb(s);
@@ -1824,10 +1821,6 @@ void upload_tables(dmrg_ctx *C, SplitTables &tb, cudaStream_t s) {
   P.nwork1 = (int)tb.w1.size();
   P.nwork2 = (int)tb.w2.size();
   P.npsum = (int)tb.psums.size();
-  for (int i = 0; i < 3; ++i) {
-    P.n1[i] = tb.n1[i];
-    P.n2[i] = tb.n2[i];
-  }
   CK(cudaStreamSynchronize(s));
   for (auto &g : w.graphs) cudaGraphExecDestroy(g.second);
   w.graphs.clear();
@@ -1839,9 +1832,9 @@ void launch_split(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s)
   CK(psi_stats(P.psi_desc, P.npsi, psi, P.pstat, s));
   CK(f16_split((const F16Split *)P.psi_split, P.npsi, P.pstat, psi, s, P.psi_tiles));
   mark(C, 1, s);
-  CK(split_gemm(P.work1, P.n1, P.next, P.seg, P.maps, P.pstat, P.err, s));
+  CK(split_gemm(P.work1, P.nwork1, P.next, P.seg, P.maps, P.pstat, P.err, s));
   mark(C, 2, s);
-  CK(split_gemm(P.work2, P.n2, P.next + 3, P.seg, P.maps, P.pstat, P.err, s));
+  CK(split_gemm(P.work2, P.nwork2, P.next + 1, P.seg, P.maps, P.pstat, P.err, s));
   mark(C, 3, s);
   CK(sum_partials(P.psum, P.npsum, sigma, s));
   mark(C, 4, s);
@@ -2995,7 +2988,7 @@ int dmrg_heff_apply_split_static(dmrg_ctx *C, const double *psi, double *sigma, 
     CK(split_prepare());
     int dev = 0;
     CK(cudaGetDevice(&dev));
-    // layout: [error flag, item counters (bytes 16..39) | tables | psi statistics |
+    // layout: [error flag, item counters (bytes 16..23) | tables | psi statistics |
     //          psi^T hi, lo | T hi, lo | partial tiles]
     struct Owner {
       long long gen = -1;
@@ -3062,9 +3055,11 @@ int dmrg_heff_apply_split_static(dmrg_ctx *C, const double *psi, double *sigma, 
     CK(psi_stats((const PsiDesc *)(b + ow.o_pdesc), (int)np, psi, pst, s));
     CK(f16_split((const F16Split *)(b + ow.o_split), (int)t.psi_split.size(), pst, psi, s,
                  split_tile_count(t.psi_split)));
-    CK(split_gemm((const TWork *)(b + ow.o_w1), t.n1, (int *)(b + 16), (const TSeg *)(b + ow.o_seg),
+    CK(split_gemm((const TWork *)(b + ow.o_w1), (int)t.w1.size(), (int *)(b + 16),
+                  (const TSeg *)(b + ow.o_seg),
                   (const CUtensorMap *)(b + ow.o_maps), pst, err, s));
-    CK(split_gemm((const TWork *)(b + ow.o_w2), t.n2, (int *)(b + 32), (const TSeg *)(b + ow.o_seg),
+    CK(split_gemm((const TWork *)(b + ow.o_w2), (int)t.w2.size(), (int *)(b + 20),
+                  (const TSeg *)(b + ow.o_seg),
                   (const CUtensorMap *)(b + ow.o_maps), pst, err, s));
     CK(sum_partials((const PartialSum *)(b + ow.o_ps), (int)t.psums.size(), sigma, s));
     note_use(w, s);
@@ -3141,8 +3136,7 @@ int dmrg_heff_split_plan(dmrg_ctx *C, double *out4) {
     return DMRG_ERR_STATE;
   }
   const SplitPlan &P = w.tf;
-  int launches = 2 + (P.npsum > 0 ? 1 : 0);
-  for (int i = 0; i < 3; ++i) launches += (P.n1[i] > 0) + (P.n2[i] > 0);
+  const int launches = 2 + (P.npsum > 0 ? 1 : 0) + (P.nwork1 > 0) + (P.nwork2 > 0);
   out4[0] = launches;
   out4[1] = P.nwork1;
   out4[2] = P.nwork2;

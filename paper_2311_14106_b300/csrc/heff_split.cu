@@ -40,16 +40,13 @@ constexpr uint32_t SUSPEND_NS = 100000;          // try_wait suspend-time hint
 constexpr int ND = 8;             // work-item descriptor slots in shared memory
 constexpr int DESC_BYTES = ND * (int)sizeof(TWork);
 
-// Pipeline geometry for a launch whose tiles are at most NT columns wide:
-// a stage holds A_hi, A_lo (128 x 64 halves each) and B_hi, B_lo (NT x 64).
-// Narrow tiles carry little work per tile, so their epilogue runs as two
-// groups of four warps that take alternate tiles; 128-wide tiles keep the
-// shared memory for a deeper operand ring and use one group.
+// Pipeline geometry for tiles at most NT columns wide (the kernel is built
+// for NT = 128 and takes any narrower tile): a stage holds A_hi, A_lo
+// (128 x 64 halves each) and B_hi, B_lo (NT x 64).
 template <int NT>
 struct Geo {
-  static constexpr int EPI_GROUPS = NT <= 64 ? 2 : 1;
-  static constexpr int NTHREADS = 96 + 128 * EPI_GROUPS;   // + descriptor warp
-  static constexpr int STAGE_OUT = 4 * EPI_GROUPS * WARP_OUT;
+  static constexpr int NTHREADS = 96 + 128;   // producer, MMA, loader + 4 epilogue warps
+  static constexpr int STAGE_OUT = 4 * WARP_OUT;
   static constexpr int TILE_B = NT * 128;
   static constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;
   static constexpr int STAGES_RAW =
@@ -58,10 +55,7 @@ struct Geo {
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 512 + STAGE_OUT + DESC_BYTES;
 };
 static_assert(Geo<128>::STAGES >= 3, "pipeline too shallow");
-static_assert(Geo<128>::SMEM_BYTES <= MAX_SMEM && Geo<64>::SMEM_BYTES <= MAX_SMEM &&
-                  Geo<32>::SMEM_BYTES <= MAX_SMEM,
-              "shared memory");
-static_assert(Geo<64>::STAGES >= 3 && Geo<32>::STAGES >= 4, "pipeline too shallow");
+static_assert(Geo<128>::SMEM_BYTES <= MAX_SMEM, "shared memory");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -210,9 +204,7 @@ __device__ __forceinline__ float pow2_scale(float m) {
 // work list in order from a device counter (the host orders the list):
 //   warp 0, lane 0   TMA producer over all K chunks of all its tiles
 //   warp 1, lane 0   MMA issuer, rotating over four TMEM accumulators
-//   warps 2..        epilogue: drain an accumulator while the next tile runs
-//                    (one or two groups of four warps; group g takes the
-//                    CTA's items g, g + groups, ...)
+//   warps 2..5       epilogue: drain an accumulator while the next tile runs
 //   last warp        claims items and copies their descriptors with plain
 //                    loads into a ring of ND shared-memory slots, as far
 //                    ahead as the ring allows, so no role waits on a global
@@ -268,7 +260,6 @@ k_split_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict_
   constexpr int STAGE_BYTES = G::STAGE_BYTES;
   constexpr int TILE_B = G::TILE_B;
   constexpr int STAGE_OUT = G::STAGE_OUT;
-  constexpr int GROUPS = G::EPI_GROUPS;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t *stage_out = smem + STAGES * STAGE_BYTES;      // 1024-byte aligned
@@ -424,14 +415,13 @@ k_split_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict_
         mma_commit(smem_u32(&sh->acc_full[acc]));
       }
     }
-  } else if (warp == 2 + 4 * GROUPS) {
+  } else if (warp == 6) {
     // ---------------- descriptor loader ----------------
     // Items are claimed from the launch's counter (list order: the CTAs
     // share the work dynamically); 12 lanes copy a 192-byte item (16 bytes
     // each), lane 0 then arrives on the slot's barrier (release: the warp's
     // stores are ordered before it by the fence and __syncwarp).  When the
-    // list is exhausted, the next slot of every epilogue group gets an end
-    // mark (mode < 0).
+    // list is exhausted, the next slot gets an end mark (mode < 0).
     int i = 0;
     bool ok = true;
     for (;; ++i) {
@@ -450,15 +440,11 @@ k_split_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict_
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&sh->dfull[sl]));
     }
-    for (int k = 0; ok && k < GROUPS; ++k, ++i) {
-      const int sl = i % ND;
-      if (k > 0 &&
-          !wait_or_abort(smem_u32(&sh->dempty[sl]), ((i / ND) & 1) ^ 1, err, 5, abort_flag))
-        break;
+    if (ok) {
       if (lane == 0) {
-        desc[sl].mode = -1;
+        desc[i % ND].mode = -1;
         __threadfence_block();
-        mbar_arrive(smem_u32(&sh->dfull[sl]));
+        mbar_arrive(smem_u32(&sh->dfull[i % ND]));
       }
       __syncwarp();
     }
@@ -472,10 +458,9 @@ k_split_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict_
     //            into FP16 (hi, lo), 64 columns per box;
     //   stage 2: C / (sT sB) as FP32, 32 columns per box.
     const int quarter = warp & 3;            // TMEM lanes 32*quarter .. +31
-    const int group = (warp - 2) >> 2;
     const uint32_t stg = smem_u32(stage_out + (warp - 2) * WARP_OUT), stg2 = stg + WARP_OUT / 2;
     const uint32_t rowoff = (uint32_t)lane * 128;
-    for (int j = group;; j += GROUPS) {
+    for (int j = 0;; ++j) {
       const int sl = j % ND;
       if (!wait_or_abort(smem_u32(&sh->dfull[sl]), (j / ND) & 1, err, 6, abort_flag)) break;
       // this warp's share of the item, read from the slot, then the slot is released
@@ -961,30 +946,19 @@ cudaError_t f16_split(const F16Split *d, int n, const PsiStat *pstat, const doub
   return cudaSuccess;
 }
 
-cudaError_t split_prepare() {
-  cudaError_t e = prepare_nt<32>();
-  if (e == cudaSuccess) e = prepare_nt<64>();
-  if (e == cudaSuccess) e = prepare_nt<128>();
-  return e;
-}
+cudaError_t split_prepare() { return prepare_nt<128>(); }
 
 cudaError_t wait_selftest(int *err, cudaStream_t s) {
   k_wait_selftest<<<1, 32, 0, s>>>(err);
   return cudaGetLastError();
 }
 
-cudaError_t split_gemm(const TWork *work, const int *nwork3, int *next3, const TSeg *seg,
+cudaError_t split_gemm(const TWork *work, int nwork, int *next, const TSeg *seg,
                        const CUtensorMap *maps, const PsiStat *pstat, int *err, cudaStream_t s) {
-  // work items are grouped by tile width: [<= 32 | <= 64 | <= 128]; the
-  // launches' item counters start at zero
-  cudaError_t e = cudaMemsetAsync(next3, 0, 3 * sizeof(int), s);
+  // the CTAs claim items from *next, which starts at zero
+  cudaError_t e = cudaMemsetAsync(next, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  e = launch_nt<32>(work, nwork3[0], next3, seg, maps, pstat, err, s);
-  if (e != cudaSuccess) return e;
-  e = launch_nt<64>(work + nwork3[0], nwork3[1], next3 + 1, seg, maps, pstat, err, s);
-  if (e != cudaSuccess) return e;
-  return launch_nt<128>(work + nwork3[0] + nwork3[1], nwork3[2], next3 + 2, seg, maps, pstat,
-                        err, s);
+  return launch_nt<128>(work, nwork, next, seg, maps, pstat, err, s);
 }
 
 }  // namespace dmrg

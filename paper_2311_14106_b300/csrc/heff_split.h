@@ -129,7 +129,6 @@ struct SplitPlan {
   TSeg *seg = nullptr;
   TWork *work1 = nullptr, *work2 = nullptr;
   int nwork1 = 0, nwork2 = 0;
-  int n1[3] = {0, 0, 0}, n2[3] = {0, 0, 0};   // per tile-width bucket
   float *ws = nullptr;              // split-K partial tiles of stage 2
   PartialSum *psum = nullptr;
   int npsum = 0;
@@ -138,7 +137,7 @@ struct SplitPlan {
   int psi_tiles = 1;                // most 32 x 32 tiles of one psi block
   PsiDesc *psi_desc = nullptr;      // psi block extents (device)
   int *err = nullptr;               // device error flag (bounded waits)
-  int *next = nullptr;              // device item counters: 3 for stage 1, 3 for stage 2
+  int *next = nullptr;              // device item counters: stage 1, stage 2
 };
 
 // Power of two s with |m| * s <= 2^14 (1 for m <= 0); host and device agree.
@@ -178,11 +177,10 @@ cudaError_t wait_selftest(int *err, cudaStream_t s);
 // Sets the kernels' shared-memory attributes (call before any stream capture).
 cudaError_t split_prepare();
 
-// work holds nwork3[0] items with ntile <= 32, then nwork3[1] with ntile <= 64,
-// then nwork3[2] with ntile <= 128 (one launch each, pipeline sized to the width).
-// The CTAs of a launch claim items in list order from a device counter;
-// next3 (3 ints, device) holds the counters and is zeroed here first.
-cudaError_t split_gemm(const TWork *work, const int *nwork3, int *next3, const TSeg *seg,
+// One launch over nwork items of any tile width (at most 128): persistent
+// CTAs claim them in list order from the device counter *next, which is
+// zeroed here first.
+cudaError_t split_gemm(const TWork *work, int nwork, int *next, const TSeg *seg,
                        const CUtensorMap *maps, const PsiStat *pstat, int *err, cudaStream_t s);
 
 }  // namespace dmrg
