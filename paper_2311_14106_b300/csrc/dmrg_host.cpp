@@ -2000,9 +2000,13 @@ constexpr double kSplitResidualFloor = 4e-6;
 constexpr int kKrylovWarmup = 12;
 
 // patience: split path only, iterations without halving the best residual
-// before a residual near the noise floor is accepted
+// before a residual near the noise floor is accepted.  probe: before
+// accepting, add one random direction to the search space and go on for
+// another `patience` iterations; accept only once such a probe has not
+// lowered the Ritz value (a start vector with almost no weight on the ground
+// state lets an excited state reach the floor first).
 int davidson(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_t s,
-             bool fp64_rq = true, int patience = 16) {
+             bool fp64_rq = true, int patience = 6, bool probe = true) {
   Window &w = C->win;
   const long long n = w.psi_len;
   const int m = std::max(4, std::min(C->cfg.davidson_max_sub, 64));
@@ -2041,6 +2045,8 @@ int davidson(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_t s,
   int k = 1, it = 0;
   double theta = S[0], rnorm = 1e300, best_r = 1e300;
   int best_it = 0;
+  bool probed = false, inject = false;
+  double theta_probe = 0.0;
   std::vector<double> y(1, 1.0);
   bool conv = false;
   for (it = 0; it < maxit; ++it) {
@@ -2079,8 +2085,16 @@ int davidson(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_t s,
       best_it = it;
     } else if (prec == DMRG_SPLIT && it - best_it >= patience &&
                rnorm < 10.0 * std::max(tol, floor)) {
-      conv = true;
-      break;
+      const bool lowered = theta < theta_probe - 1e-5 * std::max(1.0, std::fabs(theta));
+      if (probe && (!probed || lowered)) {
+        probed = true;
+        theta_probe = theta;
+        inject = true;
+        best_it = it;
+      } else {
+        conv = true;
+        break;
+      }
     }
     if (k == m) {
       // thick restart: keep the Ritz vectors of the lowest nk Ritz values
@@ -2119,7 +2133,13 @@ int davidson(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_t s,
     // interior state from an unlucky start.
     // (a caller's start vector, e.g. the StVec guess of a sweep, is already
     // close to the ground state and is preconditioned from the first step)
-    if (!random_start || it >= kKrylovWarmup) CK(launch_precond(B.t, w.diag, th, n, s));
+    if (inject) {
+      // the probe direction replaces this iteration's correction
+      CK(launch_random(B.t, n, C->cfg.seed + 104729 * (++C->start_count), s));
+      inject = false;
+    } else if (!random_start || it >= kKrylovWarmup) {
+      CK(launch_precond(B.t, w.diag, th, n, s));
+    }
     // classical Gram-Schmidt, twice: t -= V (V^T t), coefficients kept on the device
     for (int pass = 0; pass < 2; ++pass) {
       CK(launch_dots(B.V, k, n, B.t, n, B.work, B.dots, s));
@@ -2612,7 +2632,8 @@ void sweep_impl(dmrg_ctx *C, int nsw, const int *dsched, double *E, cudaStream_t
   int prev_trunc = -1;   // -1 none, 0 left, 1 right, 2 same window follows
   double e = 0;
   int it;
-  int patience = 16;
+  int patience = 6;
+  bool probe = true;
   auto step = [&](int l, int trunc_side, int D, bool last) {
     build_window(C, l);
     const long long n = C->win.psi_len;
@@ -2626,7 +2647,7 @@ void sweep_impl(dmrg_ctx *C, int nsw, const int *dsched, double *E, cudaStream_t
       CK(cudaMemsetAsync(x, 0, 8 * std::max<long long>(n, 1), s));
     }
     // the FP64 Rayleigh quotient is only needed for the reported energy
-    int rc = davidson(C, x, &e, &it, s, last, patience);
+    int rc = davidson(C, x, &e, &it, s, last, patience, probe);
     (void)rc;
     pm = meta_of(C->win);
     if (trunc_side >= 0) truncate(C, x, trunc_side, D, nullptr, nullptr, s);
@@ -2638,8 +2659,10 @@ void sweep_impl(dmrg_ctx *C, int nsw, const int *dsched, double *E, cudaStream_t
     const int D = dsched ? dsched[sw] : C->cfg.d_max;
     // the first sweep starts from a random MPS: an excited state of an early
     // window can reach the noise floor before the ground state shows up, so
-    // the split Davidson waits longer there before it accepts stagnation
-    patience = sw == 0 ? 16 : 4;
+    // the split Davidson probes with a random direction before it accepts
+    // stagnation there; later sweeps start from the transformed previous state
+    probe = sw == 0;
+    patience = sw == 0 ? 6 : 4;
     for (int l = 0; l <= N - 2; ++l) step(l, l < N - 2 ? 0 : -1, D, false);
     for (int l = N - 2; l >= 0; --l) step(l, l > 0 ? 1 : -1, D, l == 0);
     if (E) E[sw] = e;
