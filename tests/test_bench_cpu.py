@@ -51,3 +51,25 @@ def test_reference_arm_prints_one_line():
     assert d["impl"] == "reference" and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_traffic_reported_only_for_the_measured_kernel_source(monkeypatch, tmp_path):
+    sys.path.insert(0, ROOT)
+    import bench
+    # the committed figures belong to the committed kernel source
+    assert bench.traffic_of("hubbard6x6_D1024", "k_split_gemm stage1") == \
+        bench.TRAFFIC[("hubbard6x6_D1024", "k_split_gemm stage1")]
+    assert bench.traffic_of("hubbard6x6_D512", "k_split_gemm stage1") is None
+    # any other source text: no traffic figure
+    other = tmp_path / "k.cu"
+    other.write_text(open(bench.TRAFFIC_SOURCE).read() + "\n// changed\n")
+    monkeypatch.setattr(bench, "TRAFFIC_SOURCE", str(other))
+    assert bench.traffic_of("hubbard6x6_D1024", "k_split_gemm stage1") is None
+
+
+def test_peaks_fall_back_without_measured_file(monkeypatch, tmp_path):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setattr(bench, "PEAKS_PATH", str(tmp_path / "absent.json"))
+    hbm, bf16, src = bench.peaks()
+    assert (hbm, bf16, src) == (6400.0, 1800.0, "fallback")
