@@ -14,6 +14,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <list>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -2273,6 +2274,7 @@ void truncate(dmrg_ctx *C, const double *psi, int side, int D, double *disc, dou
   int *info = (int *)tmp.alloc(sizeof(int) * np);
   int info_off = 0;
   std::vector<int> info_of(np);
+  std::list<std::vector<char>> hwork;   // cuSOLVER host workspaces (stable addresses)
   for (auto &kv : bucket) {
     const std::vector<int> &ids = kv.second;
     const int first = ids[0];
@@ -2285,7 +2287,10 @@ void truncate(dmrg_ctx *C, const double *psi, int side, int D, double *disc, dou
                                             &hws, (int64_t)ids.size()) != CUSOLVER_STATUS_SUCCESS)
         fail(DMRG_ERR_CUDA, "syevBatched bufferSize failed");
       void *dw = tmp.alloc(std::max<size_t>(dws, 8));
-      std::vector<char> hw(std::max<size_t>(hws, 8));
+      // host workspaces stay alive until the stream synchronisation below,
+      // so the buckets' solves are queued back to back
+      hwork.emplace_back(std::max<size_t>(hws, 8));
+      std::vector<char> &hw = hwork.back();
       if (cusolverDnXsyevBatched(C->solver, C->solver_params, CUSOLVER_EIG_MODE_VECTOR,
                                  CUBLAS_FILL_MODE_LOWER, n, CUDA_R_64F, rho + roff[first], n,
                                  CUDA_R_64F, eval + eoff[first], CUDA_R_64F, dw, dws, hw.data(), hws,
@@ -2293,7 +2298,6 @@ void truncate(dmrg_ctx *C, const double *psi, int side, int D, double *disc, dou
         fail(DMRG_ERR_CUDA, "syevBatched failed");
       for (size_t j = 0; j < ids.size(); ++j) info_of[ids[j]] = info_off + (int)j;
       info_off += (int)ids.size();
-      CK(cudaStreamSynchronize(s));   // host workspace lifetime
     } else {
       int lw = 0;
       if (cusolverDnDsyevd_bufferSize(C->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
@@ -2368,12 +2372,17 @@ void truncate(dmrg_ctx *C, const double *psi, int side, int D, double *disc, dou
   std::unique_ptr<BlockPart> Bn(new BlockPart());
   WinBuf &bb = buf_of(C, Bn.get());
   T.d = (double *)bb.alloc(8 * std::max<long long>(off, 1));
+  // the kept columns of all sectors in one upload
+  std::vector<int> colsel, coff;
+  for (size_t j = 0; j < order.size(); ++j) {
+    coff.push_back((int)colsel.size());
+    for (int k : kept[order[j].second]) colsel.push_back(npad[order[j].second] - 1 - k);
+  }
+  int *dcs = upload(tmp, colsel, s);
   for (size_t j = 0; j < order.size(); ++j) {
     int i = order[j].second;
-    std::vector<int> colsel;
-    for (int k : kept[i]) colsel.push_back(npad[i] - 1 - k);
-    int *dc = upload(tmp, colsel, s);
-    CK(launch_select_cols(rho + roff[i], npad[i], dim[i], dc, (int)colsel.size(), T.d + T.off[j], s));
+    CK(launch_select_cols(rho + roff[i], npad[i], dim[i], dcs + coff[j], (int)kept[i].size(),
+                          T.d + T.off[j], s));
   }
   CK(cudaStreamSynchronize(s));
   C->prof[3] += now() - t0;
