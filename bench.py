@@ -41,8 +41,8 @@ CPU_SAMPLE = ("hubbard", 4, 4, (8, 8), 4.0, 64)
 
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM traffic per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, one
-# pass on the full window; profiles/launches_hubbard6x6_D1024.md), valid only for
-# the kernel source it was taken with: reported as null once that file changes.
+# pass on the full window), valid only for the kernel source it was taken with:
+# reported as null once that file changes.
 TRAFFIC_SOURCE = os.path.join(ROOT, "paper_2311_14106_b300", "csrc", "heff_split.cu")
 TRAFFIC_SHA = "986c6afcb7e53341"
 TRAFFIC = {("hubbard6x6_D1024", "k_split_gemm stage1"): 5.180e9,

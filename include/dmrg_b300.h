@@ -141,9 +141,19 @@ int dmrg_set_precision(dmrg_ctx *ctx, int precision);
 /* a5 -- sigma = H_eff * psi (Sec. II.A, Davidson matvec).  psi, sigma:
  * device pointers, psi_len doubles each, owned by the caller; sigma is
  * overwritten; psi is not modified.  Stream-ordered, no host sync.
- * Errors: STATE (no window built), ARG (NULL). */
+ * Errors: STATE (no window built), ARG (NULL), TIMEOUT.  A bounded device
+ * wait that gave up inside an earlier split-precision call (whose sigma is
+ * then incomplete) is reported as TIMEOUT by the first call of this context
+ * that runs after the status of that call has reached the host, or by
+ * dmrg_sync; it is reported once, and the call that reports it does no work. */
 int dmrg_heff_apply(dmrg_ctx *ctx, const double *psi, double *sigma,
                     void *stream);
+
+/* Synchronise `stream` and report the outcome of this context's work on it:
+ * DMRG_ERR_TIMEOUT if a bounded device wait of any earlier H_eff*psi of this
+ * context (dmrg_heff_apply or dmrg_heff_apply_split_static) gave up and has
+ * not been reported yet, else DMRG_OK.  Errors: ARG, CUDA, TIMEOUT. */
+int dmrg_sync(dmrg_ctx *ctx, void *stream);
 
 /* Allocation-free variant of dmrg_heff_apply in the split precision
  * (DMRG_SPLIT: FP16 hi + lo operands with per-block power-of-two scales).
@@ -168,6 +178,10 @@ int dmrg_heff_apply(dmrg_ctx *ctx, const double *psi, double *sigma,
  *   - All calls (all contexts) share the one array, which keeps the last
  *     call's contents; calls whose GPU work overlaps in time race with each
  *     other and give wrong results.  Serialize them (one stream, or events).
+ *   - A bounded device wait that gave up leaves an error word set in the
+ *     array; it is cleared only when read.  A later call of the same context
+ *     (once the status of the failed call has reached the host) or dmrg_sync
+ *     reports it as DMRG_ERR_TIMEOUT, once.
  */
 int dmrg_heff_apply_split_static(dmrg_ctx *ctx, const double *psi,
                                 double *sigma, void *stream);
@@ -184,9 +198,12 @@ int dmrg_heff_flops(dmrg_ctx *ctx, double *flops);
 /* a6 -- lowest eigenpair of H_eff by Davidson (Sec. II.A).  psi_inout:
  * device pointer, start vector on input (need not be normalized; a zero
  * vector means "use a seeded random start"), normalized eigenvector on
- * output.  The final energy is the FP64 Rayleigh quotient with an FP64
- * matvec, whatever the precision setting.
- * Errors: STATE, NOT_CONVERGED (psi and energy still written). */
+ * output.  With DMRG_SPLIT the split product runs until its residual
+ * stagnates near its noise floor (about 4e-6 |E|); Davidson iterations with
+ * the FP64 product, started from that vector, then take the residual to
+ * davidson_tol (mixed-precision refinement).  The energy is the Rayleigh
+ * quotient of the FP64 product whatever the precision setting.
+ * Errors: STATE, NOT_CONVERGED (psi and energy still written), TIMEOUT. */
 int dmrg_davidson(dmrg_ctx *ctx, double *psi_inout, double *energy,
                   int *iters, void *stream);
 
@@ -204,9 +221,30 @@ int dmrg_truncate(dmrg_ctx *ctx, const double *psi, int side, int d_max,
  * (truncating to the right after each window but the last).
  * d_schedule[n_sweeps] (NULL = cfg.d_max).  energies_out[n_sweeps] (host)
  * receives the energy of the final window of each sweep.
- * Errors: STATE, NOT_CONVERGED, OOM, CUDA. */
+ * Errors: STATE, OOM, CUDA, TIMEOUT; NOT_CONVERGED if any window's Davidson
+ * hit davidson_max_iter (the energies are still written; dmrg_last_error
+ * gives the number of such windows). */
 int dmrg_sweep(dmrg_ctx *ctx, int n_sweeps, const int *d_schedule,
                double *energies_out, void *stream);
+
+/* Eq. 4 -- read back one isometry of the current MPS basis: after
+ * dmrg_sweep, the isometries the sweeps made (left 1..N-2 from the last
+ * left-to-right pass, right 2..N-1 from the final right-to-left pass, which
+ * with dmrg_get_center give the final state); before any sweep, those set by
+ * dmrg_set_isometry.  side 0 = left, 1 = right isometry `site`, in the
+ * layout of dmrg_set_isometry.  *n_sectors and *n_elems (sum of rows*cols)
+ * are always written; qn[n_sectors*nq], rows[], cols[] and data[n_elems]
+ * (host, row-major per sector, concatenated) are filled when not NULL.
+ * Errors: ARG (no such isometry). */
+int dmrg_get_mps(dmrg_ctx *ctx, int side, int site, int *n_sectors,
+                 long long *n_elems, int *qn, int *rows, int *cols,
+                 double *data);
+
+/* The normalized two-site center tensor psi of the final window of the last
+ * dmrg_sweep (window *l, layout of dmrg_heff_layout for that window):
+ * *psi_len always written, psi (host, may be NULL) filled.
+ * Errors: STATE (no sweep has run). */
+int dmrg_get_center(dmrg_ctx *ctx, int *l, long long *psi_len, double *psi);
 
 /* Work of the two H_eff*psi stages of the current window (for rooflines):
  * out6 = [stage-1 flops, stage-2 flops, A-stack elements, B-stack elements,
@@ -243,6 +281,15 @@ int dmrg_heff_entries(dmrg_ctx *ctx, int *out, int max_entries, int *n_entries);
  * partial tile).  DMRG_ERR_STATE before the plan exists. */
 int dmrg_heff_split_plan(dmrg_ctx *ctx, double *out4);
 
+/* Code paths the split-precision plan of the current window exercises
+ * (for tests): out8[0] stage-1 work items, [1] stage-2 work items, [2] psi
+ * blocks with a side longer than 128 (more than one MMA tile), [3] / [4]
+ * stage-2 items packing R = 2 / R = 4 small blocks per tile, [5] largest
+ * number of split-K partial tiles of one sigma block, [6] sigma blocks with
+ * more than one partial tile, [7] unpacked stage-2 items that are not the
+ * first tile of their block.  Errors: STATE before the first split apply. */
+int dmrg_heff_split_paths(dmrg_ctx *ctx, long long *out8);
+
 /* Replay the split-precision apply from captured CUDA graphs (default 1), one
  * graph per (psi, sigma) pointer pair; 0 launches the kernels directly. */
 int dmrg_set_graphs(dmrg_ctx *ctx, int enable);
@@ -256,6 +303,15 @@ int dmrg_set_graphs(dmrg_ctx *ctx, int enable);
  * DMRG_ERR_CUDA if it did not or a CUDA call failed, DMRG_ERR_OOM if the
  * 4-byte flag could not be allocated. */
 int dmrg_selftest_bounded_wait(void *stream);
+
+/* Self-test of the time-out report (no counterpart in the paper): runs the
+ * wait of dmrg_selftest_bounded_wait on this context's error word -- which 0:
+ * the window's (needs a split plan), 1: the allocation-free path's -- so that
+ * the word is set exactly as a pipeline wait that gave up would set it, and
+ * posts it as an H_eff*psi call does.  Nothing faults; the next
+ * dmrg_heff_apply / dmrg_heff_apply_split_static / dmrg_sync of the context
+ * must then return DMRG_ERR_TIMEOUT once.  Errors: ARG, STATE, CUDA. */
+int dmrg_selftest_timeout_report(dmrg_ctx *ctx, int which, void *stream);
 
 /* Timing breakdown of the last sweep in seconds, Sec. III.B categories:
  * out[0] Diag_H, [1] Ren (block ops), [2] Tables, [3] Diag_D, [4] StVec,

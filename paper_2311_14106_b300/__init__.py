@@ -31,6 +31,8 @@ HEADER_FUNCTIONS = [
     "dmrg_heff_stage_info", "dmrg_heff_timing", "dmrg_profile",
     "dmrg_heff_apply_split_static", "dmrg_heff_tuning", "dmrg_set_graphs",
     "dmrg_heff_split_plan", "dmrg_heff_entries", "dmrg_selftest_bounded_wait",
+    "dmrg_sync", "dmrg_get_mps", "dmrg_get_center", "dmrg_heff_split_paths",
+    "dmrg_selftest_timeout_report",
 ]
 
 
@@ -77,6 +79,12 @@ _sig = {
     "dmrg_heff_split_plan": (ctypes.c_int, [_P, _D]),
     "dmrg_heff_entries": (ctypes.c_int, [_P, _I, ctypes.c_int, _I]),
     "dmrg_selftest_bounded_wait": (ctypes.c_int, [_P]),
+    "dmrg_sync": (ctypes.c_int, [_P, _P]),
+    "dmrg_get_mps": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _I,
+                                    ctypes.POINTER(ctypes.c_longlong), _I, _I, _I, _D]),
+    "dmrg_get_center": (ctypes.c_int, [_P, _I, ctypes.POINTER(ctypes.c_longlong), _D]),
+    "dmrg_heff_split_paths": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong)]),
+    "dmrg_selftest_timeout_report": (ctypes.c_int, [_P, ctypes.c_int, _P]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -252,13 +260,71 @@ class Dmrg:
         return disc.value, ent.value
 
     def sweep(self, n_sweeps, d_schedule=None, stream=None):
+        """a6-a8: two-site sweeps; returns the per-sweep energies.  A window
+        whose Davidson hit its iteration limit does not raise: the energies
+        are returned and self.sweep_converged is False."""
         E = np.zeros(n_sweeps)
         ds = None
         if d_schedule is not None:
             ds = np.ascontiguousarray(d_schedule, dtype=np.int32)
-        self._check(_lib.dmrg_sweep(self._h, n_sweeps, None if ds is None else _iptr(ds), _dptr(E),
-                                    _stream_ptr(stream)), "sweep")
+        rc = _lib.dmrg_sweep(self._h, n_sweeps, None if ds is None else _iptr(ds), _dptr(E),
+                             _stream_ptr(stream))
+        self.sweep_converged = rc == OK
+        if rc not in (OK, ERR_NOT_CONVERGED):
+            self._check(rc, "sweep")
         return E
+
+    def sync(self, stream=None):
+        """Synchronise the stream; raises DmrgError (ERR_TIMEOUT) if a bounded
+        device wait of an earlier H_eff*psi gave up."""
+        self._check(_lib.dmrg_sync(self._h, _stream_ptr(stream)), "sync")
+
+    def get_isometry(self, side, site):
+        """One isometry of the current MPS basis: {qn tuple: (rows, cols) ndarray}."""
+        ns = ctypes.c_int()
+        ne = ctypes.c_longlong()
+        self._check(_lib.dmrg_get_mps(self._h, side, site, ctypes.byref(ns), ctypes.byref(ne),
+                                      None, None, None, None), "get_mps")
+        qn = np.zeros(max(ns.value, 1) * self.nq, dtype=np.int32)
+        rows = np.zeros(max(ns.value, 1), dtype=np.int32)
+        cols = np.zeros(max(ns.value, 1), dtype=np.int32)
+        data = np.zeros(max(ne.value, 1))
+        self._check(_lib.dmrg_get_mps(self._h, side, site, ctypes.byref(ns), ctypes.byref(ne),
+                                      _iptr(qn), _iptr(rows), _iptr(cols), _dptr(data)), "get_mps")
+        out, off = {}, 0
+        for k in range(ns.value):
+            q = tuple(int(x) for x in qn[k * self.nq:(k + 1) * self.nq])
+            r, c = int(rows[k]), int(cols[k])
+            out[q] = data[off:off + r * c].reshape(r, c).copy()
+            off += r * c
+        return out
+
+    def get_mps(self):
+        """The MPS after dmrg_sweep: (right isometries {n: iso} for n = 2..N-1,
+        window l of the center, center psi as a host array)."""
+        l = ctypes.c_int()
+        n = ctypes.c_longlong()
+        self._check(_lib.dmrg_get_center(self._h, ctypes.byref(l), ctypes.byref(n), None),
+                    "get_center")
+        psi = np.zeros(max(n.value, 1))
+        self._check(_lib.dmrg_get_center(self._h, ctypes.byref(l), ctypes.byref(n), _dptr(psi)),
+                    "get_center")
+        right = {k: self.get_isometry(1, k) for k in range(l.value + 2, self.n_sites)}
+        return right, l.value, psi[:n.value]
+
+    def selftest_timeout_report(self, which, stream=None):
+        """Set this context's error word (0 window, 1 static path) the way a
+        pipeline wait that gave up does (about one second, no fault)."""
+        self._check(_lib.dmrg_selftest_timeout_report(self._h, which, _stream_ptr(stream)),
+                    "selftest_timeout_report")
+
+    def heff_split_paths(self):
+        """Code paths of the split plan (see dmrg_heff_split_paths)."""
+        out = (ctypes.c_longlong * 8)()
+        self._check(_lib.dmrg_heff_split_paths(self._h, out), "heff_split_paths")
+        keys = ["items1", "items2", "wide_blocks", "packed_r2", "packed_r4", "max_parts",
+                "multi_part_blocks", "extra_tiles"]
+        return dict(zip(keys, list(out)))
 
     def heff_stage_info(self):
         """Per-stage work: flops1, flops2, A/B/T stack elements, psi_len."""

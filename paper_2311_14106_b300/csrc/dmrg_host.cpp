@@ -318,6 +318,19 @@ struct dmrg_ctx {
   cudaStream_t cap_stream = nullptr;            // private stream for graph capture
   int ksub_choice = 0;                          // autotuned split-K range (0: not yet)
   std::vector<std::array<double, 2>> tune_log;  // (candidate, ms per apply)
+  // Bounded-wait status of the tcgen05 kernels for stream-ordered callers:
+  // after each public split apply the device error word is copied (stream
+  // ordered) into pinned host memory; the next call (or dmrg_sync) reads it
+  // once the copy's event has completed.  [0] window path, [1] static path.
+  int *hflag = nullptr;
+  cudaEvent_t flag_ev[2] = {nullptr, nullptr};
+  bool flag_pending[2] = {false, false};
+  int sticky = DMRG_OK;                         // error owed to the next call
+  std::string sticky_msg;
+  int unconverged = 0;                          // window solves of the last sweep
+  bool swept = false;                           // Lmap/Rmap hold the sweep's isometries
+  int center_l = -1;                            // final window of the last sweep
+  std::vector<double> center_psi;               // its psi (host copy)
 };
 
 namespace {
@@ -1890,13 +1903,72 @@ void apply_split(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s) 
   CK(cudaGraphLaunch(it->second, s));
 }
 
+// Synchronous read of the window's bounded-wait error word (split path).  The
+// word is cleared once read, so a time-out is reported once.
 void check_err_flag(dmrg_ctx *C, cudaStream_t s) {
   Window &w = C->win;
   if (!w.tf_ready) return;
   int e = 0;
   CK(cudaMemcpyAsync(&e, w.tf.err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  if (e) fail(DMRG_ERR_TIMEOUT, "tcgen05 kernel: bounded wait %d gave up", e);
+  if (e) {
+    CK(cudaMemsetAsync(w.tf.err, 0, sizeof(int), s));
+    CK(cudaStreamSynchronize(s));
+    fail(DMRG_ERR_TIMEOUT, "tcgen05 kernel: bounded wait %d gave up", e);
+  }
+}
+
+// After a public split apply on stream s: queue a copy of the device error
+// word (which = 0: the window's, 1: the static scratch's) into the context's
+// pinned host word.  poll_flags reads it once the copy has landed.
+void post_flag(dmrg_ctx *C, int which, const int *dflag, cudaStream_t s) {
+  if (!C->hflag) return;
+  CK(cudaMemcpyAsync(C->hflag + which, dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaEventRecord(C->flag_ev[which], s));
+  C->flag_pending[which] = true;
+}
+
+// Reads the posted error words whose copies have landed (wait: all of them).
+// A set word becomes the context's sticky error (owed to the caller) and is
+// cleared on the device on stream s.
+void poll_flags(dmrg_ctx *C, bool wait, cudaStream_t s) {
+  for (int i = 0; i < 2; ++i) {
+    if (!C->flag_pending[i]) continue;
+    if (wait) {
+      CK(cudaEventSynchronize(C->flag_ev[i]));
+    } else {
+      cudaError_t q = cudaEventQuery(C->flag_ev[i]);
+      if (q == cudaErrorNotReady) continue;
+      CK(q);
+    }
+    C->flag_pending[i] = false;
+    const int e = C->hflag[i];
+    if (!e) continue;
+    C->hflag[i] = 0;
+    if (i == 0 && C->win.tf_ready) CK(cudaMemsetAsync(C->win.tf.err, 0, sizeof(int), s));
+    if (i == 1) {
+      void *b = nullptr;
+      size_t cap = 0;
+      CK(static_scratch(&b, &cap));
+      CK(cudaMemsetAsync(b, 0, sizeof(int), s));
+    }
+    if (C->sticky == DMRG_OK) {
+      C->sticky = DMRG_ERR_TIMEOUT;
+      char buf[160];
+      snprintf(buf, sizeof buf, "tcgen05 kernel (%s path): bounded wait %d gave up in an earlier "
+               "H_eff*psi; its sigma is incomplete", i == 0 ? "window" : "static", e);
+      C->sticky_msg = buf;
+    }
+  }
+}
+
+// Raise the error owed to the caller, once.
+void take_sticky(dmrg_ctx *C) {
+  if (C->sticky == DMRG_OK) return;
+  Err e{C->sticky, C->sticky_msg};
+  C->sticky = DMRG_OK;
+  C->sticky_msg.clear();
+  throw e;
 }
 
 void apply(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s, int precision) {
@@ -2006,14 +2078,13 @@ constexpr int kKrylovWarmup = 12;
 // another `patience` iterations; accept only once such a probe has not
 // lowered the Ritz value (a start vector with almost no weight on the ground
 // state lets an excited state reach the floor first).
-int davidson(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_t s,
-             bool fp64_rq = true, int patience = 6, bool probe = true) {
+int davidson_run(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_t s, int prec,
+                 int patience, bool probe, double *rnorm_out) {
   Window &w = C->win;
   const long long n = w.psi_len;
   const int m = std::max(4, std::min(C->cfg.davidson_max_sub, 64));
   const int maxit = std::max(1, C->cfg.davidson_max_iter);
   const double tol = C->cfg.davidson_tol > 0 ? C->cfg.davidson_tol : 1e-8;
-  const int prec = C->precision;
   DavBuf B = dav_buffers(C, n, m);
   double t0 = now();
   int nmv = 0;
@@ -2167,18 +2238,35 @@ int davidson(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_t s,
   lincomb(x, B.V, y, 0.0, n, B, s);
   double nn = dot1(C, x, x, n, B, s);
   lincomb(x, x, {}, 1.0 / std::sqrt(nn), n, B, s);
-  double e = theta;
-  if (prec != DMRG_FP64 && fp64_rq) {   // FP64 Rayleigh quotient for the reported energy
-    check_err_flag(C, s);
-    apply_fp64(C, x, B.t, s);
-    ++nmv;
-    e = dot1(C, x, B.t, n, B, s);
-  }
-  *energy = e;
+  *energy = theta;
   if (iters) *iters = it;
+  if (rnorm_out) *rnorm_out = rnorm;
   C->prof[0] += now() - t0;
   C->prof[6] += nmv;
   return conv ? DMRG_OK : DMRG_ERR_NOT_CONVERGED;
+}
+
+// Lowest eigenpair of the window's H_eff.  The split path's residual stops
+// near the split product's noise floor (about 4e-6 |theta|), above
+// davidson_tol, so its result is refined by Davidson iterations with the FP64
+// product started from it (mixed-precision refinement: the bulk of the
+// matvecs stays split, a few FP64 ones take the residual to davidson_tol).
+// The reported energy is then the Rayleigh quotient of the FP64 product, and
+// the result has the FP64 path's accuracy.
+int davidson(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_t s,
+             int patience = 6, bool probe = true) {
+  const int prec = C->precision;
+  double rn = 0;
+  int it = 0;
+  int rc = davidson_run(C, x, energy, &it, s, prec, patience, probe, &rn);
+  if (prec == DMRG_SPLIT) {
+    check_err_flag(C, s);
+    int it2 = 0;
+    rc = davidson_run(C, x, energy, &it2, s, DMRG_FP64, patience, false, &rn);
+    it += it2;
+  }
+  if (iters) *iters = it;
+  return rc;
 }
 
 // ---------------------------------------------------------------------------
@@ -2621,6 +2709,10 @@ void sweep_impl(dmrg_ctx *C, int nsw, const int *dsched, double *E, cudaStream_t
     if (!C->riso.count(n)) fail(DMRG_ERR_STATE, "right isometry %d missing", n);
   C->stream = s;
   for (double &p : C->prof) p = 0;
+  C->unconverged = 0;
+  C->swept = false;
+  C->center_l = -1;
+  C->center_psi.clear();
   double t0 = now();
   C->R.clear();
   C->R[N] = vacuum(C);
@@ -2643,7 +2735,7 @@ void sweep_impl(dmrg_ctx *C, int nsw, const int *dsched, double *E, cudaStream_t
   int it;
   int patience = 6;
   bool probe = true;
-  auto step = [&](int l, int trunc_side, int D, bool last) {
+  auto step = [&](int l, int trunc_side, int D) {
     build_window(C, l);
     const long long n = C->win.psi_len;
     xb[cur].clear();
@@ -2655,9 +2747,7 @@ void sweep_impl(dmrg_ctx *C, int nsw, const int *dsched, double *E, cudaStream_t
     } else {
       CK(cudaMemsetAsync(x, 0, 8 * std::max<long long>(n, 1), s));
     }
-    // the FP64 Rayleigh quotient is only needed for the reported energy
-    int rc = davidson(C, x, &e, &it, s, last, patience, probe);
-    (void)rc;
+    if (davidson(C, x, &e, &it, s, patience, probe) == DMRG_ERR_NOT_CONVERGED) ++C->unconverged;
     pm = meta_of(C->win);
     if (trunc_side >= 0) truncate(C, x, trunc_side, D, nullptr, nullptr, s);
     prev = x;
@@ -2672,11 +2762,22 @@ void sweep_impl(dmrg_ctx *C, int nsw, const int *dsched, double *E, cudaStream_t
     // stagnation there; later sweeps start from the transformed previous state
     probe = sw == 0;
     patience = sw == 0 ? 6 : 4;
-    for (int l = 0; l <= N - 2; ++l) step(l, l < N - 2 ? 0 : -1, D, false);
-    for (int l = N - 2; l >= 0; --l) step(l, l > 0 ? 1 : -1, D, l == 0);
+    for (int l = 0; l <= N - 2; ++l) step(l, l < N - 2 ? 0 : -1, D);
+    for (int l = N - 2; l >= 0; --l) step(l, l > 0 ? 1 : -1, D);
     if (E) E[sw] = e;
   }
+  // the MPS the sweeps ended with: right isometries R_2..R_{N-1} (Rmap) and
+  // the normalized two-site center tensor of window 0
+  C->swept = true;
+  C->center_l = C->win.l;
+  C->center_psi.resize(C->win.psi_len);
+  if (prev && C->win.psi_len)
+    CK(cudaMemcpyAsync(C->center_psi.data(), prev, 8 * C->win.psi_len, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
   C->prof[5] = std::max(0.0, now() - t0 - C->prof[0] - C->prof[1] - C->prof[2] - C->prof[3] - C->prof[4]);
+  if (C->unconverged)
+    fail(DMRG_ERR_NOT_CONVERGED, "%d window solve(s) of the sweeps hit the Davidson iteration limit "
+         "(energies are still written)", C->unconverged);
 }
 
 }  // namespace
@@ -2719,6 +2820,18 @@ int dmrg_create(dmrg_ctx **out, const dmrg_config *cfg) {
   C->M = C->spinful ? 2 * C->N : C->N;
   C->target = C->spinful ? QN{cfg->n_up, cfg->n_dn} : QN{cfg->n_up, 0};
   C->precision = cfg->precision;
+  // pinned host status words for the stream-ordered time-out report
+  if (cudaHostAlloc((void **)&C->hflag, 2 * sizeof(int), cudaHostAllocDefault) != cudaSuccess ||
+      cudaEventCreateWithFlags(&C->flag_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&C->flag_ev[1], cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (C->hflag) cudaFreeHost(C->hflag);
+    for (auto &e : C->flag_ev)
+      if (e) cudaEventDestroy(e);
+    delete C;
+    return DMRG_ERR_OOM;
+  }
+  C->hflag[0] = C->hflag[1] = 0;
   *out = C;
   return DMRG_OK;
 }
@@ -2744,6 +2857,12 @@ int dmrg_destroy(dmrg_ctx *ctx) {
     if (e) cudaEventDestroy(e);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->win.use_ev) cudaEventDestroy(ctx->win.use_ev);
+  for (auto &e : ctx->flag_ev)
+    if (e) {
+      cudaEventSynchronize(e);
+      cudaEventDestroy(e);
+    }
+  if (ctx->hflag) cudaFreeHost(ctx->hflag);
   delete ctx;
   return DMRG_OK;
 }
@@ -2977,8 +3096,23 @@ int dmrg_heff_apply(dmrg_ctx *C, const double *psi, double *sigma, void *stream)
     return DMRG_ERR_STATE;
   }
   return guard(C, [&] {
-    apply(C, psi, sigma, (cudaStream_t)stream, C->precision);
-    note_use(C->win, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    poll_flags(C, false, s);
+    take_sticky(C);
+    apply(C, psi, sigma, s, C->precision);
+    if (C->precision == DMRG_SPLIT) post_flag(C, 0, C->win.tf.err, s);
+    note_use(C->win, s);
+  });
+}
+
+int dmrg_sync(dmrg_ctx *C, void *stream) {
+  if (!C) return DMRG_ERR_ARG;
+  return guard(C, [&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaStreamSynchronize(s));
+    poll_flags(C, true, s);
+    take_sticky(C);
+    check_err_flag(C, s);
   });
 }
 
@@ -2990,6 +3124,8 @@ int dmrg_heff_apply_host(dmrg_ctx *C, const double *psi_h, double *sigma_h, void
   }
   return guard(C, [&] {
     cudaStream_t s = (cudaStream_t)stream;
+    poll_flags(C, false, s);
+    take_sticky(C);
     const long long n = C->win.psi_len;
     WinBuf b(s);   // stream-ordered from the pool: no device synchronisation
     double *dp = (double *)b.alloc(8 * std::max<long long>(n, 1));
@@ -3024,6 +3160,7 @@ int dmrg_heff_apply_split_static(dmrg_ctx *C, const double *psi, double *sigma, 
     //          psi^T hi, lo | T hi, lo | partial tiles]
     struct Owner {
       long long gen = -1;
+      bool word_cleared = false;
       SplitTables tb;
       size_t o_maps, o_seg, o_w1, o_w2, o_ps, o_split, o_pdesc, o_pstat;
     };
@@ -3031,6 +3168,14 @@ int dmrg_heff_apply_split_static(dmrg_ctx *C, const double *psi, double *sigma, 
     static std::map<int, Owner> owners;
     std::lock_guard<std::mutex> lk(mu);
     Owner &ow = owners[dev];
+    // a time-out recorded by an earlier call is reported here once its status
+    // copy has landed (dmrg_sync waits for it)
+    poll_flags(C, false, s);
+    take_sticky(C);
+    if (!ow.word_cleared) {   // the error word starts at zero; later only a read clears it
+      CK(cudaMemsetAsync(base, 0, sizeof(int), s));
+      ow.word_cleared = true;
+    }
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     unsigned char *b = (unsigned char *)base;
     const int ks = w.ksub ? w.ksub : KSUB_DEFAULT;
@@ -3083,7 +3228,6 @@ int dmrg_heff_apply_split_static(dmrg_ctx *C, const double *psi, double *sigma, 
     const SplitTables &t = ow.tb;
     int *err = (int *)b;
     PsiStat *pst = (PsiStat *)(b + ow.o_pstat);
-    CK(cudaMemsetAsync(err, 0, sizeof(int), s));   // must start at zero (split_gemm zeroes its counters)
     CK(psi_stats((const PsiDesc *)(b + ow.o_pdesc), (int)np, psi, pst, s));
     CK(f16_split((const F16Split *)(b + ow.o_split), (int)t.psi_split.size(), pst, psi, s,
                  split_tile_count(t.psi_split)));
@@ -3094,6 +3238,7 @@ int dmrg_heff_apply_split_static(dmrg_ctx *C, const double *psi, double *sigma, 
                   (const TSeg *)(b + ow.o_seg),
                   (const CUtensorMap *)(b + ow.o_maps), pst, err, s));
     CK(sum_partials((const PartialSum *)(b + ow.o_ps), (int)t.psums.size(), sigma, s));
+    post_flag(C, 1, err, s);
     note_use(w, s);
   });
 }
@@ -3115,6 +3260,26 @@ int dmrg_selftest_bounded_wait(void *stream) {
     return DMRG_ERR_CUDA;
   }
   return h == 7 ? DMRG_ERR_TIMEOUT : DMRG_ERR_CUDA;
+}
+
+int dmrg_selftest_timeout_report(dmrg_ctx *C, int which, void *stream) {
+  if (!C || (which != 0 && which != 1)) return DMRG_ERR_ARG;
+  return guard(C, [&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    int *word = nullptr;
+    if (which == 0) {
+      if (!C->win.valid || !C->win.tf_ready) fail(DMRG_ERR_STATE, "no split plan: apply once with DMRG_SPLIT");
+      word = C->win.tf.err;
+    } else {
+      void *b = nullptr;
+      size_t cap = 0;
+      CK(static_scratch(&b, &cap));
+      word = (int *)b;
+    }
+    CK(cudaMemsetAsync(word, 0, sizeof(int), s));
+    CK(wait_selftest(word, s));
+    post_flag(C, which, word, s);
+  });
 }
 
 int dmrg_heff_flops(dmrg_ctx *C, double *flops) {
@@ -3173,6 +3338,76 @@ int dmrg_heff_split_plan(dmrg_ctx *C, double *out4) {
   out4[1] = P.nwork1;
   out4[2] = P.nwork2;
   out4[3] = (double)w.ksub;
+  return DMRG_OK;
+}
+
+int dmrg_heff_split_paths(dmrg_ctx *C, long long *out8) {
+  if (!C || !out8) return DMRG_ERR_ARG;
+  const Window &w = C->win;
+  if (!w.valid || !w.tf_ready) {
+    C->err = "split plan not built: apply once with DMRG_SPLIT first";
+    return DMRG_ERR_STATE;
+  }
+  const SplitTables &t = C->tables;
+  for (int i = 0; i < 8; ++i) out8[i] = 0;
+  out8[0] = (long long)t.w1.size();
+  out8[1] = (long long)t.w2.size();
+  for (const PsiBlk &p : w.psi)
+    if (p.da > 128 || p.db > 128) ++out8[2];
+  for (const TWork &x : t.w2) {
+    if (x.R == 2) ++out8[3];
+    if (x.R == 4) ++out8[4];
+    if (x.R <= 1 && (x.m0 > 0 || x.n0 > 0)) ++out8[7];
+  }
+  for (const PartialSum &p : t.psums) {
+    out8[5] = std::max<long long>(out8[5], p.nparts);
+    if (p.nparts > 1) ++out8[6];
+  }
+  return DMRG_OK;
+}
+
+int dmrg_get_mps(dmrg_ctx *C, int side, int site, int *n_sectors, long long *n_elems, int *qn,
+                 int *rows, int *cols, double *data) {
+  if (!C || (side != 0 && side != 1) || !n_sectors || !n_elems) return DMRG_ERR_ARG;
+  return guard(C, [&] {
+    const std::map<int, Iso> &m = C->swept ? (side == 0 ? C->Lmap : C->Rmap)
+                                           : (side == 0 ? C->liso : C->riso);
+    auto it = m.find(site);
+    if (it == m.end())
+      fail(DMRG_ERR_ARG, "no %s isometry %d in the current MPS", side == 0 ? "left" : "right", site);
+    const Iso &T = it->second;
+    const int nq = C->spinful ? 2 : 1;
+    long long tot = 0;
+    for (size_t k = 0; k < T.qn.size(); ++k) tot += (long long)T.rows[k] * T.cols[k];
+    *n_sectors = (int)T.qn.size();
+    *n_elems = tot;
+    for (size_t k = 0; k < T.qn.size(); ++k) {
+      if (qn)
+        for (int i = 0; i < nq; ++i) qn[k * nq + i] = T.qn[k][i];
+      if (rows) rows[k] = T.rows[k];
+      if (cols) cols[k] = T.cols[k];
+    }
+    if (data && tot) {
+      if ((long long)T.host.size() == tot) {
+        memcpy(data, T.host.data(), 8 * tot);
+      } else if (T.d) {
+        CK(cudaMemcpy(data, T.d, 8 * tot, cudaMemcpyDeviceToHost));
+      } else {
+        fail(DMRG_ERR_STATE, "isometry %d has no data", site);
+      }
+    }
+  });
+}
+
+int dmrg_get_center(dmrg_ctx *C, int *l, long long *psi_len, double *psi) {
+  if (!C || !l || !psi_len) return DMRG_ERR_ARG;
+  if (!C->swept || C->center_l < 0) {
+    C->err = "no sweep has run";
+    return DMRG_ERR_STATE;
+  }
+  *l = C->center_l;
+  *psi_len = (long long)C->center_psi.size();
+  if (psi && !C->center_psi.empty()) memcpy(psi, C->center_psi.data(), 8 * C->center_psi.size());
   return DMRG_OK;
 }
 

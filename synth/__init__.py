@@ -88,29 +88,33 @@ def _iso(rng, e, d):
     return q * s
 
 
-def random_left_isometries(n_sites, spinful, target, D, upto, seed):
-    """Isometries left[n], n = 1..upto (dict n -> {Q: matrix})."""
+def random_left_isometries(n_sites, spinful, target, D, upto, seed, spread=None):
+    """Isometries left[n], n = 1..upto (dict n -> {Q: matrix}).
+
+    spread: width (in particles) of the Gaussian sector weights; default
+    max(1, n_sites / 8).  A small spread puts D into fewer, wider sectors."""
     rng = np.random.default_rng(seed)
     dims = {tuple(0 for _ in target): 1}
     out = {}
     for n in range(1, upto + 1):
         e = _enlarged(dims, spinful, target, n_sites - n)
         nbar = sum(target) * n / n_sites
-        dn = _distribute(e, D, nbar, max(1.0, n_sites / 8), spinful)
+        dn = _distribute(e, D, nbar, spread or max(1.0, n_sites / 8), spinful)
         out[n] = {Q: _iso(rng, e[Q], dn[Q]) for Q in dn}
         dims = dn
     return out
 
 
-def random_right_isometries(n_sites, spinful, target, D, downto, seed):
-    """Isometries right[n], n = n_sites-1 .. downto (dict n -> {Q: matrix})."""
+def random_right_isometries(n_sites, spinful, target, D, downto, seed, spread=None):
+    """Isometries right[n], n = n_sites-1 .. downto (dict n -> {Q: matrix});
+    spread as for random_left_isometries."""
     rng = np.random.default_rng(seed)
     dims = {tuple(0 for _ in target): 1}
     out = {}
     for n in range(n_sites - 1, downto - 1, -1):
         e = _enlarged(dims, spinful, target, n)
         nbar = sum(target) * (n_sites - n) / n_sites
-        dn = _distribute(e, D, nbar, max(1.0, n_sites / 8), spinful)
+        dn = _distribute(e, D, nbar, spread or max(1.0, n_sites / 8), spinful)
         out[n] = {Q: _iso(rng, e[Q], dn[Q]) for Q in dn}
         dims = dn
     return out

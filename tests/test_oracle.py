@@ -78,6 +78,76 @@ def test_ed_hubbard_dimer_closed_form():
         assert E0 == pytest.approx((U - np.sqrt(U * U + 16 * t * t)) / 2, abs=1e-14)
 
 
+def test_atomic_limit_pins_interaction_terms():
+    """t = 0: the Hubbard U n_up n_dn term (V[iiii] = U/2 in the spinful Eq. 1
+    convention) and the spinless V n_i n_j term (V[ijji] per bond) against
+    hand-derived ground energies (tests/golden/atomic_limit.txt).  A factor
+    U instead of U/2, or V[ijij] instead of V[ijji] (which flips the sign of
+    the interaction), fails here."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "atomic_limit.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) >= 4
+    for mdl, Lx, Ly, nu, nd, c, E0 in rows:
+        Lx, Ly, nu, nd, c, E0 = int(Lx), int(Ly), int(nu), int(nd), float(c), float(E0)
+        if mdl == "hubbard":
+            T, V4 = lattice.hubbard(Lx, Ly, 0.0, c)
+            h, W = hamiltonian.spin_orbital(T, V4, True)
+            e = ed.ground_energy(h, W, nu + nd, n_up=nu)[0]
+        else:
+            T, V4 = lattice.spinless_tV(Lx, Ly, 0.0, 0.0, c)
+            h, W = hamiltonian.spin_orbital(T, V4, False)
+            e = ed.ground_energy(h, W, nu)[0]
+        assert e == pytest.approx(E0, abs=1e-10), (mdl, Lx, Ly, nu, nd, c, e, E0)
+
+
+def test_atomic_limit_brute_force_count():
+    """The golden spinless value agrees with a brute-force count of occupied
+    bonds over all configurations (bond list only, no Hamiltonian)."""
+    import itertools
+    bonds = lattice.torus_bonds(3, 3)
+    best = min(sum((i in occ) and (j in occ) for i, j in bonds)
+               for occ in map(set, itertools.combinations(range(9), 4)))
+    assert best == 2
+
+
+def test_c1_closed_form_minus_12():
+    """Config C1 (4x4 spinless torus, 8 particles) at V = 0: the energy is the
+    sum of the 8 lowest levels of -2t(cos kx + cos ky): -4 once, -2 four
+    times and three of the six zero levels, -12 in all; ED over all
+    C(16, 8) = 12870 states in the momentum basis reaches it."""
+    assert free_fermion_energy(4, 4, 8) == pytest.approx(-12.0, abs=1e-12)
+    m, h, W = model(4, 4, False, (8,), V=0.0, rot="mom")
+    assert ed.ground_energy(h, W, 8)[0] == pytest.approx(-12.0, abs=1e-10)
+
+
+def test_truncation_weight_and_entropy_vs_dense_svd():
+    """Window.truncate's discarded weight and block entropy against the SVD
+    of the whole psi as one (L. x .R) matrix: its singular values are the
+    union of the per-sector ones."""
+    m, h, W = model(3, 3, False, (4,))
+    li = synth.random_left_isometries(9, False, (4,), 8, 3, 1)
+    ri = synth.random_right_isometries(9, False, (4,), 8, 5, 2)
+    w = dmrg.window_from_mps(m, li, ri, 3)
+    psi = np.random.default_rng(3).standard_normal(w.size)
+    psi /= np.linalg.norm(psi)
+    na = sum(w.Ld.basis.dims)
+    nb = sum(w.Rd.basis.dims)
+    oa = dict(zip(w.Ld.basis.qns, np.cumsum([0] + w.Ld.basis.dims)))
+    ob = dict(zip(w.Rd.basis.qns, np.cumsum([0] + w.Rd.basis.dims)))
+    big = np.zeros((na, nb))
+    for qa, qb, o, da, db in w.layout:
+        big[oa[qa]:oa[qa] + da, ob[qb]:ob[qb] + db] = psi[o:o + da * db].reshape(da, db)
+    sv = np.sort(np.linalg.svd(big, compute_uv=False))[::-1]
+    for D in (3, 7, 12):
+        T, disc, ent = w.truncate(psi, D, "left")
+        kept = sv[:D] ** 2
+        assert disc == pytest.approx(float((sv[D:] ** 2).sum()), abs=1e-12)
+        p = kept / kept.sum()
+        p = p[p > 0]
+        assert ent == pytest.approx(float(-(p * np.log(p)).sum()), abs=1e-12)
+        assert sum(t.shape[1] for t in T.values()) == min(D, int((sv > 0).sum()))
+
+
 def test_rotation_leaves_spectrum_intact():
     """Sec. III.A: without truncation a unitary mode rotation keeps the spectrum."""
     T, V4 = lattice.spinless_tV(3, 3, 1.0, 0.4, 0.8)
@@ -190,13 +260,18 @@ def test_sweep_variational_hubbard_3x3():
     assert E[-1] <= hist[0][3] + 1e-10
 
 
+@pytest.mark.gpu
 @pytest.mark.slow
-@pytest.mark.skipif(not os.environ.get("DMRG_SLOW"), reason="slow oracle tier: set DMRG_SLOW=1")
 def test_paper_4x4_full_D_exact_and_D128_close():
-    """Sec. III.A claim, read for the momentum basis (see tests/golden/paper_claims.txt)."""
+    """Sec. III.A claim, read for the momentum basis (see tests/golden/paper_claims.txt).
+
+    A CPU test of the oracle alone (about 2.5 minutes); it runs in the tier
+    of the GPU tests, beside its GPU twin test_sweep_4x4_full_D_exact_and_D128_gap,
+    to keep the CPU tier short."""
     line = [l for l in open(os.path.join(GOLDEN, "paper_claims.txt"))
             if l.startswith("lattice")][0].split()
-    kv = dict(zip(line[0::2], line[1::2]))
+    assert line[1:3] == ["4", "4"]
+    kv = dict(zip(line[3::2], line[4::2]))
     m, h, W = model(4, 4, False, (8,), V=float(kv["V"]), tp=float(kv["tp"]), rot="mom")
     e_ed = ed.ground_energy(h, W, 8)[0]
     for D, tol in ((int(kv["Dfull"]), 1e-9), (int(kv["D"]), 1e-4)):
