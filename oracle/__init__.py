@@ -15,6 +15,9 @@ Modules
   dmrg         two-site DMRG with normal / complementary block operators:
                enlarged blocks, H_eff * psi, Davidson, truncation, sweeps.
   dense        explicit W^T H W projection of the Fock-space Hamiltonian.
+  su2          spin-adapted (U(1)xSU(2)) windows: exact Clebsch-Gordan
+               expansion of multiplet bases onto the S_z basis, sigma =
+               E^T H_eff E psi through the U(1)xU(1) window.
 
 Every function is pinned by tests against something other than itself
 (closed forms, brute force, invariants); see tests/test_oracle.py.
