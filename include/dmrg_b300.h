@@ -21,7 +21,17 @@
  *     Different contexts may be used concurrently.
  *
  * Quantum numbers (QN): spinless model (sym = DMRG_U1) uses (N); spinful
- * (sym = DMRG_U1U1) uses (N_up, N_dn).  Spin-orbital modes along the chain:
+ * (sym = DMRG_U1U1) uses (N_up, N_dn).  Spin-adapted (sym = DMRG_U1SU2,
+ * Sec. IV: D counts SU(2) multiplets) uses (N, 2J) for a sector of spin-J
+ * multiplets; its sectors are ordered by ((N + 2J)/2, (N - 2J)/2), and all
+ * its matrices (isometries, psi) hold reduced elements between multiplets.
+ * The site multiplets are {0} (N=0), {up, dn} (N=1, J=1/2, |1/2,+1/2> =
+ * c+_up|0>) and {updn} (N=2, J=0, c+_up c+_dn|0>); spins couple in the
+ * Jordan-Wigner order of the parts, |(j1 j2) J M> = sum_m <j1 m1 j2 m2|J M>
+ * |j1 m1>|j2 m2> (Condon-Shortley), and an enlarged sector's rows run over
+ * pieces (site multiplet, block sector) by site multiplet, then block sector.
+ * psi pairs L. sector (N_a, 2J) with .R sector (N - N_a, 2J) (total S = 0).
+ * Spin-orbital modes along the chain:
  * spinless p = i, spinful p = 2 i (up), 2 i + 1 (down); site i = DMRG site i.
  * Site states are ordered by QN: spinless {0, 1}; spinful
  * {0, dn, up, updn} = QN (0,0), (0,1), (1,0), (1,1), with |updn> =
@@ -60,17 +70,18 @@ enum {
   DMRG_ERR_NOT_CONVERGED = -6   /* Davidson hit its iteration limit */
 };
 
-enum { DMRG_U1 = 1, DMRG_U1U1 = 2 };                 /* symmetry */
+enum { DMRG_U1 = 1, DMRG_U1U1 = 2, DMRG_U1SU2 = 3 };   /* symmetry */
 enum { DMRG_FP64 = 0, DMRG_SPLIT = 1 };         /* H_eff*psi precision */
 enum { DMRG_MODEL_SPINLESS_TV = 1, DMRG_MODEL_HUBBARD = 2 };
 
 typedef struct dmrg_ctx dmrg_ctx;   /* opaque, owned by the library */
 
 typedef struct {
-  int sym;                 /* DMRG_U1 (spinless) or DMRG_U1U1 (spinful) */
+  int sym;                 /* DMRG_U1 (spinless), DMRG_U1U1 (spinful, S_z
+                              sectors) or DMRG_U1SU2 (spinful, spin-adapted) */
   int n_sites;             /* N lattice sites = spatial modes */
-  int n_up;                /* target particles (spinless: N) */
-  int n_dn;                /* target down particles (spinless: ignored) */
+  int n_up;                /* target particles (spinless: N; U1SU2: all N) */
+  int n_dn;                /* target down particles (U1U1 only) */
   int d_max;               /* bond dimension D kept by truncation */
   int precision;           /* DMRG_FP64 or DMRG_SPLIT for H_eff*psi */
   double davidson_tol;     /* residual 2-norm bound, normalized vector */
@@ -78,6 +89,7 @@ typedef struct {
   int davidson_max_iter;   /* Davidson iteration limit */
   size_t hbm_budget_bytes; /* 0 = no limit */
   uint64_t seed;           /* seed of the Davidson start vectors */
+  int twice_s;             /* U1SU2: twice the total spin S (this build: 0) */
 } dmrg_config;
 
 const char *dmrg_error_string(int code);

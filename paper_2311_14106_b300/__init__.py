@@ -18,7 +18,7 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_STATE, ERR_TIMEOUT, ERR_NOT_CONVERGED = 0, -1, -2, -3, -4, -5, -6
-U1, U1U1 = 1, 2
+U1, U1U1, U1SU2 = 1, 2, 3
 FP64, SPLIT = 0, 1
 MODEL_SPINLESS_TV, MODEL_HUBBARD = 1, 2
 
@@ -42,7 +42,7 @@ class Config(ctypes.Structure):
         ("n_dn", ctypes.c_int), ("d_max", ctypes.c_int), ("precision", ctypes.c_int),
         ("davidson_tol", ctypes.c_double), ("davidson_max_sub", ctypes.c_int),
         ("davidson_max_iter", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t),
-        ("seed", ctypes.c_uint64),
+        ("seed", ctypes.c_uint64), ("twice_s", ctypes.c_int),
     ]
 
 
@@ -152,9 +152,15 @@ class Dmrg:
     """One library context (one problem: Hamiltonian, MPS basis, window)."""
 
     def __init__(self, n_sites, n_up, n_dn=0, spinful=False, d_max=128, precision=FP64,
-                 davidson_tol=1e-8, davidson_max_sub=20, davidson_max_iter=200, seed=0):
-        cfg = Config(U1U1 if spinful else U1, n_sites, n_up, n_dn, d_max, precision,
-                     davidson_tol, davidson_max_sub, davidson_max_iter, 0, seed)
+                 davidson_tol=1e-8, davidson_max_sub=20, davidson_max_iter=200, seed=0,
+                 su2=False, twice_s=0, hbm_budget_bytes=0):
+        """su2=True: spin-adapted (U(1)xSU(2)) sectors (N, 2J); n_up is then
+        the total particle number and D counts multiplets."""
+        sym = U1SU2 if su2 else (U1U1 if spinful else U1)
+        cfg = Config(sym, n_sites, n_up, n_dn, d_max, precision,
+                     davidson_tol, davidson_max_sub, davidson_max_iter, hbm_budget_bytes, seed,
+                     twice_s)
+        spinful = spinful or su2
         h = _P()
         rc = _lib.dmrg_create(ctypes.byref(h), ctypes.byref(cfg))
         if rc != OK:

@@ -29,6 +29,7 @@
 #include "heff_split.h"
 #include "kernels.h"
 #include "model.h"
+#include "su2.h"
 
 using namespace dmrg;
 
@@ -212,6 +213,9 @@ T *upload(WinBuf &wb, const std::vector<T> &v, cudaStream_t s) {
 struct TermF {
   Fac A, B;
   double coef;
+  // spin-adapted terms [A^k (x) B^k]^0: twice the rank, adjoint factors
+  int tk = -1;
+  int adjA = 0, adjB = 0;
 };
 
 struct HClass {
@@ -287,6 +291,7 @@ struct dmrg_ctx {
   dmrg_config cfg;
   std::string err;
   bool spinful = false;
+  bool su2 = false;   // U(1)xSU(2): sectors are multiplets, QN = highest-weight (N_up, N_dn)
   int N = 0, M = 0;
   QN target{0, 0};
   std::vector<double> h, W;
@@ -503,6 +508,135 @@ SitePart make_site(const dmrg_ctx *C, int i) {
   return s;
 }
 
+// Spin-adapted site: the three multiplets {0} (N=0), {up, dn} (N=1, J=1/2;
+// |1/2,+1/2> = |up>, |1/2,-1/2> = |dn>), {updn} (N=2, J=0), and the reduced
+// matrices of every site tensor.  The tensor components are the couplings of
+// the spin-orbital site operators (make_site, S_z basis {0, dn, up, updn})
+// given in su2.h; the reduced element R(s' <- s) is read off at the highest
+// weight of s', and every component must obey the Wigner-Eckart form.
+SitePart make_site_su2(const dmrg_ctx *C, int i) {
+  const SitePart z = make_site(C, i);
+  SitePart s;
+  s.site = i;
+  s.modes = z.modes;
+  s.d = 3;
+  s.sq = {su2::label(0, 0), su2::label(1, 1), su2::label(2, 0)};
+  s.tj = {0, 1, 0};
+  auto szi = [](int mult, int tm) { return mult == 0 ? 0 : (mult == 2 ? 3 : (tm > 0 ? 2 : 1)); };
+  auto so = [](int x, int tm) { return 2 * x + (tm > 0 ? 0 : 1); };
+  auto sg = [](int tm) { return tm > 0 ? 1.0 : -1.0; };
+  auto mat = [](const SiteOp &o) {
+    Mat4 m;
+    memcpy(m.m, o.m, sizeof m.m);
+    return m;
+  };
+  auto get = [&](const std::map<int, SiteOp> &m, int k) {
+    auto it = m.find(k);
+    return it == m.end() ? Mat4() : mat(it->second);
+  };
+  auto getp = [&](const std::map<PairKey, SiteOp> &m, int a, int b) {
+    auto it = m.find({a, b});
+    return it == m.end() ? Mat4() : mat(it->second);
+  };
+  // P_ab with a, b spin-orbitals in any order (stored for a < b)
+  auto Pso = [&](int a, int b) {
+    if (a == b) return Mat4();
+    if (a < b) return getp(z.P, a, b);
+    Mat4 m = getp(z.P, b, a);
+    for (double &x : m.m) x = -x;
+    return m;
+  };
+  auto reduce = [&](const TKey &key, const std::map<int, Mat4> &comp) {
+    SiteTen t;
+    t.tk = key.tk;
+    t.parity = key.parity();
+    bool nz = false;
+    for (int so_ = 0; so_ < 3; ++so_)
+      for (int si = 0; si < 3; ++si) {
+        const int tjo = s.tj[so_], tji = s.tj[si];
+        double R = 0.0;
+        for (int tmi = -tji; tmi <= tji; tmi += 2) {
+          const int tq = tjo - tmi;
+          auto it = comp.find(tq);
+          if (it == comp.end()) continue;
+          R += su2::cg(tji, tmi, key.tk, tq, tjo, tjo) * it->second.m[szi(so_, tjo) * 4 + szi(si, tmi)];
+        }
+        t.m[so_ * 4 + si] = R;
+        nz |= R != 0.0;
+        // Wigner-Eckart check of every component
+        for (auto &kv : comp)
+          for (int tmi = -tji; tmi <= tji; tmi += 2) {
+            const int tmo = tmi + kv.first;
+            if (std::abs(tmo) > tjo) continue;
+            const double want = su2::cg(tji, tmi, key.tk, kv.first, tjo, tmo) * R;
+            const double got = kv.second.m[szi(so_, tmo) * 4 + szi(si, tmi)];
+            if (std::fabs(want - got) > 1e-12 * (1.0 + std::fabs(got)))
+              fail(DMRG_ERR_STATE, "internal: site tensor (%d,%d,%d,%d) is not a spin tensor",
+                   key.kind, key.i, key.j, key.tk);
+          }
+      }
+    if (nz) s.ten[key] = t;
+  };
+  reduce({0, 0, 0, 0}, {{0, mat(z.H)}});
+  {
+    Mat4 cm = get(z.c, so(i, 1));
+    for (double &x : cm.m) x = -x;
+    reduce({1, i, 0, 1}, {{1, get(z.c, so(i, -1))}, {-1, cm}});
+  }
+  for (int y = 0; y < C->N; ++y) {
+    if (y == i) continue;
+    Mat4 sm = get(z.S, so(y, 1));
+    for (double &x : sm.m) x = -x;
+    reduce({2, y, 0, 1}, {{1, get(z.S, so(y, -1))}, {-1, sm}});
+  }
+  // A~^0_ii = [c~_i x c~_i]^0; B^k_ii = [c+_i x c~_i]^k
+  for (int tk = 0; tk <= 2; tk += 2) {
+    std::map<int, Mat4> ca, cb;
+    for (int m1 = -1; m1 <= 1; m1 += 2)
+      for (int m2 = -1; m2 <= 1; m2 += 2) {
+        const int tq = m1 + m2;
+        if (std::abs(tq) > tk) continue;
+        const double w = su2::cg(1, m1, 1, m2, tk, tq);
+        if (w == 0.0) continue;
+        const Mat4 cc = mm(get(z.c, so(i, -m1)), get(z.c, so(i, -m2)));
+        axpy(ca[tq], w * sg(m1) * sg(m2), cc);
+        const Mat4 cd = mm(tr(get(z.c, so(i, m1))), get(z.c, so(i, -m2)));
+        axpy(cb[tq], w * sg(m2), cd);
+      }
+    if (tk == 0) reduce({3, i, i, 0}, ca);
+    reduce({4, i, i, tk}, cb);
+  }
+  // complementary pair tensors for every pair of spatial modes off the site
+  for (int x = 0; x < C->N; ++x)
+    for (int y = 0; y < C->N; ++y) {
+      if (x == i || y == i) continue;
+      for (int tk = 0; tk <= 2; tk += 2) {
+        std::map<int, Mat4> cp, cq;
+        for (int m1 = -1; m1 <= 1; m1 += 2)
+          for (int m2 = -1; m2 <= 1; m2 += 2) {
+            const int tq = m1 + m2;
+            if (std::abs(tq) > tk) continue;
+            const double w = su2::cg(1, m1, 1, m2, tk, tq);
+            if (w == 0.0) continue;
+            if (x <= y) axpy(cp[tq], w * sg(m1) * sg(m2), Pso(so(x, -m1), so(y, -m2)));
+            axpy(cq[tq], w * sg(m2), getp(z.Q, so(x, -m2), so(y, m1)));
+          }
+        if (x <= y && !(x == y && tk == 2)) reduce({5, x, y, tk}, cp);
+        reduce({6, x, y, tk}, cq);
+      }
+    }
+  return s;
+}
+
+SitePart site_of(const dmrg_ctx *C, int i) { return C->su2 ? make_site_su2(C, i) : make_site(C, i); }
+
+// The .R sector paired with L. sector qa in psi: the complement of qa in the
+// target (spin-adapted, total S = 0: the same spin, the other particles).
+QN partner(const dmrg_ctx *C, const QN &qa) {
+  if (C->su2) return su2::label(su2::n_of(C->target) - su2::n_of(qa), su2::tj_of(qa));
+  return qsub(C->target, qa);
+}
+
 // ---------------------------------------------------------------------------
 // operator classes
 // ---------------------------------------------------------------------------
@@ -510,6 +644,8 @@ struct OpSpec {
   int kind;   // 0 H, 1 c, 2 S, 3 cc, 4 cdc, 5 P, 6 Q
   int i, j;
   QN shift;
+  int tk = -1;   // spin-adapted: twice the tensor rank (-1: spin-orbital operator)
+  int g = 0;     // spin-adapted: this component's 2(J' - J)
 };
 
 QN spec_shift(const dmrg_ctx *C, int kind, int i, int j) {
@@ -522,8 +658,11 @@ QN spec_shift(const dmrg_ctx *C, int kind, int i, int j) {
   }
 }
 
+std::vector<OpSpec> block_specs_su2(const dmrg_ctx *C, const std::vector<int> &so_modes);
+
 // All operators a block holds ("both normal and complementary" policy).
 std::vector<OpSpec> block_specs(const dmrg_ctx *C, const std::vector<int> &modes) {
+  if (C->su2) return block_specs_su2(C, modes);
   std::vector<OpSpec> v;
   v.push_back({0, 0, 0, {0, 0}});
   for (int x : modes) v.push_back({1, x, 0, spec_shift(C, 1, x, 0)});
@@ -544,7 +683,54 @@ std::vector<OpSpec> block_specs(const dmrg_ctx *C, const std::vector<int> &modes
   return v;
 }
 
+// Spin-adapted parts: every tensor of the part (kinds as OpSpec; spatial
+// indices), each as its spin-change components.  Annihilation-type tensors
+// (c~, S~) lower N by 1, the pair tensors A~ and P by 2; B, Q and H keep N.
+std::vector<OpSpec> block_specs_su2(const dmrg_ctx *C, const std::vector<int> &so_modes) {
+  std::vector<int> in;
+  for (int p : so_modes)
+    if (!has(in, p >> 1)) in.push_back(p >> 1);
+  std::vector<int> out;
+  for (int y = 0; y < C->N; ++y)
+    if (!has(in, y)) out.push_back(y);
+  std::vector<OpSpec> v;
+  auto put = [&](int kind, int i, int j, int tk, int dn) {
+    for (int g = -tk; g <= tk; g += 2) {
+      OpSpec o;
+      o.kind = kind;
+      o.i = i;
+      o.j = j;
+      o.tk = tk;
+      o.g = g;
+      o.shift = su2::label(dn, g);
+      v.push_back(o);
+    }
+  };
+  put(0, 0, 0, 0, 0);
+  for (int x : in) put(1, x, 0, 1, -1);
+  for (int y : out) put(2, y, 0, 1, -1);
+  for (size_t a = 0; a < in.size(); ++a)
+    for (size_t b = a; b < in.size(); ++b)
+      for (int tk = 0; tk <= (a == b ? 0 : 2); tk += 2) put(3, in[a], in[b], tk, -2);
+  for (int p : in)
+    for (int r : in)
+      for (int tk = 0; tk <= 2; tk += 2) put(4, p, r, tk, 0);
+  for (size_t a = 0; a < out.size(); ++a)
+    for (size_t b = a; b < out.size(); ++b)
+      for (int tk = 0; tk <= (a == b ? 0 : 2); tk += 2) put(5, out[a], out[b], tk, -2);
+  for (int x : out)
+    for (int z : out)
+      for (int tk = 0; tk <= 2; tk += 2) put(6, x, z, tk, 0);
+  return v;
+}
+
 void set_ref(BlockPart &B, const OpSpec &s, Ref r) {
+  if (s.tk >= 0) {
+    TRef &t = B.ten[TKey{s.kind, s.i, s.j, s.tk}];
+    t.tk = s.tk;
+    t.r[(s.g + s.tk) / 2] = r;
+    return;
+  }
   switch (s.kind) {
     case 0: B.H = r; break;
     case 1: B.c[s.i] = r; break;
@@ -606,6 +792,18 @@ std::vector<Ref> make_classes(BlockPart &B, const std::vector<OpSpec> &specs, Wi
 }
 
 bool allowed_q(const dmrg_ctx *C, const QN &q, int cap) {
+  if (C->su2) {
+    // the other `cap` sites hold N - N_q particles, whose spin (at most
+    // min(n, 2 cap - n)/2, of the parity of n) must couple with J_q to S
+    const int n_rest = su2::n_of(C->target) - su2::n_of(q);
+    if (n_rest < 0 || n_rest > 2 * cap) return false;
+    const int jmax2 = std::min(n_rest, 2 * cap - n_rest);
+    const int tjq = su2::tj_of(q), tS = su2::tj_of(C->target);
+    if (tjq < 0) return false;
+    for (int t = std::abs(tjq - tS); t <= tjq + tS; t += 2)
+      if (t <= jmax2 && ((t - n_rest) & 1) == 0) return true;
+    return false;
+  }
   for (int k = 0; k < (C->spinful ? 2 : 1); ++k) {
     int d = C->target[k] - q[k];
     if (d < 0 || d > cap) return false;
@@ -616,8 +814,15 @@ bool allowed_q(const dmrg_ctx *C, const QN &q, int cap) {
 // ---------------------------------------------------------------------------
 // enlarged block: X x site (left) or site x X (right)
 // ---------------------------------------------------------------------------
+void enlarge_su2(dmrg_ctx *C, const BlockPart &X, const SitePart &st, bool site_first, int cap,
+                 BlockPart &U, WinBuf &wb);
+
 void enlarge(dmrg_ctx *C, const BlockPart &X, const SitePart &st, bool site_first, int cap,
              BlockPart &U, WinBuf &wb) {
+  if (C->su2) {
+    enlarge_su2(C, X, st, site_first, cap, U, wb);
+    return;
+  }
   cudaStream_t s = C->stream;
   // basis with pieces ordered by site state
   std::map<QN, std::vector<Piece>> pm;
@@ -764,6 +969,7 @@ void enlarge(dmrg_ctx *C, const BlockPart &X, const SitePart &st, bool site_firs
       for (const Piece &po : U.pieces[qo])
         for (const Piece &pi : U.pieces[qi]) {
           GSub g;
+          memset(&g, 0, sizeof g);
           g.out = oc.d;
           g.nnz_out = oc.nnz;
           g.out_off = oc.blk_off[b] + (long long)po.off * ld + pi.off;
@@ -781,6 +987,288 @@ void enlarge(dmrg_ctx *C, const BlockPart &X, const SitePart &st, bool site_firs
         }
     }
   }
+  GSub *d_subs = upload(tmp, subs, s);
+  CK(launch_gather(d_subs, (int)subs.size(), max_ops, d_terms, d_srcs, 4, s));
+  CK(cudaStreamSynchronize(s));
+}
+
+// ---------------------------------------------------------------------------
+// spin-adapted formulas
+// ---------------------------------------------------------------------------
+// Terms [X (x) Y]^k of one tensor T (rank k) of the part F u G, keyed by
+// (tensor of F, adjoint?, tensor of G, adjoint?).  The highest component
+// [T]_k is a fixed combination of spin-orbital operators (su2.h); each is
+// expanded by its spin-orbital formula (formulas.h), every product of tensor
+// components a X_qa (x) b Y_qb is projected on the coupled forms,
+//   X_qa Y_qb = sum_kappa <ka qa kb qb | kappa k> [X (x) Y]^kappa_k + ...,
+// and the kappa = k parts are summed.  The kappa != k parts must cancel
+// (T is a rank-k tensor): checked.
+using SU2Terms = std::map<std::tuple<TKey, int, TKey, int>, double>;
+
+SU2Terms derive_su2(const dmrg_ctx *C, const SideS &F, const SideS &G, const TKey &T) {
+  const int tk = T.tk, tq = T.tk;
+  SU2Terms alpha;
+  std::map<std::tuple<TKey, int, TKey, int, int>, double> other;
+  double d = 1.0, scale = 0.0;
+  auto add = [&](const SFac &A, const SFac &B, double coef) {
+    for (const TComp &a : A.c)
+      for (const TComp &b : B.c) {
+        if (a.tq + b.tq != tq) fail(DMRG_ERR_STATE, "internal: spin projection of a product");
+        const int ka = a.key.kind < 0 ? 0 : a.key.tk, kb = b.key.kind < 0 ? 0 : b.key.tk;
+        const int aa = a.key.kind < 0 ? 0 : a.adj, ba = b.key.kind < 0 ? 0 : b.adj;
+        const double base = d * coef * a.a * b.a;
+        scale += std::fabs(base);
+        for (int kap = std::abs(ka - kb); kap <= ka + kb; kap += 2) {
+          const double w = su2::cg(ka, a.tq, kb, b.tq, kap, tq);
+          if (w == 0.0) continue;
+          if (kap == tk) alpha[std::make_tuple(a.key, aa, b.key, ba)] += base * w;
+          else other[std::make_tuple(a.key, aa, b.key, ba, kap)] += base * w;
+        }
+      }
+  };
+  const double *W = C->W.data();
+  const int M = C->M;
+  auto so = [](int x, int tm) { return 2 * x + (tm > 0 ? 0 : 1); };
+  auto sg = [](int tm) { return tm > 0 ? 1.0 : -1.0; };
+  switch (T.kind) {
+    case 0: formula_H(F, G, add, true); break;
+    case 1: formula_c(F, G, so(T.i, -1), add); break;   // [c~]_{+1/2} = c_dn
+    case 2: formula_S(F, G, so(T.i, -1), add); break;   // [S~]_{+1/2} = S_dn
+    default:
+      for (int m1 = -1; m1 <= 1; m1 += 2) {
+        const int m2 = tq - m1;
+        if (std::abs(m2) != 1) continue;
+        const double w = su2::cg(1, m1, 1, m2, tk, tq);
+        if (w == 0.0) continue;
+        if (T.kind == 3) {          // [A~]_q = sum <..> s s c_{i,-m1} c_{j,-m2}
+          const int a = so(T.i, -m1), b = so(T.j, -m2);
+          if (a == b) continue;
+          d = w * sg(m1) * sg(m2);
+          if (a < b) {
+            formula_cc(F, G, a, b, add);
+          } else {
+            d = -d;
+            formula_cc(F, G, b, a, add);
+          }
+        } else if (T.kind == 4) {   // [B]_q = sum <..> s c+_{i,m1} c_{j,-m2}
+          d = w * sg(m2);
+          formula_cdc(F, G, so(T.i, m1), so(T.j, -m2), add);
+        } else if (T.kind == 5) {   // [P]_q = sum <..> s s P_{(i,-m1),(j,-m2)}
+          const int a = so(T.i, -m1), b = so(T.j, -m2);
+          if (a == b) continue;
+          d = w * sg(m1) * sg(m2);
+          formula_P(F, G, a, b, W, M, add);
+        } else {                    // [Q]_q = sum <..> s Q_{(i,-m2),(j,m1)}
+          d = w * sg(m2);
+          formula_Q(F, G, so(T.i, -m2), so(T.j, m1), W, M, add);
+        }
+      }
+  }
+  double omax = 0.0;
+  for (auto &kv : other) omax = std::max(omax, std::fabs(kv.second));
+  if (omax > 1e-10 * std::max(scale, 1e-300))
+    fail(DMRG_ERR_STATE, "internal: tensor (%d,%d,%d,%d) has a rank-%d part %.3g", T.kind, T.i, T.j,
+         T.tk, -1, omax);
+  for (auto it = alpha.begin(); it != alpha.end();)
+    it = std::fabs(it->second) <= 1e-14 * scale ? alpha.erase(it) : std::next(it);
+  return alpha;
+}
+
+SideS side_of(const BlockPart &B) {
+  SideS sd;
+  sd.so_modes = B.modes;
+  sd.has = [&B](const TKey &k) {
+    auto it = B.ten.find(k);
+    if (it == B.ten.end()) return false;
+    for (const Ref &r : it->second.r)
+      if (r.cls >= 0) return true;
+    return false;
+  };
+  return sd;
+}
+
+SideS side_of(const SitePart &st) {
+  SideS sd;
+  sd.so_modes = st.modes;
+  sd.has = [&st](const TKey &k) { return st.ten.count(k) > 0; };
+  return sd;
+}
+
+// coefficient-table slot of a term type (2 k of the block factor, of the site
+// factor, of the target; block factor adjoint)
+inline int ctype_of(int tkX, int tkS, int tk, int adj) { return ((tkX * 3 + tkS) * 3 + tk) * 2 + adj; }
+constexpr int kCtypes = 54;
+
+// enlarged spin-adapted block: X x site (left) or site x X (right)
+void enlarge_su2(dmrg_ctx *C, const BlockPart &X, const SitePart &st, bool site_first, int cap,
+                 BlockPart &U, WinBuf &wb) {
+  cudaStream_t s = C->stream;
+  std::map<QN, std::vector<Piece>> pm;
+  for (int k = 0; k < st.d; ++k)
+    for (size_t j = 0; j < X.basis.qn.size(); ++j) {
+      const QN &qb = X.basis.qn[j];
+      const int n = su2::n_of(qb) + su2::n_of(st.sq[k]);
+      const int t1 = su2::tj_of(qb), t2 = st.tj[k];
+      for (int tj = std::abs(t1 - t2); tj <= t1 + t2; tj += 2) {
+        const QN Q = su2::label(n, tj);
+        if (!allowed_q(C, Q, cap)) continue;
+        pm[Q].push_back({k, (int)j, 0, X.basis.dim[j]});
+      }
+    }
+  U.basis = Basis();
+  U.pieces.clear();
+  for (auto &kv : pm) {
+    int off = 0;
+    for (auto &p : kv.second) {
+      p.off = off;
+      off += p.dim;
+    }
+    U.basis.qn.push_back(kv.first);
+    U.basis.dim.push_back(off);
+    U.pieces.push_back(kv.second);
+  }
+  U.enlarged = true;
+  U.site_first = site_first;
+  U.modes.clear();
+  if (site_first) {
+    U.modes = st.modes;
+    U.modes.insert(U.modes.end(), X.modes.begin(), X.modes.end());
+  } else {
+    U.modes = X.modes;
+    U.modes.insert(U.modes.end(), st.modes.begin(), st.modes.end());
+  }
+  std::vector<OpSpec> specs = block_specs(C, U.modes);
+  make_classes(U, specs, wb, s);
+
+  const SideS sx = side_of(X), ss = side_of(st);
+  const SideS &F = site_first ? ss : sx;
+  const SideS &G = site_first ? sx : ss;
+  // per class, per op: terms
+  std::vector<std::vector<std::vector<GTerm>>> terms(U.cls.size());
+  for (size_t ci = 0; ci < U.cls.size(); ++ci) terms[ci].resize(U.cls[ci].nops);
+  for (auto &tv : U.ten) {
+    const TKey &T = tv.first;
+    bool any = false;
+    for (const Ref &r : tv.second.r) any |= r.cls >= 0;
+    if (!any) continue;
+    const SU2Terms al = derive_su2(C, F, G, T);
+    // merged by (source class, index, transpose, coefficient type)
+    std::map<std::array<int, 4>, GTerm> acc;
+    for (auto &kv : al) {
+      const TKey &kf = std::get<0>(kv.first), &kg = std::get<2>(kv.first);
+      const int af = std::get<1>(kv.first), ag = std::get<3>(kv.first);
+      const TKey &kx = site_first ? kg : kf, &ks = site_first ? kf : kg;
+      const int ax = site_first ? ag : af, as = site_first ? af : ag;
+      const int tkX = kx.kind < 0 ? 0 : kx.tk, tkS = ks.kind < 0 ? 0 : ks.tk;
+      // site factor (reduced, adjoint if asked), with the term's coefficient
+      double m[16] = {0};
+      if (ks.kind < 0) {
+        for (int k = 0; k < st.d; ++k) m[k * 4 + k] = 1.0;
+      } else {
+        const SiteTen &t = st.ten.at(ks);
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b)
+            m[a * 4 + b] = as ? su2::adjoint_factor(st.tj[b], st.tj[a], tkS) * t.m[b * 4 + a]
+                              : t.m[a * 4 + b];
+      }
+      const int p2 = site_first ? kx.parity() : (ks.kind < 0 ? 0 : ks.parity());
+      const int ct = ctype_of(tkX, tkS, T.tk, kx.kind < 0 ? 0 : ax);
+      auto put = [&](int src, int idx, int trans) {
+        std::array<int, 4> key{src, idx, trans, ct};
+        auto it = acc.find(key);
+        if (it == acc.end()) {
+          GTerm g;
+          memset(&g, 0, sizeof g);
+          g.src = src;
+          g.idx = idx;
+          g.trans = trans;
+          g.p2 = p2;
+          g.ctype = ct;
+          it = acc.emplace(key, g).first;
+        }
+        for (int e = 0; e < 16; ++e) it->second.m[e] += kv.second * m[e];
+      };
+      if (kx.kind < 0) {
+        put(-1, 0, 0);
+      } else {
+        const TRef &tr = X.ten.at(kx);
+        for (const Ref &r : tr.r)
+          if (r.cls >= 0) put(r.cls, r.idx, ax);
+      }
+    }
+    std::vector<GTerm> list;
+    for (auto &kv : acc) list.push_back(kv.second);
+    for (const Ref &r : tv.second.r)
+      if (r.cls >= 0) terms[r.cls][r.idx] = list;
+  }
+  // flatten terms, CSR per class
+  std::vector<GTerm> all;
+  std::vector<std::vector<int>> ptr(U.cls.size());
+  for (size_t ci = 0; ci < U.cls.size(); ++ci) {
+    ptr[ci].push_back((int)all.size());
+    for (auto &tl : terms[ci]) {
+      all.insert(all.end(), tl.begin(), tl.end());
+      ptr[ci].push_back((int)all.size());
+    }
+  }
+  WinBuf tmp(s);   // work lists, released once the gather has run
+  GTerm *d_terms = upload(tmp, all, s);
+  std::vector<int *> d_ptr(U.cls.size());
+  for (size_t ci = 0; ci < U.cls.size(); ++ci) d_ptr[ci] = upload(tmp, ptr[ci], s);
+  std::vector<GSrc> srcs;
+  for (auto &oc : X.cls) srcs.push_back({oc.d, oc.nnz, oc.d_in2blk, oc.d_blk_out, oc.d_blk_off});
+  GSrc *d_srcs = upload(tmp, srcs, s);
+  std::vector<GSub> subs;
+  std::vector<double> ctab;
+  int max_ops = 0;
+  for (size_t ci = 0; ci < U.cls.size(); ++ci) {
+    const OpClass &oc = U.cls[ci];
+    if (oc.nnz == 0) continue;
+    max_ops = std::max(max_ops, oc.nops);
+    for (size_t b = 0; b < oc.blk_in.size(); ++b) {
+      const int qi = oc.blk_in[b], qo = oc.blk_out[b];
+      const int ld = U.basis.dim[qi];
+      const int tJ = su2::tj_of(U.basis.qn[qi]), tJp = su2::tj_of(U.basis.qn[qo]);
+      for (const Piece &po : U.pieces[qo])
+        for (const Piece &pi : U.pieces[qi]) {
+          GSub g;
+          memset(&g, 0, sizeof g);
+          g.out = oc.d;
+          g.nnz_out = oc.nnz;
+          g.out_off = oc.blk_off[b] + (long long)po.off * ld + pi.off;
+          g.out_ld = ld;
+          g.rows = po.dim;
+          g.cols = pi.dim;
+          g.so = po.site_state;
+          g.si = pi.site_state;
+          g.a_out = po.blk_sector;
+          g.a_in = pi.blk_sector;
+          g.n_in = site_first ? qnum(st.sq[pi.site_state]) : qnum(X.basis.qn[pi.blk_sector]);
+          g.nops = oc.nops;
+          g.term_ptr = d_ptr[ci];
+          // recoupling coefficient of every term type for these spins
+          const int tjx = su2::tj_of(X.basis.qn[pi.blk_sector]);
+          const int tjxp = su2::tj_of(X.basis.qn[po.blk_sector]);
+          const int tjs = st.tj[pi.site_state], tjsp = st.tj[po.site_state];
+          const size_t base = ctab.size();
+          ctab.resize(base + kCtypes, 0.0);
+          for (int tkX = 0; tkX <= 2; ++tkX)
+            for (int tkS = 0; tkS <= 2; ++tkS)
+              for (int tk = 0; tk <= 2; ++tk) {
+                if (((tkX + tkS + tk) & 1) || tk > tkX + tkS || tk < std::abs(tkX - tkS)) continue;
+                const double K = site_first
+                    ? su2::coupling(tjs, tjx, tJ, tjsp, tjxp, tJp, tkS, tkX, tk)
+                    : su2::coupling(tjx, tjs, tJ, tjxp, tjsp, tJp, tkX, tkS, tk);
+                ctab[base + ctype_of(tkX, tkS, tk, 0)] = K;
+                ctab[base + ctype_of(tkX, tkS, tk, 1)] = K * su2::adjoint_factor(tjx, tjxp, tkX);
+              }
+          g.ctab = reinterpret_cast<const double *>(base);   // offset, made a pointer below
+          subs.push_back(g);
+        }
+    }
+  }
+  double *d_ctab = upload(tmp, ctab, s);
+  for (GSub &g : subs) g.ctab = d_ctab + reinterpret_cast<size_t>(g.ctab);
   GSub *d_subs = upload(tmp, subs, s);
   CK(launch_gather(d_subs, (int)subs.size(), max_ops, d_terms, d_srcs, 4, s));
   CK(cudaStreamSynchronize(s));
@@ -928,7 +1416,7 @@ void upload_iso(dmrg_ctx *C, Iso &T) {
 
 // L_n = T_n^T (L_{n-1} x site_{n-1}) T_n
 void grow_left(dmrg_ctx *C, int n, const Iso &T) {
-  SitePart st = make_site(C, n - 1);
+  SitePart st = site_of(C, n - 1);
   BlockPart U;
   WinBuf ub(C->stream);
   enlarge(C, *C->L[n - 1], st, false, C->N - n, U, ub);
@@ -941,7 +1429,7 @@ void grow_left(dmrg_ctx *C, int n, const Iso &T) {
 
 // R_n = T_n^T (site_n x R_{n+1}) T_n
 void grow_right(dmrg_ctx *C, int n, const Iso &T) {
-  SitePart st = make_site(C, n);
+  SitePart st = site_of(C, n);
   BlockPart U;
   WinBuf ub(C->stream);
   enlarge(C, *C->R[n + 1], st, true, n, U, ub);
@@ -1022,7 +1510,7 @@ void build_window(dmrg_ctx *C, int l) {
   w.flops1 = w.flops2 = 0;
   double t0 = now();
   {
-    SitePart sl = make_site(C, l), sr = make_site(C, l + 1);
+    SitePart sl = site_of(C, l), sr = site_of(C, l + 1);
     enlarge(C, *C->L[l], sl, false, C->N - l - 1, w.Ld, w.ldbuf);
     enlarge(C, *C->R[l + 2], sr, true, l + 1, w.Rd, w.rdbuf);
   }
@@ -1032,7 +1520,7 @@ void build_window(dmrg_ctx *C, int l) {
   w.a2psi.assign(w.Ld.basis.qn.size(), -1);
   long long off = 0;
   for (size_t a = 0; a < w.Ld.basis.qn.size(); ++a) {
-    int b = w.Rd.basis.find(qsub(C->target, w.Ld.basis.qn[a]));
+    int b = w.Rd.basis.find(partner(C, w.Ld.basis.qn[a]));
     if (b < 0) continue;
     w.a2psi[a] = (int)w.psi.size();
     w.psi.push_back({(int)a, b, off, w.Ld.basis.dim[a], w.Rd.basis.dim[b]});
@@ -1061,7 +1549,59 @@ void build_window(dmrg_ctx *C, int l) {
     }
     w.hc[ci].terms.push_back({A, B, coef});
   };
-  formula_H(F, G, add, true);
+  if (C->su2) {
+    // spin-adapted: H = sum alpha [A^k (x) B^k]^0; component g of A (spin
+    // change 2(J_a' - J_a) = g) pairs with component g of B (total S = 0
+    // keeps J_a = J_b); adjoint tensors use the transposed component -g
+    const SU2Terms al = derive_su2(C, side_of(w.Ld), side_of(w.Rd), TKey{0, 0, 0, 0});
+    auto comp = [](const BlockPart &P, const TKey &k, int adj, int g) {
+      Fac f;
+      if (k.kind < 0) {
+        if (g == 0) f.kind = 2;
+        return f;
+      }
+      const TRef &tr = P.ten.at(k);
+      const Ref r = tr.r[((adj ? -g : g) + tr.tk) / 2];
+      if (r.cls < 0) return f;
+      f.kind = 1;
+      f.ref = r;
+      f.trans = adj;
+      f.shift = adj ? qneg(P.cls[r.cls].shift) : P.cls[r.cls].shift;
+      f.parity = P.cls[r.cls].parity;
+      return f;
+    };
+    for (auto &kv : al) {
+      const TKey &ka = std::get<0>(kv.first), &kb = std::get<2>(kv.first);
+      const int aa = std::get<1>(kv.first), ab = std::get<3>(kv.first);
+      const int tka = ka.kind < 0 ? 0 : ka.tk, tkb = kb.kind < 0 ? 0 : kb.tk;
+      if (tka != tkb) fail(DMRG_ERR_STATE, "internal: H_eff term of ranks %d, %d", tka, tkb);
+      for (int g = -tka; g <= tka; g += 2) {
+        const Fac A = comp(w.Ld, ka, aa, g), B = comp(w.Rd, kb, ab, g);
+        if (A.kind == 0 || B.kind == 0) continue;
+        if (su2::n_of(A.shift) + su2::n_of(B.shift) != 0 || su2::tj_of(A.shift) != su2::tj_of(B.shift))
+          fail(DMRG_ERR_STATE, "internal: spin-adapted H_eff term shift");
+        auto it = cidx.find(A.shift);
+        int ci;
+        if (it == cidx.end()) {
+          ci = (int)w.hc.size();
+          cidx[A.shift] = ci;
+          HClass h;
+          h.dA = A.shift;
+          h.pB = B.parity;
+          w.hc.push_back(h);
+        } else {
+          ci = it->second;
+        }
+        TermF t{A, B, kv.second};
+        t.tk = tka;
+        t.adjA = ka.kind < 0 ? 0 : aa;
+        t.adjB = kb.kind < 0 ? 0 : ab;
+        w.hc[ci].terms.push_back(t);
+      }
+    }
+  } else {
+    formula_H(F, G, add, true);
+  }
   // stacks and T layout
   long long nA = 0, nB = 0, nT = 0;
   std::vector<SCopy> cps;
@@ -1108,6 +1648,17 @@ void build_window(dmrg_ctx *C, int l) {
       memset(&b, 0, sizeof b);
       block_src(w.Rd, t.B, p.b, q.b, b);
       b.coef = t.coef * t.B.scale;
+      if (t.tk >= 0) {
+        // recoupling of [A^k (x) B^k]^0 between the window's coupled spins
+        // (and the adjoint factors of transposed blocks)
+        const int ja = su2::tj_of(w.Ld.basis.qn[p.a]), jap = su2::tj_of(w.Ld.basis.qn[q.a]);
+        const int jb = su2::tj_of(w.Rd.basis.qn[p.b]), jbp = su2::tj_of(w.Rd.basis.qn[q.b]);
+        const int tS = su2::tj_of(C->target);
+        double f = su2::coupling(ja, jb, tS, jap, jbp, tS, t.tk, t.tk, 0);
+        if (t.adjA) f *= su2::adjoint_factor(ja, jap, t.tk);
+        if (t.adjB) f *= su2::adjoint_factor(jb, jbp, t.tk);
+        b.coef *= f;
+      }
       b.rows = q.db;
       b.cols = p.db;
       b.dst = w.Bstack + h.b_off[e.pi] + (long long)k * p.db;
@@ -2436,6 +2987,11 @@ void truncate(dmrg_ctx *C, const double *psi, int side, int D, double *disc, dou
   for (size_t j = 0; j < keep; ++j) {
     double pj = cand[j].v / std::max(wk_keep, 1e-300);
     if (pj > 0) e -= pj * std::log(pj);
+    // a kept multiplet of spin j carries its weight in 2j+1 equal Schmidt values
+    if (C->su2 && pj > 0) {
+      const QN q = side == 0 ? w.Ld.basis.qn[w.psi[cand[j].sec].a] : w.Rd.basis.qn[w.psi[cand[j].sec].b];
+      e += pj * std::log(su2::tj_of(q) + 1.0);
+    }
   }
   if (disc) *disc = wk_tot - wk_keep;
   if (ent) *ent = e;
@@ -2742,7 +3298,7 @@ void sweep_impl(dmrg_ctx *C, int nsw, const int *dsched, double *E, cudaStream_t
     double *x = (double *)xb[cur].alloc(8 * std::max<long long>(n, 1));
     if (prev && prev_trunc == 2 && pm.l == l) {
       CK(cudaMemcpyAsync(x, prev, 8 * n, cudaMemcpyDeviceToDevice, s));
-    } else if (prev && (prev_trunc == 0 || prev_trunc == 1)) {
+    } else if (prev && (prev_trunc == 0 || prev_trunc == 1) && !C->su2) {
       stvec(C, pm, prev, prev_trunc, x, s);
     } else {
       CK(cudaMemsetAsync(x, 0, 8 * std::max<long long>(n, 1), s));
@@ -2802,8 +3358,11 @@ const char *dmrg_last_error(const dmrg_ctx *ctx) { return ctx ? ctx->err.c_str()
 int dmrg_create(dmrg_ctx **out, const dmrg_config *cfg) {
   if (!out || !cfg) return DMRG_ERR_ARG;
   *out = nullptr;
-  if ((cfg->sym != DMRG_U1 && cfg->sym != DMRG_U1U1) || cfg->n_sites < 2 || cfg->n_up < 0 ||
-      cfg->d_max < 1)
+  if ((cfg->sym != DMRG_U1 && cfg->sym != DMRG_U1U1 && cfg->sym != DMRG_U1SU2) ||
+      cfg->n_sites < 2 || cfg->n_up < 0 || cfg->d_max < 1)
+    return DMRG_ERR_ARG;
+  // spin-adapted windows are built for total spin S = 0 (N even)
+  if (cfg->sym == DMRG_U1SU2 && (cfg->twice_s != 0 || (cfg->n_up & 1) || cfg->n_up > 2 * cfg->n_sites))
     return DMRG_ERR_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -2815,10 +3374,12 @@ int dmrg_create(dmrg_ctx **out, const dmrg_config *cfg) {
   C->cfg = *cfg;
   if (C->cfg.davidson_max_sub < 4) C->cfg.davidson_max_sub = 20;
   if (C->cfg.davidson_max_iter < 1) C->cfg.davidson_max_iter = 200;
-  C->spinful = cfg->sym == DMRG_U1U1;
+  C->spinful = cfg->sym == DMRG_U1U1 || cfg->sym == DMRG_U1SU2;
+  C->su2 = cfg->sym == DMRG_U1SU2;
   C->N = cfg->n_sites;
   C->M = C->spinful ? 2 * C->N : C->N;
-  C->target = C->spinful ? QN{cfg->n_up, cfg->n_dn} : QN{cfg->n_up, 0};
+  C->target = C->su2 ? su2::label(cfg->n_up, cfg->twice_s)
+                     : (C->spinful ? QN{cfg->n_up, cfg->n_dn} : QN{cfg->n_up, 0});
   C->precision = cfg->precision;
   // pinned host status words for the stream-ordered time-out report
   if (cudaHostAlloc((void **)&C->hflag, 2 * sizeof(int), cudaHostAllocDefault) != cudaSuccess ||
@@ -3018,6 +3579,11 @@ int dmrg_set_isometry(dmrg_ctx *C, int side, int site, int ns, const int *qn, co
     long long off = 0;
     for (int k = 0; k < ns; ++k) {
       QN q{qn[k * nq], nq == 2 ? qn[k * nq + 1] : 0};
+      if (C->su2) {   // (N, 2J) -> highest-weight label
+        if (q[0] < 0 || q[1] < 0 || ((q[0] + q[1]) & 1) || q[1] > q[0])
+          fail(DMRG_ERR_ARG, "bad spin-adapted sector (%d, %d)", q[0], q[1]);
+        q = su2::label(q[0], q[1]);
+      }
       if (rows[k] < 1 || cols[k] < 1 || cols[k] > rows[k]) fail(DMRG_ERR_ARG, "bad isometry shape in sector %d", k);
       T.qn.push_back(q);
       T.rows.push_back(rows[k]);
@@ -3073,9 +3639,10 @@ int dmrg_heff_layout(dmrg_ctx *C, long long *psi_len, int *n_blocks, int *blocks
   if (blocks) {
     const int nq = C->spinful ? 2 : 1;
     int k = 0;
+    auto ext = [&](const QN &q) { return C->su2 ? QN{su2::n_of(q), su2::tj_of(q)} : q; };
     for (const PsiBlk &p : w.psi) {
-      for (int i = 0; i < nq; ++i) blocks[k++] = w.Ld.basis.qn[p.a][i];
-      for (int i = 0; i < nq; ++i) blocks[k++] = w.Rd.basis.qn[p.b][i];
+      for (int i = 0; i < nq; ++i) blocks[k++] = ext(w.Ld.basis.qn[p.a])[i];
+      for (int i = 0; i < nq; ++i) blocks[k++] = ext(w.Rd.basis.qn[p.b])[i];
       blocks[k++] = p.da;
       blocks[k++] = p.db;
     }
@@ -3382,8 +3949,9 @@ int dmrg_get_mps(dmrg_ctx *C, int side, int site, int *n_sectors, long long *n_e
     *n_sectors = (int)T.qn.size();
     *n_elems = tot;
     for (size_t k = 0; k < T.qn.size(); ++k) {
+      const QN q = C->su2 ? QN{su2::n_of(T.qn[k]), su2::tj_of(T.qn[k])} : T.qn[k];
       if (qn)
-        for (int i = 0; i < nq; ++i) qn[k * nq + i] = T.qn[k][i];
+        for (int i = 0; i < nq; ++i) qn[k * nq + i] = q[i];
       if (rows) rows[k] = T.rows[k];
       if (cols) cols[k] = T.cols[k];
     }

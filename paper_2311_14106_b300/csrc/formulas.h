@@ -103,13 +103,18 @@ inline Fac transpose(const Fac &f) {
 
 using AddFn = std::function<void(const Fac &, const Fac &, double)>;
 
-inline void add_hc(const AddFn &add, const Fac &A, const Fac &B, double c) {
+// The formulas below are templates over the part type (Side: spin-orbital
+// operators of the U(1) and U(1)xU(1) code; SideS in su2.h: spin-adapted
+// tensors) and the callback add(A, B, coef) that receives every product.
+template <class AddF, class FacT>
+void add_hc(const AddF &add, const FacT &A, const FacT &B, double c) {
   add(A, B, c);
   add(transpose(A), transpose(B), (A.parity & B.parity) ? -c : c);
 }
 
 // Cross terms of H^{F u G} - H^F - H^G (plus H^F x 1 and 1 x H^G if whole).
-inline void formula_H(const Side &F, const Side &G, const AddFn &add, bool whole) {
+template <class SideT, class AddF>
+void formula_H(const SideT &F, const SideT &G, const AddF &add, bool whole) {
   if (whole) {
     add(F.H(), G.I(), 1.0);
     add(F.I(), G.H(), 1.0);
@@ -140,12 +145,14 @@ inline bool has(const std::vector<int> &v, int x) {
   return false;
 }
 
-inline void formula_c(const Side &F, const Side &G, int x, const AddFn &add) {
+template <class SideT, class AddF>
+void formula_c(const SideT &F, const SideT &G, int x, const AddF &add) {
   if (has(F.modes(), x)) add(F.c(x), G.I(), 1.0);
   else add(F.I(), G.c(x), 1.0);
 }
 
-inline void formula_S(const Side &F, const Side &G, int y, const AddFn &add) {
+template <class SideT, class AddF>
+void formula_S(const SideT &F, const SideT &G, int y, const AddF &add) {
   add(F.S(y), G.I(), 1.0);
   add(F.I(), G.S(y), 1.0);
   for (int t : G.modes()) add(F.Q(y, t), G.c(t), -4.0);
@@ -154,14 +161,16 @@ inline void formula_S(const Side &F, const Side &G, int y, const AddFn &add) {
   for (int q : G.modes()) add(F.P(y, q), transpose(G.c(q)), 2.0);
 }
 
-inline void formula_cc(const Side &F, const Side &G, int p, int q, const AddFn &add) {
+template <class SideT, class AddF>
+void formula_cc(const SideT &F, const SideT &G, int p, int q, const AddF &add) {
   bool pf = has(F.modes(), p), qf = has(F.modes(), q);
   if (pf && qf) add(F.cc(p, q), G.I(), 1.0);
   else if (!pf && !qf) add(F.I(), G.cc(p, q), 1.0);
   else add(F.c(p), G.c(q), 1.0);   // p < q, so p in F and q in G
 }
 
-inline void formula_cdc(const Side &F, const Side &G, int p, int r, const AddFn &add) {
+template <class SideT, class AddF>
+void formula_cdc(const SideT &F, const SideT &G, int p, int r, const AddF &add) {
   bool pf = has(F.modes(), p), rf = has(F.modes(), r);
   if (pf && rf) add(F.cdc(p, r), G.I(), 1.0);
   else if (!pf && !rf) add(F.I(), G.cdc(p, r), 1.0);
@@ -169,8 +178,9 @@ inline void formula_cdc(const Side &F, const Side &G, int p, int r, const AddFn 
   else add(F.c(r), transpose(G.c(p)), -1.0);
 }
 
-inline void formula_P(const Side &F, const Side &G, int x, int z, const double *W, int M,
-                      const AddFn &add) {
+template <class SideT, class AddF>
+void formula_P(const SideT &F, const SideT &G, int x, int z, const double *W, int M,
+               const AddF &add) {
   add(F.P(x, z), G.I(), 1.0);
   add(F.I(), G.P(x, z), 1.0);
   for (int a : F.modes())
@@ -180,8 +190,9 @@ inline void formula_P(const Side &F, const Side &G, int x, int z, const double *
     }
 }
 
-inline void formula_Q(const Side &F, const Side &G, int x, int z, const double *W, int M,
-                      const AddFn &add) {
+template <class SideT, class AddF>
+void formula_Q(const SideT &F, const SideT &G, int x, int z, const double *W, int M,
+               const AddF &add) {
   add(F.Q(x, z), G.I(), 1.0);
   add(F.I(), G.Q(x, z), 1.0);
   for (int a : F.modes())

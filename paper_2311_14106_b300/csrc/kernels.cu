@@ -132,6 +132,7 @@ k_gather(const GSub *__restrict__ subs, const GTerm *__restrict__ terms,
         const GTerm &T = terms[ti];
         double w = T.m[sidx];
         if (w == 0.0) continue;
+        if (s.ctab) w *= s.ctab[T.ctype];
         if (T.p2 && odd_in) w = -w;
         double v;
         if (T.src < 0) {

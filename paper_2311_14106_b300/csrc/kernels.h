@@ -45,6 +45,8 @@ struct GTerm {
   int idx;     // operator index inside the source class
   int trans;   // use the transpose of the block operator
   int p2;      // parity of the second factor of the product
+  int ctype;   // spin-adapted parts: index into the sub-block's coefficient table
+  int pad;
   double m[16];  // site factor, 4x4 frame m[so*4+si], coefficient folded in
 };
 
@@ -61,6 +63,9 @@ struct GSub {
   int n_in;              // particle number used by the fermion sign
   int nops;
   const int *term_ptr;   // per op CSR into the term array (device)
+  // spin-adapted parts: recoupling coefficient of each term type (GTerm::ctype)
+  // for this sub-block's spins; NULL: all 1
+  const double *ctab;
 };
 
 // Copy (optionally transposed, scaled) operator blocks into a stack.

@@ -64,6 +64,30 @@ struct Ref {
 
 using PairKey = std::pair<int, int>;
 
+// Spin-adapted (U(1)xSU(2)) operators are SU(2) tensors; a tensor is named
+// by its kind (0 H, 1 c~, 2 S~, 3 A~, 4 B, 5 P, 6 Q, as the spin-orbital
+// OpSpec kinds), spatial indices and twice its rank.
+struct TKey {
+  int kind = 0, i = 0, j = 0, tk = 0;
+  bool operator<(const TKey &o) const {
+    if (kind != o.kind) return kind < o.kind;
+    if (i != o.i) return i < o.i;
+    if (j != o.j) return j < o.j;
+    return tk < o.tk;
+  }
+  bool operator==(const TKey &o) const {
+    return kind == o.kind && i == o.i && j == o.j && tk == o.tk;
+  }
+  int parity() const { return (kind == 1 || kind == 2) ? 1 : 0; }
+};
+
+// A tensor of rank k stored as its spin-change components J' - J = -k..k:
+// r[(2(J'-J) + 2k) / 2], each a block-sparse operator of one class.
+struct TRef {
+  int tk = 0;
+  Ref r[3];
+};
+
 // A renormalized block, an enlarged block (block x site) or the vacuum.
 struct BlockPart {
   Basis basis;
@@ -72,6 +96,7 @@ struct BlockPart {
   Ref H;
   std::map<int, Ref> c, S;
   std::map<PairKey, Ref> cc, cdc, P, Q;
+  std::map<TKey, TRef> ten;   // spin-adapted parts: all operators as tensors
   // enlarged blocks only
   bool enlarged = false;
   int site_first = 0;
@@ -91,6 +116,14 @@ struct SiteOp {
   double m[16] = {0};
 };
 
+// Reduced matrix of a site tensor between the site multiplets (3 x 3 used in
+// the 4 x 4 frame, m[so*4 + si]).
+struct SiteTen {
+  int tk = 0;
+  int parity = 0;
+  double m[16] = {0};
+};
+
 struct SitePart {
   int site = 0;
   int d = 2;
@@ -99,6 +132,8 @@ struct SitePart {
   SiteOp H, I;
   std::map<int, SiteOp> c, S;
   std::map<PairKey, SiteOp> cc, cdc, P, Q;
+  std::map<TKey, SiteTen> ten;   // spin-adapted site: multiplets {0}, {up,dn}, {updn}
+  std::vector<int> tj;           // spin-adapted site: twice the spin of each multiplet
 };
 
 // Factor of an operator product: block op / block identity / site matrix.
