@@ -28,16 +28,28 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 WORKLOADS = {
-    # name: (model, Lx, Ly, particles (up, dn), U or V, D, description)
-    "hubbard6x6_D1024": ("hubbard", 6, 6, (18, 18), 4.0, 1024,
+    # name: (model, Lx, Ly, particles, U or V, D, symmetry, Haar seed of the
+    #        rotation or None, description)
+    "hubbard6x6_su2_D1024": ("hubbard", 6, 6, (36, 0), 4.0, 1024, "su2", None,
+                             "Hubbard 6x6 torus, half filling (36 e, S=0), t=1, U=4, momentum "
+                             "basis, U(1)xSU(2) spin-adapted, D=1024 SU(2) multiplets, middle "
+                             "window l=17, psi random normal in every allowed sector (seed 1)"),
+    "hubbard8x8_su2_D2048": ("hubbard", 8, 8, (56, 0), 4.0, 2048, "su2", 2,
+                             "Hubbard 8x8 torus, filling 0.875 (56 e, S=0), t=1, U=4, momentum "
+                             "basis times a seeded Haar rotation (seed 2), U(1)xSU(2), D=2048 "
+                             "multiplets, middle window l=31"),
+    "hubbard6x6_D1024": ("hubbard", 6, 6, (18, 18), 4.0, 1024, "u1u1", None,
                          "Hubbard 6x6 torus, 36 e (S_z=0), t=1, U=4, momentum basis, "
                          "U(1)xU(1), D=1024 states, middle window l=17"),
-    "hubbard6x6_D512": ("hubbard", 6, 6, (18, 18), 4.0, 512,
-                        "Hubbard 6x6 torus, 36 e, U=4, momentum basis, U(1)xU(1), D=512"),
-    "spinless4x4_D128": ("spinless", 4, 4, (8, 0), 1.0, 128,
+    "spinless4x4_D128": ("spinless", 4, 4, (8, 0), 1.0, 128, "u1", None,
                          "spinless t-V 4x4 torus, N=8, t=1, V=1, momentum basis, U(1), D=128"),
 }
-CPU_SAMPLE = ("hubbard", 4, 4, (8, 8), 4.0, 64)
+# The oracle cannot build the blocks of the 6x6 windows in bench time: at D = 8
+# multiplets the 6x6 middle window alone takes about 100 s of block building
+# on one core (72 spin-orbitals: ~5e3 complementary operators per block), and
+# its cost grows as D^2 N^2.  Its H_eff*psi is timed on the 4x4 lattice of the
+# same model instead.
+CPU_SAMPLE = ("hubbard", 4, 4, 16, 4.0, 32)
 
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM traffic per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, one
@@ -130,42 +142,57 @@ def job_value(flops_per_step, ms, world):
 
 
 def build_problem(lib, wl, dev_stream):
-    model, Lx, Ly, (nu, nd), coup, D, _ = wl
-    spinful = model == "hubbard"
+    model, Lx, Ly, (nu, nd), coup, D, sym, rot, _ = wl
     N = Lx * Ly
-    target = (nu, nd) if spinful else (nu,)
-    if spinful:
+    if model == "hubbard":
         T, V = lib.lattice_hamiltonian(lib.MODEL_HUBBARD, Lx, Ly, 1.0, 0.0, coup)
     else:
         T, V = lib.lattice_hamiltonian(lib.MODEL_SPINLESS_TV, Lx, Ly, 1.0, 0.0, coup)
     U = lib.momentum_basis(Lx, Ly)
+    if rot is not None:
+        U = U @ synth.haar_rotation(N, rot)
     l = N // 2 - 1
-    g = lib.Dmrg(N, nu, nd, spinful=spinful, d_max=D, davidson_tol=1e-6, davidson_max_sub=24,
-                 davidson_max_iter=400)
+    kw = dict(d_max=D, davidson_tol=1e-6, davidson_max_sub=24, davidson_max_iter=400)
+    if sym == "su2":
+        g = lib.Dmrg(N, nu, su2=True, **kw)
+        li = synth.random_left_isometries_su2(N, (nu, 0), D, l, 5)
+        ri = synth.random_right_isometries_su2(N, (nu, 0), D, l + 2, 6)
+    else:
+        spinful = sym == "u1u1"
+        target = (nu, nd) if spinful else (nu,)
+        g = lib.Dmrg(N, nu, nd, spinful=spinful, **kw)
+        li = synth.random_left_isometries(N, spinful, target, D, l, 5)
+        ri = synth.random_right_isometries(N, spinful, target, D, l + 2, 6)
     g.set_hamiltonian(T, V, U)
-    g.set_mps(synth.random_left_isometries(N, spinful, target, D, l, 5),
-              synth.random_right_isometries(N, spinful, target, D, l + 2, 6))
+    g.set_mps(li, ri)
     t0 = time.time()
     g.build_block_ops(l, dev_stream)
     return g, l, time.time() - t0
 
 
 def cpu_baseline(budget_s=15.0):
-    """The FP64 oracle's H_eff*psi on a bounded sample (single process)."""
+    """The FP64 oracle's spin-adapted H_eff*psi on a bounded sample (one
+    process).  Its spin-adapted sigma goes through the U(1)xU(1) window of the
+    Clebsch-Gordan-expanded MPS; the rate counts the flops of that window's
+    products (the oracle's own arithmetic, more than the spin-adapted count of
+    the same sigma, so the rate is an upper bound in the library's units)."""
     from oracle import dmrg as odmrg
-    from oracle import hamiltonian, lattice
-    model, L, _, (nu, nd), U, D = CPU_SAMPLE
+    from oracle import hamiltonian, lattice, su2
+    model, L, _, ne, U, D = CPU_SAMPLE
     N = L * L
     T, V = lattice.hubbard(L, L, 1.0, U)
     T, V = lattice.rotate(T, V, lattice.momentum_basis(L, L))
     h, W = hamiltonian.spin_orbital(T, V, True)
-    m = odmrg.Model(h, W, True, (nu, nd))
+    m = odmrg.Model(h, W, True, (ne // 2, ne // 2))
     l = N // 2 - 1
-    w = odmrg.window_from_mps(m, synth.random_left_isometries(N, True, (nu, nd), D, l, 5),
-                              synth.random_right_isometries(N, True, (nu, nd), D, l + 2, 6), l)
+    t_build = time.time()
+    w = su2.Su2Window(m, N, (ne, 0), synth.random_left_isometries_su2(N, (ne, 0), D, l, 5),
+                      synth.random_right_isometries_su2(N, (ne, 0), D, l + 2, 6), l)
+    t_build = time.time() - t_build
+    wz = w.wz
     flops = 0.0
-    for A, B, c in w.terms:
-        for qa, qb, o, da, db in w.layout:
+    for A, B, c in wz.terms:
+        for qa, qb, o, da, db in wz.layout:
             a, b = A.blocks.get(qa), B.blocks.get(qb)
             if a is None or b is None:
                 continue
@@ -178,9 +205,31 @@ def cpu_baseline(budget_s=15.0):
     dt = (time.time() - t0) / n
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-            "sample": f"oracle H_eff*psi, Hubbard {L}x{L} U={U} momentum basis, U(1)xU(1), "
-                      f"D={D}, middle window (psi_len {w.size}), {n} applies in {n * dt:.1f} s",
+            "sample": f"oracle spin-adapted H_eff*psi, Hubbard {L}x{L} U={U} {ne} e S=0, momentum "
+                      f"basis, U(1)xSU(2), D={D} multiplets, middle window (psi_len {w.size}; "
+                      f"S_z window {wz.size}), {n} applies in {n * dt:.1f} s after a "
+                      f"{t_build:.0f} s block build; flops of the S_z products",
             "ms_per_apply": dt * 1e3}
+
+
+def c1_sweeps(lib, stream):
+    """Config C1: spinless t-V 4x4 torus, N = 8, V = 1, momentum basis, U(1),
+    D = 128, FP64 throughout, 6 sweeps from a seeded random MPS; seconds per
+    sweep and per matvec (the library's Sec. III.B time breakdown)."""
+    T, V = lib.lattice_hamiltonian(lib.MODEL_SPINLESS_TV, 4, 4, 1.0, 0.0, 1.0)
+    g = lib.Dmrg(16, 8, d_max=128, precision=lib.FP64, davidson_tol=1e-8, seed=0)
+    g.set_hamiltonian(T, V, lib.momentum_basis(4, 4))
+    g.set_mps(right=synth.random_right_isometries(16, False, (8,), 128, 1, 0))
+    t0 = time.perf_counter()
+    E = g.sweep(6, stream=stream)
+    wall = time.perf_counter() - t0
+    prof = g.profile()
+    g.close()
+    return {"energies": E.tolist(), "seconds": wall, "seconds_per_sweep": wall / 6,
+            "matvecs": int(prof["n_matvec"]),
+            "ms_per_matvec": 1e3 * prof["Diag_H"] / max(prof["n_matvec"], 1),
+            "profile_s": {k: v for k, v in prof.items() if k != "n_matvec"},
+            "converged": bool(g.sweep_converged)}
 
 
 def run_reference(args, rank, world):
@@ -194,7 +243,7 @@ def run_reference(args, rank, world):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": cb["ms_per_apply"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": args.workload, "description": wl[6],
+            "config": {"workload": args.workload, "description": wl[8],
                        "reference_sample": cb["sample"]},
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
@@ -208,10 +257,11 @@ def main():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="hubbard6x6_D1024", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="hubbard6x6_su2_D1024", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-c1", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -304,8 +354,10 @@ def main():
         from paper_2311_14106_b300 import serving as srvmod
         mix = [("spinless", 4, 4, (0.0, 4.0), [64, 128]), ("hubbard", 4, 4, (0.0, 8.0), [64, 128])]
         serving_out = {"stream": "12 requests, exponential inter-arrival mean 0.1 s (seed 3); "
-                                 "spinless 4x4 V~U[0,4] and Hubbard 4x4 U~U[0,8], D in {64,128}, "
-                                 "2 sweeps each, 4 slots"}
+                                 "spinless 4x4 V~U[0,4] (U(1), D states) and Hubbard 4x4 "
+                                 "U~U[0,8] (U(1)xSU(2), D multiplets), D in {64,128}, 2 sweeps "
+                                 "each, 4 slots; the 64-request 6x6/8x8 stream with D up to "
+                                 "2048 takes hours on the FP64 arm"}
         # untimed warm-up with the stream's own shapes: loads the eigensolver and
         # kernel modules (lazily, per kernel) once per process, so that neither
         # arm pays it
@@ -318,6 +370,10 @@ def main():
             serving_out[name] = srv.run(reqs)
         serving_out["solves_per_s_ratio_split_over_fp64"] = (
             serving_out["split"]["solves_per_s"] / max(serving_out["fp64"]["solves_per_s"], 1e-12))
+    # config C1 (4x4 spinless, D = 128, FP64, 6 sweeps): per sweep and per matvec
+    c1 = None
+    if not args.no_c1 and rank == 0:
+        c1 = c1_sweeps(lib, stream)
     hbm, bf16, src = peaks()
     tc_peak = bf16 * F16_OVER_BF16
     si = g.heff_stage_info()
@@ -340,7 +396,7 @@ def main():
         "ms_per_step": ms_split, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "fp16 hi+lo split with per-block power-of-two scales, 3 products (fp32 accumulate), fp64 in/out",
         "data": "synthetic",
-        "config": {"workload": args.workload, "description": wl[6], "psi_len": n,
+        "config": {"workload": args.workload, "description": wl[8], "psi_len": n,
                    "algorithmic_flops_per_step": flops, "l2": "operator stacks >> L2; no flush",
                    "parallelism": f"replicas x{world}", "block_build_seconds": t_build},
         "fp64": {"ms_per_step": ms_64, "tflops": flops / (ms_64 * 1e-3) / 1e12,
@@ -351,6 +407,7 @@ def main():
         "sigma_rel_diff_split_vs_fp64": err_sigma,
         "solve": solve,
         "serving": serving_out,
+        "c1_spinless4x4_D128_fp64_6_sweeps": c1,
         "e2e": {"value": world * flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
                 "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n, "ms_per_step": e2e_ms},
         "clocks": clocks,

@@ -3084,7 +3084,8 @@ int iso_find(const Iso &T, const QN &q) {
 
 void push_gemm(std::vector<GemmDesc> &dd, std::vector<GemmSeg> &gg, long long &tt, double *Cp,
                long long c_rs, int M, int N, int K, const double *A, long long a_rs,
-               long long a_cs, const double *Bp, long long b_rs, long long b_cs) {
+               long long a_cs, const double *Bp, long long b_rs, long long b_cs,
+               double alpha = 1.0) {
   if (M <= 0 || N <= 0) return;
   GemmSeg g;
   memset(&g, 0, sizeof g);
@@ -3097,7 +3098,7 @@ void push_gemm(std::vector<GemmDesc> &dd, std::vector<GemmSeg> &gg, long long &t
   d.M = M; d.N = N; d.batch = 1;
   d.seg0 = (int)gg.size(); d.nseg = 1;
   d.tiles_m = (M + 63) / 64; d.tiles_n = (N + 63) / 64;
-  d.alpha = 1.0; d.beta = 0.0;
+  d.alpha = alpha; d.beta = 0.0;
   d.tile0 = tt;
   tt += (long long)d.tiles_m * d.tiles_n;
   gg.push_back(g);
@@ -3116,7 +3117,10 @@ void run_gemms(std::vector<GemmDesc> &dd, std::vector<GemmSeg> &gg, long long tt
 // side 0: old window l was truncated to the left (L_{l+1} = U^T L.); the guess
 // for window l+1 is psi'[(l', s1), (s2, r')] = sum_r (U^T psi)[l', (s1, r)] TR[(s2, r'), r]
 // with TR the isometry of R_{l+2}.  side 1 mirrors it with V (R_{l+1}) and TL
-// (the isometry of L_l).
+// (the isometry of L_l).  Spin-adapted windows also recouple the three spins
+// of L, the moved site and R: |(L (s R) b) S> -> |((L s) a R) S> with the
+// coefficient <((L s) a R) S | (L (s R) b) S> (and its transpose for side 1).
+inline int site_tj(int k) { return k == 1 ? 1 : 0; }   // spin-adapted site multiplets
 void stvec(dmrg_ctx *C, const WinMeta &old, const double *psi_old, int side, double *psi_new,
            cudaStream_t s) {
   Window &w = C->win;
@@ -3157,6 +3161,7 @@ void stvec(dmrg_ctx *C, const WinMeta &old, const double *psi_old, int side, dou
     gg.clear();
     tt = 0;
     const BlockPart &Lnew = *C->L[old.l + 1];
+    const BlockPart &R2 = *C->R[old.l + 2];
     for (const PsiBlk &P : w.psi) {
       const int dB = w.Rd.basis.dim[P.b];
       for (const Piece &pc : w.Ld.pieces[P.a]) {
@@ -3167,15 +3172,21 @@ void stvec(dmrg_ctx *C, const WinMeta &old, const double *psi_old, int side, dou
         const PsiBlk &p = old.psi[pi];
         const Piece *rp = nullptr;
         for (const Piece &q : old.Rp[p.b])
-          if (q.site_state == pc.site_state) rp = &q;
+          if (q.site_state == pc.site_state &&
+              (!C->su2 || R2.basis.qn[q.blk_sector] == w.Rd.basis.qn[P.b]))
+            rp = &q;
         if (!rp) continue;
-        const BlockPart &R2 = *C->R[old.l + 2];
         const QN qr = R2.basis.qn[rp->blk_sector];
         if (qr != w.Rd.basis.qn[P.b]) continue;
         int ti = iso_find(TR, qr);
         if (ti < 0 || TR.rows[ti] != dB) continue;
+        double f = 1.0;
+        if (C->su2)
+          f = su2::recouple(su2::tj_of(Lnew.basis.qn[pc.blk_sector]), site_tj(pc.site_state),
+                            su2::tj_of(qr), su2::tj_of(w.Ld.basis.qn[P.a]), su2::tj_of(old.Rb.qn[p.b]),
+                            su2::tj_of(C->target));
         push_gemm(dd, gg, tt, psi_new + P.off + (long long)pc.off * dB, dB, pc.dim, dB, rp->dim,
-                  X + xo[pi] + rp->off, p.db, 1, TR.d + TR.off[ti], 1, TR.cols[ti]);
+                  X + xo[pi] + rp->off, p.db, 1, TR.d + TR.off[ti], 1, TR.cols[ti], f);
       }
     }
     run_gemms(dd, gg, tt, s);
@@ -3212,10 +3223,12 @@ void stvec(dmrg_ctx *C, const WinMeta &old, const double *psi_old, int side, dou
       int ti = iso_find(TL, qA);
       if (ti < 0 || TL.rows[ti] != dA) continue;
       for (const Piece &pc : w.Rd.pieces[P.b]) {
-        // old L. sector holding (site state, L_l sector with QN qA)
-        int ib = old.Rb.find(Rnew.basis.qn[pc.blk_sector]);
-        (void)ib;
-        const QN qa_old = qadd(qA, qsub(w.Rd.basis.qn[P.b], Rnew.basis.qn[pc.blk_sector]));
+        // old L. sector holding (site state, L_l sector with QN qA): spin-
+        // adapted, the one whose spin pairs with the R_{l+1} sector's
+        const QN qR = Rnew.basis.qn[pc.blk_sector];
+        const QN qa_old = C->su2 ? su2::label(su2::n_of(qA) + (pc.site_state == 0 ? 0 : pc.site_state == 1 ? 1 : 2),
+                                              su2::tj_of(qR))
+                                 : qadd(qA, qsub(w.Rd.basis.qn[P.b], qR));
         int ia = old.Lb.find(qa_old);
         if (ia < 0 || !a2p.count(ia)) continue;
         int pi = a2p[ia];
@@ -3223,13 +3236,16 @@ void stvec(dmrg_ctx *C, const WinMeta &old, const double *psi_old, int side, dou
         const PsiBlk &p = old.psi[pi];
         const Piece *lp = nullptr;
         for (const Piece &q : old.Lp[p.a])
-          if (q.site_state == pc.site_state) lp = &q;
+          if (q.site_state == pc.site_state && C->L[old.l]->basis.qn[q.blk_sector] == qA) lp = &q;
         if (!lp) continue;
-        if (C->L[old.l]->basis.qn[lp->blk_sector] != qA) continue;
         if (ky[pi] != pc.dim) continue;
+        double f = 1.0;
+        if (C->su2)
+          f = su2::recouple(su2::tj_of(qA), site_tj(pc.site_state), su2::tj_of(qR), su2::tj_of(qa_old),
+                            su2::tj_of(w.Rd.basis.qn[P.b]), su2::tj_of(C->target));
         push_gemm(dd, gg, tt, psi_new + P.off + pc.off, dB, dA, pc.dim, lp->dim,
                   TL.d + TL.off[ti], TL.cols[ti], 1, Y + yo[pi] + (long long)lp->off * ky[pi],
-                  ky[pi], 1);
+                  ky[pi], 1, f);
       }
     }
     run_gemms(dd, gg, tt, s);
@@ -3298,7 +3314,7 @@ void sweep_impl(dmrg_ctx *C, int nsw, const int *dsched, double *E, cudaStream_t
     double *x = (double *)xb[cur].alloc(8 * std::max<long long>(n, 1));
     if (prev && prev_trunc == 2 && pm.l == l) {
       CK(cudaMemcpyAsync(x, prev, 8 * n, cudaMemcpyDeviceToDevice, s));
-    } else if (prev && (prev_trunc == 0 || prev_trunc == 1) && !C->su2) {
+    } else if (prev && (prev_trunc == 0 || prev_trunc == 1)) {
       stvec(C, pm, prev, prev_trunc, x, s);
     } else {
       CK(cudaMemsetAsync(x, 0, 8 * std::max<long long>(n, 1), s));

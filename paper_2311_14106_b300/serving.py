@@ -35,6 +35,7 @@ class Request:
     arrival: float        # seconds after the stream starts
     seed: int = 0
     filling: tuple = None  # (n_up, n_dn); default half filling / S_z = 0
+    su2: bool = True       # hubbard: spin-adapted sectors, D counts multiplets
 
 
 @dataclass
@@ -74,6 +75,10 @@ def estimate_bytes(req):
     d = 4 if req.model == "hubbard" else 2
     nsec = max(4.0, (M / 4.0) ** (2 if req.model == "hubbard" else 1))
     per_op = 8.0 * req.D * req.D / nsec
+    if req.model == "hubbard" and req.su2:
+        # multiplet blocks: fewer sectors, and half the tensors of the
+        # spin-orbital operator set
+        per_op = 8.0 * req.D * req.D / max(4.0, M / 4.0) / 2.0
     blocks = N * 2.0 * M * M * per_op
     window = 6.0 * d * d * M * M * per_op
     return 1.5 * (blocks + window) + 256e6
@@ -89,16 +94,25 @@ def run_one(req, precision, stream=None, davidson_tol=1e-7, rng_iso=None):
         T, V = lattice_hamiltonian(MODEL_HUBBARD, req.Lx, req.Ly, 1.0, 0.0, req.coupling)
     else:
         T, V = lattice_hamiltonian(MODEL_SPINLESS_TV, req.Lx, req.Ly, 1.0, 0.0, req.coupling)
-    g = Dmrg(N, tgt[0], tgt[1] if spinful else 0, spinful=spinful, d_max=req.D,
-             precision=precision, davidson_tol=davidson_tol, seed=req.seed)
+    su2 = spinful and req.su2 and tgt[0] == tgt[1]
+    if su2:
+        g = Dmrg(N, tgt[0] + tgt[1], su2=True, d_max=req.D, precision=precision,
+                 davidson_tol=davidson_tol, seed=req.seed)
+    else:
+        g = Dmrg(N, tgt[0], tgt[1] if spinful else 0, spinful=spinful, d_max=req.D,
+                 precision=precision, davidson_tol=davidson_tol, seed=req.seed)
     # Concurrent solves launch directly: a CUDA-graph capture in one thread can
     # be invalidated by device-synchronising calls (allocation, stream
     # creation) made by the other solves' threads.
     g.set_graphs(False)
     try:
         g.set_hamiltonian(T, V, momentum_basis(req.Lx, req.Ly))
-        g.set_mps(right=synth.random_right_isometries(N, spinful, tgt if spinful else (tgt[0],),
-                                                      req.D, 1, req.seed))
+        if su2:
+            g.set_mps(right=synth.random_right_isometries_su2(N, (tgt[0] + tgt[1], 0), req.D, 1,
+                                                              req.seed))
+        else:
+            g.set_mps(right=synth.random_right_isometries(N, spinful, tgt if spinful else (tgt[0],),
+                                                          req.D, 1, req.seed))
         E = g.sweep(req.n_sweeps, stream=stream)
         prof = g.profile()
     finally:

@@ -56,7 +56,9 @@ def test_same_result_alone_and_in_the_mix(prec):
     reqs = serving.poisson_stream(6, 0.02, 11, mix, sweeps=2)
     for r in reqs:
         if r.model == "hubbard":
-            r.filling = (5, 4)
+            # S_z = 1/2 runs in U(1)xU(1) sectors, S = 0 spin-adapted
+            r.filling = (5, 4) if r.rid % 2 else (4, 4)
+    assert {r.filling for r in reqs if r.model == "hubbard"} == {(5, 4), (4, 4)}
     srv = serving.Server(precision=prec, slots=3, hbm_budget=50e9, davidson_tol=1e-9)
     out = srv.run(reqs)
     assert out["solves"] == len(reqs) and out["errors"] == 0, srv.errors
