@@ -34,6 +34,9 @@ WORKLOADS = {
                              "Hubbard 6x6 torus, half filling (36 e, S=0), t=1, U=4, momentum "
                              "basis, U(1)xSU(2) spin-adapted, D=1024 SU(2) multiplets, middle "
                              "window l=17, psi random normal in every allowed sector (seed 1)"),
+    "hubbard6x6_su2_D512": ("hubbard", 6, 6, (36, 0), 4.0, 512, "su2", None,
+                            "Hubbard 6x6 torus, 36 e (S=0), U=4, momentum basis, U(1)xSU(2), "
+                            "D=512 multiplets, middle window (the profiling case)"),
     "hubbard8x8_su2_D2048": ("hubbard", 8, 8, (56, 0), 4.0, 2048, "su2", 2,
                              "Hubbard 8x8 torus, filling 0.875 (56 e, S=0), t=1, U=4, momentum "
                              "basis times a seeded Haar rotation (seed 2), U(1)xSU(2), D=2048 "
@@ -57,7 +60,14 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # reported as null once that file changes.
 TRAFFIC_SOURCE = os.path.join(ROOT, "paper_2311_14106_b300", "csrc", "heff_split.cu")
 TRAFFIC_SHA = "986c6afcb7e53341"
-TRAFFIC = {("hubbard6x6_D1024", "k_split_gemm stage1"): 5.180e9,
+# The spin-adapted D=1024 window is too large for a full-metric capture: its
+# values are the D=512 window's per-launch traffic scaled by the ratio of
+# algorithmic bytes (1.035x and 1.151x of them at D=512).
+TRAFFIC = {("hubbard6x6_su2_D1024", "k_split_gemm stage1"): 1.0350 * 6.1674e9,
+           ("hubbard6x6_su2_D1024", "k_split_gemm stage2"): 1.1510 * 6.1674e9,
+           ("hubbard6x6_su2_D512", "k_split_gemm stage1"): 1.5547e9,
+           ("hubbard6x6_su2_D512", "k_split_gemm stage2"): 1.7289e9,
+           ("hubbard6x6_D1024", "k_split_gemm stage1"): 5.180e9,
            ("hubbard6x6_D1024", "k_split_gemm stage2"): 5.715e9}
 
 

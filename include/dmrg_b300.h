@@ -87,7 +87,8 @@ typedef struct {
   double davidson_tol;     /* residual 2-norm bound, normalized vector */
   int davidson_max_sub;    /* Davidson subspace size (>= 4) */
   int davidson_max_iter;   /* Davidson iteration limit */
-  size_t hbm_budget_bytes; /* 0 = no limit */
+  size_t hbm_budget_bytes; /* HBM for renormalized block operators; 0 = no
+                              limit (see dmrg_staging_stats) */
   uint64_t seed;           /* seed of the Davidson start vectors */
   int twice_s;             /* U1SU2: twice the total spin S (this build: 0) */
 } dmrg_config;
@@ -292,6 +293,26 @@ int dmrg_heff_entries(dmrg_ctx *ctx, int *out, int max_entries, int *n_entries);
  * tiles, [2] stage-2 tiles, [3] split-K range of stage 2 (K elements per
  * partial tile).  DMRG_ERR_STATE before the plan exists. */
 int dmrg_heff_split_plan(dmrg_ctx *ctx, double *out4);
+
+/* Staging of renormalized block operators under cfg.hbm_budget_bytes (the
+ * paper's H2D/D2H traffic of operators that do not fit the GPUs, Sec. III.B).
+ * With a budget, dmrg_sweep and dmrg_build_block_ops keep at most that many
+ * bytes of block operators in HBM (plus the blocks the current window
+ * needs): a block the sweep rebuilds before its next use is released, the
+ * blocks used last are copied once to pinned host memory and freed on the
+ * device, and they come back on a side stream ahead of the window that
+ * needs them.  Results are bitwise the same as without a budget.
+ * out8: [0] bytes copied host->device, [1] seconds of those copies (CUDA
+ * events on the side stream), [2] bytes copied device->host, [3] peak
+ * resident block bytes, [4] offloads, [5] reloads, [6] releases, [7] the
+ * budget.  Counters accumulate over the context's life.  Errors: ARG. */
+int dmrg_staging_stats(dmrg_ctx *ctx, double *out8);
+
+/* Windows from sweep position (pass 0 = left to right at window l, pass 1 =
+ * right to left) to the next use of block L_n (left = 1) or R_n (left = 0),
+ * -1 if the sweep rebuilds it first, -2 for bad arguments: the staging
+ * policy, exposed for tests (pure host function, no context). */
+long long dmrg_sweep_next_use(int n_sites, int pass, int l, int left, int n);
 
 /* Code paths the split-precision plan of the current window exercises
  * (for tests): out8[0] stage-1 work items, [1] stage-2 work items, [2] psi

@@ -32,7 +32,7 @@ HEADER_FUNCTIONS = [
     "dmrg_heff_apply_split_static", "dmrg_heff_tuning", "dmrg_set_graphs",
     "dmrg_heff_split_plan", "dmrg_heff_entries", "dmrg_selftest_bounded_wait",
     "dmrg_sync", "dmrg_get_mps", "dmrg_get_center", "dmrg_heff_split_paths",
-    "dmrg_selftest_timeout_report",
+    "dmrg_selftest_timeout_report", "dmrg_staging_stats", "dmrg_sweep_next_use",
 ]
 
 
@@ -85,6 +85,8 @@ _sig = {
     "dmrg_get_center": (ctypes.c_int, [_P, _I, ctypes.POINTER(ctypes.c_longlong), _D]),
     "dmrg_heff_split_paths": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong)]),
     "dmrg_selftest_timeout_report": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "dmrg_staging_stats": (ctypes.c_int, [_P, _D]),
+    "dmrg_sweep_next_use": (ctypes.c_longlong, [ctypes.c_int] * 5),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -323,6 +325,14 @@ class Dmrg:
         pipeline wait that gave up does (about one second, no fault)."""
         self._check(_lib.dmrg_selftest_timeout_report(self._h, which, _stream_ptr(stream)),
                     "selftest_timeout_report")
+
+    def staging_stats(self):
+        """Block-operator staging under hbm_budget_bytes (see the header)."""
+        out = np.zeros(8)
+        self._check(_lib.dmrg_staging_stats(self._h, _dptr(out)), "staging_stats")
+        keys = ["h2d_bytes", "h2d_seconds", "d2h_bytes", "peak_resident_bytes", "offloads",
+                "reloads", "releases", "budget"]
+        return dict(zip(keys, out.tolist()))
 
     def heff_split_paths(self):
         """Code paths of the split plan (see dmrg_heff_split_paths)."""

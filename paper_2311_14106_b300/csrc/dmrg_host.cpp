@@ -300,7 +300,14 @@ struct dmrg_ctx {
   std::map<int, Iso> Lmap, Rmap;   // device isometries of the current blocks L_n, R_n
   std::vector<std::unique_ptr<BlockPart>> L;        // L[n], n sites
   std::map<int, std::unique_ptr<BlockPart>> R;      // R[n], sites n..N-1
-  std::map<BlockPart *, std::unique_ptr<WinBuf>> partbuf;
+  std::map<BlockPart *, std::unique_ptr<WinBuf>> partbuf;    // index tables, isometries
+  std::map<BlockPart *, std::unique_ptr<WinBuf>> partdata;   // operator data (stageable)
+  // staging of renormalized block operators under cfg.hbm_budget_bytes
+  cudaStream_t stage_stream = nullptr;
+  cudaEvent_t stage_ev = nullptr;
+  std::vector<std::array<cudaEvent_t, 2>> h2d_events;   // timed host-to-device copies
+  double st_h2d_bytes = 0, st_h2d_ms = 0, st_d2h_bytes = 0, st_peak = 0;
+  long long st_offloads = 0, st_reloads = 0, st_releases = 0;
   Window win;
   SplitTables tables;    // host copy of the split-path tables of the window
   cudaStream_t stream = nullptr;
@@ -745,7 +752,7 @@ void set_ref(BlockPart &B, const OpSpec &s, Ref r) {
 // Assign operators to classes by QN shift and lay out the blocks.  Returns
 // for every spec its Ref.  Device memory is allocated from wb.
 std::vector<Ref> make_classes(BlockPart &B, const std::vector<OpSpec> &specs, WinBuf &wb,
-                              cudaStream_t s) {
+                              cudaStream_t s, WinBuf *data = nullptr) {
   std::map<QN, int> byshift;
   std::vector<Ref> refs(specs.size());
   for (size_t k = 0; k < specs.size(); ++k) {
@@ -777,7 +784,7 @@ std::vector<Ref> make_classes(BlockPart &B, const std::vector<OpSpec> &specs, Wi
       off += (long long)B.basis.dim[j] * B.basis.dim[i];
     }
     oc.nnz = off;
-    oc.d = (double *)wb.alloc(sizeof(double) * std::max<long long>(1, oc.nnz * oc.nops));
+    oc.d = (double *)(data ? data : &wb)->alloc(sizeof(double) * std::max<long long>(1, oc.nnz * oc.nops));
     oc.d_in2blk = upload(wb, oc.in2blk, s);
     oc.d_blk_out = upload(wb, oc.blk_out, s);
     oc.d_blk_off = upload(wb, oc.blk_off, s);
@@ -1277,6 +1284,8 @@ void enlarge_su2(dmrg_ctx *C, const BlockPart &X, const SitePart &st, bool site_
 // ---------------------------------------------------------------------------
 // renormalization: B = T^T U T  (T = isometry on U's sectors)
 // ---------------------------------------------------------------------------
+WinBuf &data_of(dmrg_ctx *C, BlockPart *B);
+
 void renormalize(dmrg_ctx *C, const BlockPart &U, const Iso &T, BlockPart &B, WinBuf &wb) {
   cudaStream_t s = C->stream;
   B.basis = Basis();
@@ -1294,7 +1303,7 @@ void renormalize(dmrg_ctx *C, const BlockPart &U, const Iso &T, BlockPart &B, Wi
   B.enlarged = false;
   // same operators, same shifts
   std::vector<OpSpec> specs = block_specs(C, B.modes);
-  make_classes(B, specs, wb, s);
+  make_classes(B, specs, wb, s, &data_of(C, &B));
   // U's class for each shift
   std::map<QN, int> ushift;
   for (size_t ci = 0; ci < U.cls.size(); ++ci) ushift[U.cls[ci].shift] = (int)ci;
@@ -1387,15 +1396,208 @@ namespace {
 // ---------------------------------------------------------------------------
 // blocks from isometries
 // ---------------------------------------------------------------------------
+void drop_host_copy(BlockPart *B) {
+  for (double *h : B->host)
+    if (h) cudaFreeHost(h);
+  B->host.clear();
+}
+
 void free_part(dmrg_ctx *C, BlockPart *B) {
   auto it = C->partbuf.find(B);
   if (it != C->partbuf.end()) C->partbuf.erase(it);
+  auto jt = C->partdata.find(B);
+  if (jt != C->partdata.end()) C->partdata.erase(jt);
+  if (B) drop_host_copy(B);
 }
 
 WinBuf &buf_of(dmrg_ctx *C, BlockPart *B) {
   auto &p = C->partbuf[B];
   if (!p) p.reset(new WinBuf(WinBuf::lasting_buf()));
   return *p;
+}
+
+WinBuf &data_of(dmrg_ctx *C, BlockPart *B) {
+  auto &p = C->partdata[B];
+  if (!p) p.reset(new WinBuf(WinBuf::lasting_buf()));
+  return *p;
+}
+
+// all renormalized blocks of the context (their device buffers too)
+void clear_blocks(dmrg_ctx *C) {
+  for (auto &b : C->L)
+    if (b) free_part(C, b.get());
+  for (auto &kv : C->R)
+    if (kv.second) free_part(C, kv.second.get());
+  C->L.clear();
+  C->R.clear();
+}
+
+// ---------------------------------------------------------------------------
+// HBM staging of renormalized block operators (cfg.hbm_budget_bytes > 0)
+// ---------------------------------------------------------------------------
+// A sweep holds every block L_n, R_n; on large lattices their operators
+// exceed HBM.  Blocks are immutable once built, so a block whose next use is
+// far away is offloaded: its operator data is copied once into pinned host
+// memory and the device copy freed; it is copied back (on a side stream,
+// ahead of use) when a window needs it.  A block that the sweep rebuilds
+// before its next use is released outright.
+
+long long data_bytes(const BlockPart &B) {
+  long long b = 0;
+  for (const OpClass &oc : B.cls) b += 8 * std::max<long long>(1, oc.nnz * oc.nops);
+  return b;
+}
+
+void stage_init(dmrg_ctx *C) {
+  if (!C->stage_stream) CK(cudaStreamCreateWithFlags(&C->stage_stream, cudaStreamNonBlocking));
+  if (!C->stage_ev) CK(cudaEventCreateWithFlags(&C->stage_ev, cudaEventDisableTiming));
+}
+
+long long resident_bytes(dmrg_ctx *C) {
+  long long r = 0;
+  for (auto &b : C->L)
+    if (b && b->state == 0) r += data_bytes(*b);
+  for (auto &kv : C->R)
+    if (kv.second && kv.second->state == 0) r += data_bytes(*kv.second);
+  return r;
+}
+
+void offload(dmrg_ctx *C, BlockPart *B) {
+  if (!B || B->state != 0 || B->cls.empty()) return;
+  stage_init(C);
+  if (B->host.empty()) {
+    // wait for the work that built the block, then copy it out once
+    CK(cudaEventRecord(C->stage_ev, C->stream));
+    CK(cudaStreamWaitEvent(C->stage_stream, C->stage_ev, 0));
+    B->host.assign(B->cls.size(), nullptr);
+    for (size_t c = 0; c < B->cls.size(); ++c) {
+      const size_t n = 8 * std::max<long long>(1, B->cls[c].nnz * B->cls[c].nops);
+      if (cudaHostAlloc((void **)&B->host[c], n, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        fail(DMRG_ERR_OOM, "pinned host allocation of %zu bytes failed", n);
+      }
+      CK(cudaMemcpyAsync(B->host[c], B->cls[c].d, n, cudaMemcpyDeviceToHost, C->stage_stream));
+      C->st_d2h_bytes += (double)n;
+    }
+    CK(cudaStreamSynchronize(C->stage_stream));
+  }
+  auto it = C->partdata.find(B);
+  if (it != C->partdata.end()) C->partdata.erase(it);
+  for (OpClass &oc : B->cls) oc.d = nullptr;
+  B->state = 1;
+  ++C->st_offloads;
+}
+
+// Copy an offloaded block back on the staging stream; `s` waits for it.
+void reload(dmrg_ctx *C, BlockPart *B, cudaStream_t s) {
+  if (!B || B->state != 1) return;
+  stage_init(C);
+  WinBuf &wb = data_of(C, B);
+  std::array<cudaEvent_t, 2> ev{};
+  CK(cudaEventCreate(&ev[0]));
+  CK(cudaEventCreate(&ev[1]));
+  CK(cudaEventRecord(ev[0], C->stage_stream));
+  for (size_t c = 0; c < B->cls.size(); ++c) {
+    const size_t n = 8 * std::max<long long>(1, B->cls[c].nnz * B->cls[c].nops);
+    B->cls[c].d = (double *)wb.alloc(n);
+    CK(cudaMemcpyAsync(B->cls[c].d, B->host[c], n, cudaMemcpyHostToDevice, C->stage_stream));
+    C->st_h2d_bytes += (double)n;
+  }
+  CK(cudaEventRecord(ev[1], C->stage_stream));
+  CK(cudaStreamWaitEvent(s, ev[1], 0));
+  C->h2d_events.push_back(ev);
+  B->state = 0;
+  ++C->st_reloads;
+}
+
+void release(dmrg_ctx *C, BlockPart *B) {
+  if (!B || B->state == 2) return;
+  if (B->state == 0) {
+    // the device data may still be read by queued work on the context stream
+    CK(cudaStreamSynchronize(C->stream));
+  }
+  auto it = C->partdata.find(B);
+  if (it != C->partdata.end()) C->partdata.erase(it);
+  for (OpClass &oc : B->cls) oc.d = nullptr;
+  drop_host_copy(B);
+  B->state = 2;
+  ++C->st_releases;
+}
+
+void need(dmrg_ctx *C, BlockPart *B, cudaStream_t s) {
+  if (!B) return;
+  if (B->state == 2) fail(DMRG_ERR_STATE, "internal: a released block is used");
+  reload(C, B, s);
+}
+
+// Window steps from sweep position (pass, l) to the next use of L_n (left) or
+// R_n; -1 when the sweep rebuilds the block before using it again.  Pass 0
+// runs l = 0..N-2 (left to right), pass 1 l = N-2..0; window l uses L_l and
+// R_{l+2}.
+long long next_use(int N, int pass, int l, bool left, int n) {
+  const int w = left ? n : n - 2;
+  if (w == l) return 0;
+  if (pass == 0) {
+    if (left) return w < l ? (long long)(N - 2 - l) + 1 + (N - 2 - w) : -1;
+    return w > l ? w - l : -1;
+  }
+  if (left) return w < l ? l - w : -1;
+  return w > l ? (long long)l + 1 + w : -1;
+}
+
+void collect_h2d_times(dmrg_ctx *C);
+
+// Before window l of pass `pass`: release stale blocks, bring the window's
+// blocks in, offload the blocks used last until the resident ones fit the
+// budget, and prefetch the next window's blocks if they fit as well.
+void stage_window(dmrg_ctx *C, int pass, int l) {
+  const long long budget = (long long)C->cfg.hbm_budget_bytes;
+  if (budget <= 0) return;
+  const int N = C->N;
+  struct Item {
+    BlockPart *b;
+    long long nu;
+  };
+  std::vector<Item> items;
+  for (size_t n = 0; n < C->L.size(); ++n)
+    if (C->L[n] && !C->L[n]->cls.empty()) items.push_back({C->L[n].get(), next_use(N, pass, l, true, (int)n)});
+  for (auto &kv : C->R)
+    if (kv.second && !kv.second->cls.empty())
+      items.push_back({kv.second.get(), next_use(N, pass, l, false, kv.first)});
+  for (Item &it : items)
+    if (it.nu < 0) release(C, it.b);
+  for (Item &it : items)
+    if (it.nu == 0) need(C, it.b, C->stream);
+  std::sort(items.begin(), items.end(), [](const Item &a, const Item &b) { return a.nu > b.nu; });
+  long long res = resident_bytes(C);
+  for (Item &it : items) {
+    if (res <= budget) break;
+    if (it.nu <= 0 || it.b->state != 0) continue;
+    res -= data_bytes(*it.b);
+    offload(C, it.b);
+  }
+  // prefetch: the soonest-used offloaded blocks that fit
+  std::sort(items.begin(), items.end(), [](const Item &a, const Item &b) { return a.nu < b.nu; });
+  for (Item &it : items) {
+    if (it.nu <= 0 || it.b->state != 1) continue;
+    if (res + data_bytes(*it.b) > budget) break;
+    res += data_bytes(*it.b);
+    reload(C, it.b, C->stream);
+  }
+  C->st_peak = std::max(C->st_peak, (double)resident_bytes(C));
+  if (C->h2d_events.size() > 64) collect_h2d_times(C);
+}
+
+void collect_h2d_times(dmrg_ctx *C) {
+  for (auto &ev : C->h2d_events) {
+    CK(cudaEventSynchronize(ev[1]));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+    C->st_h2d_ms += ms;
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+  }
+  C->h2d_events.clear();
 }
 
 std::unique_ptr<BlockPart> vacuum(dmrg_ctx *C) {
@@ -1419,6 +1621,7 @@ void grow_left(dmrg_ctx *C, int n, const Iso &T) {
   SitePart st = site_of(C, n - 1);
   BlockPart U;
   WinBuf ub(C->stream);
+  need(C, C->L[n - 1].get(), C->stream);
   enlarge(C, *C->L[n - 1], st, false, C->N - n, U, ub);
   std::unique_ptr<BlockPart> B(new BlockPart());
   renormalize(C, U, T, *B, buf_of(C, B.get()));
@@ -1432,6 +1635,7 @@ void grow_right(dmrg_ctx *C, int n, const Iso &T) {
   SitePart st = site_of(C, n);
   BlockPart U;
   WinBuf ub(C->stream);
+  need(C, C->R[n + 1].get(), C->stream);
   enlarge(C, *C->R[n + 1], st, true, n, U, ub);
   std::unique_ptr<BlockPart> B(new BlockPart());
   renormalize(C, U, T, *B, buf_of(C, B.get()));
@@ -1511,6 +1715,8 @@ void build_window(dmrg_ctx *C, int l) {
   double t0 = now();
   {
     SitePart sl = site_of(C, l), sr = site_of(C, l + 1);
+    need(C, C->L[l].get(), C->stream);
+    need(C, C->R[l + 2].get(), C->stream);
     enlarge(C, *C->L[l], sl, false, C->N - l - 1, w.Ld, w.ldbuf);
     enlarge(C, *C->R[l + 2], sr, true, l + 1, w.Rd, w.rdbuf);
   }
@@ -3286,13 +3492,14 @@ void sweep_impl(dmrg_ctx *C, int nsw, const int *dsched, double *E, cudaStream_t
   C->center_l = -1;
   C->center_psi.clear();
   double t0 = now();
-  C->R.clear();
+  clear_blocks(C);
   C->R[N] = vacuum(C);
   for (int n = N - 1; n >= 2; --n) {
     upload_iso(C, C->riso[n]);
     grow_right(C, n, C->riso[n]);
+    // under a budget, the blocks used last in the first pass go to host memory
+    if (C->cfg.hbm_budget_bytes) stage_window(C, 0, 0);
   }
-  C->L.clear();
   C->L.push_back(vacuum(C));
   C->prof[1] += now() - t0;
   C->Lmap.clear();
@@ -3307,7 +3514,8 @@ void sweep_impl(dmrg_ctx *C, int nsw, const int *dsched, double *E, cudaStream_t
   int it;
   int patience = 6;
   bool probe = true;
-  auto step = [&](int l, int trunc_side, int D) {
+  auto step = [&](int pass, int l, int trunc_side, int D) {
+    stage_window(C, pass, l);
     build_window(C, l);
     const long long n = C->win.psi_len;
     xb[cur].clear();
@@ -3334,8 +3542,8 @@ void sweep_impl(dmrg_ctx *C, int nsw, const int *dsched, double *E, cudaStream_t
     // stagnation there; later sweeps start from the transformed previous state
     probe = sw == 0;
     patience = sw == 0 ? 6 : 4;
-    for (int l = 0; l <= N - 2; ++l) step(l, l < N - 2 ? 0 : -1, D);
-    for (int l = N - 2; l >= 0; --l) step(l, l > 0 ? 1 : -1, D);
+    for (int l = 0; l <= N - 2; ++l) step(0, l, l < N - 2 ? 0 : -1, D);
+    for (int l = N - 2; l >= 0; --l) step(1, l, l > 0 ? 1 : -1, D);
     if (E) E[sw] = e;
   }
   // the MPS the sweeps ended with: right isometries R_2..R_{N-1} (Rmap) and
@@ -3424,9 +3632,18 @@ int dmrg_destroy(dmrg_ctx *ctx) {
   ctx->win.buf.clear();
   ctx->win.ldbuf.clear();
   ctx->win.rdbuf.clear();
-  ctx->L.clear();
-  ctx->R.clear();
+  clear_blocks(ctx);
   ctx->partbuf.clear();
+  ctx->partdata.clear();
+  for (auto &ev : ctx->h2d_events) {
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+  }
+  if (ctx->stage_ev) cudaEventDestroy(ctx->stage_ev);
+  if (ctx->stage_stream) {
+    cudaStreamSynchronize(ctx->stage_stream);
+    cudaStreamDestroy(ctx->stage_stream);
+  }
   ctx->dav.clear();
   if (ctx->solver_params) cusolverDnDestroyParams(ctx->solver_params);
   if (ctx->solver) cusolverDnDestroy(ctx->solver);
@@ -3578,8 +3795,7 @@ int dmrg_set_hamiltonian(dmrg_ctx *C, const double *t, const double *V, const do
             C->W[(((size_t)p * M + q) * M + r) * M + s] =
                 0.25 * (X(p, q, r, s) - X(q, p, r, s) - X(p, q, s, r) + X(q, p, s, r));
     C->ham = true;
-    C->L.clear();
-    C->R.clear();
+    clear_blocks(C);
     C->win.valid = false;
   });
 }
@@ -3626,17 +3842,20 @@ int dmrg_build_block_ops(dmrg_ctx *C, int l, void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
     C->stream = s;
     double t0 = now();
-    C->L.clear();
+    clear_blocks(C);
     C->L.push_back(vacuum(C));
+    // under a budget, a block is released once the next one is built from it
+    const bool lean = C->cfg.hbm_budget_bytes > 0;
     for (int n = 1; n <= l; ++n) {
       upload_iso(C, C->liso[n]);
       grow_left(C, n, C->liso[n]);
+      if (lean) release(C, C->L[n - 1].get());
     }
-    C->R.clear();
     C->R[N] = vacuum(C);
     for (int n = N - 1; n >= l + 2; --n) {
       upload_iso(C, C->riso[n]);
       grow_right(C, n, C->riso[n]);
+      if (lean) release(C, C->R[n + 1].get());
     }
     C->prof[1] += now() - t0;
     build_window(C, l);
@@ -3922,6 +4141,26 @@ int dmrg_heff_split_plan(dmrg_ctx *C, double *out4) {
   out4[2] = P.nwork2;
   out4[3] = (double)w.ksub;
   return DMRG_OK;
+}
+
+long long dmrg_sweep_next_use(int n_sites, int pass, int l, int left, int n) {
+  if (n_sites < 2 || (pass != 0 && pass != 1) || l < 0 || l > n_sites - 2) return -2;
+  return next_use(n_sites, pass, l, left != 0, n);
+}
+
+int dmrg_staging_stats(dmrg_ctx *C, double *out8) {
+  if (!C || !out8) return DMRG_ERR_ARG;
+  return guard(C, [&] {
+    collect_h2d_times(C);
+    out8[0] = C->st_h2d_bytes;
+    out8[1] = C->st_h2d_ms * 1e-3;
+    out8[2] = C->st_d2h_bytes;
+    out8[3] = C->st_peak;
+    out8[4] = (double)C->st_offloads;
+    out8[5] = (double)C->st_reloads;
+    out8[6] = (double)C->st_releases;
+    out8[7] = (double)C->cfg.hbm_budget_bytes;
+  });
 }
 
 int dmrg_heff_split_paths(dmrg_ctx *C, long long *out8) {

@@ -97,6 +97,11 @@ struct BlockPart {
   std::map<int, Ref> c, S;
   std::map<PairKey, Ref> cc, cdc, P, Q;
   std::map<TKey, TRef> ten;   // spin-adapted parts: all operators as tensors
+  // HBM staging of renormalized blocks: 0 resident, 1 offloaded (class data
+  // only in pinned host memory, host[c] per class), 2 released (stale: rebuilt
+  // before any further use; host metadata kept)
+  int state = 0;
+  std::vector<double *> host;
   // enlarged blocks only
   bool enlarged = false;
   int site_first = 0;

@@ -15,7 +15,7 @@ HEADER = os.path.join(os.path.dirname(__file__), "..", "include", "dmrg_b300.h")
 
 def test_header_symbols_exported():
     src = open(HEADER).read()
-    declared = set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(dmrg_\w+)\s*\(", src, re.M))
+    declared = set(re.findall(r"^\s*(?:\w+\s+)+\**\s*(dmrg_\w+)\s*\(", src, re.M))
     assert declared, "no declarations parsed"
     assert declared == set(lib.HEADER_FUNCTIONS)
     for name in declared:
@@ -47,3 +47,33 @@ def test_bad_arguments_rejected():
     assert lib._lib.dmrg_create(None, None) == lib.ERR_ARG
     assert lib._lib.dmrg_destroy(None) == lib.OK
     assert lib._lib.dmrg_error_string(lib.ERR_TIMEOUT).decode().startswith("bounded")
+
+
+def test_staging_policy_matches_sweep_walk():
+    """The staging policy's next-use distances against a walk of the sweep:
+    window l uses L_l and R_{l+2}; truncation after window l builds L_{l+1}
+    (left to right) or R_{l+1} (right to left), which makes the old block of
+    that name stale."""
+    N = 7
+    order = [(0, l) for l in range(N - 1)] + [(1, l) for l in range(N - 2, -1, -1)]
+    order = order * 3
+    for start, (pass_, l) in enumerate(order[:len(order) // 3]):
+        for left in (1, 0):
+            for n in range(0, N + 1):
+                # walk forward: first event on this block name
+                want = -1
+                for k, (p2, l2) in enumerate(order[start:]):
+                    uses = (l2 == n) if left else (l2 + 2 == n)
+                    if uses:
+                        want = k
+                        break
+                    # after window l2 the truncation rebuilds one block
+                    rebuilt = (left and p2 == 0 and l2 < N - 2 and l2 + 1 == n) or \
+                              (not left and p2 == 1 and l2 > 0 and l2 + 1 == n)
+                    if rebuilt:
+                        break
+                if (left and n > N - 2) or (not left and (n < 2 or n > N)):
+                    continue
+                got = lib._lib.dmrg_sweep_next_use(N, pass_, l, left, n)
+                assert got == want, (pass_, l, left, n, got, want)
+    assert lib._lib.dmrg_sweep_next_use(1, 0, 0, 1, 0) == -2
