@@ -222,6 +222,24 @@ def cpu_baseline(budget_s=15.0):
             "ms_per_apply": dt * 1e3}
 
 
+def fp64_peak_probe(torch):
+    """Measured FP64 denominator for the FP64 path: cuBLAS DGEMM (torch.matmul,
+    float64, 4096^3, best of 5, CUDA events)."""
+    a = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+    b = torch.randn_like(a)
+    c = a @ b
+    best = 1e30
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        c = a @ b
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del a, b, c
+    return {"dgemm_tflops": 2 * 4096 ** 3 / (best * 1e-3) / 1e12, "how": "cuBLAS DGEMM 4096^3, best of 5"}
+
+
 def c1_sweeps(lib, stream):
     """Config C1: spinless t-V 4x4 torus, N = 8, V = 1, momentum basis, U(1),
     D = 128, FP64 throughout, 6 sweeps from a seeded random MPS; seconds per
@@ -324,6 +342,32 @@ def main():
         ms_split, st_split = timed(lib.SPLIT, args.steps, args.warmup)
     clocks = clk.summary()
     sig_split = sig.clone()
+    # several vectors in one pass of the split kernels (operator tiles served
+    # from L2 to all of them): ms per batched apply and per vector
+    batched = []
+    g.set_precision(lib.SPLIT)
+    for nv in (2, 4, 8):
+        try:
+            X = torch.tensor(np.stack([synth.random_psi(layout, 1 + v) for v in range(nv)]),
+                             device="cuda")
+            Y = torch.empty_like(X)
+            with torch.cuda.stream(stream):
+                for _ in range(2):
+                    g.heff_apply_batch(X, Y, stream)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                reps = max(3, min(args.steps // nv, 50))
+                e0.record(stream)
+                for _ in range(reps):
+                    g.heff_apply_batch(X, Y, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            batched.append({"nv": nv, "ms_per_apply": ms, "ms_per_vector": ms / nv,
+                            "tflops": nv * flops / (ms * 1e-3) / 1e12})
+            del X, Y
+        except Exception as e:   # a batch that does not fit is reported, not fatal
+            batched.append({"nv": nv, "error": repr(e)[:200]})
     # FP64 path (fewer steps: FP64 throughput is ~1/100 of the split path)
     k64 = max(2, min(args.steps, 5))
     ms_64, st_64 = timed(lib.FP64, k64, 1)
@@ -380,6 +424,7 @@ def main():
             serving_out[name] = srv.run(reqs)
         serving_out["solves_per_s_ratio_split_over_fp64"] = (
             serving_out["split"]["solves_per_s"] / max(serving_out["fp64"]["solves_per_s"], 1e-12))
+    fp64_peak = fp64_peak_probe(torch) if rank == 0 else None
     # config C1 (4x4 spinless, D = 128, FP64, 6 sweeps): per sweep and per matvec
     c1 = None
     if not args.no_c1 and rank == 0:
@@ -410,11 +455,16 @@ def main():
                    "algorithmic_flops_per_step": flops, "l2": "operator stacks >> L2; no flush",
                    "parallelism": f"replicas x{world}", "block_build_seconds": t_build},
         "fp64": {"ms_per_step": ms_64, "tflops": flops / (ms_64 * 1e-3) / 1e12,
-                 "stage_ms": st_64[1:3].tolist()},
+                 "stage_ms": st_64[1:3].tolist(), "peak_probe": fp64_peak,
+                 "frac_of_dgemm": (flops / (ms_64 * 1e-3) / 1e12 / fp64_peak["dgemm_tflops"])
+                 if fp64_peak else None},
         "split_kernel_ms": dict(zip(["psi_split", "stage1", "stage2", "partial_sum"],
                                     st_split[:4].tolist())),
-        "autotuner": [{"ksub": k, "ms_per_apply": v} for k, v in g.heff_tuning()],
+        "autotuner": [({"ksub": k} if k < 100000 else
+                       {"stage1_tile_cap": (k - 100000) // 10, "stage1_order": (k - 100000) % 10})
+                      | {"ms_per_apply": v} for k, v in g.heff_tuning()],
         "sigma_rel_diff_split_vs_fp64": err_sigma,
+        "batched_split": batched,
         "solve": solve,
         "serving": serving_out,
         "c1_spinless4x4_D128_fp64_6_sweeps": c1,

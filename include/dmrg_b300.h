@@ -162,6 +162,18 @@ int dmrg_set_precision(dmrg_ctx *ctx, int precision);
 int dmrg_heff_apply(dmrg_ctx *ctx, const double *psi, double *sigma,
                     void *stream);
 
+/* a5, several vectors -- sigma_v = H_eff * psi_v for v = 0..nv-1 (1 <= nv
+ * <= 64): psi and sigma are device pointers to nv * psi_len doubles, vector v
+ * at v * psi_len.  With DMRG_SPLIT the nv products run in one pass of the
+ * split kernels (the batched sector algebra of Sec. III.B): every work item
+ * appears once per vector, the copies side by side in the claim order, so an
+ * operator tile read from HBM serves all nv vectors from L2.  Each sigma_v is
+ * bitwise the result of dmrg_heff_apply on psi_v.  With DMRG_FP64 the
+ * vectors are applied one by one.  Stream-ordered; errors as dmrg_heff_apply
+ * (ARG for nv out of range). */
+int dmrg_heff_apply_batch(dmrg_ctx *ctx, int nv, const double *psi, double *sigma,
+                          void *stream);
+
 /* Synchronise `stream` and report the outcome of this context's work on it:
  * DMRG_ERR_TIMEOUT if a bounded device wait of any earlier H_eff*psi of this
  * context (dmrg_heff_apply or dmrg_heff_apply_split_static) gave up and has
@@ -275,10 +287,15 @@ int dmrg_heff_stage_info(dmrg_ctx *ctx, double *out6);
  * apply. */
 int dmrg_heff_timing(dmrg_ctx *ctx, int enable, double *out5);
 
-/* Autotuner record of this context: *n_entries pairs (candidate split-K
- * range, milliseconds per split-precision apply) timed on the first large
- * window; the fastest candidate is used for the rest of the context.  out
- * (may be NULL) receives up to max_entries pairs. */
+/* Autotuner record of this context: *n_entries pairs (candidate,
+ * milliseconds per split-precision apply) timed on the first window whose
+ * operator stacks exceed 256 MB: first the stage-2 split-K ranges (candidate
+ * = the range, 1024 / 2048 / 4096), then, with the chosen range, the stage-1
+ * schedules (candidate = 100000 + 10 * tile-width cap + item order; caps 128
+ * and 64; order 0 rounds from the heavy, light and middle thirds of the
+ * cost-sorted items, 1 cost order, 2 heaviest and lightest alternating).  The
+ * fastest of each (a later candidate must win by 1.5 %) is used for the rest
+ * of the context.  out (may be NULL) receives up to max_entries pairs. */
 int dmrg_heff_tuning(dmrg_ctx *ctx, double *out, int max_entries, int *n_entries);
 
 /* Term structure of the window's H_eff: entry i couples input psi block
@@ -293,6 +310,16 @@ int dmrg_heff_entries(dmrg_ctx *ctx, int *out, int max_entries, int *n_entries);
  * tiles, [2] stage-2 tiles, [3] split-K range of stage 2 (K elements per
  * partial tile).  DMRG_ERR_STATE before the plan exists. */
 int dmrg_heff_split_plan(dmrg_ctx *ctx, double *out4);
+
+/* One-particle reduced density matrix (Sec. II.B: gamma_ij = <c+_j c_i>,
+ * used for natural orbitals and, back-rotated, for order parameters) of the
+ * state psi (device pointer, the current window's layout, normalized by the
+ * caller) from the window's block operators: gamma[i*N + j] (host, N*N) =
+ * sum over spin of <c+_{j s} c_{i s}> in the rotated mode basis of
+ * dmrg_set_hamiltonian (spinless: <c+_j c_i>).  The real-space matrix is
+ * U gamma U^T with U the mode rotation.  Synchronises the stream.
+ * Errors: ARG, STATE (no window). */
+int dmrg_rdm1(dmrg_ctx *ctx, const double *psi, double *gamma, void *stream);
 
 /* Staging of renormalized block operators under cfg.hbm_budget_bytes (the
  * paper's H2D/D2H traffic of operators that do not fit the GPUs, Sec. III.B).

@@ -120,3 +120,46 @@ def ground_energy(h, W, n_part, n_up=None, k=1, tol=1e-12, dense_max=3000):
     w = spla.eigsh(op, k=k, which="SA", tol=tol, v0=rng.standard_normal(d),
                    return_eigenvectors=False, ncv=max(20, 2 * k + 1))
     return np.sort(w)
+
+
+def ground_state(h, W, n_part, n_up=None, tol=1e-13):
+    """Lowest eigenpair in the sector: (E0, v on the whole fixed-n_part Fock
+    space (zero outside the sector), FockSpace)."""
+    M = h.shape[0]
+    fs = FockSpace(M, n_part)
+    idx = np.nonzero(fs.sector_mask(n_up))[0]
+    d = len(idx)
+
+    def mv(x):
+        full = np.zeros(fs.dim)
+        full[idx] = x
+        return fs.apply_H(h, W, full)[idx]
+
+    if d <= 3000:
+        Hm = np.stack([mv(e) for e in np.eye(d)], axis=1)
+        w, V = np.linalg.eigh(0.5 * (Hm + Hm.T))
+        e0, x = w[0], V[:, 0]
+    else:
+        op = spla.LinearOperator((d, d), matvec=mv, dtype=float)
+        rng = np.random.default_rng(12345)
+        w, V = spla.eigsh(op, k=1, which="SA", tol=tol, v0=rng.standard_normal(d), ncv=24)
+        e0, x = w[0], V[:, 0]
+    v = np.zeros(fs.dim)
+    v[idx] = x / np.linalg.norm(x)
+    return e0, v, fs
+
+
+def rdm1(fs, v):
+    """Spin-orbital one-particle density matrix gamma[p, q] = <c+_q c_p>
+    (the paper's gamma_{i,j} = <c+_j c_i>, Sec. II.B)."""
+    M = fs.M
+    g = np.empty((M, M))
+    for p in range(M):
+        for q in range(M):
+            g[p, q] = v @ (fs.E(q, p) @ v)
+    return g
+
+
+def expectation(fs, h, W, v):
+    """<v| H(h, W) |v> for an operator in the spin-orbital Eq. 1 form."""
+    return float(v @ fs.apply_H(h, W, v))

@@ -138,3 +138,23 @@ def rotate(T, V4, U):
     W = W.transpose(0, 1, 3, 2)                       # a b c l
     W = np.tensordot(W, U, axes=([3], [0]))           # a b c d
     return Tp, W
+
+
+def cdw_square(Lx, Ly):
+    """(n_even - n_odd)^2 in Eq. 1 form, real space (the operator of the CDW
+    order parameter C_CDW = <(n_even - n_odd)^2> / N^2, Sec. III.C).
+
+    With s_i = +1 on sites with x + y even and -1 otherwise,
+    (sum_i s_i n_i)^2 = sum_i n_i + sum_ij s_i s_j c^+_i c^+_j c_j c_i
+    (n_i n_j = delta_ij n_i + c^+_i c^+_j c_j c_i, s_i^2 = 1): T = identity,
+    V[i, j, j, i] = s_i s_j; in the spinful convention the a = b terms of
+    sum_ab V_iiii c^+_ia c^+_ib c_ib c_ia vanish, so the same (T, V) holds.
+    """
+    N = Lx * Ly
+    s = np.array([1.0 - 2.0 * (((i % Lx) + (i // Lx)) % 2) for i in range(N)])
+    T = np.eye(N)
+    V4 = np.zeros((N, N, N, N))
+    for i in range(N):
+        for j in range(N):
+            V4[i, j, j, i] = s[i] * s[j]
+    return T, V4

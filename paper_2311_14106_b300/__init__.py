@@ -33,6 +33,7 @@ HEADER_FUNCTIONS = [
     "dmrg_heff_split_plan", "dmrg_heff_entries", "dmrg_selftest_bounded_wait",
     "dmrg_sync", "dmrg_get_mps", "dmrg_get_center", "dmrg_heff_split_paths",
     "dmrg_selftest_timeout_report", "dmrg_staging_stats", "dmrg_sweep_next_use",
+    "dmrg_rdm1", "dmrg_heff_apply_batch",
 ]
 
 
@@ -87,6 +88,8 @@ _sig = {
     "dmrg_selftest_timeout_report": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "dmrg_staging_stats": (ctypes.c_int, [_P, _D]),
     "dmrg_sweep_next_use": (ctypes.c_longlong, [ctypes.c_int] * 5),
+    "dmrg_rdm1": (ctypes.c_int, [_P, _P, _D, _P]),
+    "dmrg_heff_apply_batch": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -168,6 +171,8 @@ class Dmrg:
         if rc != OK:
             raise DmrgError(rc, "dmrg_create")
         self._h = h
+        self.kwargs = dict(n_sites=n_sites, n_up=n_up, n_dn=n_dn, spinful=spinful, d_max=d_max,
+                           su2=su2, twice_s=twice_s)
         self.spinful = spinful
         self.nq = 2 if spinful else 1
         self.n_sites = n_sites
@@ -231,6 +236,13 @@ class Dmrg:
         """a5: sigma = H_eff psi on device buffers (torch float64 CUDA tensors)."""
         self._check(_lib.dmrg_heff_apply(self._h, _tensor_ptr(psi), _tensor_ptr(sigma),
                                          _stream_ptr(stream)), "heff_apply")
+
+    def heff_apply_batch(self, psi, sigma, stream=None):
+        """sigma[v] = H_eff psi[v] for the rows of a contiguous (nv, psi_len)
+        float64 CUDA tensor, in one batched pass on the split path."""
+        nv = psi.shape[0] if psi.dim() == 2 else 1
+        self._check(_lib.dmrg_heff_apply_batch(self._h, nv, _tensor_ptr(psi), _tensor_ptr(sigma),
+                                               _stream_ptr(stream)), "heff_apply_batch")
 
     def heff_apply_static(self, psi, sigma, stream=None):
         """Split-precision H_eff psi that allocates no device memory: its
@@ -326,6 +338,15 @@ class Dmrg:
         self._check(_lib.dmrg_selftest_timeout_report(self._h, which, _stream_ptr(stream)),
                     "selftest_timeout_report")
 
+    def rdm1(self, psi, stream=None):
+        """One-particle reduced density matrix of psi (device tensor, this
+        window's layout): gamma[i, j] = sum_s <c+_{j s} c_{i s}>, rotated
+        mode basis."""
+        g = np.zeros((self.n_sites, self.n_sites))
+        self._check(_lib.dmrg_rdm1(self._h, _tensor_ptr(psi), _dptr(g), _stream_ptr(stream)),
+                    "rdm1")
+        return g
+
     def staging_stats(self):
         """Block-operator staging under hbm_budget_bytes (see the header)."""
         out = np.zeros(8)
@@ -373,7 +394,9 @@ class Dmrg:
         return out
 
     def heff_tuning(self):
-        """Autotuner record: [(split-K range, ms per apply), ...]."""
+        """Autotuner record: [(candidate, ms per apply), ...]; candidates below
+        100000 are stage-2 split-K ranges, 100000 + 10 cap + order stage-1
+        schedules (see the header)."""
         n = ctypes.c_int()
         self._check(_lib.dmrg_heff_tuning(self._h, None, 0, ctypes.byref(n)), "heff_tuning")
         out = np.zeros(2 * max(n.value, 1))

@@ -245,6 +245,23 @@ struct SplitTables {
   std::vector<PartialSum> psums;
 };
 
+// Split-precision plan for nv vectors applied together (dmrg_heff_apply_batch):
+// its own per-apply scratch and device tables, built from the window's FP16
+// operator copies and the autotuner's choices.
+struct BatchPlan {
+  int nv = 0;
+  SplitTables tb;
+  __half *Ph = nullptr, *Pl = nullptr, *Th = nullptr, *Tl = nullptr;
+  float *ws = nullptr;
+  PsiStat *pstat = nullptr;
+  PsiDesc *pdesc = nullptr;
+  int *next = nullptr;
+  void *dsplit = nullptr, *dmaps = nullptr, *dseg = nullptr, *dw1 = nullptr, *dw2 = nullptr,
+       *dps = nullptr;
+  int psi_tiles = 1;
+  std::map<std::pair<const void *, const void *>, cudaGraphExec_t> graphs;
+};
+
 struct Window {
   bool valid = false;
   int l = -1;
@@ -277,12 +294,14 @@ struct Window {
   bool tf_ready = false;
   bool tf_copies = false;            // FP16 (hi, lo) copies of the operator stacks exist
   int ksub = 0;                      // split-K range in use
+  int cap1 = 128, order1 = 0;        // stage-1 schedule in use (tile-width cap, item order)
   void *tbl_ptr[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   size_t tbl_cap[6] = {0, 0, 0, 0, 0, 0};
   std::map<std::pair<const void *, const void *>, cudaGraphExec_t> graphs;
   std::vector<long long> offA, ldA, offBp, bpad;   // split copies (halves)
   std::vector<float> sA, sB, rnA;                   // per entry: scales, largest A row norm
   long long gen = 0;                 // build counter of this window
+  std::map<int, BatchPlan> batch;    // multi-vector split plans by vector count
 };
 
 }  // namespace
@@ -329,6 +348,7 @@ struct dmrg_ctx {
   bool use_graphs = true;
   cudaStream_t cap_stream = nullptr;            // private stream for graph capture
   int ksub_choice = 0;                          // autotuned split-K range (0: not yet)
+  int cap1_choice = 0, order1_choice = 0;       // autotuned stage-1 schedule (0: not yet)
   std::vector<std::array<double, 2>> tune_log;  // (candidate, ms per apply)
   // Bounded-wait status of the tcgen05 kernels for stream-ordered callers:
   // after each public split apply the device error word is copied (stream
@@ -1700,6 +1720,9 @@ void build_window(dmrg_ctx *C, int l) {
   w.tf_copies = false;
   for (auto &g : w.graphs) cudaGraphExecDestroy(g.second);
   w.graphs.clear();
+  for (auto &b : w.batch)
+    for (auto &g : b.second.graphs) cudaGraphExecDestroy(g.second);
+  w.batch.clear();
   for (int i = 0; i < 6; ++i) {
     w.tbl_ptr[i] = nullptr;
     w.tbl_cap[i] = 0;
@@ -2257,13 +2280,33 @@ std::vector<PsiDesc> psi_descs(const Window &w) {
   return out;
 }
 
+// Stage-1 schedule: tiles of psi blocks wider than cap1 (128 or 64) are cap1
+// wide; order1 = 0 rounds of one item per SM from the heavy, light and middle
+// thirds of the cost-sorted items in turn, 1 cost order alone, 2 heaviest and
+// lightest items alternating.
+// nv > 1: one plan for nv vectors stored one after the other psi_stride
+// apart (psi and sigma); vector v uses the v-th copy of the per-apply scratch
+// (z sizes each: P at v * z.nP, T at v * z.nT, partial tiles at v * z.nws)
+// and psi statistics v * np + block.  Every work item appears once per
+// vector, the copies next to each other in the claim order, so that they run
+// at about the same time and the copies after the first take the shared
+// operator tile from L2.
 void split_tables(const Window &w, const SplitScratch &z, __half *Ph, __half *Pl, __half *Th,
-                  __half *Tl, float *ws, SplitTables &out, int KSUB) {
+                  __half *Tl, float *ws, SplitTables &out, int KSUB, int cap1 = 128,
+                  int order1 = 0, int nv = 1, long long psi_stride = 0) {
+  auto ntile1 = [cap1](int n) { return std::min(ntile_of(n), cap1); };
   const SplitPlan &P = w.tf;
   const auto &E = w.s1info;
   const size_t ne = E.size(), np = w.psi.size();
   out = SplitTables();
-  out.psi_split = psi_split_descs(w, z, Ph, Pl);
+  for (int v = 0; v < nv; ++v) {
+    std::vector<F16Split> d = psi_split_descs(w, z, Ph + (long long)v * z.nP, Pl + (long long)v * z.nP);
+    for (F16Split &x : d) {
+      x.src_off += v * psi_stride;
+      x.pblk += v * (int)np;
+    }
+    out.psi_split.insert(out.psi_split.end(), d.begin(), d.end());
+  }
   auto &maps = out.maps;
   auto mk = [&](const __half *base, long long rows, long long cols, long long ld, int box) {
     CUtensorMap m;
@@ -2287,18 +2330,20 @@ void split_tables(const Window &w, const SplitScratch &z, __half *Ph, __half *Pl
     maps.push_back(m);
     return (int)maps.size() - 1;
   };
-  std::vector<int> mPh(np), mPl(np);
-  for (size_t i = 0; i < np; ++i) {
-    const PsiBlk &p = w.psi[i];
-    mPh[i] = mk(Ph + z.offP[i], p.db, p.da, z.ldP[i], ntile_of(p.db));
-    mPl[i] = mk(Pl + z.offP[i], p.db, p.da, z.ldP[i], ntile_of(p.db));
-  }
+  std::vector<int> mPh(nv * np), mPl(nv * np);
+  for (int v = 0; v < nv; ++v)
+    for (size_t i = 0; i < np; ++i) {
+      const PsiBlk &p = w.psi[i];
+      const long long o = (long long)v * z.nP + z.offP[i];
+      mPh[v * np + i] = mk(Ph + o, p.db, p.da, z.ldP[i], ntile1(p.db));
+      mPl[v * np + i] = mk(Pl + o, p.db, p.da, z.ldP[i], ntile1(p.db));
+    }
   auto &segs = out.segs;
   auto &w1 = out.w1;
   auto &w2 = out.w2;
   const auto into = entries_into(w);
-  // per entry: stage-1 tiles, and the maps stage 2 reads
-  std::vector<int> mThi(ne), mTlo(ne), mBhi(ne), mBlo(ne);
+  // per entry: stage-1 tiles, and the maps stage 2 reads (T per vector)
+  std::vector<int> mThi(nv * ne), mTlo(nv * ne), mBhi(ne), mBlo(ne);
   // stage-2 packing of small sigma blocks: R segments per 128 x 128 tile
   std::vector<int> Rq(np, 1);
   for (size_t po = 0; po < np; ++po) {
@@ -2318,96 +2363,114 @@ void split_tables(const Window &w, const SplitScratch &z, __half *Ph, __half *Pl
     // T as stage-1 output: rows (a', k), columns b (padded); as stage-2
     // operand: rows a', K = (k, b)
     const long long rowsT = (long long)q.da * n;
-    const int sThi = mk3h(Th + z.offT[i], bp, rowsT, bp);
-    const int sTlo = mk3h(Tl + z.offT[i], bp, rowsT, bp);
     const int R = Rq[E[i].po];
-    mThi[i] = mk(Th + z.offT[i], q.da, (long long)n * bp, (long long)n * bp, 128 / R);
-    mTlo[i] = mk(Tl + z.offT[i], q.da, (long long)n * bp, (long long)n * bp, 128 / R);
+    std::vector<int> sThi(nv), sTlo(nv), seg(nv);
+    for (int v = 0; v < nv; ++v) {
+      const long long o = (long long)v * z.nT + z.offT[i];
+      sThi[v] = mk3h(Th + o, bp, rowsT, bp);
+      sTlo[v] = mk3h(Tl + o, bp, rowsT, bp);
+      mThi[v * ne + i] = mk(Th + o, q.da, (long long)n * bp, (long long)n * bp, 128 / R);
+      mTlo[v * ne + i] = mk(Tl + o, q.da, (long long)n * bp, (long long)n * bp, 128 / R);
+      TSeg sg;
+      memset(&sg, 0, sizeof sg);
+      sg.mA_hi = ahi; sg.mA_lo = alo;
+      sg.mB_hi = mPh[v * np + E[i].pi]; sg.mB_lo = mPl[v * np + E[i].pi];
+      sg.K = p.da;
+      sg.k0 = 0;
+      seg[v] = (int)segs.size();
+      segs.push_back(sg);
+    }
     int bbox = R > 1 ? 128 / R : ntile_of(q.db);
     mBhi[i] = mk(P.Bh + w.offBp[i], q.db, (long long)n * w.bpad[i], (long long)n * w.bpad[i], bbox);
     mBlo[i] = mk(P.Bl + w.offBp[i], q.db, (long long)n * w.bpad[i], (long long)n * w.bpad[i], bbox);
-    TSeg sg;
-    memset(&sg, 0, sizeof sg);
-    sg.mA_hi = ahi; sg.mA_lo = alo; sg.mB_hi = mPh[E[i].pi]; sg.mB_lo = mPl[E[i].pi];
-    sg.K = p.da;
-    sg.k0 = 0;
-    int seg = (int)segs.size();
-    segs.push_back(sg);
-    const int M = q.da * n, N = p.db, nt = ntile_of(N);
+    const int M = q.da * n, N = p.db, nt = ntile1(N);
     for (int m0 = 0; m0 < M; m0 += 128)
-      for (int n0 = 0; n0 < N; n0 += nt) {
-        TWork t;
-        memset(&t, 0, sizeof t);
-        t.s = segs[seg];
-        t.M = M; t.N = N; t.m0 = m0; t.n0 = n0; t.ntile = nt;
-        t.mode = TW_SPLIT; t.alpha = alpha[i];
-        t.fa = 1.f / w.sA[i];
-        t.rn = w.rnA[i];
-        t.pblk = E[i].pi;
-        t.mOut_hi = sThi; t.mOut_lo = sTlo; t.zout = 0;
-        w1.push_back(t);
-      }
+      for (int n0 = 0; n0 < N; n0 += nt)
+        for (int v = 0; v < nv; ++v) {
+          TWork t;
+          memset(&t, 0, sizeof t);
+          t.s = segs[seg[v]];
+          t.M = M; t.N = N; t.m0 = m0; t.n0 = n0; t.ntile = nt;
+          t.mode = TW_SPLIT; t.alpha = alpha[i];
+          t.fa = 1.f / w.sA[i];
+          t.rn = w.rnA[i];
+          t.pblk = v * (int)np + E[i].pi;
+          t.mOut_hi = sThi[v]; t.mOut_lo = sTlo[v]; t.zout = 0;
+          w1.push_back(t);
+        }
   }
   // per sigma block: split-K ranges (one entry each), each one FP32 partial
   // tile per output tile; the partials are summed in a fixed order.
   long long wsn = 0;
   struct PackCand {
-    int seg, mOut, z, R, nchunk, entry;
+    int seg, mOut, z, R, nchunk, entry, vec;
   };
   std::vector<PackCand> pk;
   for (size_t po = 0; po < np; ++po) {
     const PsiBlk &q = w.psi[po];
     const long long ldw = r4(q.db), blk = (long long)q.da * ldw;
     const int M = q.da, N = q.db, nt = ntile_of(N);
-    PartialSum ps;
-    memset(&ps, 0, sizeof ps);
-    ps.ws = ws + wsn;
-    ps.stride = blk;
-    ps.off = q.off;
-    ps.ld = ldw;
-    ps.n = q.da * q.db;
-    ps.cols = q.db;
-    std::vector<TSeg> ranges;
-    std::vector<int> rent;   // entry of each range
+    std::vector<int> rent;   // entry of each K range
+    std::vector<int> rk0, rK;
     for (int i : into[po]) {
       const HClass &h = w.hc[E[i].ci];
       const int K = (int)(h.terms.size() * w.bpad[i]);
       for (int k0 = 0; k0 < K; k0 += KSUB) {
-        TSeg sg;
-        memset(&sg, 0, sizeof sg);
-        sg.mA_hi = mThi[i]; sg.mA_lo = mTlo[i]; sg.mB_hi = mBhi[i]; sg.mB_lo = mBlo[i];
-        sg.k0 = k0;
-        sg.K = std::min(KSUB, K - k0);
-        sg.xoob = (K + 63) / 64 * 64;
-        ranges.push_back(sg);
         rent.push_back(i);
+        rk0.push_back(k0);
+        rK.push_back(std::min(KSUB, K - k0));
       }
     }
-    const int nparts = (int)ranges.size();
-    ps.nparts = nparts;   // 0: no term reaches this block, sigma = 0
-    out.psums.push_back(ps);
+    const int nparts = (int)rent.size();
+    std::vector<int> mW(nv, -1);
+    for (int v = 0; v < nv; ++v) {
+      PartialSum ps;
+      memset(&ps, 0, sizeof ps);
+      ps.ws = ws + (long long)v * z.nws + wsn;
+      ps.stride = blk;
+      ps.off = v * psi_stride + q.off;
+      ps.ld = ldw;
+      ps.n = q.da * q.db;
+      ps.cols = q.db;
+      ps.nparts = nparts;   // 0: no term reaches this block, sigma = 0
+      out.psums.push_back(ps);
+      if (nparts) mW[v] = mk3(ws + (long long)v * z.nws + wsn, q.db, q.da, nparts, ldw, blk, 32, 32, 1);
+    }
     if (nparts == 0) continue;
-    const int mW = mk3(ws + wsn, q.db, q.da, nparts, ldw, blk, 32, 32, 1);
     for (int pi = 0; pi < nparts; ++pi) {
-      int seg = (int)segs.size();
-      segs.push_back(ranges[pi]);
+      const int i = rent[pi];
+      const HClass &h = w.hc[E[i].ci];
+      const int K = (int)(h.terms.size() * w.bpad[i]);
+      std::vector<int> seg(nv);
+      for (int v = 0; v < nv; ++v) {
+        TSeg sg;
+        memset(&sg, 0, sizeof sg);
+        sg.mA_hi = mThi[v * ne + i]; sg.mA_lo = mTlo[v * ne + i];
+        sg.mB_hi = mBhi[i]; sg.mB_lo = mBlo[i];
+        sg.k0 = rk0[pi];
+        sg.K = rK[pi];
+        sg.xoob = (K + 63) / 64 * 64;
+        seg[v] = (int)segs.size();
+        segs.push_back(sg);
+      }
       if (Rq[po] > 1) {
-        pk.push_back({seg, mW, pi, Rq[po], (ranges[pi].K + 63) / 64, rent[pi]});
+        for (int v = 0; v < nv; ++v) pk.push_back({seg[v], mW[v], pi, Rq[po], (rK[pi] + 63) / 64, i, v});
         continue;
       }
       for (int m0 = 0; m0 < M; m0 += 128)
-        for (int n0 = 0; n0 < N; n0 += nt) {
-          TWork t;
-          memset(&t, 0, sizeof t);
-          t.s = segs[seg];
-          t.M = M; t.N = N; t.m0 = m0; t.n0 = n0; t.ntile = nt;
-          t.mode = TW_PARTIAL; t.alpha = 1.f;
-          t.fa = 1.f / w.sB[rent[pi]];
-          t.rn = w.rnA[rent[pi]];
-          t.pblk = E[rent[pi]].pi;
-          t.mOut_hi = mW; t.mOut_lo = mW; t.zout = pi;
-          w2.push_back(t);
-        }
+        for (int n0 = 0; n0 < N; n0 += nt)
+          for (int v = 0; v < nv; ++v) {
+            TWork t;
+            memset(&t, 0, sizeof t);
+            t.s = segs[seg[v]];
+            t.M = M; t.N = N; t.m0 = m0; t.n0 = n0; t.ntile = nt;
+            t.mode = TW_PARTIAL; t.alpha = 1.f;
+            t.fa = 1.f / w.sB[i];
+            t.rn = w.rnA[i];
+            t.pblk = v * (int)np + E[i].pi;
+            t.mOut_hi = mW[v]; t.mOut_lo = mW[v]; t.zout = pi;
+            w2.push_back(t);
+          }
     }
     wsn += a64((long long)nparts * blk);
   }
@@ -2432,7 +2495,7 @@ void split_tables(const Window &w, const SplitScratch &z, __half *Ph, __half *Pl
       t.pz[r] = pk[i].z;
       t.pfa[r] = 1.f / w.sB[pk[i].entry];
       t.prn[r] = w.rnA[pk[i].entry];
-      t.ppb[r] = E[pk[i].entry].pi;
+      t.ppb[r] = pk[i].vec * (int)np + E[pk[i].entry].pi;
       t.nchunk = std::max(t.nchunk, pk[i].nchunk);
     }
     t.s = segs[t.pseg[0]];
@@ -2459,7 +2522,15 @@ void split_tables(const Window &w, const SplitScratch &z, __half *Ph, __half *Pl
   std::stable_sort(w1.begin(), w1.end(), [&](const TWork &a, const TWork &b) {
     return cost(a) > cost(b);
   });
-  {
+  if (order1 == 2) {
+    std::vector<TWork> alt;
+    alt.reserve(w1.size());
+    for (size_t i = 0, j = w1.size(); i < j;) {
+      alt.push_back(w1[i++]);
+      if (i < j) alt.push_back(w1[--j]);
+    }
+    w1.swap(alt);
+  } else if (order1 == 0) {
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
@@ -2542,13 +2613,41 @@ void build_split(dmrg_ctx *C) {
       }
       C->tune_log.push_back({(double)ks, ms / 3.0});
     }
+    C->ksub_choice = best;
+    // stage-1 schedule with that range: tile-width cap x item order, the
+    // current default (128, mixed thirds) first; another must win by 1.5 %
+    const int cand[6][2] = {{128, 0}, {128, 1}, {128, 2}, {64, 0}, {64, 1}, {64, 2}};
+    SplitScratch zb = split_scratch_sizes(w, best);
+    float best1 = 1e30f;
+    int bc = 128, bo = 0;
+    for (auto &c : cand) {
+      split_tables(w, zb, P.Ph, P.Pl, P.Th, P.Tl, P.ws, C->tables, best, c[0], c[1]);
+      upload_tables(C, C->tables, s);
+      launch_split(C, x, y, s);   // warm
+      CK(cudaEventRecord(e0, s));
+      for (int r = 0; r < 3; ++r) launch_split(C, x, y, s);
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best1 * 0.985f) {
+        best1 = ms;
+        bc = c[0];
+        bo = c[1];
+      }
+      // logged as 100000 + 10 * cap + order, beside the split-K ranges
+      C->tune_log.push_back({100000.0 + 10.0 * c[0] + c[1], ms / 3.0});
+    }
+    C->cap1_choice = bc;
+    C->order1_choice = bo;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    C->ksub_choice = best;
   }
   w.ksub = best;
+  w.cap1 = C->cap1_choice ? C->cap1_choice : 128;
+  w.order1 = C->cap1_choice ? C->order1_choice : 0;
   SplitScratch z = split_scratch_sizes(w, best);
-  split_tables(w, z, P.Ph, P.Pl, P.Th, P.Tl, P.ws, C->tables, best);
+  split_tables(w, z, P.Ph, P.Pl, P.Th, P.Tl, P.ws, C->tables, best, w.cap1, w.order1);
   upload_tables(C, C->tables, s);
   CK(cudaStreamSynchronize(s));
   w.tf_ready = true;
@@ -2662,6 +2761,106 @@ void apply_split(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s) 
 
 // Synchronous read of the window's bounded-wait error word (split path).  The
 // word is cleared once read, so a time-out is reported once.
+void apply(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s, int precision);
+
+// ---------------------------------------------------------------------------
+// multi-vector split apply: nv vectors against one pass over the operators
+// ---------------------------------------------------------------------------
+BatchPlan &batch_plan(dmrg_ctx *C, int nv, cudaStream_t s) {
+  Window &w = C->win;
+  auto it = w.batch.find(nv);
+  if (it != w.batch.end()) return it->second;
+  if (!w.tf_ready) {
+    cudaStream_t save = C->stream;
+    C->stream = s;
+    build_split(C);
+    C->stream = save;
+  }
+  BatchPlan &b = w.batch[nv];
+  b.nv = nv;
+  const SplitScratch z = split_scratch_sizes(w, w.ksub);
+  auto fl = [&](long long n) { return (float *)w.buf.alloc(4 * std::max<long long>(n, 64)); };
+  auto hf = [&](long long n) { return (__half *)w.buf.alloc(2 * std::max<long long>(n, 64)); };
+  b.Ph = hf(nv * z.nP);
+  b.Pl = hf(nv * z.nP);
+  b.Th = hf(nv * z.nT);
+  b.Tl = hf(nv * z.nT);
+  b.ws = fl(nv * z.nws);
+  const size_t np = w.psi.size();
+  b.pstat = (PsiStat *)w.buf.alloc(sizeof(PsiStat) * std::max<size_t>(nv * np, 1));
+  std::vector<PsiDesc> pd;
+  for (int v = 0; v < nv; ++v)
+    for (const PsiDesc &d : psi_descs(w)) pd.push_back({d.off + v * w.psi_len, d.rows, d.cols});
+  b.pdesc = upload(w.buf, pd, s);
+  b.next = (int *)w.buf.alloc(2 * sizeof(int));
+  split_tables(w, z, b.Ph, b.Pl, b.Th, b.Tl, b.ws, b.tb, w.ksub, w.cap1, w.order1, nv, w.psi_len);
+  b.dsplit = upload(w.buf, b.tb.psi_split, s);
+  b.dmaps = upload(w.buf, b.tb.maps, s);
+  b.dseg = upload(w.buf, b.tb.segs, s);
+  b.dw1 = upload(w.buf, b.tb.w1, s);
+  b.dw2 = upload(w.buf, b.tb.w2, s);
+  b.dps = upload(w.buf, b.tb.psums, s);
+  b.psi_tiles = split_tile_count(b.tb.psi_split);
+  CK(cudaStreamSynchronize(s));
+  return b;
+}
+
+void launch_batch(dmrg_ctx *C, BatchPlan &b, const double *psi, double *sigma, cudaStream_t s) {
+  Window &w = C->win;
+  const int nps = (int)(b.nv * w.psi.size());
+  CK(psi_stats(b.pdesc, nps, psi, b.pstat, s));
+  CK(f16_split((const F16Split *)b.dsplit, (int)b.tb.psi_split.size(), b.pstat, psi, s, b.psi_tiles));
+  CK(split_gemm((const TWork *)b.dw1, (int)b.tb.w1.size(), b.next, (const TSeg *)b.dseg,
+                (const CUtensorMap *)b.dmaps, b.pstat, w.tf.err, s));
+  CK(split_gemm((const TWork *)b.dw2, (int)b.tb.w2.size(), b.next + 1, (const TSeg *)b.dseg,
+                (const CUtensorMap *)b.dmaps, b.pstat, w.tf.err, s));
+  CK(sum_partials((const PartialSum *)b.dps, (int)b.tb.psums.size(), sigma, s));
+}
+
+// nv vectors psi[v * psi_len ...] -> sigma[v * psi_len ...]; FP64 precision
+// applies them one by one, the split precision in one batched pass (graph
+// replay per (psi, sigma) pair as for single vectors)
+void apply_batch(dmrg_ctx *C, int nv, const double *psi, double *sigma, cudaStream_t s) {
+  Window &w = C->win;
+  if (C->precision == DMRG_FP64 || nv == 1) {
+    for (int v = 0; v < nv; ++v)
+      apply(C, psi + (long long)v * w.psi_len, sigma + (long long)v * w.psi_len, s, C->precision);
+    return;
+  }
+  BatchPlan &b = batch_plan(C, nv, s);
+  if (!C->use_graphs) {
+    launch_batch(C, b, psi, sigma, s);
+    return;
+  }
+  auto key = std::make_pair((const void *)psi, (const void *)sigma);
+  auto it = b.graphs.find(key);
+  if (it == b.graphs.end()) {
+    if (b.graphs.size() >= 16) {
+      for (auto &g : b.graphs) cudaGraphExecDestroy(g.second);
+      b.graphs.clear();
+    }
+    if (!C->cap_stream) CK(cudaStreamCreateWithFlags(&C->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = C->cap_stream;
+    cudaGraph_t g;
+    {
+      std::unique_lock<std::shared_mutex> lk(capture_lock());
+      CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      try {
+        launch_batch(C, b, psi, sigma, cs);
+      } catch (...) {
+        cudaStreamEndCapture(cs, &g);
+        throw;
+      }
+      CK(cudaStreamEndCapture(cs, &g));
+    }
+    cudaGraphExec_t ge;
+    CK(cudaGraphInstantiate(&ge, g, 0));
+    cudaGraphDestroy(g);
+    it = b.graphs.emplace(key, ge).first;
+  }
+  CK(cudaGraphLaunch(it->second, s));
+}
+
 void check_err_flag(dmrg_ctx *C, cudaStream_t s) {
   Window &w = C->win;
   if (!w.tf_ready) return;
@@ -3459,6 +3658,245 @@ void stvec(dmrg_ctx *C, const WinMeta &old, const double *psi_old, int side, dou
   C->prof[4] += now() - t0;
 }
 
+// ---------------------------------------------------------------------------
+// one-particle reduced density matrix at the window (Sec. II.B, III.C)
+// ---------------------------------------------------------------------------
+// gamma_ij = <c+_j c_i> = <c_j psi | c_i psi>: with w_k = c_k psi for every
+// mode k of the window (block products with the window's operators, in the
+// layout of the state space with one particle fewer), gamma = W W^T.
+// Spin-adapted: w_k = c~_k psi is a spin-1/2 state; its reduced coefficients
+// on the coupled pairs (a', b') carry the recoupling of [c~ (x) 1]^(1/2) (or
+// [1 (x) c~]^(1/2)) from the S = 0 window, and the spin-summed
+// gamma_ij = sum_sigma <c+_{j sigma} c_{i sigma}> = 2 w_j . w_i.
+// Output: spatial, spin-summed, in the rotated mode basis, gamma[i*N + j].
+void rdm1(dmrg_ctx *C, const double *psi, double *gamma, cudaStream_t s) {
+  Window &w = C->win;
+  const int N = C->N;
+  std::fill(gamma, gamma + (size_t)N * N, 0.0);
+  struct ModeOp {
+    int row;       // row of W
+    int spatial;   // output index
+    bool left;     // mode of L. (else .R)
+    const BlockPart *P;
+    std::vector<Ref> comps;
+  };
+  // classes of modes whose annihilators share one target layout
+  std::vector<std::vector<ModeOp>> classes;
+  if (C->su2) {
+    std::vector<ModeOp> v;
+    for (int side = 0; side < 2; ++side) {
+      const BlockPart &P = side == 0 ? w.Ld : w.Rd;
+      std::vector<int> sp;
+      for (int p : P.modes)
+        if (!has(sp, p >> 1)) sp.push_back(p >> 1);
+      for (int x : sp) {
+        auto it = P.ten.find(TKey{1, x, 0, 1});
+        if (it == P.ten.end()) continue;
+        ModeOp m{(int)v.size(), x, side == 0, &P, {}};
+        for (const Ref &r : it->second.r)
+          if (r.cls >= 0) m.comps.push_back(r);
+        v.push_back(m);
+      }
+    }
+    classes.push_back(v);
+  } else {
+    const int ncls = C->spinful ? 2 : 1;
+    classes.resize(ncls);
+    for (int side = 0; side < 2; ++side) {
+      const BlockPart &P = side == 0 ? w.Ld : w.Rd;
+      for (int p : P.modes) {
+        auto it = P.c.find(p);
+        if (it == P.c.end() || it->second.cls < 0) continue;
+        auto &v = classes[C->spinful ? (p & 1) : 0];
+        v.push_back(ModeOp{(int)v.size(), C->spinful ? p >> 1 : p, side == 0, &P, {it->second}});
+      }
+    }
+  }
+  const int tS = su2::tj_of(C->target);
+  WinBuf tmp(s);
+  for (auto &modes : classes) {
+    if (modes.empty()) continue;
+    // target layout: every (a', b') some w_k reaches
+    std::map<std::pair<int, int>, long long> off;
+    struct Job {
+      const ModeOp *m;
+      const PsiBlk *p;
+      int ao, bo;
+      const double *blk;
+      int ld;
+      double coef;
+    };
+    std::vector<Job> jobs;
+    for (const ModeOp &m : modes)
+      for (const Ref &r : m.comps) {
+        const OpClass &oc = m.P->cls[r.cls];
+        for (const PsiBlk &p : w.psi) {
+          const int in = m.left ? p.a : p.b;
+          const int b = oc.in2blk[in];
+          if (b < 0) continue;
+          const int out = oc.blk_out[b];
+          const int ao = m.left ? out : p.a, bo = m.left ? p.b : out;
+          double coef = 1.0;
+          if (!m.left && (qnum(w.Ld.basis.qn[p.a]) & 1)) coef = -1.0;   // c on .R passes L.'s particles
+          if (C->su2) {
+            const int ja = su2::tj_of(w.Ld.basis.qn[p.a]), jb = su2::tj_of(w.Rd.basis.qn[p.b]);
+            const int jao = su2::tj_of(w.Ld.basis.qn[ao]), jbo = su2::tj_of(w.Rd.basis.qn[bo]);
+            coef *= m.left ? su2::coupling(ja, jb, tS, jao, jbo, 1, 1, 0, 1)
+                           : su2::coupling(ja, jb, tS, jao, jbo, 1, 0, 1, 1);
+            if (coef == 0.0) continue;
+          }
+          const std::pair<int, int> key{ao, bo};
+          if (!off.count(key)) {
+            off[key] = 0;
+          }
+          jobs.push_back({&m, &p, ao, bo, oc.d + (long long)r.idx * oc.nnz + oc.blk_off[b],
+                          m.left ? p.da : p.db, coef});
+        }
+      }
+    long long len = 0;
+    for (auto &kv : off) {
+      kv.second = len;
+      len += (long long)w.Ld.basis.dim[kv.first.first] * w.Rd.basis.dim[kv.first.second];
+    }
+    const int nm = (int)modes.size();
+    double *W = (double *)tmp.alloc(8 * std::max<long long>(1, (long long)nm * len));
+    CK(cudaMemsetAsync(W, 0, 8 * std::max<long long>(1, (long long)nm * len), s));
+    std::vector<GemmDesc> dd;
+    std::vector<GemmSeg> gg;
+    long long tt = 0;
+    // blocks reached by several components of one mode accumulate (beta = 1)
+    for (const Job &j : jobs) {
+      const int dao = w.Ld.basis.dim[j.ao], dbo = w.Rd.basis.dim[j.bo];
+      double *dst = W + (long long)j.m->row * len + off[{j.ao, j.bo}];
+      const double *ps = psi + j.p->off;
+      if (j.m->left)   // (dao x da) . (da x db)
+        push_gemm(dd, gg, tt, dst, dbo, dao, dbo, j.p->da, j.blk, j.ld, 1, ps, j.p->db, 1, j.coef);
+      else             // (da x db) . (dbo x db)^T
+        push_gemm(dd, gg, tt, dst, dbo, dao, dbo, j.p->db, ps, j.p->db, 1, j.blk, 1, j.ld, j.coef);
+      dd.back().beta = 1.0;
+    }
+    // the beta = 1 accumulation needs the descriptors of one output block in
+    // order: run them in separate launches per component index
+    {
+      std::vector<GemmDesc> d1;
+      std::vector<GemmSeg> g1;
+      long long t1 = 0;
+      std::map<double *, int> seen;
+      std::vector<std::pair<GemmDesc, GemmSeg>> later;
+      for (size_t i = 0; i < dd.size(); ++i) {
+        if (seen[dd[i].C]++) {
+          later.push_back({dd[i], gg[dd[i].seg0]});
+          continue;
+        }
+        GemmDesc d = dd[i];
+        d.seg0 = (int)g1.size();
+        d.tile0 = t1;
+        t1 += (long long)d.tiles_m * d.tiles_n;
+        g1.push_back(gg[dd[i].seg0]);
+        d1.push_back(d);
+      }
+      run_gemms(d1, g1, t1, s);
+      for (auto &pr : later) {
+        std::vector<GemmDesc> d2{pr.first};
+        std::vector<GemmSeg> g2{pr.second};
+        d2[0].seg0 = 0;
+        d2[0].tile0 = 0;
+        run_gemms(d2, g2, (long long)d2[0].tiles_m * d2[0].tiles_n, s);
+      }
+    }
+    // G = W W^T, split over K ranges, partials summed in a fixed order
+    const long long KS = 16384;
+    const int nparts = (int)std::max<long long>(1, (len + KS - 1) / KS);
+    double *ws = (double *)tmp.alloc(8 * (size_t)nparts * nm * nm);
+    double *G = (double *)tmp.alloc(8 * (size_t)nm * nm);
+    dd.clear();
+    gg.clear();
+    tt = 0;
+    for (int pch = 0; pch < nparts; ++pch) {
+      const long long k0 = (long long)pch * KS, kl = std::min(KS, len - k0);
+      push_gemm(dd, gg, tt, ws + (size_t)pch * nm * nm, nm, nm, nm, (int)std::max<long long>(kl, 0),
+                W + k0, len, 1, W + k0, 1, len);
+    }
+    run_gemms(dd, gg, tt, s);
+    PartialSum64 ps;
+    ps.ws = ws;
+    ps.stride = (long long)nm * nm;
+    ps.off = 0;
+    ps.n = nm * nm;
+    ps.nparts = nparts;
+    std::vector<PartialSum64> psv{ps};
+    PartialSum64 *dps = upload(tmp, psv, s);
+    CK(launch_sum_partials64(dps, 1, G, s));
+    std::vector<double> Gh((size_t)nm * nm);
+    CK(cudaMemcpyAsync(Gh.data(), G, 8 * Gh.size(), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double f = C->su2 ? 2.0 : 1.0;
+    for (const ModeOp &a : modes)
+      for (const ModeOp &b : modes)   // gamma_ij = w_j . w_i, modes on opposite sides
+        if (a.left != b.left) gamma[(size_t)a.spatial * N + b.spatial] += f * Gh[(size_t)b.row * nm + a.row];
+  }
+  // Two modes of one side: the renormalized single operators of a block are
+  // projections, so <c_j psi | c_i psi> would miss the part of c_i psi outside
+  // the kept basis; the pair operator c+_j c_i renormalized as a whole gives
+  // the exact value, <psi| O (x) 1 |psi> = <O, rho_L.> with rho_L. = psi psi^T
+  // per sector (.R: psi^T psi).  Spin-adapted: E_ji = -sqrt(2) B^0_ji.
+  for (int side = 0; side < 2; ++side) {
+    const BlockPart &P = side == 0 ? w.Ld : w.Rd;
+    int c0 = -1;
+    for (size_t c = 0; c < P.cls.size(); ++c)
+      if (P.cls[c].shift == QN{0, 0} && P.cls[c].nnz > 0) c0 = (int)c;
+    if (c0 < 0) continue;
+    const OpClass &oc = P.cls[c0];
+    double *rho = (double *)tmp.alloc(8 * std::max<long long>(1, oc.nnz));
+    CK(cudaMemsetAsync(rho, 0, 8 * std::max<long long>(1, oc.nnz), s));
+    std::vector<GemmDesc> dd;
+    std::vector<GemmSeg> gg;
+    long long tt = 0;
+    for (size_t b = 0; b < oc.blk_in.size(); ++b) {
+      const int sec = oc.blk_in[b];
+      for (const PsiBlk &p : w.psi) {
+        if ((side == 0 ? p.a : p.b) != sec) continue;
+        double *dst = rho + oc.blk_off[b];
+        const double *ps = psi + p.off;
+        if (side == 0)   // psi psi^T (da x da)
+          push_gemm(dd, gg, tt, dst, p.da, p.da, p.da, p.db, ps, p.db, 1, ps, 1, p.db);
+        else             // psi^T psi (db x db)
+          push_gemm(dd, gg, tt, dst, p.db, p.db, p.db, p.da, ps, 1, p.db, ps, p.db, 1);
+      }
+    }
+    run_gemms(dd, gg, tt, s);
+    // <O_k, rho> for every operator k of the class: (nops x nnz) . (nnz)
+    double *vals = (double *)tmp.alloc(8 * std::max(1, oc.nops));
+    dd.clear();
+    gg.clear();
+    tt = 0;
+    push_gemm(dd, gg, tt, vals, 1, oc.nops, 1, (int)oc.nnz, oc.d, oc.nnz, 1, rho, 1, 0);
+    run_gemms(dd, gg, tt, s);
+    std::vector<double> vh(oc.nops);
+    CK(cudaMemcpyAsync(vh.data(), vals, 8 * vh.size(), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<int> sp;
+    for (int p : P.modes)
+      if (!has(sp, C->spinful ? p >> 1 : p)) sp.push_back(C->spinful ? p >> 1 : p);
+    auto val = [&](const Ref &r) { return (r.cls == c0) ? vh[r.idx] : 0.0; };
+    for (int j : sp)
+      for (int i : sp) {
+        double g = 0.0;
+        if (C->su2) {
+          auto it = P.ten.find(TKey{4, j, i, 0});
+          if (it != P.ten.end()) g = -std::sqrt(2.0) * val(it->second.r[0]);
+        } else {
+          for (int sgm = 0; sgm < (C->spinful ? 2 : 1); ++sgm) {
+            const int pj = C->spinful ? 2 * j + sgm : j, pi = C->spinful ? 2 * i + sgm : i;
+            auto it = P.cdc.find({pj, pi});
+            if (it != P.cdc.end()) g += val(it->second);
+          }
+        }
+        gamma[(size_t)i * N + j] = g;   // gamma_ij = <c+_j c_i>
+      }
+  }
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -3907,6 +4345,22 @@ int dmrg_heff_apply(dmrg_ctx *C, const double *psi, double *sigma, void *stream)
   });
 }
 
+int dmrg_heff_apply_batch(dmrg_ctx *C, int nv, const double *psi, double *sigma, void *stream) {
+  if (!C || !psi || !sigma || nv < 1 || nv > 64) return DMRG_ERR_ARG;
+  if (!C->win.valid) {
+    C->err = "no window built";
+    return DMRG_ERR_STATE;
+  }
+  return guard(C, [&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    poll_flags(C, false, s);
+    take_sticky(C);
+    apply_batch(C, nv, psi, sigma, s);
+    if (C->precision == DMRG_SPLIT) post_flag(C, 0, C->win.tf.err, s);
+    note_use(C->win, s);
+  });
+}
+
 int dmrg_sync(dmrg_ctx *C, void *stream) {
   if (!C) return DMRG_ERR_ARG;
   return guard(C, [&] {
@@ -3987,7 +4441,7 @@ int dmrg_heff_apply_split_static(dmrg_ctx *C, const double *psi, double *sigma, 
       // table sizes do not depend on the pointers: size them with a dry run
       SplitTables probe;
       __half *hb = (__half *)b;
-      split_tables(w, z, hb, hb, hb, hb, (float *)b, probe, ks);
+      split_tables(w, z, hb, hb, hb, hb, (float *)b, probe, ks, w.cap1, w.order1);
       size_t off = 256;
       ow.o_maps = off; off = al(off + probe.maps.size() * sizeof(CUtensorMap));
       ow.o_seg = off; off = al(off + probe.segs.size() * sizeof(TSeg));
@@ -4012,7 +4466,7 @@ int dmrg_heff_apply_split_static(dmrg_ctx *C, const double *psi, double *sigma, 
                            "(use dmrg_heff_apply for larger windows)", off, cap);
       ow.gen = -1;
       split_tables(w, z, (__half *)(b + oPh), (__half *)(b + oPl), (__half *)(b + oTh),
-                   (__half *)(b + oTl), (float *)(b + oW), ow.tb, ks);
+                   (__half *)(b + oTl), (float *)(b + oW), ow.tb, ks, w.cap1, w.order1);
       const SplitTables &t = ow.tb;
       const std::vector<PsiDesc> pd = psi_descs(w);
       auto put = [&](size_t o, const void *src, size_t n) {
@@ -4146,6 +4600,15 @@ int dmrg_heff_split_plan(dmrg_ctx *C, double *out4) {
 long long dmrg_sweep_next_use(int n_sites, int pass, int l, int left, int n) {
   if (n_sites < 2 || (pass != 0 && pass != 1) || l < 0 || l > n_sites - 2) return -2;
   return next_use(n_sites, pass, l, left != 0, n);
+}
+
+int dmrg_rdm1(dmrg_ctx *C, const double *psi, double *gamma, void *stream) {
+  if (!C || !psi || !gamma) return DMRG_ERR_ARG;
+  if (!C->win.valid) {
+    C->err = "no window built";
+    return DMRG_ERR_STATE;
+  }
+  return guard(C, [&] { rdm1(C, psi, gamma, (cudaStream_t)stream); });
 }
 
 int dmrg_staging_stats(dmrg_ctx *C, double *out8) {
