@@ -66,9 +66,7 @@ TRAFFIC_SHA = "986c6afcb7e53341"
 TRAFFIC = {("hubbard6x6_su2_D1024", "k_split_gemm stage1"): 1.0350 * 6.1674e9,
            ("hubbard6x6_su2_D1024", "k_split_gemm stage2"): 1.1510 * 6.1674e9,
            ("hubbard6x6_su2_D512", "k_split_gemm stage1"): 1.5547e9,
-           ("hubbard6x6_su2_D512", "k_split_gemm stage2"): 1.7289e9,
-           ("hubbard6x6_D1024", "k_split_gemm stage1"): 5.180e9,
-           ("hubbard6x6_D1024", "k_split_gemm stage2"): 5.715e9}
+           ("hubbard6x6_su2_D512", "k_split_gemm stage2"): 1.7289e9}
 
 
 def traffic_of(workload, kernel):
@@ -290,6 +288,9 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-c1", action="store_true")
+    ap.add_argument("--profile-batch", type=int, default=0,
+                    help="build the window, then run one NV-vector split apply inside the "
+                         "NVTX range 'batch' (for an ncu capture) and exit")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -311,6 +312,20 @@ def main():
     flops = g.heff_flops()
     psi = torch.tensor(synth.random_psi(layout, 1), device="cuda")
     sig = torch.empty_like(psi)
+    if args.profile_batch:
+        nv = args.profile_batch
+        g.set_precision(lib.SPLIT)
+        X = torch.tensor(np.stack([synth.random_psi(layout, 1 + v) for v in range(nv)]),
+                         device="cuda")
+        Y = torch.empty_like(X)
+        g.heff_apply_batch(X, Y, stream)      # plan, tuner and graph outside the range
+        stream.synchronize()
+        torch.cuda.nvtx.range_push("batch")
+        g.heff_apply_batch(X, Y, stream)
+        stream.synchronize()
+        torch.cuda.nvtx.range_pop()
+        g.close()
+        return
 
     def timed(prec, steps, warmup):
         """Mean ms per apply over `steps` (graph replay, CUDA events on the

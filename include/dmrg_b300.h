@@ -137,6 +137,15 @@ int dmrg_set_isometry(dmrg_ctx *ctx, int side, int site, int n_sectors,
                       const int *qn, const int *rows, const int *cols,
                       const double *data);
 
+/* Eq. 4 -- a seeded random right-canonical MPS basis as the start of
+ * dmrg_sweep (the paper's runs start from a warm-up state the configs do not
+ * fix): right isometries 1..N-1 made by the library, each sector's columns
+ * an orthonormalised Gaussian matrix (splitmix64 / Box-Muller deviates),
+ * keeping at most d_max states (multiplets) spread over the sectors in
+ * proportion to their dimension (at least one per sector).  Replaces the
+ * right isometries set before.  Errors: ARG. */
+int dmrg_random_start(dmrg_ctx *ctx, uint64_t seed);
+
 /* a3/a4 -- build the renormalized block operators L_0..L_l and R_N..R_{l+2}
  * from the isometries, the enlarged blocks L. and .R of window (l, l+1) and
  * the sector tables of H_eff (Sec. II.A "Tables").  Errors: STATE, OOM, CUDA. */

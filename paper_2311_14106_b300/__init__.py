@@ -33,7 +33,7 @@ HEADER_FUNCTIONS = [
     "dmrg_heff_split_plan", "dmrg_heff_entries", "dmrg_selftest_bounded_wait",
     "dmrg_sync", "dmrg_get_mps", "dmrg_get_center", "dmrg_heff_split_paths",
     "dmrg_selftest_timeout_report", "dmrg_staging_stats", "dmrg_sweep_next_use",
-    "dmrg_rdm1", "dmrg_heff_apply_batch",
+    "dmrg_rdm1", "dmrg_heff_apply_batch", "dmrg_random_start",
 ]
 
 
@@ -90,6 +90,7 @@ _sig = {
     "dmrg_sweep_next_use": (ctypes.c_longlong, [ctypes.c_int] * 5),
     "dmrg_rdm1": (ctypes.c_int, [_P, _P, _D, _P]),
     "dmrg_heff_apply_batch": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
+    "dmrg_random_start": (ctypes.c_int, [_P, ctypes.c_uint64]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -211,6 +212,10 @@ class Dmrg:
             self.set_isometry(0, n, iso)
         for n, iso in (right or {}).items():
             self.set_isometry(1, n, iso)
+
+    def random_start(self, seed):
+        """A seeded random right-canonical MPS basis made by the library."""
+        self._check(_lib.dmrg_random_start(self._h, seed), "random_start")
 
     def build_block_ops(self, l, stream=None):
         self._check(_lib.dmrg_build_block_ops(self._h, l, _stream_ptr(stream)), "build_block_ops")

@@ -4238,6 +4238,89 @@ int dmrg_set_hamiltonian(dmrg_ctx *C, const double *t, const double *V, const do
   });
 }
 
+int dmrg_random_start(dmrg_ctx *C, uint64_t seed) {
+  if (!C) return DMRG_ERR_ARG;
+  return guard(C, [&] {
+    // site states (the enlargement's order)
+    std::vector<QN> sq;
+    std::vector<int> stj;
+    if (C->su2) {
+      sq = {su2::label(0, 0), su2::label(1, 1), su2::label(2, 0)};
+      stj = {0, 1, 0};
+    } else if (C->spinful) {
+      sq = {{0, 0}, {0, 1}, {1, 0}, {1, 1}};
+    } else {
+      sq = {{0, 0}, {1, 0}};
+    }
+    // counter-based normal deviates (splitmix64 + Box-Muller)
+    uint64_t ctr = seed * 0x9E3779B97F4A7C15ull + 1;
+    auto u01 = [&]() {
+      uint64_t z = (ctr += 0x9E3779B97F4A7C15ull);
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z ^= z >> 31;
+      return ((z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    };
+    auto normal = [&]() { return std::sqrt(-2.0 * std::log(u01())) * std::cos(6.283185307179586 * u01()); };
+    const int D = std::max(1, C->cfg.d_max);
+    std::map<QN, int> dims{{QN{0, 0}, 1}};
+    for (int n = C->N - 1; n >= 1; --n) {
+      // sectors of site_n x R_{n+1} that can still reach the target
+      std::map<QN, int> e;
+      for (size_t k = 0; k < sq.size(); ++k)
+        for (auto &kv : dims) {
+          if (C->su2) {
+            const int t1 = su2::tj_of(kv.first), t2 = stj[k];
+            for (int tj = std::abs(t1 - t2); tj <= t1 + t2; tj += 2) {
+              const QN Q = su2::label(su2::n_of(kv.first) + su2::n_of(sq[k]), tj);
+              if (allowed_q(C, Q, n)) e[Q] += kv.second;
+            }
+          } else {
+            const QN Q = qadd(kv.first, sq[k]);
+            if (allowed_q(C, Q, n)) e[Q] += kv.second;
+          }
+        }
+      long long tot = 0;
+      for (auto &kv : e) tot += kv.second;
+      std::map<QN, int> keep;
+      for (auto &kv : e) {
+        int d = tot <= D ? kv.second : (int)((long long)D * kv.second / tot);
+        d = std::min(kv.second, std::max(d, 1));
+        keep[kv.first] = d;
+      }
+      Iso T;
+      long long off = 0;
+      for (auto &kv : keep) {
+        const int rows = e[kv.first], cols = kv.second;
+        std::vector<double> m((size_t)rows * cols);
+        for (double &x : m) x = normal();
+        // orthonormal columns: modified Gram-Schmidt, twice
+        for (int c = 0; c < cols; ++c)
+          for (int pass = 0; pass < 2; ++pass) {
+            for (int c2 = 0; c2 < c; ++c2) {
+              double d = 0;
+              for (int r = 0; r < rows; ++r) d += m[(size_t)r * cols + c] * m[(size_t)r * cols + c2];
+              for (int r = 0; r < rows; ++r) m[(size_t)r * cols + c] -= d * m[(size_t)r * cols + c2];
+            }
+            double nn = 0;
+            for (int r = 0; r < rows; ++r) nn += m[(size_t)r * cols + c] * m[(size_t)r * cols + c];
+            nn = std::sqrt(nn);
+            if (!(nn > 1e-12)) fail(DMRG_ERR_STATE, "internal: degenerate random isometry");
+            for (int r = 0; r < rows; ++r) m[(size_t)r * cols + c] /= nn;
+          }
+        T.qn.push_back(kv.first);
+        T.rows.push_back(rows);
+        T.cols.push_back(cols);
+        T.off.push_back(off);
+        off += (long long)rows * cols;
+        T.host.insert(T.host.end(), m.begin(), m.end());
+      }
+      C->riso[n] = std::move(T);
+      dims = keep;
+    }
+  });
+}
+
 int dmrg_set_isometry(dmrg_ctx *C, int side, int site, int ns, const int *qn, const int *rows,
                       const int *cols, const double *data) {
   if (!C || (side != 0 && side != 1) || site < 1 || site > C->N - 1 || ns < 1 || !qn || !rows ||

@@ -86,7 +86,6 @@ def estimate_bytes(req):
 
 def run_one(req, precision, stream=None, davidson_tol=1e-7, rng_iso=None):
     """Solve one request synchronously; returns (energies, profile)."""
-    import synth
     spinful = req.model == "hubbard"
     N = req.Lx * req.Ly
     tgt = target_of(req)
@@ -107,12 +106,7 @@ def run_one(req, precision, stream=None, davidson_tol=1e-7, rng_iso=None):
     g.set_graphs(False)
     try:
         g.set_hamiltonian(T, V, momentum_basis(req.Lx, req.Ly))
-        if su2:
-            g.set_mps(right=synth.random_right_isometries_su2(N, (tgt[0] + tgt[1], 0), req.D, 1,
-                                                              req.seed))
-        else:
-            g.set_mps(right=synth.random_right_isometries(N, spinful, tgt if spinful else (tgt[0],),
-                                                          req.D, 1, req.seed))
+        g.random_start(req.seed)
         E = g.sweep(req.n_sweeps, stream=stream)
         prof = g.profile()
     finally:

@@ -57,14 +57,14 @@ def test_traffic_reported_only_for_the_measured_kernel_source(monkeypatch, tmp_p
     sys.path.insert(0, ROOT)
     import bench
     # the committed figures belong to the committed kernel source
-    assert bench.traffic_of("hubbard6x6_D1024", "k_split_gemm stage1") == \
-        bench.TRAFFIC[("hubbard6x6_D1024", "k_split_gemm stage1")]
+    assert bench.traffic_of("hubbard6x6_su2_D1024", "k_split_gemm stage1") == \
+        bench.TRAFFIC[("hubbard6x6_su2_D1024", "k_split_gemm stage1")]
     assert bench.traffic_of("hubbard6x6_D512", "k_split_gemm stage1") is None
     # any other source text: no traffic figure
     other = tmp_path / "k.cu"
     other.write_text(open(bench.TRAFFIC_SOURCE).read() + "\n// changed\n")
     monkeypatch.setattr(bench, "TRAFFIC_SOURCE", str(other))
-    assert bench.traffic_of("hubbard6x6_D1024", "k_split_gemm stage1") is None
+    assert bench.traffic_of("hubbard6x6_su2_D1024", "k_split_gemm stage1") is None
 
 
 def test_peaks_fall_back_without_measured_file(monkeypatch, tmp_path):

@@ -324,3 +324,15 @@ def test_graph_cache_many_buffer_pairs():
     for o in outs:
         assert torch.equal(o, ref)
     g.close()
+
+
+def test_sweep_from_library_random_start_matches_ed():
+    """dmrg_random_start (the library's own seeded start, used by serving):
+    spinless 3x3, two sweeps at D = 20 reach the ED ground energy."""
+    model, ham, h, W = problem(3, 3, False, (4,))
+    e_ed = ed.ground_energy(h, W, 4)[0]
+    g = make_gpu(9, (4,), False, ham, d_max=20, davidson_tol=1e-10)
+    g.random_start(11)
+    E = g.sweep(2)
+    assert abs(E[-1] - e_ed) <= 1e-9 * abs(e_ed), (E, e_ed)
+    g.close()

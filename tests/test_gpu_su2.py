@@ -179,3 +179,16 @@ def test_su2_split_sweeps_match_fp64_at_truncated_D():
         g.close()
     for a, b in zip(E[lib.SPLIT], E[lib.FP64]):
         assert abs(a - b) <= 1e-9 * abs(b), E
+
+
+def test_su2_sweep_from_library_random_start():
+    """dmrg_random_start in multiplet sectors: Hubbard 3x3, 8 electrons, full
+    D, two sweeps reach the ED ground energy."""
+    ham = hubbard(3, 3)
+    model, h, W = oracle_model(ham, 8)
+    e_ed = ed.ground_energy(h, W, 8, n_up=4)[0]
+    g = library(9, 8, ham, 400, davidson_tol=1e-10)
+    g.random_start(5)
+    E = g.sweep(2)
+    assert abs(E[-1] - e_ed) <= 1e-9 * abs(e_ed), (E, e_ed)
+    g.close()
