@@ -2100,6 +2100,7 @@ namespace {
 // ---------------------------------------------------------------------------
 long long r4(long long x) { return (x + 3) & ~3LL; }
 long long r8(long long x) { return (x + 7) & ~7LL; }
+long long r16(long long x) { return (x + 15) & ~15LL; }
 long long a64(long long x) { return (x + 63) & ~63LL; }
 int ntile_of(int n) { return n > 128 ? 128 : ((n + 15) / 16) * 16; }
 
@@ -2137,7 +2138,7 @@ SplitScratch split_scratch_sizes(const Window &w, int KSUB) {
     z.nT += a64(q.da * n * z.ldT[i]);
   }
   for (size_t i = 0; i < np; ++i) {
-    z.ldP[i] = r8(w.psi[i].da);
+    z.ldP[i] = r16(w.psi[i].da);   // K of stage 1, zero-padded to 16 halves
     z.offP[i] = z.nP;
     z.nP += a64(w.psi[i].db * z.ldP[i]);
   }
@@ -2180,7 +2181,7 @@ void split_operator_copies(dmrg_ctx *C) {
     const HClass &h = w.hc[E[i].ci];
     const PsiBlk &p = w.psi[E[i].pi], &q = w.psi[E[i].po];
     const long long n = (long long)h.terms.size();
-    w.ldA[i] = r8(p.da);
+    w.ldA[i] = r16(p.da);   // K of stage 1, zero-padded to 16 halves
     w.offA[i] = nA;
     nA += a64(q.da * n * w.ldA[i]);
     w.bpad[i] = r8(p.db);
@@ -2335,8 +2336,8 @@ void split_tables(const Window &w, const SplitScratch &z, __half *Ph, __half *Pl
     for (size_t i = 0; i < np; ++i) {
       const PsiBlk &p = w.psi[i];
       const long long o = (long long)v * z.nP + z.offP[i];
-      mPh[v * np + i] = mk(Ph + o, p.db, p.da, z.ldP[i], ntile1(p.db));
-      mPl[v * np + i] = mk(Pl + o, p.db, p.da, z.ldP[i], ntile1(p.db));
+      mPh[v * np + i] = mk(Ph + o, p.db, z.ldP[i], z.ldP[i], ntile1(p.db));
+      mPl[v * np + i] = mk(Pl + o, p.db, z.ldP[i], z.ldP[i], ntile1(p.db));
     }
   auto &segs = out.segs;
   auto &w1 = out.w1;
@@ -2358,8 +2359,8 @@ void split_tables(const Window &w, const SplitScratch &z, __half *Ph, __half *Pl
     const int nl = qnum(w.Ld.basis.qn[p.a]);
     alpha[i] = (h.pB && (nl & 1)) ? -1.f : 1.f;
     const long long bp = z.ldT[i];   // = r8(p.db)
-    const int ahi = mk(P.Ah + w.offA[i], (long long)q.da * n, p.da, w.ldA[i], 128);
-    const int alo = mk(P.Al + w.offA[i], (long long)q.da * n, p.da, w.ldA[i], 128);
+    const int ahi = mk(P.Ah + w.offA[i], (long long)q.da * n, w.ldA[i], w.ldA[i], 128);
+    const int alo = mk(P.Al + w.offA[i], (long long)q.da * n, w.ldA[i], w.ldA[i], 128);
     // T as stage-1 output: rows (a', k), columns b (padded); as stage-2
     // operand: rows a', K = (k, b)
     const long long rowsT = (long long)q.da * n;

@@ -724,7 +724,10 @@ __global__ void k_f16_split(const F16Split *__restrict__ ds, const PsiStat *__re
   const F16Split d = ds[blockIdx.z];
   const double *src = d.src ? d.src : bind + d.src_off;
   const double s = d.scale > 0.f ? (double)d.scale : (double)pow2_scale(pstat[d.pblk].mx);
-  const int tr = (d.rows + 31) / 32, tc = (d.cols + 31) / 32;
+  // the destination's padding (columns up to dst_ld) is written with zeros:
+  // the tensor maps of the tcgen05 stages read K up to the padded width
+  const int prow = d.trans ? d.dst_ld : d.rows, pcol = d.trans ? d.cols : d.dst_ld;
+  const int tr = (prow + 31) / 32, tc = (pcol + 31) / 32;
   for (int t = blockIdx.x; t < tr * tc; t += gridDim.x) {
     const int r0 = (t / tc) * 32, c0 = (t % tc) * 32;
     for (int j = threadIdx.y; j < 32; j += blockDim.y) {
@@ -744,7 +747,7 @@ __global__ void k_f16_split(const F16Split *__restrict__ ds, const PsiStat *__re
         c = c0 + threadIdx.x;
         x = tile[j][threadIdx.x];
       }
-      if (c < d.cols && r < d.rows) {
+      if (c < pcol && r < prow) {
         const double y = x * s;
         const __half h = __double2half(y);
         const __half l = __double2half(y - (double)__half2float(h));

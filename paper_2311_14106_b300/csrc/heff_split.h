@@ -119,7 +119,7 @@ struct F16Split {
 };
 
 struct SplitPlan {
-  // operand storage (FP16 hi, lo; rows padded to 8 halves)
+  // operand storage (FP16 hi, lo; A rows zero-padded to 16 halves, B rows to 8)
   __half *Ah = nullptr, *Al = nullptr;   // [a'][k][a]
   __half *Bh = nullptr, *Bl = nullptr;   // [b'][k][b_pad]
   __half *Th = nullptr, *Tl = nullptr;   // [a'][k][b_pad], per apply
