@@ -149,7 +149,7 @@ def job_value(flops_per_step, ms, world):
     return world * flops_per_step / (ms * 1e-3) / 1e12
 
 
-def build_problem(lib, wl, dev_stream):
+def build_problem(lib, wl, dev_stream, hbm_budget=0):
     model, Lx, Ly, (nu, nd), coup, D, sym, rot, _ = wl
     N = Lx * Ly
     if model == "hubbard":
@@ -160,7 +160,8 @@ def build_problem(lib, wl, dev_stream):
     if rot is not None:
         U = U @ synth.haar_rotation(N, rot)
     l = N // 2 - 1
-    kw = dict(d_max=D, davidson_tol=1e-6, davidson_max_sub=24, davidson_max_iter=400)
+    kw = dict(d_max=D, davidson_tol=1e-6, davidson_max_sub=24, davidson_max_iter=400,
+              hbm_budget_bytes=int(hbm_budget))
     if sym == "su2":
         g = lib.Dmrg(N, nu, su2=True, **kw)
         li = synth.random_left_isometries_su2(N, (nu, 0), D, l, 5)
@@ -288,6 +289,13 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-c1", action="store_true")
+    ap.add_argument("--hbm-budget-gb", type=float, default=0.0,
+                    help="cfg.hbm_budget_bytes of the context: blocks are released once the "
+                         "next one is built, and the FP64 stacks once the split path has its "
+                         "FP16 copies (needed for the 8x8 D=2048 window)")
+    ap.add_argument("--split-only", action="store_true",
+                    help="time the split path alone (no FP64 leg, solve, serving or C1): "
+                         "for windows whose FP64 and split stacks do not fit together")
     ap.add_argument("--profile-batch", type=int, default=0,
                     help="build the window, then run one NV-vector split apply inside the "
                          "NVTX range 'batch' (for an ncu capture) and exit")
@@ -307,7 +315,9 @@ def main():
         dist.init_process_group("nccl")
     wl = WORKLOADS[args.workload]
     stream = torch.cuda.Stream()
-    g, l, t_build = build_problem(lib, wl, stream)
+    g, l, t_build = build_problem(lib, wl, stream, args.hbm_budget_gb * 1e9)
+    free_b, total_b = torch.cuda.mem_get_info()
+    mem_used_gb = (total_b - free_b) / 1e9
     n, layout = g.heff_layout()
     flops = g.heff_flops()
     psi = torch.tensor(synth.random_psi(layout, 1), device="cuda")
@@ -384,10 +394,12 @@ def main():
         except Exception as e:   # a batch that does not fit is reported, not fatal
             batched.append({"nv": nv, "error": repr(e)[:200]})
     # FP64 path (fewer steps: FP64 throughput is ~1/100 of the split path)
-    k64 = max(2, min(args.steps, 5))
-    ms_64, st_64 = timed(lib.FP64, k64, 1)
-    sig_64 = sig.clone()
-    err_sigma = float((sig_split - sig_64).norm() / sig_64.norm())
+    ms_64, st_64, err_sigma = None, None, None
+    if not args.split_only:
+        k64 = max(2, min(args.steps, 5))
+        ms_64, st_64 = timed(lib.FP64, k64, 1)
+        sig_64 = sig.clone()
+        err_sigma = float((sig_split - sig_64).norm() / sig_64.norm())
     # end-to-end through the host-buffer entry point (pinned host memory)
     g.set_precision(lib.SPLIT)
     hp = torch.tensor(synth.random_psi(layout, 1)).pin_memory()
@@ -404,7 +416,7 @@ def main():
     e2e_ms = (time.perf_counter() - t0) / args.steps * 1e3
     # Davidson solves of the window with both paths (energy at FP64 RQ)
     solve = {}
-    if not args.no_solve:
+    if not args.no_solve and not args.split_only:
         for name, prec in (("split", lib.SPLIT), ("fp64", lib.FP64)):
             g.set_precision(prec)
             x = torch.zeros_like(psi)
@@ -419,7 +431,7 @@ def main():
     # serving stream: Poisson arrivals of independent solves (config-4 pattern,
     # reduced to 4x4 lattices and D <= 128 so that both arms fit in a minute)
     serving_out = None
-    if not args.no_serving and rank == 0:
+    if not args.no_serving and not args.split_only and rank == 0:
         from paper_2311_14106_b300 import serving as srvmod
         mix = [("spinless", 4, 4, (0.0, 4.0), [64, 128]), ("hubbard", 4, 4, (0.0, 8.0), [64, 128])]
         serving_out = {"stream": "12 requests, exponential inter-arrival mean 0.1 s (seed 3); "
@@ -442,7 +454,7 @@ def main():
     fp64_peak = fp64_peak_probe(torch) if rank == 0 else None
     # config C1 (4x4 spinless, D = 128, FP64, 6 sweeps): per sweep and per matvec
     c1 = None
-    if not args.no_c1 and rank == 0:
+    if not args.no_c1 and not args.split_only and rank == 0:
         c1 = c1_sweeps(lib, stream)
     hbm, bf16, src = peaks()
     tc_peak = bf16 * F16_OVER_BF16
@@ -468,11 +480,17 @@ def main():
         "data": "synthetic",
         "config": {"workload": args.workload, "description": wl[8], "psi_len": n,
                    "algorithmic_flops_per_step": flops, "l2": "operator stacks >> L2; no flush",
-                   "parallelism": f"replicas x{world}", "block_build_seconds": t_build},
-        "fp64": {"ms_per_step": ms_64, "tflops": flops / (ms_64 * 1e-3) / 1e12,
-                 "stage_ms": st_64[1:3].tolist(), "peak_probe": fp64_peak,
-                 "frac_of_dgemm": (flops / (ms_64 * 1e-3) / 1e12 / fp64_peak["dgemm_tflops"])
-                 if fp64_peak else None},
+                   "parallelism": f"replicas x{world}", "block_build_seconds": t_build,
+                   "hbm_budget_bytes": int(args.hbm_budget_gb * 1e9),
+                   "device_memory_used_gb": mem_used_gb,
+                   "split_only": "FP64 leg, solve, serving and C1 not run (FP64 and split "
+                                 "stacks of this window do not fit together)"
+                                 if args.split_only else None},
+        "fp64": None if ms_64 is None else {
+            "ms_per_step": ms_64, "tflops": flops / (ms_64 * 1e-3) / 1e12,
+            "stage_ms": st_64[1:3].tolist(), "peak_probe": fp64_peak,
+            "frac_of_dgemm": (flops / (ms_64 * 1e-3) / 1e12 / fp64_peak["dgemm_tflops"])
+            if fp64_peak else None},
         "split_kernel_ms": dict(zip(["psi_split", "stage1", "stage2", "partial_sum"],
                                     st_split[:4].tolist())),
         "autotuner": [({"ksub": k} if k < 100000 else

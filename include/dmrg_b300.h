@@ -344,6 +344,17 @@ int dmrg_rdm1(dmrg_ctx *ctx, const double *psi, double *gamma, void *stream);
  * budget.  Counters accumulate over the context's life.  Errors: ARG. */
 int dmrg_staging_stats(dmrg_ctx *ctx, double *out8);
 
+/* Memory of the FP64 path of the current window.  Its operator stacks and
+ * its intermediate T sit at fixed device addresses whose physical memory can
+ * be given back: T is backed on the first FP64 H_eff*psi, and with
+ * cfg.hbm_budget_bytes > 0 the stacks and T are given back as soon as the
+ * split path has built its FP16 copies (the next FP64 H_eff*psi gathers the
+ * stacks again from the window's blocks, stream-ordered; results are
+ * bitwise the same).  out4: [0] 1 if the FP64 stacks are backed, [1] 1 if T
+ * is backed, [2] bytes of the stacks, [3] bytes of T.  Errors: ARG, STATE
+ * (no window). */
+int dmrg_heff_fp64_state(dmrg_ctx *ctx, long long *out4);
+
 /* Windows from sweep position (pass 0 = left to right at window l, pass 1 =
  * right to left) to the next use of block L_n (left = 1) or R_n (left = 0),
  * -1 if the sweep rebuilds it first, -2 for bad arguments: the staging

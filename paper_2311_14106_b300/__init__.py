@@ -33,7 +33,7 @@ HEADER_FUNCTIONS = [
     "dmrg_heff_split_plan", "dmrg_heff_entries", "dmrg_selftest_bounded_wait",
     "dmrg_sync", "dmrg_get_mps", "dmrg_get_center", "dmrg_heff_split_paths",
     "dmrg_selftest_timeout_report", "dmrg_staging_stats", "dmrg_sweep_next_use",
-    "dmrg_rdm1", "dmrg_heff_apply_batch", "dmrg_random_start",
+    "dmrg_rdm1", "dmrg_heff_apply_batch", "dmrg_random_start", "dmrg_heff_fp64_state",
 ]
 
 
@@ -91,6 +91,7 @@ _sig = {
     "dmrg_rdm1": (ctypes.c_int, [_P, _P, _D, _P]),
     "dmrg_heff_apply_batch": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
     "dmrg_random_start": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "dmrg_heff_fp64_state": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong)]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -359,6 +360,13 @@ class Dmrg:
         keys = ["h2d_bytes", "h2d_seconds", "d2h_bytes", "peak_resident_bytes", "offloads",
                 "reloads", "releases", "budget"]
         return dict(zip(keys, out.tolist()))
+
+    def heff_fp64_state(self):
+        """Physical memory of the window's FP64 path (see dmrg_heff_fp64_state)."""
+        out = (ctypes.c_longlong * 4)()
+        self._check(_lib.dmrg_heff_fp64_state(self._h, out), "heff_fp64_state")
+        return {"stacks_backed": bool(out[0]), "t_backed": bool(out[1]),
+                "stack_bytes": int(out[2]), "t_bytes": int(out[3])}
 
     def heff_split_paths(self):
         """Code paths of the split plan (see dmrg_heff_split_paths)."""

@@ -3,6 +3,7 @@
 // (normal and complementary), the two-site window, H_eff*psi, Davidson,
 // truncation and sweeps.  All bulk arithmetic runs in the CUDA kernels of
 // kernels.cu / heff_split.cu; this file builds their work lists.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cusolverDn.h>
 
@@ -203,6 +204,127 @@ struct WinBuf {
   ~WinBuf() { clear(); }
 };
 
+// Device memory at a fixed virtual address whose physical memory can be
+// given back and taken again (CUDA virtual memory management): the work
+// descriptors that point into it stay valid while it is unmapped.  Used for
+// the FP64 operator stacks and the FP64 intermediate of a window, which the
+// split-precision path needs only while it builds its FP16 copies.
+struct VmmFns {
+  CUresult (*reserve)(CUdeviceptr *, size_t, size_t, CUdeviceptr, unsigned long long);
+  CUresult (*addr_free)(CUdeviceptr, size_t);
+  CUresult (*create)(CUmemGenericAllocationHandle *, size_t, const CUmemAllocationProp *,
+                     unsigned long long);
+  CUresult (*release)(CUmemGenericAllocationHandle);
+  CUresult (*map)(CUdeviceptr, size_t, size_t, CUmemGenericAllocationHandle, unsigned long long);
+  CUresult (*unmap)(CUdeviceptr, size_t);
+  CUresult (*set_access)(CUdeviceptr, size_t, const CUmemAccessDesc *, size_t);
+  CUresult (*granularity)(size_t *, const CUmemAllocationProp *, CUmemAllocationGranularity_flags);
+};
+
+const VmmFns &vmm() {
+  static const VmmFns f = [] {
+    VmmFns v;
+    memset(&v, 0, sizeof v);
+    auto get = [](const char *name, void **p) {
+      cudaDriverEntryPointQueryResult q;
+      if (cudaGetDriverEntryPoint(name, p, cudaEnableDefault, &q) != cudaSuccess ||
+          q != cudaDriverEntryPointSuccess)
+        *p = nullptr;
+    };
+    get("cuMemAddressReserve", (void **)&v.reserve);
+    get("cuMemAddressFree", (void **)&v.addr_free);
+    get("cuMemCreate", (void **)&v.create);
+    get("cuMemRelease", (void **)&v.release);
+    get("cuMemMap", (void **)&v.map);
+    get("cuMemUnmap", (void **)&v.unmap);
+    get("cuMemSetAccess", (void **)&v.set_access);
+    get("cuMemGetAllocationGranularity", (void **)&v.granularity);
+    return v;
+  }();
+  return f;
+}
+
+struct VmmBuf {
+  CUdeviceptr va = 0;
+  size_t size = 0;
+  CUmemGenericAllocationHandle h = 0;
+  bool mapped = false;
+  int dev = 0;
+  VmmBuf() = default;
+  VmmBuf(const VmmBuf &) = delete;
+  VmmBuf &operator=(const VmmBuf &) = delete;
+  CUmemAllocationProp prop() const {
+    CUmemAllocationProp p;
+    memset(&p, 0, sizeof p);
+    p.type = CU_MEM_ALLOCATION_TYPE_PINNED;
+    p.location.type = CU_MEM_LOCATION_TYPE_DEVICE;
+    p.location.id = dev;
+    return p;
+  }
+  // address range only
+  void reserve(size_t bytes) {
+    free_all();
+    const VmmFns &f = vmm();
+    if (!f.reserve || !f.create || !f.map || !f.set_access || !f.granularity)
+      fail(DMRG_ERR_CUDA, "CUDA virtual memory management entry points unavailable");
+    CK(cudaGetDevice(&dev));
+    const CUmemAllocationProp p = prop();
+    size_t g = 0;
+    if (f.granularity(&g, &p, CU_MEM_ALLOC_GRANULARITY_RECOMMENDED) != CUDA_SUCCESS || g == 0)
+      g = 2 << 20;
+    size = (std::max<size_t>(bytes, 1) + g - 1) / g * g;
+    if (f.reserve(&va, size, 0, 0, 0) != CUDA_SUCCESS) {
+      va = 0;
+      fail(DMRG_ERR_OOM, "cuMemAddressReserve(%zu) failed", size);
+    }
+  }
+  // physical memory behind the range
+  void map() {
+    if (mapped || !va) return;
+    const VmmFns &f = vmm();
+    std::shared_lock<std::shared_mutex> lk(capture_lock());
+    const CUmemAllocationProp p = prop();
+    if (f.create(&h, size, &p, 0) != CUDA_SUCCESS) {
+      h = 0;
+      fail(DMRG_ERR_OOM, "cuMemCreate(%zu) failed", size);
+    }
+    if (f.map(va, size, 0, h, 0) != CUDA_SUCCESS) {
+      f.release(h);
+      h = 0;
+      fail(DMRG_ERR_OOM, "cuMemMap(%zu) failed", size);
+    }
+    CUmemAccessDesc a;
+    memset(&a, 0, sizeof a);
+    a.location = p.location;
+    a.flags = CU_MEM_ACCESS_FLAGS_PROT_READWRITE;
+    if (f.set_access(va, size, &a, 1) != CUDA_SUCCESS) {
+      f.unmap(va, size);
+      f.release(h);
+      h = 0;
+      fail(DMRG_ERR_CUDA, "cuMemSetAccess failed");
+    }
+    mapped = true;
+  }
+  // give the physical memory back (the caller has finished all work on it)
+  void unmap() {
+    if (!mapped) return;
+    const VmmFns &f = vmm();
+    std::shared_lock<std::shared_mutex> lk(capture_lock());
+    f.unmap(va, size);
+    f.release(h);
+    h = 0;
+    mapped = false;
+  }
+  void free_all() {
+    unmap();
+    if (va) vmm().addr_free(va, size);
+    va = 0;
+    size = 0;
+  }
+  double *ptr() const { return (double *)va; }
+  ~VmmBuf() { free_all(); }
+};
+
 template <class T>
 T *upload(WinBuf &wb, const std::vector<T> &v, cudaStream_t s) {
   T *d = (T *)wb.alloc(sizeof(T) * std::max<size_t>(v.size(), 1));
@@ -275,7 +397,13 @@ struct Window {
   long long psi_len = 0;
   std::vector<int> a2psi;
   std::vector<HClass> hc;
-  WinBuf buf = WinBuf::lasting_buf();   // stacks, T, descriptors
+  WinBuf buf = WinBuf::lasting_buf();   // descriptors, split-path copies and scratch
+  // FP64 stacks and T at fixed addresses; T is backed on the first FP64
+  // apply, and under an HBM budget A and B are given back once the split
+  // path has its FP16 copies (and gathered again by the next FP64 apply)
+  VmmBuf vA, vB, vT;
+  std::vector<SCopy> stack_copies;   // the gather that fills A and B
+  bool fp64_stacks = false;          // A and B hold the window's operators
   double *Astack = nullptr, *Bstack = nullptr, *T = nullptr;
   long long nA = 0, nB = 0, nT = 0;
   GemmDesc *d1 = nullptr, *d2 = nullptr;
@@ -1711,6 +1839,14 @@ void build_window(dmrg_ctx *C, int l) {
   Window &w = C->win;
   cudaStream_t s = C->stream;
   w.valid = false;
+  // the FP64 stacks are unmapped on the host: the previous window's work ends first
+  if (w.used) CK(cudaEventSynchronize(w.use_ev));
+  CK(cudaStreamSynchronize(s));
+  w.vA.free_all();
+  w.vB.free_all();
+  w.vT.free_all();
+  w.fp64_stacks = false;
+  w.stack_copies.clear();
   release_after_use(w);
   if (!w.use_ev) CK(cudaEventCreateWithFlags(&w.use_ev, cudaEventDisableTiming));
   w.buf.clear();
@@ -1855,9 +1991,14 @@ void build_window(dmrg_ctx *C, int l) {
   w.nA = nA;
   w.nB = nB;
   w.nT = nT;
-  w.Astack = (double *)w.buf.alloc(8 * std::max<long long>(nA, 1));
-  w.Bstack = (double *)w.buf.alloc(8 * std::max<long long>(nB, 1));
-  w.T = (double *)w.buf.alloc(8 * std::max<long long>(nT, 1));
+  w.vA.reserve(8 * (size_t)std::max<long long>(nA, 1));
+  w.vA.map();
+  w.vB.reserve(8 * (size_t)std::max<long long>(nB, 1));
+  w.vB.map();
+  w.vT.reserve(8 * (size_t)std::max<long long>(nT, 1));   // backed by the first FP64 apply
+  w.Astack = w.vA.ptr();
+  w.Bstack = w.vB.ptr();
+  w.T = w.vT.ptr();
   for (const S1 &e : s1list) {
     HClass &h = w.hc[e.ci];
     const PsiBlk &p = w.psi[e.pi], &q = w.psi[e.po];
@@ -1901,6 +2042,8 @@ void build_window(dmrg_ctx *C, int l) {
     CK(launch_stack_copy(d, (int)cps.size(), s));
     CK(cudaStreamSynchronize(s));
   }
+  w.stack_copies = cps;
+  w.fp64_stacks = true;
   // stage 1: T[(a',k), b] = A[(a',k), a] psi[a, b] * sign
   // stage 2: sigma[a', b'] = sum_classes T[a', (k,b)] B[b', (k,b)]^T
   std::vector<GemmDesc> d1, d2;
@@ -2078,8 +2221,35 @@ void mark(dmrg_ctx *C, int i, cudaStream_t s) {
   if (i == 4) C->pending = true;
 }
 
+// The FP64 path's memory: T backed on first use; A and B gathered again from
+// the window's enlarged blocks if they were given back (stream-ordered on s).
+void ensure_fp64(dmrg_ctx *C, cudaStream_t s) {
+  Window &w = C->win;
+  if (!w.vT.mapped) w.vT.map();
+  if (w.fp64_stacks) return;
+  w.vA.map();
+  w.vB.map();
+  WinBuf tmp(s);
+  SCopy *d = upload(tmp, w.stack_copies, s);
+  CK(launch_stack_copy(d, (int)w.stack_copies.size(), s));
+  w.fp64_stacks = true;
+}
+
+// Under an HBM budget the split path keeps only its FP16 copies: A, B and T
+// of the FP64 path are given back (their addresses stay reserved).
+void drop_fp64(dmrg_ctx *C) {
+  Window &w = C->win;
+  CK(cudaStreamSynchronize(C->stream));
+  if (w.used) CK(cudaEventSynchronize(w.use_ev));
+  w.vA.unmap();
+  w.vB.unmap();
+  w.vT.unmap();
+  w.fp64_stacks = false;
+}
+
 void apply_fp64(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s) {
   Window &w = C->win;
+  ensure_fp64(C, s);
   mark(C, 0, s);
   mark(C, 1, s);
   CK(launch_gemm_f64(w.d1, w.nd1, w.s1, w.tiles1, s, psi, nullptr));
@@ -2568,7 +2738,10 @@ void build_split(dmrg_ctx *C) {
   Window &w = C->win;
   cudaStream_t s = C->stream;
   SplitPlan &P = w.tf;
-  if (!w.tf_copies) split_operator_copies(C);
+  if (!w.tf_copies) {
+    split_operator_copies(C);
+    if (C->cfg.hbm_budget_bytes) drop_fp64(C);
+  }
   CK(split_prepare());
   const bool tune = C->ksub_choice == 0 && (double)(w.nA + w.nB) * 8.0 > 256e6;
   int best = C->ksub_choice ? C->ksub_choice : KSUB_DEFAULT;
@@ -4067,6 +4240,11 @@ int dmrg_destroy(dmrg_ctx *ctx) {
   if (ctx->cap_stream) cudaStreamSynchronize(ctx->cap_stream);
   for (auto &g : ctx->win.graphs) cudaGraphExecDestroy(g.second);
   ctx->win.graphs.clear();
+  // the FP64 stacks are unmapped at once: wait for the last apply callers enqueued
+  if (ctx->win.used) cudaEventSynchronize(ctx->win.use_ev);
+  ctx->win.vA.free_all();
+  ctx->win.vB.free_all();
+  ctx->win.vT.free_all();
   release_after_use(ctx->win);
   ctx->win.buf.clear();
   ctx->win.ldbuf.clear();
@@ -4708,6 +4886,20 @@ int dmrg_staging_stats(dmrg_ctx *C, double *out8) {
     out8[6] = (double)C->st_releases;
     out8[7] = (double)C->cfg.hbm_budget_bytes;
   });
+}
+
+int dmrg_heff_fp64_state(dmrg_ctx *C, long long *out4) {
+  if (!C || !out4) return DMRG_ERR_ARG;
+  const Window &w = C->win;
+  if (!w.valid) {
+    C->err = "no window built";
+    return DMRG_ERR_STATE;
+  }
+  out4[0] = (w.fp64_stacks && w.vA.mapped && w.vB.mapped) ? 1 : 0;
+  out4[1] = w.vT.mapped ? 1 : 0;
+  out4[2] = (long long)(w.vA.size + w.vB.size);
+  out4[3] = (long long)w.vT.size;
+  return DMRG_OK;
 }
 
 int dmrg_heff_split_paths(dmrg_ctx *C, long long *out8) {

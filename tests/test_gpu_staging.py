@@ -62,3 +62,35 @@ def test_window_build_under_a_budget():
             assert g.staging_stats()["releases"] >= N - 4
         g.close()
     assert np.array_equal(out[0], out[1])
+
+
+def test_fp64_stacks_given_back_under_a_budget():
+    """With a budget the FP64 stacks and T are given back once the split path
+    has its FP16 copies, and the next FP64 apply gathers the stacks again:
+    sigma of both paths bitwise the same as in a context without a budget."""
+    N, ne, D, l = 16, 16, 64, 7
+    li = synth.random_left_isometries_su2(N, (ne, 0), D, l, 5)
+    ri = synth.random_right_isometries_su2(N, (ne, 0), D, l + 2, 6)
+    out = {}
+    for budget in (0, 1):
+        g = _hubbard4x4(budget, lib.SPLIT)
+        g.set_mps(li, ri)
+        g.build_block_ops(l)
+        st = g.heff_fp64_state()
+        assert st["stacks_backed"] and not st["t_backed"], st   # T backed on first FP64 use
+        n, lay = g.heff_layout()
+        psi = synth.random_psi(lay, 2)
+        s_split = g.heff_apply_host(psi)
+        st = g.heff_fp64_state()
+        assert st["stacks_backed"] == (budget == 0), st
+        g.set_precision(lib.FP64)
+        s_64 = g.heff_apply_host(psi)
+        st = g.heff_fp64_state()
+        assert st["stacks_backed"] and st["t_backed"], st
+        g.set_precision(lib.SPLIT)
+        s_split2 = g.heff_apply_host(psi)
+        out[budget] = (s_split, s_64, s_split2)
+        g.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
+    assert np.array_equal(out[1][0], out[1][2])
