@@ -59,14 +59,14 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # pass on the full window), valid only for the kernel source it was taken with:
 # reported as null once that file changes.
 TRAFFIC_SOURCE = os.path.join(ROOT, "paper_2311_14106_b300", "csrc", "heff_split.cu")
-TRAFFIC_SHA = "986c6afcb7e53341"
+TRAFFIC_SHA = "d253e9b7e425d37e"
 # The spin-adapted D=1024 window is too large for a full-metric capture: its
 # values are the D=512 window's per-launch traffic scaled by the ratio of
-# algorithmic bytes (1.035x and 1.151x of them at D=512).
-TRAFFIC = {("hubbard6x6_su2_D1024", "k_split_gemm stage1"): 1.0350 * 6.1674e9,
-           ("hubbard6x6_su2_D1024", "k_split_gemm stage2"): 1.1510 * 6.1674e9,
-           ("hubbard6x6_su2_D512", "k_split_gemm stage1"): 1.5547e9,
-           ("hubbard6x6_su2_D512", "k_split_gemm stage2"): 1.7289e9}
+# algorithmic bytes (1.075x and 1.128x of them at D=512).
+TRAFFIC = {("hubbard6x6_su2_D1024", "k_split_gemm stage1"): 1.0749 * 6.1674e9,
+           ("hubbard6x6_su2_D1024", "k_split_gemm stage2"): 1.1283 * 6.1674e9,
+           ("hubbard6x6_su2_D512", "k_split_gemm stage1"): 1.6145e9,
+           ("hubbard6x6_su2_D512", "k_split_gemm stage2"): 1.6946e9}
 
 
 def traffic_of(workload, kernel):
@@ -505,6 +505,7 @@ def main():
                 "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n, "ms_per_step": e2e_ms},
         "clocks": clocks,
         "split_plan": plan,
+        "memory_bytes": g.memory_stats(),
         "gpu_launches": plan["launches"] * args.steps,
         "roofline": {"kernel": dom, "bound": "tensor",
                      "achieved": None, "peak": tc_peak, "unit": "TFLOP/s", "frac": None,

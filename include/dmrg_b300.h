@@ -398,6 +398,15 @@ int dmrg_selftest_timeout_report(dmrg_ctx *ctx, int which, void *stream);
  * [5] Other; out[6] = number of H_eff*psi calls. */
 int dmrg_profile(dmrg_ctx *ctx, double *out7);
 
+/* Device memory of the context's largest objects so far, in bytes: out6[0]
+ * largest renormalized block (operator data), [1] largest enlarged block
+ * (block x site, before renormalization, or a window's L. / .R), [2] largest
+ * renormalization temporary (the products U_k T_i are computed in chunks of
+ * at most 2 GB), [3] FP64 operator stacks of the last window, [4] its split
+ * FP16 (hi, lo) copies, [5] device memory in use (all processes) after the
+ * last window build.  Errors: ARG. */
+int dmrg_memory_stats(dmrg_ctx *ctx, double *out6);
+
 #ifdef __cplusplus
 }
 #endif

@@ -34,6 +34,7 @@ HEADER_FUNCTIONS = [
     "dmrg_sync", "dmrg_get_mps", "dmrg_get_center", "dmrg_heff_split_paths",
     "dmrg_selftest_timeout_report", "dmrg_staging_stats", "dmrg_sweep_next_use",
     "dmrg_rdm1", "dmrg_heff_apply_batch", "dmrg_random_start", "dmrg_heff_fp64_state",
+    "dmrg_memory_stats",
 ]
 
 
@@ -92,6 +93,7 @@ _sig = {
     "dmrg_heff_apply_batch": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
     "dmrg_random_start": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "dmrg_heff_fp64_state": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong)]),
+    "dmrg_memory_stats": (ctypes.c_int, [_P, _D]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -419,6 +421,14 @@ class Dmrg:
 
     def set_graphs(self, enable):
         self._check(_lib.dmrg_set_graphs(self._h, int(enable)), "set_graphs")
+
+    def memory_stats(self):
+        """Largest device objects so far (bytes; see dmrg_memory_stats)."""
+        out = np.zeros(6)
+        self._check(_lib.dmrg_memory_stats(self._h, _dptr(out)), "memory_stats")
+        keys = ["block", "enlarged_block", "ren_temp", "fp64_stacks", "split_copies",
+                "device_in_use"]
+        return dict(zip(keys, out.tolist()))
 
     def profile(self):
         out = np.zeros(7)

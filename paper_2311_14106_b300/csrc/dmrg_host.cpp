@@ -169,7 +169,10 @@ struct WinBuf {
     const cudaStream_t as = lasting ? release_stream() : st;
     if ((ordered ? cudaMallocAsync(&p, bytes, as) : cudaMalloc(&p, bytes)) != cudaSuccess) {
       cudaGetLastError();
-      fail(DMRG_ERR_OOM, "cudaMalloc(%zu) failed", bytes);
+      size_t fr = 0, tot = 0;
+      cudaMemGetInfo(&fr, &tot);
+      fail(DMRG_ERR_OOM, "cudaMalloc(%zu) failed (%.1f GB of %.1f GB free)", bytes, fr / 1e9,
+           tot / 1e9);
     }
     if (lasting) CK(cudaStreamSynchronize(as));   // usable on any stream from here
     ptrs.push_back(p);
@@ -286,7 +289,10 @@ struct VmmBuf {
     const CUmemAllocationProp p = prop();
     if (f.create(&h, size, &p, 0) != CUDA_SUCCESS) {
       h = 0;
-      fail(DMRG_ERR_OOM, "cuMemCreate(%zu) failed", size);
+      size_t fr = 0, tot = 0;
+      cudaMemGetInfo(&fr, &tot);
+      fail(DMRG_ERR_OOM, "cuMemCreate(%zu) failed (%.1f GB of %.1f GB free)", size, fr / 1e9,
+           tot / 1e9);
     }
     if (f.map(va, size, 0, h, 0) != CUDA_SUCCESS) {
       f.release(h);
@@ -462,6 +468,7 @@ struct dmrg_ctx {
   cusolverDnParams_t solver_params = nullptr;
   int precision = DMRG_FP64;
   double prof[7] = {0};
+  double mem_max[6] = {0};   // dmrg_memory_stats
   // optional per-stage event timing of H_eff*psi
   bool timing = false;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -1434,6 +1441,9 @@ void enlarge_su2(dmrg_ctx *C, const BlockPart &X, const SitePart &st, bool site_
 // ---------------------------------------------------------------------------
 WinBuf &data_of(dmrg_ctx *C, BlockPart *B);
 
+// Temporaries of one renormalization chunk: 2^28 doubles (2 GB).
+constexpr long long kRenTmpDoubles = 1LL << 28;
+
 void renormalize(dmrg_ctx *C, const BlockPart &U, const Iso &T, BlockPart &B, WinBuf &wb) {
   cudaStream_t s = C->stream;
   B.basis = Basis();
@@ -1455,8 +1465,6 @@ void renormalize(dmrg_ctx *C, const BlockPart &U, const Iso &T, BlockPart &B, Wi
   // U's class for each shift
   std::map<QN, int> ushift;
   for (size_t ci = 0; ci < U.cls.size(); ++ci) ushift[U.cls[ci].shift] = (int)ci;
-  std::vector<GemmDesc> d1, d2;
-  std::vector<GemmSeg> s1, s2;
   long long tmp_total = 0;
   struct Job {
     int bc, bb, uc, ub;
@@ -1474,14 +1482,39 @@ void renormalize(dmrg_ctx *C, const BlockPart &U, const Iso &T, BlockPart &B, Wi
       int ki = ob.blk_in[b], ko = ob.blk_out[b];
       int ub = ou.in2blk[u_of[ki]];
       if (ub < 0 || ou.blk_out[ub] != u_of[ko]) fail(DMRG_ERR_STATE, "internal: block mismatch");
-      jobs.push_back({(int)bc, (int)b, it->second, ub, tmp_total});
-      tmp_total += (long long)ob.nops * U.basis.dim[u_of[ko]] * T.cols[ki];
+      jobs.push_back({(int)bc, (int)b, it->second, ub, 0});
     }
   }
+  // The intermediates U_k T_i are computed for chunks of jobs whose
+  // temporaries fit kRenTmpDoubles (a job larger than that is a chunk of its
+  // own); the chunks run one after the other on the stream, reusing one buffer.
+  std::vector<size_t> chunk{0};
+  {
+    long long cur = 0;
+    for (size_t i = 0; i < jobs.size(); ++i) {
+      const Job &j = jobs[i];
+      const long long t = (long long)B.cls[j.bc].nops *
+                          U.basis.dim[u_of[B.cls[j.bc].blk_out[j.bb]]] *
+                          T.cols[B.cls[j.bc].blk_in[j.bb]];
+      if (cur > 0 && cur + t > kRenTmpDoubles) {
+        chunk.push_back(i);
+        cur = 0;
+      }
+      jobs[i].tmp = cur;
+      cur += t;
+      tmp_total = std::max(tmp_total, cur);
+    }
+    chunk.push_back(jobs.size());
+  }
+  C->mem_max[2] = std::max(C->mem_max[2], 8.0 * tmp_total);
   WinBuf work(s);   // intermediate products and work lists of this call
   double *tmp = (double *)work.alloc(sizeof(double) * std::max<long long>(tmp_total, 1));
+  for (size_t c = 0; c + 1 < chunk.size(); ++c) {
+  std::vector<GemmDesc> d1, d2;
+  std::vector<GemmSeg> s1, s2;
   long long t1 = 0, t2 = 0;
-  for (const Job &j : jobs) {
+  for (size_t ji = chunk[c]; ji < chunk[c + 1]; ++ji) {
+    const Job &j = jobs[ji];
     const OpClass &ob = B.cls[j.bc];
     const OpClass &ou = U.cls[j.uc];
     int ki = ob.blk_in[j.bb], ko = ob.blk_out[j.bb];
@@ -1528,11 +1561,12 @@ void renormalize(dmrg_ctx *C, const BlockPart &U, const Iso &T, BlockPart &B, Wi
     s2.push_back(g2);
     d2.push_back(e);
   }
-  if (!jobs.empty()) {
+  if (!d1.empty()) {
     GemmDesc *dd1 = upload(work, d1, s), *dd2 = upload(work, d2, s);
     GemmSeg *ss1 = upload(work, s1, s), *ss2 = upload(work, s2, s);
     CK(launch_gemm_f64(dd1, (int)d1.size(), ss1, t1, s));
     CK(launch_gemm_f64(dd2, (int)d2.size(), ss2, t2, s));
+  }
   }
   CK(cudaStreamSynchronize(s));
 }
@@ -1765,6 +1799,17 @@ void upload_iso(dmrg_ctx *C, Iso &T) {
 }
 
 // L_n = T_n^T (L_{n-1} x site_{n-1}) T_n
+double part_bytes(const BlockPart &P) {
+  double b = 0;
+  for (const OpClass &oc : P.cls) b += 8.0 * (double)oc.nnz * oc.nops;
+  return b;
+}
+
+void note_parts(dmrg_ctx *C, const BlockPart &U, const BlockPart &B) {
+  C->mem_max[1] = std::max(C->mem_max[1], part_bytes(U));
+  C->mem_max[0] = std::max(C->mem_max[0], part_bytes(B));
+}
+
 void grow_left(dmrg_ctx *C, int n, const Iso &T) {
   SitePart st = site_of(C, n - 1);
   BlockPart U;
@@ -1773,6 +1818,7 @@ void grow_left(dmrg_ctx *C, int n, const Iso &T) {
   enlarge(C, *C->L[n - 1], st, false, C->N - n, U, ub);
   std::unique_ptr<BlockPart> B(new BlockPart());
   renormalize(C, U, T, *B, buf_of(C, B.get()));
+  note_parts(C, U, *B);
   if ((int)C->L.size() <= n) C->L.resize(n + 1);
   if (C->L[n]) free_part(C, C->L[n].get());
   C->L[n] = std::move(B);
@@ -1787,6 +1833,7 @@ void grow_right(dmrg_ctx *C, int n, const Iso &T) {
   enlarge(C, *C->R[n + 1], st, true, n, U, ub);
   std::unique_ptr<BlockPart> B(new BlockPart());
   renormalize(C, U, T, *B, buf_of(C, B.get()));
+  note_parts(C, U, *B);
   if (C->R.count(n)) free_part(C, C->R[n].get());
   C->R[n] = std::move(B);
 }
@@ -2044,6 +2091,8 @@ void build_window(dmrg_ctx *C, int l) {
   }
   w.stack_copies = cps;
   w.fp64_stacks = true;
+  C->mem_max[1] = std::max({C->mem_max[1], part_bytes(w.Ld), part_bytes(w.Rd)});
+  C->mem_max[3] = (double)(w.vA.size + w.vB.size);
   // stage 1: T[(a',k), b] = A[(a',k), a] psi[a, b] * sign
   // stage 2: sigma[a', b'] = sum_classes T[a', (k,b)] B[b', (k,b)]^T
   std::vector<GemmDesc> d1, d2;
@@ -2200,6 +2249,8 @@ void build_window(dmrg_ctx *C, int l) {
   }
   C->prof[2] += now() - t0;
   w.valid = true;
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) C->mem_max[5] = (double)(tot - fr);
 }
 
 void collect_timing(dmrg_ctx *C) {
@@ -2419,6 +2470,7 @@ void split_operator_copies(dmrg_ctx *C) {
   CK(f16_split(upload(tmp, sp, s), (int)sp.size(), nullptr, nullptr, s, split_tile_count(sp)));
   CK(cudaStreamSynchronize(s));
   w.tf_copies = true;
+  C->mem_max[4] = 4.0 * (double)(nA + nBp);
 }
 
 // psi (FP64, [a][b] per sector block) -> scaled FP16 (hi, lo), transposed to
@@ -5019,6 +5071,12 @@ int dmrg_heff_tuning(dmrg_ctx *C, double *out, int max_entries, int *n_entries) 
 int dmrg_set_graphs(dmrg_ctx *C, int enable) {
   if (!C) return DMRG_ERR_ARG;
   C->use_graphs = enable != 0;
+  return DMRG_OK;
+}
+
+int dmrg_memory_stats(dmrg_ctx *C, double *out6) {
+  if (!C || !out6) return DMRG_ERR_ARG;
+  for (int i = 0; i < 6; ++i) out6[i] = C->mem_max[i];
   return DMRG_OK;
 }
 
