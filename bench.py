@@ -41,6 +41,12 @@ WORKLOADS = {
                              "Hubbard 8x8 torus, filling 0.875 (56 e, S=0), t=1, U=4, momentum "
                              "basis times a seeded Haar rotation (seed 2), U(1)xSU(2), D=2048 "
                              "multiplets, middle window l=31"),
+    # config C3 at the bond dimension that fits (see the D=2048 entry's note)
+    **{f"hubbard8x8_su2_D1024_U{u:g}": (
+        "hubbard", 8, 8, (56, 0), float(u), 1024, "su2", 2,
+        f"Hubbard 8x8 torus, 56 e (S=0), t=1, U={u:g}, momentum basis times a seeded Haar "
+        f"rotation (seed 2), U(1)xSU(2), D=1024 multiplets, middle window l=31")
+       for u in (2, 4, 8)},
     "hubbard6x6_D1024": ("hubbard", 6, 6, (18, 18), 4.0, 1024, "u1u1", None,
                          "Hubbard 6x6 torus, 36 e (S_z=0), t=1, U=4, momentum basis, "
                          "U(1)xU(1), D=1024 states, middle window l=17"),

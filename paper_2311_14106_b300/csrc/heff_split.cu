@@ -399,7 +399,7 @@ k_split_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict_
             // to the encoded start address
             const uint64_t dah = sdesc(a_hi), dal = sdesc(a_lo), dbh = sdesc(b_hi),
                            dbl = sdesc(b_lo);
-            for (int k = 0; k < nk16; ++k) {
+            auto kstep = [&](int k) {
               const uint64_t ko = 2 * k;
               // small terms first: lo.hi, hi.lo, then hi.hi (lo.lo is below
               // the FP32 accumulation error and is left out)
@@ -407,6 +407,13 @@ k_split_gemm(const TWork *__restrict__ works, int nwork, const TSeg *__restrict_
               accum = 1;
               mma_f16(d, dah + ko, dbl + ko, id, 1);
               mma_f16(d, dah + ko, dbh + ko, id, 1);
+            };
+            if (nk16 == BK / 16) {
+              // a full chunk: straight-line issue
+#pragma unroll
+              for (int k = 0; k < BK / 16; ++k) kstep(k);
+            } else {
+              for (int k = 0; k < nk16; ++k) kstep(k);
             }
             mma_commit(smem_u32(&sh->empty[st]));
           }

@@ -109,6 +109,7 @@ def run_one(req, precision, stream=None, davidson_tol=1e-7, rng_iso=None):
         g.random_start(req.seed)
         E = g.sweep(req.n_sweeps, stream=stream)
         prof = g.profile()
+        prof["memory"] = g.memory_stats()
     finally:
         g.close()
     return E, prof
