@@ -299,6 +299,9 @@ def main():
                     help="cfg.hbm_budget_bytes of the context: blocks are released once the "
                          "next one is built, and the FP64 stacks once the split path has its "
                          "FP16 copies (needed for the 8x8 D=2048 window)")
+    ap.add_argument("--serving", default="small", choices=["small", "c4"],
+                    help="serving stream: small (12 requests on 4x4 lattices, the default) or "
+                         "c4 (32 requests on 6x6 lattices, C4's arrival process and model mix)")
     ap.add_argument("--split-only", action="store_true",
                     help="time the split path alone (no FP64 leg, solve, serving or C1): "
                          "for windows whose FP64 and split stacks do not fit together")
@@ -373,6 +376,13 @@ def main():
         ms_split, st_split = timed(lib.SPLIT, args.steps, args.warmup)
     clocks = clk.summary()
     sig_split = sig.clone()
+    # FP64 path (fewer steps: FP64 throughput is ~1/100 of the split path)
+    ms_64, st_64, err_sigma = None, None, None
+    if not args.split_only:
+        k64 = max(2, min(args.steps, 5))
+        ms_64, st_64 = timed(lib.FP64, k64, 1)
+        sig_64 = sig.clone()
+        err_sigma = float((sig_split - sig_64).norm() / sig_64.norm())
     # several vectors in one pass of the split kernels (operator tiles served
     # from L2 to all of them): ms per batched apply and per vector
     batched = []
@@ -399,13 +409,6 @@ def main():
             del X, Y
         except Exception as e:   # a batch that does not fit is reported, not fatal
             batched.append({"nv": nv, "error": repr(e)[:200]})
-    # FP64 path (fewer steps: FP64 throughput is ~1/100 of the split path)
-    ms_64, st_64, err_sigma = None, None, None
-    if not args.split_only:
-        k64 = max(2, min(args.steps, 5))
-        ms_64, st_64 = timed(lib.FP64, k64, 1)
-        sig_64 = sig.clone()
-        err_sigma = float((sig_split - sig_64).norm() / sig_64.norm())
     # end-to-end through the host-buffer entry point (pinned host memory)
     g.set_precision(lib.SPLIT)
     hp = torch.tensor(synth.random_psi(layout, 1)).pin_memory()
@@ -423,8 +426,12 @@ def main():
     # Davidson solves of the window with both paths (energy at FP64 RQ)
     solve = {}
     if not args.no_solve and not args.split_only:
-        for name, prec in (("split", lib.SPLIT), ("fp64", lib.FP64)):
+        # split: the refinement's correction steps use the split product
+        # (default); split_plain_refinement: diagonal preconditioner only
+        for name, prec, steps in (("split", lib.SPLIT, 20), ("split_plain_refinement", lib.SPLIT, 0),
+                                  ("fp64", lib.FP64, 20)):
             g.set_precision(prec)
+            g.set_refinement(steps, 1e10)
             x = torch.zeros_like(psi)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -432,6 +439,7 @@ def main():
             torch.cuda.synchronize()
             solve[name] = {"seconds": time.perf_counter() - t0, "energy": e, "iters": it,
                            "converged": conv}
+        g.set_refinement(20, 1e10)
         solve["rel_energy_diff"] = abs(solve["split"]["energy"] - solve["fp64"]["energy"]) / abs(
             solve["fp64"]["energy"])
     # serving stream: Poisson arrivals of independent solves (config-4 pattern,
@@ -439,12 +447,21 @@ def main():
     serving_out = None
     if not args.no_serving and not args.split_only and rank == 0:
         from paper_2311_14106_b300 import serving as srvmod
-        mix = [("spinless", 4, 4, (0.0, 4.0), [64, 128]), ("hubbard", 4, 4, (0.0, 8.0), [64, 128])]
-        serving_out = {"stream": "12 requests, exponential inter-arrival mean 0.1 s (seed 3); "
-                                 "spinless 4x4 V~U[0,4] (U(1), D states) and Hubbard 4x4 "
-                                 "U~U[0,8] (U(1)xSU(2), D multiplets), D in {64,128}, 2 sweeps "
-                                 "each, 4 slots; the 64-request 6x6/8x8 stream with D up to "
-                                 "2048 takes hours on the FP64 arm"}
+        if args.serving == "c4":
+            L, n_req, gap = 6, 32, 0.5
+            serving_out = {"stream": "32 requests, exponential inter-arrival mean 0.5 s (seed 3); "
+                                     "spinless 6x6 N=18 V~U[0,4] (U(1), D states) and Hubbard "
+                                     "6x6 half filling U~U[0,8] (U(1)xSU(2), D multiplets), D in "
+                                     "{64,128}, 2 sweeps each, 4 slots (config C4 reduced: a "
+                                     "6x6 Hubbard sweep at D=256 takes 20-30 s on either arm, "
+                                     "so 64 requests with D up to 2048 on 8x8 take hours)"}
+        else:
+            L, n_req, gap = 4, 12, 0.1
+            serving_out = {"stream": "12 requests, exponential inter-arrival mean 0.1 s (seed 3); "
+                                     "spinless 4x4 V~U[0,4] (U(1), D states) and Hubbard 4x4 "
+                                     "U~U[0,8] (U(1)xSU(2), D multiplets), D in {64,128}, 2 "
+                                     "sweeps each, 4 slots (bench.py --serving c4: 6x6)"}
+        mix = [("spinless", L, L, (0.0, 4.0), [64, 128]), ("hubbard", L, L, (0.0, 8.0), [64, 128])]
         # untimed warm-up with the stream's own shapes: loads the eigensolver and
         # kernel modules (lazily, per kernel) once per process, so that neither
         # arm pays it
@@ -452,7 +469,7 @@ def main():
             for model in ("spinless", "hubbard"):
                 srvmod.run_one(srvmod.Request(-1, model, 4, 4, 2.0, 128, 1, 0.0, seed=1), prec)
         for name, prec in (("split", lib.SPLIT), ("fp64", lib.FP64)):
-            reqs = srvmod.poisson_stream(12, 0.1, 3, mix, sweeps=2)
+            reqs = srvmod.poisson_stream(n_req, gap, 3, mix, sweeps=2)
             srv = srvmod.Server(precision=prec, slots=4, hbm_budget=200e9, davidson_tol=1e-7)
             serving_out[name] = srv.run(reqs)
         serving_out["solves_per_s_ratio_split_over_fp64"] = (

@@ -157,6 +157,17 @@ int dmrg_build_block_ops(dmrg_ctx *ctx, int l, void *stream);
 int dmrg_heff_layout(dmrg_ctx *ctx, long long *psi_len, int *n_blocks,
                      int *blocks);
 
+/* Mixed-precision refinement of split-precision Davidson solves (see
+ * dmrg_davidson): on windows whose H_eff*psi has at least min_window_flops
+ * algorithmic flops, each FP64 refinement step expands its subspace with an
+ * approximate solution of the Jacobi-Davidson correction equation
+ * (I - u u^T)(H - theta)(I - u u^T) t = -r, from inner_steps preconditioned
+ * conjugate-gradient steps with the split-precision product, instead of the
+ * diagonally preconditioned residual; the FP64 Rayleigh-Ritz step keeps the
+ * result exact to FP64 (fewer FP64 products per solve).  inner_steps = 0
+ * turns it off.  Defaults: 20 steps, 1e10 flops.  Errors: ARG. */
+int dmrg_set_refinement(dmrg_ctx *ctx, int inner_steps, double min_window_flops);
+
 /* Select the arithmetic of dmrg_heff_apply: DMRG_FP64 or DMRG_SPLIT. */
 int dmrg_set_precision(dmrg_ctx *ctx, int precision);
 
@@ -403,8 +414,8 @@ int dmrg_profile(dmrg_ctx *ctx, double *out7);
  * (block x site, before renormalization, or a window's L. / .R), [2] largest
  * renormalization temporary (the products U_k T_i are computed in chunks of
  * at most 2 GB), [3] FP64 operator stacks of the last window, [4] its split
- * FP16 (hi, lo) copies, [5] device memory in use (all processes) after the
- * last window build.  Errors: ARG. */
+ * FP16 (hi, lo) copies, [5] the most device memory in use (all processes)
+ * seen after a window build.  Errors: ARG. */
 int dmrg_memory_stats(dmrg_ctx *ctx, double *out6);
 
 #ifdef __cplusplus

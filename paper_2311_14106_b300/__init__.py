@@ -34,7 +34,7 @@ HEADER_FUNCTIONS = [
     "dmrg_sync", "dmrg_get_mps", "dmrg_get_center", "dmrg_heff_split_paths",
     "dmrg_selftest_timeout_report", "dmrg_staging_stats", "dmrg_sweep_next_use",
     "dmrg_rdm1", "dmrg_heff_apply_batch", "dmrg_random_start", "dmrg_heff_fp64_state",
-    "dmrg_memory_stats",
+    "dmrg_memory_stats", "dmrg_set_refinement",
 ]
 
 
@@ -94,6 +94,7 @@ _sig = {
     "dmrg_random_start": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "dmrg_heff_fp64_state": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong)]),
     "dmrg_memory_stats": (ctypes.c_int, [_P, _D]),
+    "dmrg_set_refinement": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -236,6 +237,11 @@ class Dmrg:
             qb = tuple(int(x) for x in b[self.nq: 2 * self.nq])
             out.append((qa, qb, int(b[-2]), int(b[-1])))
         return n.value, out
+
+    def set_refinement(self, inner_steps, min_window_flops):
+        """Split-precision correction steps of the FP64 refinement (see the header)."""
+        self._check(_lib.dmrg_set_refinement(self._h, inner_steps, min_window_flops),
+                    "set_refinement")
 
     def set_precision(self, p):
         self._check(_lib.dmrg_set_precision(self._h, p), "set_precision")

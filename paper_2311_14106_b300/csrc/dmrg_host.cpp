@@ -479,6 +479,11 @@ struct dmrg_ctx {
   long long dav_n = 0;
   double *V = nullptr, *AV = nullptr, *work = nullptr, *small = nullptr, *r = nullptr;
   double *rs = nullptr;   // thick-restart scratch (3 vectors)
+  double *jd = nullptr;   // correction-equation scratch (4 vectors)
+  // refinement of split solves: split-precision CG steps per correction,
+  // on windows of at least this many algorithmic flops per apply
+  int refine_steps = 20;
+  double refine_min_flops = 1e10;
   uint64_t start_count = 0;
   bool use_graphs = true;
   cudaStream_t cap_stream = nullptr;            // private stream for graph capture
@@ -2250,7 +2255,8 @@ void build_window(dmrg_ctx *C, int l) {
   C->prof[2] += now() - t0;
   w.valid = true;
   size_t fr = 0, tot = 0;
-  if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) C->mem_max[5] = (double)(tot - fr);
+  if (cudaMemGetInfo(&fr, &tot) == cudaSuccess)
+    C->mem_max[5] = std::max(C->mem_max[5], (double)(tot - fr));
 }
 
 void collect_timing(dmrg_ctx *C) {
@@ -3212,6 +3218,7 @@ DavBuf dav_buffers(dmrg_ctx *C, long long n, int m) {
     C->AV = (double *)C->dav.alloc(8 * (size_t)n * m);
     C->r = (double *)C->dav.alloc(8 * (size_t)n * 2);
     C->rs = (double *)C->dav.alloc(8 * (size_t)n * 3);
+    C->jd = (double *)C->dav.alloc(8 * (size_t)n * 4);
     C->work = (double *)C->dav.alloc(8 * 296 * (size_t)(m + 2));
     C->small = (double *)C->dav.alloc(8 * 4 * (size_t)(m + 2));
     C->dav_n = n;
@@ -3251,6 +3258,54 @@ void lincomb(double *out, const double *V, const std::vector<double> &c, double 
   CK(cudaStreamSynchronize(s));
 }
 
+// Correction of the mixed-precision refinement (Jacobi-Davidson form):
+// approximately solve  (I - u u^T)(H - theta)(I - u u^T) t = -r,  t orthogonal
+// to the Ritz vector u (B.u), with `steps` preconditioned conjugate-gradient
+// steps whose products use the split-precision path.  theta is the lowest
+// Ritz value, so the projected operator is positive definite on u's
+// complement; the diagonal preconditioner is (diag - theta)^-1, projected.
+// On entry B.t holds the residual r = (H - theta) u (orthogonal to u); on
+// exit the correction.  The FP64 Rayleigh-Ritz step that uses it keeps the
+// result exact to FP64: the split product only shapes the search direction.
+void jd_correction(dmrg_ctx *C, DavBuf &B, long long n, double theta, const double *th_dev,
+                   int steps, cudaStream_t s) {
+  Window &w = C->win;
+  double *res = C->jd, *z = C->jd + n, *p = C->jd + 2 * n, *q = C->jd + 3 * n;
+  auto project = [&](double *v) {
+    const double a = dot1(C, B.u, v, n, B, s);
+    lincomb(v, B.u, {-a}, 1.0, n, B, s);
+  };
+  auto precond = [&]() {
+    CK(cudaMemcpyAsync(z, res, 8 * n, cudaMemcpyDeviceToDevice, s));
+    CK(launch_precond(z, w.diag, th_dev, n, s));
+    project(z);
+  };
+  CK(cudaMemcpyAsync(res, B.t, 8 * n, cudaMemcpyDeviceToDevice, s));
+  lincomb(res, res, {}, -1.0, n, B, s);
+  CK(cudaMemsetAsync(B.t, 0, 8 * n, s));
+  const double r0 = std::sqrt(std::max(0.0, dot1(C, res, res, n, B, s)));
+  precond();
+  CK(cudaMemcpyAsync(p, z, 8 * n, cudaMemcpyDeviceToDevice, s));
+  double rz = dot1(C, res, z, n, B, s);
+  for (int it = 0; it < steps && rz > 0.0; ++it) {
+    apply(C, p, q, s, DMRG_SPLIT);
+    lincomb(q, p, {-theta}, 1.0, n, B, s);
+    project(q);
+    const double pq = dot1(C, p, q, n, B, s);
+    if (!(pq > 0.0)) break;
+    const double alpha = rz / pq;
+    lincomb(B.t, p, {alpha}, 1.0, n, B, s);
+    lincomb(res, q, {-alpha}, 1.0, n, B, s);
+    const double rr = std::sqrt(std::max(0.0, dot1(C, res, res, n, B, s)));
+    if (rr < 1e-3 * r0) break;
+    precond();
+    const double rz2 = dot1(C, res, z, n, B, s);
+    const double beta = rz2 / rz;
+    rz = rz2;
+    lincomb(p, z, {1.0}, beta, n, B, s);
+  }
+}
+
 constexpr double kSplitResidualFloor = 4e-6;
 constexpr int kKrylovWarmup = 12;
 
@@ -3261,7 +3316,7 @@ constexpr int kKrylovWarmup = 12;
 // lowered the Ritz value (a start vector with almost no weight on the ground
 // state lets an excited state reach the floor first).
 int davidson_run(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_t s, int prec,
-                 int patience, bool probe, double *rnorm_out) {
+                 int patience, bool probe, double *rnorm_out, int jd_steps = 0) {
   Window &w = C->win;
   const long long n = w.psi_len;
   const int m = std::max(4, std::min(C->cfg.davidson_max_sub, 64));
@@ -3391,6 +3446,10 @@ int davidson_run(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_
       // the probe direction replaces this iteration's correction
       CK(launch_random(B.t, n, C->cfg.seed + 104729 * (++C->start_count), s));
       inject = false;
+    } else if (jd_steps > 0) {
+      // mixed-precision refinement: split-precision correction equation
+      lincomb(B.u, B.V, y, 0.0, n, B, s);
+      jd_correction(C, B, n, theta, th, jd_steps, s);
     } else if (!random_start || it >= kKrylovWarmup) {
       CK(launch_precond(B.t, w.diag, th, n, s));
     }
@@ -3444,7 +3503,8 @@ int davidson(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_t s,
   if (prec == DMRG_SPLIT) {
     check_err_flag(C, s);
     int it2 = 0;
-    rc = davidson_run(C, x, energy, &it2, s, DMRG_FP64, patience, false, &rn);
+    const int jd = C->win.flops >= C->refine_min_flops ? C->refine_steps : 0;
+    rc = davidson_run(C, x, energy, &it2, s, DMRG_FP64, patience, false, &rn, jd);
     it += it2;
   }
   if (iters) *iters = it;
@@ -4634,6 +4694,13 @@ int dmrg_heff_layout(dmrg_ctx *C, long long *psi_len, int *n_blocks, int *blocks
       blocks[k++] = p.db;
     }
   }
+  return DMRG_OK;
+}
+
+int dmrg_set_refinement(dmrg_ctx *C, int inner_steps, double min_window_flops) {
+  if (!C || inner_steps < 0 || inner_steps > 1000 || !(min_window_flops >= 0.0)) return DMRG_ERR_ARG;
+  C->refine_steps = inner_steps;
+  C->refine_min_flops = min_window_flops;
   return DMRG_OK;
 }
 

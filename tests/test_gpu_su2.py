@@ -181,6 +181,23 @@ def test_su2_split_sweeps_match_fp64_at_truncated_D():
         assert abs(a - b) <= 1e-9 * abs(b), E
 
 
+@pytest.mark.parametrize("steps", [8, 20])
+def test_su2_split_sweeps_with_correction_equation_refinement(steps):
+    """The same two sweeps with the refinement's correction-equation steps
+    forced on every window (dmrg_set_refinement with no flop threshold): the
+    split path still ends within 1e-9 relative of the FP64 path."""
+    ham = hubbard(4, 4)
+    E = {}
+    for prec in (lib.FP64, lib.SPLIT):
+        g = library(16, 16, ham, 48, davidson_tol=1e-10, precision=prec, seed=3)
+        g.set_refinement(steps, 0.0)
+        g.set_mps(right=synth.random_right_isometries_su2(16, (16, 0), 48, 1, 7))
+        E[prec] = g.sweep(2)
+        g.close()
+    for a, b in zip(E[lib.SPLIT], E[lib.FP64]):
+        assert abs(a - b) <= 1e-9 * abs(b), E
+
+
 def test_su2_sweep_from_library_random_start():
     """dmrg_random_start in multiplet sectors: Hubbard 3x3, 8 electrons, full
     D, two sweeps reach the ED ground energy."""

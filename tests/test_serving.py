@@ -66,3 +66,20 @@ def test_same_result_alone_and_in_the_mix(prec):
     for r in reqs:
         E, _ = serving.run_one(r, prec, None, 1e-9)
         assert abs(E[-1] - mixed[r.rid]) <= 1e-9 * abs(E[-1]), (r, E[-1], mixed[r.rid])
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("model,L,D", [("spinless", 4, 128), ("hubbard", 4, 128),
+                                        ("spinless", 6, 64), ("hubbard", 6, 64)])
+def test_footprint_estimate_bounds_the_measured_footprint(model, L, D):
+    """Admission uses serving.estimate_bytes: it must not undercount what a
+    solve holds on the device (the most memory in use at any window build of
+    the solve, dmrg_memory_stats, above what was in use before it)."""
+    torch = pytest.importorskip("torch")
+    torch.cuda.synchronize()
+    free0, total = torch.cuda.mem_get_info()
+    req = serving.Request(0, model, L, L, 4.0 if model == "hubbard" else 2.0, D, 1, 0.0, seed=5)
+    E, prof = serving.run_one(req, lib.SPLIT, torch.cuda.Stream())
+    used = prof["memory"]["device_in_use"] - (total - free0)
+    assert used > 0
+    assert serving.estimate_bytes(req) >= used, (serving.estimate_bytes(req), used)
