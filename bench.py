@@ -65,14 +65,14 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # pass on the full window), valid only for the kernel source it was taken with:
 # reported as null once that file changes.
 TRAFFIC_SOURCE = os.path.join(ROOT, "paper_2311_14106_b300", "csrc", "heff_split.cu")
-TRAFFIC_SHA = "d253e9b7e425d37e"
+TRAFFIC_SHA = "0a271accd146d45a"
 # The spin-adapted D=1024 window is too large for a full-metric capture: its
 # values are the D=512 window's per-launch traffic scaled by the ratio of
 # algorithmic bytes (1.075x and 1.128x of them at D=512).
 TRAFFIC = {("hubbard6x6_su2_D1024", "k_split_gemm stage1"): 1.0749 * 6.1674e9,
-           ("hubbard6x6_su2_D1024", "k_split_gemm stage2"): 1.1283 * 6.1674e9,
-           ("hubbard6x6_su2_D512", "k_split_gemm stage1"): 1.6145e9,
-           ("hubbard6x6_su2_D512", "k_split_gemm stage2"): 1.6946e9}
+           ("hubbard6x6_su2_D1024", "k_split_gemm stage2"): 1.1279 * 6.1674e9,
+           ("hubbard6x6_su2_D512", "k_split_gemm stage1"): 1.6144e9,
+           ("hubbard6x6_su2_D512", "k_split_gemm stage2"): 1.6941e9}
 
 
 def traffic_of(workload, kernel):
