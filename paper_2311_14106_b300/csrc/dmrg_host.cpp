@@ -390,6 +390,14 @@ struct BatchPlan {
   std::map<std::pair<const void *, const void *>, cudaGraphExec_t> graphs;
 };
 
+// One launch of the grouped FP64 GEMM: descriptors of one tile size.
+struct F64Launch {
+  GemmDesc *d;
+  int nd;
+  long long tiles;
+  int tm;
+};
+
 struct Window {
   bool valid = false;
   int l = -1;
@@ -414,6 +422,7 @@ struct Window {
   long long nA = 0, nB = 0, nT = 0;
   GemmDesc *d1 = nullptr, *d2 = nullptr;
   GemmSeg *s1 = nullptr, *s2 = nullptr;
+  std::vector<F64Launch> f64_1, f64_2;   // the FP64 stages by tile size
   int nd1 = 0, nd2 = 0;
   long long tiles1 = 0, tiles2 = 0;
   double flops = 0, flops1 = 0, flops2 = 0;
@@ -1446,6 +1455,59 @@ void enlarge_su2(dmrg_ctx *C, const BlockPart &X, const SitePart &st, bool site_
 // ---------------------------------------------------------------------------
 WinBuf &data_of(dmrg_ctx *C, BlockPart *B);
 
+// Grouped FP64 GEMM with the tile size chosen per descriptor: an operator
+// block of a few rows or columns would leave most of a 64 x 64 tile idle, so
+// each descriptor takes the tile (16, 32 or 64) that issues the fewest
+// multiply-adds, a small penalty favouring larger tiles; one launch per tile
+// size.  Descriptors' tile fields are recomputed here.
+std::vector<F64Launch> plan_gemm_f64(std::vector<GemmDesc> d, WinBuf &wb, cudaStream_t s) {
+  std::vector<F64Launch> out;
+  if (d.empty()) return out;
+  const int tms[3] = {16, 32, 64};
+  std::vector<GemmDesc> bucket[3];
+  for (GemmDesc &x : d) {
+    int best = 2;
+    double bc = 0;
+    for (int q = 0; q < 3; ++q) {
+      const int tm = tms[q];
+      const double tiles = (double)((x.M + tm - 1) / tm) * ((x.N + tm - 1) / tm);
+      const double c = tiles * tm * tm * (1.0 + 8.0 / tm);
+      if (q == 0 || c < bc) {
+        bc = c;
+        best = q;
+      }
+    }
+    bucket[best].push_back(x);
+  }
+  for (int q = 0; q < 3; ++q) {
+    std::vector<GemmDesc> &b = bucket[q];
+    if (b.empty()) continue;
+    const int tm = tms[q];
+    long long t = 0;
+    for (GemmDesc &x : b) {
+      x.tiles_m = (x.M + tm - 1) / tm;
+      x.tiles_n = (x.N + tm - 1) / tm;
+      x.tile0 = t;
+      t += (long long)x.tiles_m * x.tiles_n * x.batch;
+    }
+    out.push_back({upload(wb, b, s), (int)b.size(), t, tm});
+  }
+  return out;
+}
+
+void run_gemm_f64(const std::vector<F64Launch> &plan, const GemmSeg *dseg, cudaStream_t s,
+                  const double *bindB = nullptr, double *bindC = nullptr) {
+  for (const F64Launch &l : plan)
+    CK(launch_gemm_f64(l.d, l.nd, dseg, l.tiles, s, bindB, bindC, l.tm));
+}
+
+void gemm_f64_grouped(const std::vector<GemmDesc> &d, const std::vector<GemmSeg> &g, WinBuf &wb,
+                      cudaStream_t s) {
+  if (d.empty()) return;
+  const GemmSeg *dg = upload(wb, g, s);
+  run_gemm_f64(plan_gemm_f64(d, wb, s), dg, s);
+}
+
 // Temporaries of one renormalization chunk: 2^28 doubles (2 GB).
 constexpr long long kRenTmpDoubles = 1LL << 28;
 
@@ -1567,10 +1629,8 @@ void renormalize(dmrg_ctx *C, const BlockPart &U, const Iso &T, BlockPart &B, Wi
     d2.push_back(e);
   }
   if (!d1.empty()) {
-    GemmDesc *dd1 = upload(work, d1, s), *dd2 = upload(work, d2, s);
-    GemmSeg *ss1 = upload(work, s1, s), *ss2 = upload(work, s2, s);
-    CK(launch_gemm_f64(dd1, (int)d1.size(), ss1, t1, s));
-    CK(launch_gemm_f64(dd2, (int)d2.size(), ss2, t2, s));
+    gemm_f64_grouped(d1, s1, work, s);
+    gemm_f64_grouped(d2, s2, work, s);
   }
   }
   CK(cudaStreamSynchronize(s));
@@ -2208,6 +2268,8 @@ void build_window(dmrg_ctx *C, int l) {
   w.s1 = upload(w.buf, w.seg1, s);
   w.d2 = upload(w.buf, w.stage2, s);
   w.s2 = upload(w.buf, w.seg2, s);
+  w.f64_1 = plan_gemm_f64(w.stage1, w.buf, s);
+  w.f64_2 = plan_gemm_f64(w.stage2, w.buf, s);
   w.d_ps64 = upload(w.buf, w.ps64, s);
   w.s1info = s1list;
   // diagonal of H_eff for the Davidson preconditioner: shift-0 class terms
@@ -2309,9 +2371,9 @@ void apply_fp64(dmrg_ctx *C, const double *psi, double *sigma, cudaStream_t s) {
   ensure_fp64(C, s);
   mark(C, 0, s);
   mark(C, 1, s);
-  CK(launch_gemm_f64(w.d1, w.nd1, w.s1, w.tiles1, s, psi, nullptr));
+  run_gemm_f64(w.f64_1, w.s1, s, psi, nullptr);
   mark(C, 2, s);
-  CK(launch_gemm_f64(w.d2, w.nd2, w.s2, w.tiles2, s));
+  run_gemm_f64(w.f64_2, w.s2, s);
   CK(launch_sum_partials64(w.d_ps64, (int)w.ps64.size(), sigma, s));
   mark(C, 3, s);
   mark(C, 4, s);

@@ -17,16 +17,20 @@
 namespace dmrg {
 
 // ----------------------------------------------------------------------------
-// grouped FP64 GEMM: 64x64 tile, K chunk 16, 256 threads, 4x4 per thread
+// grouped FP64 GEMM: TM x TM tiles (TM = 16, 32 or 64), K chunk 16, 256
+// threads, (TM/16)^2 outputs per thread.  The host picks TM per descriptor
+// (small operator blocks waste most of a 64-wide tile).
 // ----------------------------------------------------------------------------
-constexpr int GT = 64, GK = 16;
+constexpr int GK = 16;
 
+template <int TM>
 __global__ void __launch_bounds__(256)
 k_gemm_f64(const GemmDesc *__restrict__ descs, int nd,
            const GemmSeg *__restrict__ segs, long long total,
            const double *__restrict__ bindB, double *__restrict__ bindC) {
-  __shared__ double As[GK][GT + 1];
-  __shared__ double Bs[GK][GT + 1];
+  constexpr int R = TM / 16;
+  __shared__ double As[GK][TM + 1];
+  __shared__ double Bs[GK][TM + 1];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
@@ -41,13 +45,13 @@ k_gemm_f64(const GemmDesc *__restrict__ descs, int nd,
     const int per_b = d.tiles_m * d.tiles_n;
     const int b = (int)(lt / per_b);
     const int rem = (int)(lt % per_b);
-    const int m0 = (rem / d.tiles_n) * GT;
-    const int n0 = (rem % d.tiles_n) * GT;
-    double acc[4][4];
+    const int m0 = (rem / d.tiles_n) * TM;
+    const int n0 = (rem % d.tiles_n) * TM;
+    double acc[R][R];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < R; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+      for (int j = 0; j < R; ++j) acc[i][j] = 0.0;
     for (int sgi = 0; sgi < d.nseg; ++sgi) {
       const GemmSeg sg = segs[d.seg0 + sgi];
       const double *A = sg.A + (long long)b * sg.a_bs;
@@ -55,38 +59,38 @@ k_gemm_f64(const GemmDesc *__restrict__ descs, int nd,
       const double *B = sg.B ? sg.B + (long long)b * sg.b_bs : bindB + sg.b_bs;
       for (int k0 = 0; k0 < sg.K; k0 += GK) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < R; ++j) {
           int idx = tid + 256 * j;
           int kk = idx & 15, r = idx >> 4;
           int m = m0 + r, k = k0 + kk;
           As[kk][r] = (m < d.M && k < sg.K) ? A[m * sg.a_rs + k * sg.a_cs] : 0.0;
-          int kb = idx >> 6, c = idx & 63;
+          int kb = idx / TM, c = idx % TM;
           int n = n0 + c, k2 = k0 + kb;
           Bs[kb][c] = (n < d.N && k2 < sg.K) ? B[k2 * sg.b_rs + n * sg.b_cs] : 0.0;
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < GK; ++kk) {
-          double a[4], bb[4];
+          double a[R], bb[R];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+          for (int i = 0; i < R; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+          for (int j = 0; j < R; ++j) bb[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
+          for (int i = 0; i < R; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+            for (int j = 0; j < R; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
         }
         __syncthreads();
       }
     }
     double *C = d.C ? d.C + (long long)b * d.c_bs : bindC + d.c_bs;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < R; ++i) {
       int m = m0 + ty + 16 * i;
       if (m >= d.M) continue;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < R; ++j) {
         int n = n0 + tx + 16 * j;
         if (n >= d.N) continue;
         double *p = C + m * d.c_rs + n * d.c_cs;
@@ -100,10 +104,15 @@ k_gemm_f64(const GemmDesc *__restrict__ descs, int nd,
 
 cudaError_t launch_gemm_f64(const GemmDesc *d_desc, int ndesc,
                             const GemmSeg *d_seg, long long total_tiles,
-                            cudaStream_t s, const double *bindB, double *bindC) {
+                            cudaStream_t s, const double *bindB, double *bindC, int tm) {
   if (ndesc <= 0 || total_tiles <= 0) return cudaSuccess;
   long long grid = total_tiles < (1LL << 20) ? total_tiles : (1LL << 20);
-  k_gemm_f64<<<(unsigned)grid, 256, 0, s>>>(d_desc, ndesc, d_seg, total_tiles, bindB, bindC);
+  if (tm == 16)
+    k_gemm_f64<16><<<(unsigned)grid, 256, 0, s>>>(d_desc, ndesc, d_seg, total_tiles, bindB, bindC);
+  else if (tm == 32)
+    k_gemm_f64<32><<<(unsigned)grid, 256, 0, s>>>(d_desc, ndesc, d_seg, total_tiles, bindB, bindC);
+  else
+    k_gemm_f64<64><<<(unsigned)grid, 256, 0, s>>>(d_desc, ndesc, d_seg, total_tiles, bindB, bindC);
   return cudaGetLastError();
 }
 

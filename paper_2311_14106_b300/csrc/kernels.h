@@ -85,7 +85,7 @@ struct SCopy {
 cudaError_t launch_gemm_f64(const GemmDesc *d_desc, int ndesc,
                             const GemmSeg *d_seg, long long total_tiles,
                             cudaStream_t s, const double *bindB = nullptr,
-                            double *bindC = nullptr);
+                            double *bindC = nullptr, int tm = 64);
 cudaError_t launch_gather(const GSub *d_sub, int nsub, int max_ops,
                           const GTerm *d_terms, const GSrc *d_src, int d,
                           cudaStream_t s);
