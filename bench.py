@@ -265,6 +265,41 @@ def c1_sweeps(lib, stream):
             "converged": bool(g.sweep_converged)}
 
 
+def staging_sweeps(lib, stream, budget_gb=2.0):
+    """Out-of-HBM block operators (config C5's mechanism on a lattice whose
+    sweep fits the time budget): Hubbard 6x6, 36 e, S = 0, U = 4, momentum
+    basis, spin-adapted, D = 256 multiplets, one split-precision sweep from the
+    same random MPS without a budget and with `budget_gb` of HBM for block
+    operators; wall time, staged bytes and the H2D rate of the side-stream
+    copies (CUDA events on the staging stream)."""
+    T, V = lib.lattice_hamiltonian(lib.MODEL_HUBBARD, 6, 6, 1.0, 0.0, 4.0)
+    U = lib.momentum_basis(6, 6)
+    iso = synth.random_right_isometries_su2(36, (36, 0), 256, 1, 3)
+    out = {"workload": "Hubbard 6x6, 36 e, S=0, U=4, momentum basis, U(1)xSU(2), D=256, "
+                       "one split sweep from a seeded random MPS",
+           "budget_gb": budget_gb}
+    for name, budget in (("resident", 0), ("staged", int(budget_gb * 1e9))):
+        g = lib.Dmrg(36, 36, su2=True, d_max=256, precision=lib.SPLIT, davidson_tol=1e-7,
+                     seed=3, hbm_budget_bytes=budget)
+        g.set_hamiltonian(T, V, U)
+        g.set_mps(right=iso)
+        torch_sync = __import__("torch").cuda.synchronize
+        torch_sync()
+        t0 = time.perf_counter()
+        E = g.sweep(1, stream=stream)
+        torch_sync()
+        wall = time.perf_counter() - t0
+        st = g.staging_stats()
+        mem = g.memory_stats()
+        g.close()
+        out[name] = {"seconds": wall, "energy": float(E[-1]), "staging": st,
+                     "h2d_gb_per_s": st["h2d_bytes"] / st["h2d_seconds"] / 1e9
+                     if st["h2d_seconds"] > 0 else None,
+                     "largest_block_gb": mem["block"] / 1e9}
+    out["energies_equal"] = out["resident"]["energy"] == out["staged"]["energy"]
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -302,6 +337,9 @@ def main():
     ap.add_argument("--serving", default="small", choices=["small", "c4"],
                     help="serving stream: small (12 requests on 4x4 lattices, the default) or "
                          "c4 (32 requests on 6x6 lattices, C4's arrival process and model mix)")
+    ap.add_argument("--staging", action="store_true",
+                    help="also run one 6x6 D=256 sweep with and without an HBM budget for "
+                         "block operators (staged bytes, H2D GB/s)")
     ap.add_argument("--split-only", action="store_true",
                     help="time the split path alone (no FP64 leg, solve, serving or C1): "
                          "for windows whose FP64 and split stacks do not fit together")
@@ -475,6 +513,7 @@ def main():
         serving_out["solves_per_s_ratio_split_over_fp64"] = (
             serving_out["split"]["solves_per_s"] / max(serving_out["fp64"]["solves_per_s"], 1e-12))
     fp64_peak = fp64_peak_probe(torch) if rank == 0 else None
+    staging = staging_sweeps(lib, stream) if args.staging and rank == 0 else None
     # config C1 (4x4 spinless, D = 128, FP64, 6 sweeps): per sweep and per matvec
     c1 = None
     if not args.no_c1 and not args.split_only and rank == 0:
@@ -524,6 +563,7 @@ def main():
         "solve": solve,
         "serving": serving_out,
         "c1_spinless4x4_D128_fp64_6_sweeps": c1,
+        "staging": staging,
         "e2e": {"value": world * flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
                 "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n, "ms_per_step": e2e_ms},
         "clocks": clocks,

@@ -395,7 +395,7 @@ struct F64Launch {
   GemmDesc *d;
   int nd;
   long long tiles;
-  int tm;
+  int tm, tn;
 };
 
 struct Window {
@@ -1455,42 +1455,59 @@ void enlarge_su2(dmrg_ctx *C, const BlockPart &X, const SitePart &st, bool site_
 // ---------------------------------------------------------------------------
 WinBuf &data_of(dmrg_ctx *C, BlockPart *B);
 
-// Grouped FP64 GEMM with the tile size chosen per descriptor: an operator
-// block of a few rows or columns would leave most of a 64 x 64 tile idle, so
-// each descriptor takes the tile (16, 32 or 64) that issues the fewest
-// multiply-adds, a small penalty favouring larger tiles; one launch per tile
-// size.  Descriptors' tile fields are recomputed here.
-std::vector<F64Launch> plan_gemm_f64(std::vector<GemmDesc> d, WinBuf &wb, cudaStream_t s) {
+// Grouped FP64 GEMM with the tile shape chosen per descriptor: an operator
+// block of a few rows or columns would leave most of a 64 x 64 tile idle.  A
+// batch of problems that share one operand (the isometry in a
+// renormalization) can be folded into the rows or columns of one problem.
+// Each descriptor takes the shape and folding that issue the fewest
+// multiply-adds, with a small penalty on small tiles; one launch per shape.
+// Descriptors' tile fields are recomputed here.
+std::vector<F64Launch> plan_gemm_f64(std::vector<GemmDesc> d, const std::vector<GemmSeg> &g,
+                                     WinBuf &wb, cudaStream_t s, bool square_only = false) {
   std::vector<F64Launch> out;
   if (d.empty()) return out;
-  const int tms[3] = {16, 32, 64};
-  std::vector<GemmDesc> bucket[3];
+  static const int shapes[5][2] = {{16, 16}, {32, 32}, {64, 64}, {64, 16}, {16, 64}};
+  std::vector<GemmDesc> bucket[5];
   for (GemmDesc &x : d) {
-    int best = 2;
-    double bc = 0;
-    for (int q = 0; q < 3; ++q) {
-      const int tm = tms[q];
-      const double tiles = (double)((x.M + tm - 1) / tm) * ((x.N + tm - 1) / tm);
-      const double c = tiles * tm * tm * (1.0 + 8.0 / tm);
-      if (q == 0 || c < bc) {
-        bc = c;
-        best = q;
-      }
+    bool f1 = x.batch > 1, f2 = x.batch > 1;
+    for (int q = 0; q < x.nseg; ++q) {
+      const GemmSeg &sg = g[x.seg0 + q];
+      f1 = f1 && sg.B != nullptr && sg.b_bs == 0;
+      f2 = f2 && sg.a_bs == 0;
     }
+    int best = 2, bfold = 0;
+    double bc = -1;
+    for (int q = 0; q < (square_only ? 3 : 5); ++q)
+      for (int f = 0; f < (square_only ? 1 : 3); ++f) {
+        if ((f == 1 && !f1) || (f == 2 && !f2)) continue;
+        const int tm = shapes[q][0], tn = shapes[q][1];
+        const double Mt = f == 1 ? (double)x.batch * x.M : x.M;
+        const double Nt = f == 2 ? (double)x.batch * x.N : x.N;
+        const double tiles = std::ceil(Mt / tm) * std::ceil(Nt / tn) * (f ? 1 : x.batch);
+        const double c = tiles * tm * tn * (1.0 + 4.0 / tm + 4.0 / tn);
+        if (bc < 0 || c < bc) {
+          bc = c;
+          best = q;
+          bfold = f;
+        }
+      }
+    x.fold = bfold;
     bucket[best].push_back(x);
   }
-  for (int q = 0; q < 3; ++q) {
+  for (int q = 0; q < 5; ++q) {
     std::vector<GemmDesc> &b = bucket[q];
     if (b.empty()) continue;
-    const int tm = tms[q];
+    const int tm = shapes[q][0], tn = shapes[q][1];
     long long t = 0;
     for (GemmDesc &x : b) {
-      x.tiles_m = (x.M + tm - 1) / tm;
-      x.tiles_n = (x.N + tm - 1) / tm;
+      const long long Mt = x.fold == 1 ? (long long)x.batch * x.M : x.M;
+      const long long Nt = x.fold == 2 ? (long long)x.batch * x.N : x.N;
+      x.tiles_m = (int)((Mt + tm - 1) / tm);
+      x.tiles_n = (int)((Nt + tn - 1) / tn);
       x.tile0 = t;
-      t += (long long)x.tiles_m * x.tiles_n * x.batch;
+      t += (long long)x.tiles_m * x.tiles_n * (x.fold ? 1 : x.batch);
     }
-    out.push_back({upload(wb, b, s), (int)b.size(), t, tm});
+    out.push_back({upload(wb, b, s), (int)b.size(), t, tm, tn});
   }
   return out;
 }
@@ -1498,14 +1515,14 @@ std::vector<F64Launch> plan_gemm_f64(std::vector<GemmDesc> d, WinBuf &wb, cudaSt
 void run_gemm_f64(const std::vector<F64Launch> &plan, const GemmSeg *dseg, cudaStream_t s,
                   const double *bindB = nullptr, double *bindC = nullptr) {
   for (const F64Launch &l : plan)
-    CK(launch_gemm_f64(l.d, l.nd, dseg, l.tiles, s, bindB, bindC, l.tm));
+    CK(launch_gemm_f64(l.d, l.nd, dseg, l.tiles, s, bindB, bindC, l.tm, l.tn));
 }
 
 void gemm_f64_grouped(const std::vector<GemmDesc> &d, const std::vector<GemmSeg> &g, WinBuf &wb,
                       cudaStream_t s) {
   if (d.empty()) return;
   const GemmSeg *dg = upload(wb, g, s);
-  run_gemm_f64(plan_gemm_f64(d, wb, s), dg, s);
+  run_gemm_f64(plan_gemm_f64(d, g, wb, s), dg, s);
 }
 
 // Temporaries of one renormalization chunk: 2^28 doubles (2 GB).
@@ -2268,8 +2285,10 @@ void build_window(dmrg_ctx *C, int l) {
   w.s1 = upload(w.buf, w.seg1, s);
   w.d2 = upload(w.buf, w.stage2, s);
   w.s2 = upload(w.buf, w.seg2, s);
-  w.f64_1 = plan_gemm_f64(w.stage1, w.buf, s);
-  w.f64_2 = plan_gemm_f64(w.stage2, w.buf, s);
+  // the H_eff stages (one problem per descriptor) run on square tiles; the
+  // rectangular ones measured slower there
+  w.f64_1 = plan_gemm_f64(w.stage1, w.seg1, w.buf, s, true);
+  w.f64_2 = plan_gemm_f64(w.stage2, w.seg2, w.buf, s, true);
   w.d_ps64 = upload(w.buf, w.ps64, s);
   w.s1info = s1list;
   // diagonal of H_eff for the Davidson preconditioner: shift-0 class terms

@@ -17,20 +17,22 @@
 namespace dmrg {
 
 // ----------------------------------------------------------------------------
-// grouped FP64 GEMM: TM x TM tiles (TM = 16, 32 or 64), K chunk 16, 256
-// threads, (TM/16)^2 outputs per thread.  The host picks TM per descriptor
-// (small operator blocks waste most of a 64-wide tile).
+// grouped FP64 GEMM: TM x TN tiles (16, 32 or 64 each), K chunk 16, 256
+// threads, (TM/16) x (TN/16) outputs per thread.  The host picks the tile
+// shape per descriptor, and may fold a batch of problems that share one
+// operand into the rows or columns of a single problem (small operator blocks
+// would otherwise waste most of a tile).
 // ----------------------------------------------------------------------------
 constexpr int GK = 16;
 
-template <int TM>
+template <int TM, int TN>
 __global__ void __launch_bounds__(256)
 k_gemm_f64(const GemmDesc *__restrict__ descs, int nd,
            const GemmSeg *__restrict__ segs, long long total,
            const double *__restrict__ bindB, double *__restrict__ bindC) {
-  constexpr int R = TM / 16;
+  constexpr int RM = TM / 16, RN = TN / 16;
   __shared__ double As[GK][TM + 1];
-  __shared__ double Bs[GK][TM + 1];
+  __shared__ double Bs[GK][TN + 1];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
@@ -43,15 +45,17 @@ k_gemm_f64(const GemmDesc *__restrict__ descs, int nd,
     const GemmDesc d = descs[lo];
     long long lt = t - d.tile0;
     const int per_b = d.tiles_m * d.tiles_n;
-    const int b = (int)(lt / per_b);
+    const int b = d.fold ? 0 : (int)(lt / per_b);
     const int rem = (int)(lt % per_b);
     const int m0 = (rem / d.tiles_n) * TM;
-    const int n0 = (rem % d.tiles_n) * TM;
-    double acc[R][R];
+    const int n0 = (rem % d.tiles_n) * TN;
+    const int Mt = d.fold == 1 ? d.batch * d.M : d.M;
+    const int Nt = d.fold == 2 ? d.batch * d.N : d.N;
+    double acc[RM][RN];
 #pragma unroll
-    for (int i = 0; i < R; ++i)
+    for (int i = 0; i < RM; ++i)
 #pragma unroll
-      for (int j = 0; j < R; ++j) acc[i][j] = 0.0;
+      for (int j = 0; j < RN; ++j) acc[i][j] = 0.0;
     for (int sgi = 0; sgi < d.nseg; ++sgi) {
       const GemmSeg sg = segs[d.seg0 + sgi];
       const double *A = sg.A + (long long)b * sg.a_bs;
@@ -59,41 +63,73 @@ k_gemm_f64(const GemmDesc *__restrict__ descs, int nd,
       const double *B = sg.B ? sg.B + (long long)b * sg.b_bs : bindB + sg.b_bs;
       for (int k0 = 0; k0 < sg.K; k0 += GK) {
 #pragma unroll
-        for (int j = 0; j < R; ++j) {
+        for (int j = 0; j < RM; ++j) {
           int idx = tid + 256 * j;
           int kk = idx & 15, r = idx >> 4;
           int m = m0 + r, k = k0 + kk;
-          As[kk][r] = (m < d.M && k < sg.K) ? A[m * sg.a_rs + k * sg.a_cs] : 0.0;
-          int kb = idx / TM, c = idx % TM;
+          double v = 0.0;
+          if (m < Mt && k < sg.K) {
+            if (d.fold == 1) {
+              const int bb = m / d.M;
+              v = A[(long long)bb * sg.a_bs + (m - bb * d.M) * sg.a_rs + k * sg.a_cs];
+            } else {
+              v = A[m * sg.a_rs + k * sg.a_cs];
+            }
+          }
+          As[kk][r] = v;
+        }
+#pragma unroll
+        for (int j = 0; j < RN; ++j) {
+          int idx = tid + 256 * j;
+          int kb = idx / TN, c = idx % TN;
           int n = n0 + c, k2 = k0 + kb;
-          Bs[kb][c] = (n < d.N && k2 < sg.K) ? B[k2 * sg.b_rs + n * sg.b_cs] : 0.0;
+          double v = 0.0;
+          if (n < Nt && k2 < sg.K) {
+            if (d.fold == 2) {
+              const int bb = n / d.N;
+              v = B[(long long)bb * sg.b_bs + k2 * sg.b_rs + (n - bb * d.N) * sg.b_cs];
+            } else {
+              v = B[k2 * sg.b_rs + n * sg.b_cs];
+            }
+          }
+          Bs[kb][c] = v;
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < GK; ++kk) {
-          double a[R], bb[R];
+          double a[RM], bb[RN];
 #pragma unroll
-          for (int i = 0; i < R; ++i) a[i] = As[kk][ty + 16 * i];
+          for (int i = 0; i < RM; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-          for (int j = 0; j < R; ++j) bb[j] = Bs[kk][tx + 16 * j];
+          for (int j = 0; j < RN; ++j) bb[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-          for (int i = 0; i < R; ++i)
+          for (int i = 0; i < RM; ++i)
 #pragma unroll
-            for (int j = 0; j < R; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+            for (int j = 0; j < RN; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
         }
         __syncthreads();
       }
     }
     double *C = d.C ? d.C + (long long)b * d.c_bs : bindC + d.c_bs;
 #pragma unroll
-    for (int i = 0; i < R; ++i) {
+    for (int i = 0; i < RM; ++i) {
       int m = m0 + ty + 16 * i;
-      if (m >= d.M) continue;
+      if (m >= Mt) continue;
 #pragma unroll
-      for (int j = 0; j < R; ++j) {
+      for (int j = 0; j < RN; ++j) {
         int n = n0 + tx + 16 * j;
-        if (n >= d.N) continue;
-        double *p = C + m * d.c_rs + n * d.c_cs;
+        if (n >= Nt) continue;
+        long long o;
+        if (d.fold == 1) {
+          const int bb = m / d.M;
+          o = (long long)bb * d.c_bs + (m - bb * d.M) * d.c_rs + n * d.c_cs;
+        } else if (d.fold == 2) {
+          const int bb = n / d.N;
+          o = (long long)bb * d.c_bs + m * d.c_rs + (n - bb * d.N) * d.c_cs;
+        } else {
+          o = m * d.c_rs + n * d.c_cs;
+        }
+        double *p = C + o;
         double v = d.alpha * acc[i][j];
         if (d.beta != 0.0) v += d.beta * *p;
         *p = v;
@@ -102,19 +138,27 @@ k_gemm_f64(const GemmDesc *__restrict__ descs, int nd,
   }
 }
 
+#define GEMM_F64_CASE(a, b)                                                              \
+  if (tm == a && tn == b) {                                                              \
+    k_gemm_f64<a, b><<<(unsigned)grid, 256, 0, s>>>(d_desc, ndesc, d_seg, total_tiles,   \
+                                                    bindB, bindC);                       \
+    return cudaGetLastError();                                                           \
+  }
+
 cudaError_t launch_gemm_f64(const GemmDesc *d_desc, int ndesc,
                             const GemmSeg *d_seg, long long total_tiles,
-                            cudaStream_t s, const double *bindB, double *bindC, int tm) {
+                            cudaStream_t s, const double *bindB, double *bindC, int tm,
+                            int tn) {
   if (ndesc <= 0 || total_tiles <= 0) return cudaSuccess;
   long long grid = total_tiles < (1LL << 20) ? total_tiles : (1LL << 20);
-  if (tm == 16)
-    k_gemm_f64<16><<<(unsigned)grid, 256, 0, s>>>(d_desc, ndesc, d_seg, total_tiles, bindB, bindC);
-  else if (tm == 32)
-    k_gemm_f64<32><<<(unsigned)grid, 256, 0, s>>>(d_desc, ndesc, d_seg, total_tiles, bindB, bindC);
-  else
-    k_gemm_f64<64><<<(unsigned)grid, 256, 0, s>>>(d_desc, ndesc, d_seg, total_tiles, bindB, bindC);
-  return cudaGetLastError();
+  GEMM_F64_CASE(16, 16)
+  GEMM_F64_CASE(32, 32)
+  GEMM_F64_CASE(64, 64)
+  GEMM_F64_CASE(64, 16)
+  GEMM_F64_CASE(16, 64)
+  return cudaErrorInvalidValue;
 }
+#undef GEMM_F64_CASE
 
 // ----------------------------------------------------------------------------
 // Kronecker gather for enlarged-block operators

@@ -27,6 +27,11 @@ struct GemmDesc {
   int tiles_m, tiles_n;
   double alpha, beta;
   long long tile0;   // prefix sum of tiles over descriptors
+  // 0: `batch` separate problems; 1: the batch folded into the rows (one
+  // problem of batch*M rows, row b*M + m; every segment's B shared, b_bs = 0);
+  // 2: folded into the columns (batch*N columns; every segment's A shared)
+  int fold;
+  int pad;
 };
 
 // Source operator class for the Kronecker gather (op-major storage: op k of
@@ -85,7 +90,7 @@ struct SCopy {
 cudaError_t launch_gemm_f64(const GemmDesc *d_desc, int ndesc,
                             const GemmSeg *d_seg, long long total_tiles,
                             cudaStream_t s, const double *bindB = nullptr,
-                            double *bindC = nullptr, int tm = 64);
+                            double *bindC = nullptr, int tm = 64, int tn = 64);
 cudaError_t launch_gather(const GSub *d_sub, int nsub, int max_ops,
                           const GTerm *d_terms, const GSrc *d_src, int d,
                           cudaStream_t s);
