@@ -420,11 +420,8 @@ struct Window {
   bool fp64_stacks = false;          // A and B hold the window's operators
   double *Astack = nullptr, *Bstack = nullptr, *T = nullptr;
   long long nA = 0, nB = 0, nT = 0;
-  GemmDesc *d1 = nullptr, *d2 = nullptr;
   GemmSeg *s1 = nullptr, *s2 = nullptr;
   std::vector<F64Launch> f64_1, f64_2;   // the FP64 stages by tile size
-  int nd1 = 0, nd2 = 0;
-  long long tiles1 = 0, tiles2 = 0;
   double flops = 0, flops1 = 0, flops2 = 0;
   double *diag = nullptr;
   std::vector<S1> s1info;                 // stage-1 regions (class, psi in, psi out)
@@ -448,6 +445,10 @@ struct Window {
 };
 
 }  // namespace
+
+// spin-adapted formula of one target tensor: (factor, adjoint, factor,
+// adjoint) -> coefficient
+using SU2Terms = std::map<std::tuple<TKey, int, TKey, int>, double>;
 
 struct dmrg_ctx {
   dmrg_config cfg;
@@ -478,6 +479,10 @@ struct dmrg_ctx {
   int precision = DMRG_FP64;
   double prof[7] = {0};
   double mem_max[6] = {0};   // dmrg_memory_stats
+  // spin-adapted formulas already derived for this Hamiltonian, by (modes of
+  // the first part, modes of the second, target tensor)
+  std::map<std::pair<std::vector<int>, std::vector<int>>, std::map<TKey, SU2Terms>> derive_cache;
+  long long derive_cache_terms = 0;
   // optional per-stage event timing of H_eff*psi
   bool timing = false;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -1179,7 +1184,6 @@ void enlarge(dmrg_ctx *C, const BlockPart &X, const SitePart &st, bool site_firs
 //   X_qa Y_qb = sum_kappa <ka qa kb qb | kappa k> [X (x) Y]^kappa_k + ...,
 // and the kappa = k parts are summed.  The kappa != k parts must cancel
 // (T is a rank-k tensor): checked.
-using SU2Terms = std::map<std::tuple<TKey, int, TKey, int>, double>;
 
 SU2Terms derive_su2(const dmrg_ctx *C, const SideS &F, const SideS &G, const TKey &T) {
   const int tk = T.tk, tq = T.tk;
@@ -1270,6 +1274,40 @@ SideS side_of(const SitePart &st) {
   return sd;
 }
 
+// A block's tensors as the formulas see them when derived once for every
+// block of the same modes: a tensor counts if the block defines it, even if
+// all its classes are empty in the current basis (those terms are zero and
+// the users of the derived terms skip factors without data).
+SideS side_of_defined(const BlockPart &B) {
+  SideS sd;
+  sd.so_modes = B.modes;
+  sd.has = [&B](const TKey &k) { return B.ten.count(k) > 0; };
+  return sd;
+}
+
+// derive_su2 memoised per context: the terms depend only on the parts' modes,
+// the target tensor and the Hamiltonian (cleared when it changes).  A sweep
+// meets every enlargement (block x site) again in its other pass, and every
+// later sweep meets them all again.  derive_table returns the table of one
+// pair of parts (looked up once per enlargement), derive_in one tensor's terms.
+std::map<TKey, SU2Terms> &derive_table(dmrg_ctx *C, const SideS &F, const SideS &G) {
+  // bounded host memory: start over past 2^24 cached terms
+  if (C->derive_cache_terms > (1LL << 24)) {
+    C->derive_cache.clear();
+    C->derive_cache_terms = 0;
+  }
+  return C->derive_cache[std::make_pair(F.so_modes, G.so_modes)];
+}
+
+const SU2Terms &derive_in(dmrg_ctx *C, std::map<TKey, SU2Terms> &tab, const SideS &F,
+                          const SideS &G, const TKey &T) {
+  auto it = tab.find(T);
+  if (it != tab.end()) return it->second;
+  SU2Terms al = derive_su2(C, F, G, T);
+  C->derive_cache_terms += (long long)al.size() + 1;
+  return tab.emplace(T, std::move(al)).first->second;
+}
+
 // coefficient-table slot of a term type (2 k of the block factor, of the site
 // factor, of the target; block factor adjoint)
 inline int ctype_of(int tkX, int tkS, int tk, int adj) { return ((tkX * 3 + tkS) * 3 + tk) * 2 + adj; }
@@ -1316,9 +1354,10 @@ void enlarge_su2(dmrg_ctx *C, const BlockPart &X, const SitePart &st, bool site_
   std::vector<OpSpec> specs = block_specs(C, U.modes);
   make_classes(U, specs, wb, s);
 
-  const SideS sx = side_of(X), ss = side_of(st);
+  const SideS sx = side_of_defined(X), ss = side_of(st);
   const SideS &F = site_first ? ss : sx;
   const SideS &G = site_first ? sx : ss;
+  std::map<TKey, SU2Terms> &dtab = derive_table(C, F, G);
   // per class, per op: terms
   std::vector<std::vector<std::vector<GTerm>>> terms(U.cls.size());
   for (size_t ci = 0; ci < U.cls.size(); ++ci) terms[ci].resize(U.cls[ci].nops);
@@ -1327,9 +1366,10 @@ void enlarge_su2(dmrg_ctx *C, const BlockPart &X, const SitePart &st, bool site_
     bool any = false;
     for (const Ref &r : tv.second.r) any |= r.cls >= 0;
     if (!any) continue;
-    const SU2Terms al = derive_su2(C, F, G, T);
-    // merged by (source class, index, transpose, coefficient type)
-    std::map<std::array<int, 4>, GTerm> acc;
+    const SU2Terms &al = derive_in(C, dtab, F, G, T);
+    // merged by (source class, index, transpose, coefficient type); a tensor
+    // has a few such terms, so a linear search is the cheapest map
+    std::vector<GTerm> acc;
     for (auto &kv : al) {
       const TKey &kf = std::get<0>(kv.first), &kg = std::get<2>(kv.first);
       const int af = std::get<1>(kv.first), ag = std::get<3>(kv.first);
@@ -1350,9 +1390,13 @@ void enlarge_su2(dmrg_ctx *C, const BlockPart &X, const SitePart &st, bool site_
       const int p2 = site_first ? kx.parity() : (ks.kind < 0 ? 0 : ks.parity());
       const int ct = ctype_of(tkX, tkS, T.tk, kx.kind < 0 ? 0 : ax);
       auto put = [&](int src, int idx, int trans) {
-        std::array<int, 4> key{src, idx, trans, ct};
-        auto it = acc.find(key);
-        if (it == acc.end()) {
+        GTerm *gt = nullptr;
+        for (GTerm &x : acc)
+          if (x.src == src && x.idx == idx && x.trans == trans && x.ctype == ct) {
+            gt = &x;
+            break;
+          }
+        if (!gt) {
           GTerm g;
           memset(&g, 0, sizeof g);
           g.src = src;
@@ -1360,9 +1404,10 @@ void enlarge_su2(dmrg_ctx *C, const BlockPart &X, const SitePart &st, bool site_
           g.trans = trans;
           g.p2 = p2;
           g.ctype = ct;
-          it = acc.emplace(key, g).first;
+          acc.push_back(g);
+          gt = &acc.back();
         }
-        for (int e = 0; e < 16; ++e) it->second.m[e] += kv.second * m[e];
+        for (int e = 0; e < 16; ++e) gt->m[e] += kv.second * m[e];
       };
       if (kx.kind < 0) {
         put(-1, 0, 0);
@@ -1372,10 +1417,13 @@ void enlarge_su2(dmrg_ctx *C, const BlockPart &X, const SitePart &st, bool site_
           if (r.cls >= 0) put(r.cls, r.idx, ax);
       }
     }
-    std::vector<GTerm> list;
-    for (auto &kv : acc) list.push_back(kv.second);
+    // (source class, index, transpose, coefficient type) order, as a map would give
+    std::sort(acc.begin(), acc.end(), [](const GTerm &a, const GTerm &b) {
+      return std::make_tuple(a.src, a.idx, a.trans, a.ctype) <
+             std::make_tuple(b.src, b.idx, b.trans, b.ctype);
+    });
     for (const Ref &r : tv.second.r)
-      if (r.cls >= 0) terms[r.cls][r.idx] = list;
+      if (r.cls >= 0) terms[r.cls][r.idx] = acc;
   }
   // flatten terms, CSR per class
   std::vector<GTerm> all;
@@ -2047,7 +2095,8 @@ void build_window(dmrg_ctx *C, int l) {
     // spin-adapted: H = sum alpha [A^k (x) B^k]^0; component g of A (spin
     // change 2(J_a' - J_a) = g) pairs with component g of B (total S = 0
     // keeps J_a = J_b); adjoint tensors use the transposed component -g
-    const SU2Terms al = derive_su2(C, side_of(w.Ld), side_of(w.Rd), TKey{0, 0, 0, 0});
+    const SideS sl = side_of_defined(w.Ld), sr = side_of_defined(w.Rd);
+    const SU2Terms &al = derive_in(C, derive_table(C, sl, sr), sl, sr, TKey{0, 0, 0, 0});
     auto comp = [](const BlockPart &P, const TKey &k, int adj, int g) {
       Fac f;
       if (k.kind < 0) {
@@ -2273,17 +2322,11 @@ void build_window(dmrg_ctx *C, int l) {
   }
   w.ps64 = ps64;
   w.flops = flops;
-  w.tiles1 = t1;
-  w.tiles2 = t2;
-  w.nd1 = (int)d1.size();
-  w.nd2 = (int)d2.size();
   w.stage1 = d1;
   w.seg1 = g1;
   w.stage2 = d2;
   w.seg2 = g2;
-  w.d1 = upload(w.buf, w.stage1, s);
   w.s1 = upload(w.buf, w.seg1, s);
-  w.d2 = upload(w.buf, w.stage2, s);
   w.s2 = upload(w.buf, w.seg2, s);
   // the H_eff stages (one problem per descriptor) run on square tiles; the
   // rectangular ones measured slower there
@@ -4543,6 +4586,8 @@ int dmrg_momentum_basis(int Lx, int Ly, double *U) {
 int dmrg_set_hamiltonian(dmrg_ctx *C, const double *t, const double *V, const double *U) {
   if (!C || !t || !V) return DMRG_ERR_ARG;
   return guard(C, [&] {
+    C->derive_cache.clear();
+    C->derive_cache_terms = 0;
     const int N = C->N;
     const size_t N2 = (size_t)N * N, N4 = N2 * N2;
     double vmax = 0;

@@ -79,20 +79,17 @@ inline double cg_raw(int tj1, int tm1, int tj2, int tm2, int tJ, int tM) {
   return (double)(s * std::sqrt(pref));
 }
 
+// Cached per host thread (no lock: concurrent solves run on their own
+// threads and each fills its own small table).
 inline double cg(int tj1, int tm1, int tj2, int tm2, int tJ, int tM) {
-  static std::mutex mu;
-  static std::unordered_map<unsigned long long, double> cache;
+  thread_local std::unordered_map<unsigned long long, double> cache;
   auto enc = [](int x) { return (unsigned long long)(x + 128) & 0xff; };
   const unsigned long long key = enc(tj1) | enc(tm1) << 8 | enc(tj2) << 16 | enc(tm2) << 24 |
                                  enc(tJ) << 32 | enc(tM) << 40;
-  {
-    std::lock_guard<std::mutex> lk(mu);
-    auto it = cache.find(key);
-    if (it != cache.end()) return it->second;
-  }
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
   const double v = cg_raw(tj1, tm1, tj2, tm2, tJ, tM);
-  std::lock_guard<std::mutex> lk(mu);
-  cache[key] = v;
+  cache.emplace(key, v);
   return v;
 }
 
@@ -133,17 +130,20 @@ inline double coupling_raw(int tjF, int tjG, int tJ, int tjFp, int tjGp, int tJp
 
 inline double coupling(int tjF, int tjG, int tJ, int tjFp, int tjGp, int tJp, int tkF, int tkG,
                        int tk) {
-  static std::mutex mu;
-  static std::map<std::array<int, 9>, double> cache;
-  const std::array<int, 9> key{tjF, tjG, tJ, tjFp, tjGp, tJp, tkF, tkG, tk};
-  {
-    std::lock_guard<std::mutex> lk(mu);
-    auto it = cache.find(key);
-    if (it != cache.end()) return it->second;
+  // cached per host thread; the doubled spins of a key fit in 7 bits each
+  thread_local std::unordered_map<unsigned long long, double> cache;
+  const int v9[9] = {tjF, tjG, tJ, tjFp, tjGp, tJp, tkF, tkG, tk};
+  unsigned long long key = 0;
+  bool fits = true;
+  for (int i = 0; i < 9; ++i) {
+    fits = fits && v9[i] >= 0 && v9[i] < 128;
+    key = (key << 7) | (unsigned long long)(v9[i] & 127);
   }
+  if (!fits) return coupling_raw(tjF, tjG, tJ, tjFp, tjGp, tJp, tkF, tkG, tk);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
   const double v = coupling_raw(tjF, tjG, tJ, tjFp, tjGp, tJp, tkF, tkG, tk);
-  std::lock_guard<std::mutex> lk(mu);
-  cache[key] = v;
+  cache.emplace(key, v);
   return v;
 }
 
