@@ -23,6 +23,7 @@
 #include <shared_mutex>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/dmrg_b300.h"
@@ -1290,6 +1291,38 @@ SideS side_of_defined(const BlockPart &B) {
 // meets every enlargement (block x site) again in its other pass, and every
 // later sweep meets them all again.  derive_table returns the table of one
 // pair of parts (looked up once per enlargement), derive_in one tensor's terms.
+// f(0..n-1) on up to 8 host threads (items claimed 16 at a time); the first
+// exception of any thread is rethrown here.  For independent host work only.
+template <class Fn>
+void parallel_for(size_t n, Fn &&f) {
+  const size_t hw = std::max(1u, std::thread::hardware_concurrency());
+  const size_t nt = std::min<size_t>(std::min<size_t>(hw, 8), (n + 63) / 64);
+  if (nt <= 1) {
+    for (size_t i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::atomic<size_t> next{0};
+  std::exception_ptr err;
+  std::mutex em;
+  auto run = [&]() {
+    try {
+      for (;;) {
+        const size_t i = next.fetch_add(16);
+        if (i >= n) break;
+        for (size_t j = i; j < std::min(n, i + 16); ++j) f(j);
+      }
+    } catch (...) {
+      std::lock_guard<std::mutex> lk(em);
+      if (!err) err = std::current_exception();
+    }
+  };
+  std::vector<std::thread> th;
+  for (size_t t = 1; t < nt; ++t) th.emplace_back(run);
+  run();
+  for (auto &t : th) t.join();
+  if (err) std::rethrow_exception(err);
+}
+
 std::map<TKey, SU2Terms> &derive_table(dmrg_ctx *C, const SideS &F, const SideS &G) {
   // bounded host memory: start over past 2^24 cached terms
   if (C->derive_cache_terms > (1LL << 24)) {
@@ -1361,12 +1394,32 @@ void enlarge_su2(dmrg_ctx *C, const BlockPart &X, const SitePart &st, bool site_
   // per class, per op: terms
   std::vector<std::vector<std::vector<GTerm>>> terms(U.cls.size());
   for (size_t ci = 0; ci < U.cls.size(); ++ci) terms[ci].resize(U.cls[ci].nops);
+  // the tensors with data; formulas not derived yet for these parts are
+  // derived on several host threads and cached in order, then every tensor's
+  // terms are built on several threads (each writes only its own slots)
+  std::vector<std::pair<const TKey *, const TRef *>> work;
   for (auto &tv : U.ten) {
-    const TKey &T = tv.first;
     bool any = false;
     for (const Ref &r : tv.second.r) any |= r.cls >= 0;
-    if (!any) continue;
-    const SU2Terms &al = derive_in(C, dtab, F, G, T);
+    if (any) work.push_back({&tv.first, &tv.second});
+  }
+  std::vector<const SU2Terms *> alp(work.size(), nullptr);
+  std::vector<size_t> miss;
+  for (size_t i = 0; i < work.size(); ++i) {
+    auto it = dtab.find(*work[i].first);
+    if (it != dtab.end()) alp[i] = &it->second;
+    else miss.push_back(i);
+  }
+  std::vector<SU2Terms> fresh(miss.size());
+  parallel_for(miss.size(), [&](size_t k) { fresh[k] = derive_su2(C, F, G, *work[miss[k]].first); });
+  for (size_t k = 0; k < miss.size(); ++k) {
+    C->derive_cache_terms += (long long)fresh[k].size() + 1;
+    alp[miss[k]] = &dtab.emplace(*work[miss[k]].first, std::move(fresh[k])).first->second;
+  }
+  parallel_for(work.size(), [&](size_t wi) {
+    const TKey &T = *work[wi].first;
+    const TRef &tref = *work[wi].second;
+    const SU2Terms &al = *alp[wi];
     // merged by (source class, index, transpose, coefficient type); a tensor
     // has a few such terms, so a linear search is the cheapest map
     std::vector<GTerm> acc;
@@ -1422,9 +1475,9 @@ void enlarge_su2(dmrg_ctx *C, const BlockPart &X, const SitePart &st, bool site_
       return std::make_tuple(a.src, a.idx, a.trans, a.ctype) <
              std::make_tuple(b.src, b.idx, b.trans, b.ctype);
     });
-    for (const Ref &r : tv.second.r)
+    for (const Ref &r : tref.r)
       if (r.cls >= 0) terms[r.cls][r.idx] = acc;
-  }
+  });
   // flatten terms, CSR per class
   std::vector<GTerm> all;
   std::vector<std::vector<int>> ptr(U.cls.size());
