@@ -168,6 +168,14 @@ int dmrg_heff_layout(dmrg_ctx *ctx, long long *psi_len, int *n_blocks,
  * turns it off.  Defaults: 20 steps, 1e10 flops.  Errors: ARG. */
 int dmrg_set_refinement(dmrg_ctx *ctx, int inner_steps, double min_window_flops);
 
+/* Split-precision contexts solve the windows whose H_eff*psi has fewer than
+ * min_window_flops algorithmic flops with the FP64 product alone (Davidson
+ * and the energy as in a DMRG_FP64 context); dmrg_heff_apply itself is not
+ * affected.  Small windows are launch-bound on both paths, and the split
+ * Davidson's noise floor and refinement cost it more products there.
+ * Default 0 (every window split).  Errors: ARG. */
+int dmrg_set_split_min_flops(dmrg_ctx *ctx, double min_window_flops);
+
 /* Select the arithmetic of dmrg_heff_apply: DMRG_FP64 or DMRG_SPLIT. */
 int dmrg_set_precision(dmrg_ctx *ctx, int precision);
 
@@ -371,6 +379,17 @@ int dmrg_heff_fp64_state(dmrg_ctx *ctx, long long *out4);
  * -1 if the sweep rebuilds it first, -2 for bad arguments: the staging
  * policy, exposed for tests (pure host function, no context). */
 long long dmrg_sweep_next_use(int n_sites, int pass, int l, int left, int n);
+
+/* Tile shape and folding the grouped FP64 GEMM picks for `batch` problems of
+ * M x N (renormalization products, FP64 H_eff stages): out3 = {tile rows,
+ * tile columns, fold} with fold 0 (separate problems), 1 (batch folded into
+ * the rows; allowed if fold_rows_ok, i.e. all problems share the B operand)
+ * or 2 (into the columns; fold_cols_ok, shared A); square_only restricts the
+ * shapes to 16, 32 and 64 squares without folding.  The choice issues the
+ * fewest multiply-adds, with a small penalty on small tiles (pure host
+ * function, exposed for tests).  Errors: ARG. */
+int dmrg_gemm_tile_choice(int M, int N, int batch, int fold_rows_ok, int fold_cols_ok,
+                          int square_only, int *out3);
 
 /* Code paths the split-precision plan of the current window exercises
  * (for tests): out8[0] stage-1 work items, [1] stage-2 work items, [2] psi

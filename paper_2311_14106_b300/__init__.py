@@ -34,7 +34,8 @@ HEADER_FUNCTIONS = [
     "dmrg_sync", "dmrg_get_mps", "dmrg_get_center", "dmrg_heff_split_paths",
     "dmrg_selftest_timeout_report", "dmrg_staging_stats", "dmrg_sweep_next_use",
     "dmrg_rdm1", "dmrg_heff_apply_batch", "dmrg_random_start", "dmrg_heff_fp64_state",
-    "dmrg_memory_stats", "dmrg_set_refinement",
+    "dmrg_memory_stats", "dmrg_set_refinement", "dmrg_set_split_min_flops",
+    "dmrg_gemm_tile_choice",
 ]
 
 
@@ -95,6 +96,8 @@ _sig = {
     "dmrg_heff_fp64_state": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong)]),
     "dmrg_memory_stats": (ctypes.c_int, [_P, _D]),
     "dmrg_set_refinement": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double]),
+    "dmrg_set_split_min_flops": (ctypes.c_int, [_P, ctypes.c_double]),
+    "dmrg_gemm_tile_choice": (ctypes.c_int, [ctypes.c_int] * 6 + [_I]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -156,6 +159,16 @@ def momentum_basis(Lx, Ly):
     if rc != OK:
         raise DmrgError(rc, "momentum_basis")
     return U
+
+
+def gemm_tile_choice(M, N, batch, fold_rows_ok=False, fold_cols_ok=False, square_only=False):
+    """(tile rows, tile columns, fold) of the grouped FP64 GEMM (see the header)."""
+    out = np.zeros(3, dtype=np.int32)
+    rc = _lib.dmrg_gemm_tile_choice(M, N, batch, int(fold_rows_ok), int(fold_cols_ok),
+                                    int(square_only), _iptr(out))
+    if rc != OK:
+        raise DmrgError(rc, "gemm_tile_choice")
+    return tuple(int(x) for x in out)
 
 
 class Dmrg:
@@ -242,6 +255,11 @@ class Dmrg:
         """Split-precision correction steps of the FP64 refinement (see the header)."""
         self._check(_lib.dmrg_set_refinement(self._h, inner_steps, min_window_flops),
                     "set_refinement")
+
+    def set_split_min_flops(self, min_window_flops):
+        """Windows below this many flops per product solve in FP64 (see the header)."""
+        self._check(_lib.dmrg_set_split_min_flops(self._h, min_window_flops),
+                    "set_split_min_flops")
 
     def set_precision(self, p):
         self._check(_lib.dmrg_set_precision(self._h, p), "set_precision")

@@ -499,6 +499,9 @@ struct dmrg_ctx {
   // on windows of at least this many algorithmic flops per apply
   int refine_steps = 20;
   double refine_min_flops = 1e10;
+  // split contexts solve windows below this many flops per product with the
+  // FP64 product alone (dmrg_set_split_min_flops)
+  double split_min_flops = 0;
   uint64_t start_count = 0;
   bool use_graphs = true;
   cudaStream_t cap_stream = nullptr;            // private stream for graph capture
@@ -1563,11 +1566,37 @@ WinBuf &data_of(dmrg_ctx *C, BlockPart *B);
 // Each descriptor takes the shape and folding that issue the fewest
 // multiply-adds, with a small penalty on small tiles; one launch per shape.
 // Descriptors' tile fields are recomputed here.
+const int kGemmShapes[5][2] = {{16, 16}, {32, 32}, {64, 64}, {64, 16}, {16, 64}};
+
+// Tile shape (index into kGemmShapes) and folding (0 none, 1 rows, 2 columns)
+// that issue the fewest multiply-adds for `batch` problems of M x N, folding
+// into rows allowed if f1, into columns if f2; a small penalty per tile edge
+// favours larger tiles.
+void gemm_tile_choice(int M, int N, int batch, bool f1, bool f2, bool square_only, int *shape,
+                      int *fold) {
+  double bc = -1;
+  *shape = 2;
+  *fold = 0;
+  for (int q = 0; q < (square_only ? 3 : 5); ++q)
+    for (int f = 0; f < (square_only ? 1 : 3); ++f) {
+      if ((f == 1 && !f1) || (f == 2 && !f2)) continue;
+      const int tm = kGemmShapes[q][0], tn = kGemmShapes[q][1];
+      const double Mt = f == 1 ? (double)batch * M : M;
+      const double Nt = f == 2 ? (double)batch * N : N;
+      const double tiles = std::ceil(Mt / tm) * std::ceil(Nt / tn) * (f ? 1 : batch);
+      const double c = tiles * tm * tn * (1.0 + 4.0 / tm + 4.0 / tn);
+      if (bc < 0 || c < bc) {
+        bc = c;
+        *shape = q;
+        *fold = f;
+      }
+    }
+}
+
 std::vector<F64Launch> plan_gemm_f64(std::vector<GemmDesc> d, const std::vector<GemmSeg> &g,
                                      WinBuf &wb, cudaStream_t s, bool square_only = false) {
   std::vector<F64Launch> out;
   if (d.empty()) return out;
-  static const int shapes[5][2] = {{16, 16}, {32, 32}, {64, 64}, {64, 16}, {16, 64}};
   std::vector<GemmDesc> bucket[5];
   for (GemmDesc &x : d) {
     bool f1 = x.batch > 1, f2 = x.batch > 1;
@@ -1577,28 +1606,14 @@ std::vector<F64Launch> plan_gemm_f64(std::vector<GemmDesc> d, const std::vector<
       f2 = f2 && sg.a_bs == 0;
     }
     int best = 2, bfold = 0;
-    double bc = -1;
-    for (int q = 0; q < (square_only ? 3 : 5); ++q)
-      for (int f = 0; f < (square_only ? 1 : 3); ++f) {
-        if ((f == 1 && !f1) || (f == 2 && !f2)) continue;
-        const int tm = shapes[q][0], tn = shapes[q][1];
-        const double Mt = f == 1 ? (double)x.batch * x.M : x.M;
-        const double Nt = f == 2 ? (double)x.batch * x.N : x.N;
-        const double tiles = std::ceil(Mt / tm) * std::ceil(Nt / tn) * (f ? 1 : x.batch);
-        const double c = tiles * tm * tn * (1.0 + 4.0 / tm + 4.0 / tn);
-        if (bc < 0 || c < bc) {
-          bc = c;
-          best = q;
-          bfold = f;
-        }
-      }
+    gemm_tile_choice(x.M, x.N, x.batch, f1, f2, square_only, &best, &bfold);
     x.fold = bfold;
     bucket[best].push_back(x);
   }
   for (int q = 0; q < 5; ++q) {
     std::vector<GemmDesc> &b = bucket[q];
     if (b.empty()) continue;
-    const int tm = shapes[q][0], tn = shapes[q][1];
+    const int tm = kGemmShapes[q][0], tn = kGemmShapes[q][1];
     long long t = 0;
     for (GemmDesc &x : b) {
       const long long Mt = x.fold == 1 ? (long long)x.batch * x.M : x.M;
@@ -3673,7 +3688,8 @@ int davidson_run(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_
 // the result has the FP64 path's accuracy.
 int davidson(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_t s,
              int patience = 6, bool probe = true) {
-  const int prec = C->precision;
+  const int prec = (C->precision == DMRG_SPLIT && C->win.flops < C->split_min_flops)
+                       ? DMRG_FP64 : C->precision;
   double rn = 0;
   int it = 0;
   int rc = davidson_run(C, x, energy, &it, s, prec, patience, probe, &rn);
@@ -4873,6 +4889,23 @@ int dmrg_heff_layout(dmrg_ctx *C, long long *psi_len, int *n_blocks, int *blocks
       blocks[k++] = p.db;
     }
   }
+  return DMRG_OK;
+}
+
+int dmrg_gemm_tile_choice(int M, int N, int batch, int fold_rows_ok, int fold_cols_ok,
+                          int square_only, int *out3) {
+  if (M < 1 || N < 1 || batch < 1 || !out3) return DMRG_ERR_ARG;
+  int q = 0, f = 0;
+  gemm_tile_choice(M, N, batch, fold_rows_ok != 0, fold_cols_ok != 0, square_only != 0, &q, &f);
+  out3[0] = kGemmShapes[q][0];
+  out3[1] = kGemmShapes[q][1];
+  out3[2] = f;
+  return DMRG_OK;
+}
+
+int dmrg_set_split_min_flops(dmrg_ctx *C, double min_window_flops) {
+  if (!C || !(min_window_flops >= 0.0)) return DMRG_ERR_ARG;
+  C->split_min_flops = min_window_flops;
   return DMRG_OK;
 }
 

@@ -77,3 +77,32 @@ def test_staging_policy_matches_sweep_walk():
                 got = lib._lib.dmrg_sweep_next_use(N, pass_, l, left, n)
                 assert got == want, (pass_, l, left, n, got, want)
     assert lib._lib.dmrg_sweep_next_use(1, 0, 0, 1, 0) == -2
+
+
+def test_fp64_gemm_tile_choice():
+    """The grouped FP64 GEMM's tile plan (pure host function): tiny operator
+    blocks that share an operand are folded into one tall or wide problem,
+    large blocks keep square tiles, square_only never folds, and the choice
+    never issues much more work than any candidate shape."""
+    import math
+    shapes = [(16, 16), (32, 32), (64, 64), (64, 16), (16, 64)]
+
+    def issued(M, N, b, tm, tn, fold):
+        Mt, Nt = (b * M if fold == 1 else M), (b * N if fold == 2 else N)
+        return math.ceil(Mt / tm) * math.ceil(Nt / tn) * (1 if fold else b) * tm * tn
+
+    assert lib.gemm_tile_choice(10, 5, 4000, fold_rows_ok=True) == (64, 16, 1)
+    assert lib.gemm_tile_choice(5, 10, 4000, fold_cols_ok=True) == (16, 64, 2)
+    tm, tn, f = lib.gemm_tile_choice(10, 5, 4000, True, True, square_only=True)
+    assert f == 0 and tm == tn
+    assert lib.gemm_tile_choice(500, 500, 1)[2] == 0
+    for M, N, b, f1, f2 in [(3, 7, 50, True, False), (130, 129, 1, False, False),
+                            (64, 8, 200, False, True), (17, 200, 9, True, True)]:
+        tm, tn, f = lib.gemm_tile_choice(M, N, b, f1, f2)
+        assert (tm, tn) in shapes and (f != 1 or f1) and (f != 2 or f2)
+        mine = issued(M, N, b, tm, tn, f)
+        for (a, c) in shapes:
+            for g in [0] + ([1] if f1 else []) + ([2] if f2 else []):
+                assert mine <= 1.5 * issued(M, N, b, a, c, g)
+    with pytest.raises(lib.DmrgError):
+        lib.gemm_tile_choice(0, 4, 1)

@@ -188,6 +188,20 @@ def test_sweep_split_matches_ed_spinless_3x3():
     assert abs(E[-1] - e_ed) <= 1e-9 * abs(e_ed), (E, e_ed)
 
 
+def test_split_min_flops_solves_small_windows_in_fp64():
+    """dmrg_set_split_min_flops above every window's flops: a split context
+    sweeps exactly as an FP64 one (bitwise equal energies)."""
+    model, ham, h, W = problem(3, 3, False, (4,))
+    E = {}
+    for prec in (lib.FP64, lib.SPLIT):
+        g = make_gpu(9, (4,), False, ham, d_max=20, davidson_tol=1e-9, precision=prec)
+        g.set_split_min_flops(1e30)
+        g.set_mps(right=synth.random_right_isometries(9, False, (4,), 20, 1, 0))
+        E[prec] = g.sweep(2)
+        g.close()
+    assert np.array_equal(E[lib.FP64], E[lib.SPLIT]), E
+
+
 # Hubbard runs in U(1)xU(1) sectors: the members of a spin multiplet have
 # exactly equal Schmidt weights in different S_z sectors, so where the cut at
 # D falls inside a multiplet, which members are kept is decided by rounding
