@@ -231,7 +231,7 @@ const VmmFns &vmm() {
     memset(&v, 0, sizeof v);
     auto get = [](const char *name, void **p) {
       cudaDriverEntryPointQueryResult q;
-      if (cudaGetDriverEntryPoint(name, p, cudaEnableDefault, &q) != cudaSuccess ||
+      if (cudaGetDriverEntryPointByVersion(name, p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
           q != cudaDriverEntryPointSuccess)
         *p = nullptr;
     };
@@ -528,10 +528,6 @@ namespace {
 // ---------------------------------------------------------------------------
 // Hamiltonian
 // ---------------------------------------------------------------------------
-inline double &W4(std::vector<double> &W, int M, int p, int q, int r, int s) {
-  return W[(((size_t)p * M + q) * M + r) * M + s];
-}
-
 void torus_bonds(int Lx, int Ly, bool nnn, std::vector<std::pair<int, int>> &out) {
   for (int y = 0; y < Ly; ++y)
     for (int x = 0; x < Lx; ++x) {
@@ -1256,19 +1252,6 @@ SU2Terms derive_su2(const dmrg_ctx *C, const SideS &F, const SideS &G, const TKe
   for (auto it = alpha.begin(); it != alpha.end();)
     it = std::fabs(it->second) <= 1e-14 * scale ? alpha.erase(it) : std::next(it);
   return alpha;
-}
-
-SideS side_of(const BlockPart &B) {
-  SideS sd;
-  sd.so_modes = B.modes;
-  sd.has = [&B](const TKey &k) {
-    auto it = B.ten.find(k);
-    if (it == B.ten.end()) return false;
-    for (const Ref &r : it->second.r)
-      if (r.cls >= 0) return true;
-    return false;
-  };
-  return sd;
 }
 
 SideS side_of(const SitePart &st) {
