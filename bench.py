@@ -337,6 +337,8 @@ def main():
     ap.add_argument("--serving", default="small", choices=["small", "c4"],
                     help="serving stream: small (12 requests on 4x4 lattices, the default) or "
                          "c4 (32 requests on 6x6 lattices, C4's arrival process and model mix)")
+    ap.add_argument("--slots", type=int, default=4,
+                    help="concurrent solves admitted by the serving loop")
     ap.add_argument("--staging", action="store_true",
                     help="also run one 6x6 D=256 sweep with and without an HBM budget for "
                          "block operators (staged bytes, H2D GB/s)")
@@ -490,15 +492,16 @@ def main():
             serving_out = {"stream": "32 requests, exponential inter-arrival mean 0.5 s (seed 3); "
                                      "spinless 6x6 N=18 V~U[0,4] (U(1), D states) and Hubbard "
                                      "6x6 half filling U~U[0,8] (U(1)xSU(2), D multiplets), D in "
-                                     "{64,128}, 2 sweeps each, 4 slots (config C4 reduced: a "
+                                     "{64,128}, 2 sweeps each, %d slots (config C4 reduced: a "
                                      "6x6 Hubbard sweep at D=256 takes 20-30 s on either arm, "
-                                     "so 64 requests with D up to 2048 on 8x8 take hours)"}
+                                     "so 64 requests with D up to 2048 on 8x8 take hours)"
+                                     % args.slots}
         else:
             L, n_req, gap = 4, 12, 0.1
             serving_out = {"stream": "12 requests, exponential inter-arrival mean 0.1 s (seed 3); "
                                      "spinless 4x4 V~U[0,4] (U(1), D states) and Hubbard 4x4 "
                                      "U~U[0,8] (U(1)xSU(2), D multiplets), D in {64,128}, 2 "
-                                     "sweeps each, 4 slots (bench.py --serving c4: 6x6)"}
+                                     "sweeps each, %d slots (bench.py --serving c4: 6x6)" % args.slots}
         mix = [("spinless", L, L, (0.0, 4.0), [64, 128]), ("hubbard", L, L, (0.0, 8.0), [64, 128])]
         # untimed warm-up with the stream's own shapes: loads the eigensolver and
         # kernel modules (lazily, per kernel) once per process, so that neither
@@ -508,7 +511,8 @@ def main():
                 srvmod.run_one(srvmod.Request(-1, model, 4, 4, 2.0, 128, 1, 0.0, seed=1), prec)
         for name, prec in (("split", lib.SPLIT), ("fp64", lib.FP64)):
             reqs = srvmod.poisson_stream(n_req, gap, 3, mix, sweeps=2)
-            srv = srvmod.Server(precision=prec, slots=4, hbm_budget=200e9, davidson_tol=1e-7)
+            srv = srvmod.Server(precision=prec, slots=args.slots, hbm_budget=200e9,
+                                davidson_tol=1e-7)
             serving_out[name] = srv.run(reqs)
         serving_out["solves_per_s_ratio_split_over_fp64"] = (
             serving_out["split"]["solves_per_s"] / max(serving_out["fp64"]["solves_per_s"], 1e-12))
