@@ -3633,17 +3633,27 @@ int davidson_run(dmrg_ctx *C, double *x, double *energy, int *iters, cudaStream_
       CK(launch_dots(B.V, k, n, B.t, n, B.work, B.dots, s));
       CK(launch_lincomb_d(B.t, B.V, k, n, B.dots, -1.0, 1.0, n, s));
     }
-    double nt = std::sqrt(std::max(0.0, dot1(C, B.t, B.t, n, B, s)));
+    // the product is taken of the unnormalised t: its norm and the new column
+    // of V^T A V come back in one transfer, and both are scaled afterwards
+    double *vk = B.V + (long long)k * n;
+    double *avk = B.AV + (long long)k * n;
+    CK(cudaMemcpyAsync(vk, B.t, 8 * n, cudaMemcpyDeviceToDevice, s));
+    apply(C, vk, avk, s, prec);
+    ++nmv;
+    CK(launch_dots(B.V, k + 1, n, avk, n, B.work, B.dots, s));
+    CK(launch_dots(vk, 1, n, vk, n, B.work, B.dots + k + 1, s));
+    col.resize(k + 2);
+    CK(cudaMemcpyAsync(col.data(), B.dots, 8 * (k + 2), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double nt = std::sqrt(std::max(0.0, col[k + 1]));
     if (!(nt > 1e-14)) {
       conv = rnorm < 10 * tol;
       break;
     }
-    double *vk = B.V + (long long)k * n;
-    CK(cudaMemcpyAsync(vk, B.t, 8 * n, cudaMemcpyDeviceToDevice, s));
     lincomb(vk, vk, {}, 1.0 / nt, n, B, s);
-    apply(C, vk, B.AV + (long long)k * n, s, prec);
-    ++nmv;
-    dots(C, B.V, k + 1, n, B.AV + (long long)k * n, B, col, s);
+    lincomb(avk, avk, {}, 1.0 / nt, n, B, s);
+    for (int i = 0; i < k; ++i) col[i] /= nt;
+    col[k] /= nt * nt;
     for (int i = 0; i <= k; ++i) {
       S[i * m + k] = col[i];
       S[k * m + i] = col[i];
