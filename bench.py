@@ -471,7 +471,7 @@ def main():
         for name, prec, steps in (("split", lib.SPLIT, 20), ("split_plain_refinement", lib.SPLIT, 0),
                                   ("fp64", lib.FP64, 20)):
             g.set_precision(prec)
-            g.set_refinement(steps, 1e10)
+            g.set_refinement(steps, 1e8)
             x = torch.zeros_like(psi)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -479,7 +479,7 @@ def main():
             torch.cuda.synchronize()
             solve[name] = {"seconds": time.perf_counter() - t0, "energy": e, "iters": it,
                            "converged": conv}
-        g.set_refinement(20, 1e10)
+        g.set_refinement(20, 1e8)
         solve["rel_energy_diff"] = abs(solve["split"]["energy"] - solve["fp64"]["energy"]) / abs(
             solve["fp64"]["energy"])
     # serving stream: Poisson arrivals of independent solves (config-4 pattern,

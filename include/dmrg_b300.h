@@ -165,7 +165,7 @@ int dmrg_heff_layout(dmrg_ctx *ctx, long long *psi_len, int *n_blocks,
  * conjugate-gradient steps with the split-precision product, instead of the
  * diagonally preconditioned residual; the FP64 Rayleigh-Ritz step keeps the
  * result exact to FP64 (fewer FP64 products per solve).  inner_steps = 0
- * turns it off.  Defaults: 20 steps, 1e10 flops.  Errors: ARG. */
+ * turns it off.  Defaults: 20 steps, 1e8 flops.  Errors: ARG. */
 int dmrg_set_refinement(dmrg_ctx *ctx, int inner_steps, double min_window_flops);
 
 /* Split-precision contexts solve the windows whose H_eff*psi has fewer than

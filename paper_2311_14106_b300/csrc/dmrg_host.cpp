@@ -498,7 +498,7 @@ struct dmrg_ctx {
   // refinement of split solves: split-precision CG steps per correction,
   // on windows of at least this many algorithmic flops per apply
   int refine_steps = 20;
-  double refine_min_flops = 1e10;
+  double refine_min_flops = 1e8;
   // split contexts solve windows below this many flops per product with the
   // FP64 product alone (dmrg_set_split_min_flops)
   double split_min_flops = 0;
