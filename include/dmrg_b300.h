@@ -254,7 +254,10 @@ int dmrg_heff_flops(dmrg_ctx *ctx, double *flops);
  * output.  With DMRG_SPLIT the split product runs until its residual
  * stagnates near its noise floor (about 4e-6 |E|); Davidson iterations with
  * the FP64 product, started from that vector, then take the residual to
- * davidson_tol (mixed-precision refinement).  The energy is the Rayleigh
+ * davidson_tol (mixed-precision refinement; on windows of at least
+ * dmrg_set_refinement's flops those iterations expand with a split-precision
+ * solution of the correction equation; windows below dmrg_set_split_min_flops
+ * are solved with the FP64 product alone).  The energy is the Rayleigh
  * quotient of the FP64 product whatever the precision setting.
  * Errors: STATE, NOT_CONVERGED (psi and energy still written), TIMEOUT. */
 int dmrg_davidson(dmrg_ctx *ctx, double *psi_inout, double *energy,
